@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark: GMM forward + gradient (and reprojection VJP) on B300.
+
+One step = one pass of the hot path over one batch of synthetic input: the GMM
+objective and its gradient for N = 2^20 points, D = 64, K = 200 components
+(parameter expansion, forward log-joint + logsumexp, backward Accum of the
+weighted moments, finalize) through the C ABI (gmm_vjp with the log-joint
+recomputed in the workspace). The reprojection VJP on 8192 cameras, 500 000
+points and 4 000 000 observations is measured in the same run and reported in
+the "secondary" block.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank processes its own batch
+(weak scaling, no collective on the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GMM_N, GMM_D, GMM_K = 1 << 20, 64, 200
+RP_C, RP_P, RP_M = 8192, 500000, 4000000
+METRIC = "GMM fwd+grad (pt*comp)/s"
+UNIT = "pt*comp/s"
+# algorithmic work per (point, component) pair: forward D^2 + 3D, backward D^2 + 3D
+FLOPS_PER_PAIR_FWD = GMM_D * GMM_D + 3 * GMM_D
+FLOPS_PER_PAIR_BWD = GMM_D * GMM_D + 3 * GMM_D
+# algorithmic HBM bytes per observation of the reprojection VJP: indices 8, cotangent 8,
+# camera and point parameters read once 1.6, gradient read-modify-write 3.2
+BYTES_PER_OBS_VJP = 20.8
+BYTES_PER_OBS_FUSED = 25.6 + 3.2
+# FP32 CUDA-core peak: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        top = max(r[0] for r in rows)
+        loaded = [r[0] for r in rows if r[0] >= 0.5 * top] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_record(kernel: str):
+    """(bytes per launch, note) from the committed ncu summary, if it still
+    matches the kernel source; else (None, why)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None, "no ncu capture committed"
+    src = os.path.join(ROOT, "paper_2104_05372_b300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(src)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(src, name), "rb").read())
+    digest = h.hexdigest()[:16]
+    for line in open(p):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        if parts[0] == kernel:
+            if parts[1] != digest:
+                return None, "kernel source changed since the ncu capture"
+            return float(parts[2]), "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
+    return None, "kernel not in the ncu summary"
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300 import _lib
+    import synth
+
+    g = synth.gmm_inputs(GMM_N, GMM_D, GMM_K, seed=1000 + rank)
+    dev = torch.device("cuda", local)
+    x, a, mu, q, l = (torch.from_numpy(t).to(dev) for t in (g.x, g.alpha, g.mu, g.q, g.l))
+    ws = _lib.workspace(gpa.gpa_gmm_workspace_bytes(GMM_N, GMM_D, GMM_K, 0, 0), dev)
+    t = GMM_D * (GMM_D - 1) // 2
+    grads = [torch.zeros(GMM_K, device=dev), torch.zeros(GMM_K, GMM_D, device=dev),
+             torch.zeros(GMM_K, GMM_D, device=dev), torch.zeros(GMM_K, t, device=dev)]
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for gb in grads:
+            gb.zero_()
+        gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, logjoint_in=None, lse_in=None, seed=1.0, d_alpha=grads[0],
+                    d_mu=grads[1], d_q=grads[2], d_l=grads[3], out=out, ws=ws)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    _lib.gpa_trace_enable(True)
+    _lib.gpa_trace_summary()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+    _lib.gpa_trace_enable(False)
+    trace = _lib.gpa_trace_summary()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    pairs = GMM_N * GMM_K
+    value = pairs * world / (ms_step / 1e3)
+    clocks = clk.summary()
+    launches = sum(c for c, _ in trace.values())
+
+    # dominant kernel and its roofline (FP32 CUDA-core ALU bound)
+    dom = max(trace.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_cnt, dom_ms) = dom
+    per_launch_ms = dom_ms / dom_cnt
+    fl = {"gmm_fwd": FLOPS_PER_PAIR_FWD, "gmm_bwd": FLOPS_PER_PAIR_BWD}.get(dom_name, 0)
+    achieved = fl * pairs / (per_launch_ms / 1e3) / 1e12
+    traffic, traffic_note = traffic_record(dom_name)
+    roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": traffic, "traffic_note": traffic_note,
+                "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 flop x 2032 MHz (max SM clock)",
+                "kernel_ms_per_launch": round(per_launch_ms, 4),
+                "kernels": {k: {"launches": c, "ms_per_launch": round(v / c, 4),
+                                "share": round(v / sum(vv for _, vv in trace.values()), 4)}
+                            for k, (c, v) in trace.items()}}
+
+    # end to end: host buffers, copies inside the timed region
+    e2e = run_e2e(args, gpa, _lib, g, dev, ws, stream)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "GMM objective+gradient, N=2^20 points, D=64, K=200, gamma=1, m=0, FP32 "
+                               "(log-joint recomputed in the workspace)",
+                   "N": GMM_N, "D": GMM_D, "K": GMM_K, "parallelism": f"replica x{world}",
+                   "l2": "inputs larger than L2 (x is 256 MiB, log-joint 800 MiB)"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
+    }
+    if not args.no_secondary:
+        result["secondary"] = run_reproj(args, gpa, _lib, dev, stream, rank)
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, gpa, _lib, g, dev, ws, stream):
+    import torch
+    host = [torch.from_numpy(t).pin_memory() for t in (g.x, g.alpha, g.mu, g.q, g.l)]
+    dbuf = [torch.empty(t.shape, dtype=t.dtype, device=dev) for t in host]
+    t = GMM_D * (GMM_D - 1) // 2
+    grads = [torch.zeros(GMM_K, device=dev), torch.zeros(GMM_K, GMM_D, device=dev),
+             torch.zeros(GMM_K, GMM_D, device=dev), torch.zeros(GMM_K, t, device=dev)]
+    hgrads = [torch.empty(gb.shape, dtype=gb.dtype).pin_memory() for gb in grads]
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    hout = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def step():
+        for d_, h_ in zip(dbuf, host):
+            d_.copy_(h_, non_blocking=True)
+        for gb in grads:
+            gb.zero_()
+        gpa.gmm_vjp(*dbuf, g.gamma, g.m, seed=1.0, d_alpha=grads[0], d_mu=grads[1], d_q=grads[2], d_l=grads[3],
+                    out=out, ws=ws)
+        for h_, d_ in zip(hgrads, grads):
+            h_.copy_(d_, non_blocking=True)
+        hout.copy_(out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    h2d = sum(h.numel() * h.element_size() for h in host)
+    d2h = sum(h.numel() * h.element_size() for h in hgrads) + 8
+    return {"value": GMM_N * GMM_K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def run_reproj(args, gpa, _lib, dev, stream, rank):
+    import torch
+    import synth
+    r = synth.reproj_inputs(RP_C, RP_P, RP_M, seed=2000 + rank)
+    cams, pts, obs, tgt, w = (torch.from_numpy(t).to(dev) for t in (r.cams, r.pts, r.obs, r.tgt, r.w))
+    ws = _lib.workspace(gpa.gpa_reproj_workspace_bytes(RP_C, RP_P, RP_M), dev)
+    plan = gpa.gpa_obs_plan_build(obs, RP_C, RP_P)
+    dcm = torch.zeros(RP_C, 11, device=dev)
+    dpt = torch.zeros(RP_P, 3, device=dev)
+    res = torch.empty(RP_M, 2, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    peaks, src = measured_peaks()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)  # evict inputs from L2 between timed iterations
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / args.steps
+
+    out = {"workload": "reprojection, 8192 cameras x 11, 500000 points, 4000000 observations, FP32",
+           "l2": "flushed between timed iterations", "unit": "obs/s"}
+    for strat in ("sort", "atomic", "warpagg"):
+        ms = timed(lambda: gpa.reproj_vjp(cams, pts, obs, w, d_cams=dcm, d_pts=dpt, strat=strat,
+                                          plan=plan if strat == "sort" else None, ws=ws))
+        gbs = BYTES_PER_OBS_VJP * RP_M / (ms / 1e3) / 1e9
+        out[f"vjp_{strat}"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms, "hbm_gbs_algorithmic": gbs,
+                               "frac": gbs / peaks["hbm_gbs"]}
+    ms = timed(lambda: gpa.reproj_residual(cams, pts, obs, tgt, res=res, ws=ws))
+    out["residual"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
+                       "hbm_gbs_algorithmic": 25.6 * RP_M / (ms / 1e3) / 1e9}
+    ms = timed(lambda: gpa.reproj_residual_vjp(cams, pts, obs, tgt, 1.0, res=res, d_cams=dcm, d_pts=dpt,
+                                               strat="sort", plan=plan, ws=ws))
+    out["fused_residual_vjp_sort"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
+                                      "hbm_gbs_algorithmic": BYTES_PER_OBS_FUSED * RP_M / (ms / 1e3) / 1e9}
+    best = max(("sort", "atomic", "warpagg"), key=lambda s_: out[f"vjp_{s_}"]["obs_per_s"])
+    out["metric"] = "reproj VJP obs/s"
+    out["value"] = out[f"vjp_{best}"]["obs_per_s"]
+    out["best_strategy"] = best
+    out["roofline"] = {"bound": "hbm", "achieved": out[f"vjp_{best}"]["hbm_gbs_algorithmic"],
+                       "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": out[f"vjp_{best}"]["frac"],
+                       "peak_source": src, "bytes_per_obs": BYTES_PER_OBS_VJP}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_sample(n_points: int):
+    import synth
+    return synth.gmm_inputs(n_points, GMM_D, GMM_K, seed=3000)
+
+
+def cpu_baseline(target_s: float = 12.0):
+    import oracle
+    n = 2048
+    g = _oracle_sample(n)
+    t0 = time.perf_counter()
+    oracle.gmm_grad(g)
+    dt = time.perf_counter() - t0
+    # grow the sample to about target_s of CPU work
+    n2 = int(min(GMM_N, max(n, n * target_s / max(dt, 1e-3))) // 128 * 128)
+    if n2 > n:
+        g = _oracle_sample(n2)
+        t0 = time.perf_counter()
+        oracle.gmm_grad(g)
+        dt = time.perf_counter() - t0
+        n = n2
+    return {"value": n * GMM_K / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle objective+gradient on {n} of the 2^20 points (D=64, K=200), {dt:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    n = 1024
+    g = _oracle_sample(n)
+    t0 = time.perf_counter()
+    oracle.gmm_grad(g)
+    dt = time.perf_counter() - t0
+    # each step about 4 s of CPU work
+    n = int(max(1024, min(GMM_N, n * 4.0 / max(dt, 1e-3))) // 128 * 128)
+    g = _oracle_sample(n)
+    for _ in range(args.warmup):
+        oracle.gmm_grad(g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.gmm_grad(g)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n * GMM_K / dt
+    sample = f"FP64 oracle objective+gradient on {n} of the 2^20 points (D=64, K=200) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "GMM objective+gradient, N=2^20 points, D=64, K=200, gamma=1, m=0 (bounded sample "
+                               "per step)", "N": GMM_N, "D": GMM_D, "K": GMM_K},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * gpa.h -- C ABI of libgpa: forward passes and reverse-mode gradients of two
+ * pointful array programs on one NVIDIA B300 (sm_103a), where the adjoint of
+ * every gather is an associative accumulation (the Accum effect of
+ * "Getting to the Point", arXiv 2104.05372, Sec. 2.3.2), so that the backward
+ * pass stays parallel and work-efficient (Sec. 5.3.3, Sec. 6.1.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory.   Every pointer argument is DEVICE memory owned by the caller, unless
+ *           the argument's comment says otherwise. Arrays are dense, row-major,
+ *           and flatten their index sets in row-major order (tuple index sets,
+ *           Sec. 3.4). The library never allocates: scratch space is the
+ *           caller's workspace `ws` of `ws_bytes` bytes (256-byte aligned), sized
+ *           by the matching *_workspace_bytes query. Workspace contents need no
+ *           initialisation and are meaningless after the call.
+ * Streams.  Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *           stream) and returns immediately; results are valid once the stream
+ *           has been synchronised.
+ * Accum.    Gradient outputs (d_*) follow runAccum semantics: the call ADDS its
+ *           contribution (+=) into buffers the caller initialised, typically to
+ *           zero (Sec. 2.3.2, rule VarTranspose of Fig. "transpose"). Each
+ *           element has one writer per call unless the strategy says atomics.
+ * Errors.   Host-detectable problems (null pointer, size out of range,
+ *           unsupported shape, workspace too small, misaligned pointer) return a
+ *           nonzero gpa_status at once and enqueue nothing. Data-dependent
+ *           problems found on the device (an index outside its index set, a
+ *           bounded wait that ran out) are OR-ed into *dev_status (device int32,
+ *           nullable; the caller zeroes it and reads it after synchronising);
+ *           the offending element is skipped and the kernel never traps.
+ *           GPA_ERR_CUDA reports a failed launch (cudaGetLastError).
+ * Precision. Inputs and outputs are float32; objectives are float64 scalars.
+ *           GPA_PREC_FP32 computes every product and sum in float32 (sums over
+ *           points in float64 where stated); GPA_PREC_BF16_TC runs the dense
+ *           contractions on the tensor cores with bfloat16 operands and float32
+ *           accumulation.
+ */
+#ifndef GPA_H
+#define GPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gpa_stream_t; /* same type as cudaStream_t */
+
+#if defined(__GNUC__)
+#define GPA_API __attribute__((visibility("default")))
+#else
+#define GPA_API
+#endif
+
+typedef enum {
+    GPA_OK = 0,
+    GPA_ERR_ARG = 1,         /* null pointer, non-positive or too-large size */
+    GPA_ERR_INDEX = 2,       /* (device) an index outside its index set */
+    GPA_ERR_CUDA = 3,        /* a CUDA launch or runtime call failed */
+    GPA_ERR_WORKSPACE = 4,   /* ws_bytes smaller than the query asked for */
+    GPA_ERR_TIMEOUT = 5,     /* (device) a bounded wait gave up */
+    GPA_ERR_UNSUPPORTED = 6, /* shape / precision / strategy not provided */
+    GPA_ERR_ALIGN = 7        /* a pointer lacks the stated alignment */
+} gpa_status;
+
+typedef enum { GPA_PREC_FP32 = 0, GPA_PREC_BF16_TC = 1 } gpa_prec;
+
+typedef enum {
+    GPA_SCATTER_AUTO = 0,    /* SORT when a plan is given, else ATOMIC */
+    GPA_SCATTER_ATOMIC = 1,  /* one red.global.add per element */
+    GPA_SCATTER_WARPAGG = 2, /* lanes of a warp with equal keys combine first */
+    GPA_SCATTER_SORT = 3     /* key-sorted order from a plan, segmented warp sums */
+} gpa_scatter;
+
+/* Human-readable name of a gpa_status value (static string, never NULL). */
+GPA_API const char* gpa_status_string(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+GPA_API int gpa_version(void);
+
+/* ========================================================================= */
+/* Gaussian mixture with a Wishart prior                                     */
+/* ========================================================================= */
+/*
+ * Parameters (K components in D dimensions, T = D(D-1)/2):
+ *   alpha [K]      log-weights
+ *   mu    [K][D]   means
+ *   q     [K][D]   log-diagonal of the inverse-Cholesky factor Q_k
+ *   l     [K][T]   strict-lower entries of Q_k, row-major packing:
+ *                  Q_k[r][c] = l[k][r(r-1)/2 + c] for r > c, Q_k[r][r] = exp(q[k][r])
+ *   x     [N][D]   points
+ * Objective (log posterior, float64):
+ *   f = sum_i logsumexp_k( alpha_k + sum_d q_kd - |Q_k (x_i - mu_k)|^2 / 2 )
+ *       - N logsumexp(alpha) - (N D / 2) log(2 pi)
+ *       + sum_k [ m sum_d q_kd - (gamma^2 / 2)(sum_d exp(2 q_kd) + sum_t l_kt^2) ]
+ *       + K [ n D log(gamma) - (n D / 2) log 2 - log Gamma_D(n / 2) ],  n = D + m + 1,
+ *   i.e. the mixture log-likelihood plus a Wishart(n, gamma^-2 I) log-prior on
+ *   each precision matrix Q_k^T Q_k.
+ * The log-joint s[k][i] = alpha_k + sum_d q_kd - |Q_k (x_i - mu_k)|^2 / 2 and
+ * lse[i] = logsumexp_k s[k][i] are the per-point statistics the gradient needs.
+ * Supported shapes: 1 <= D <= 128, 1 <= K <= 4096, 1 <= N <= 2^31 - 1.
+ * Alignment: every pointer 4-byte aligned.
+ */
+
+/* Bytes of workspace needed by gmm_objective / gmm_vjp for this shape.
+ * logjoint_points: how many points' log-joint columns (K floats each) the
+ * workspace must hold for gmm_vjp when it recomputes the log-joint itself
+ * (logjoint_in == NULL). 0 means "all N" (one pass); smaller values bound the
+ * memory and make gmm_vjp run the forward pass in chunks of that many points
+ * (rounded down to a multiple of 128, at least 128). gmm_objective needs no
+ * log-joint space. */
+GPA_API size_t gpa_gmm_workspace_bytes(int64_t n, int32_t d, int32_t k, int32_t prec,
+                               int64_t logjoint_points);
+
+/*
+ * Forward pass: *out = f (device float64). Optionally writes lse_out [N]
+ * (device float32, nullable) and logjoint_out [K][N] (device float32,
+ * nullable; component-major so that each component's column is contiguous).
+ * Sums over points are taken in float64 per 128-point tile and combined in a
+ * fixed order (run-to-run deterministic).
+ */
+GPA_API int gmm_objective(const float* x, const float* alpha, const float* mu, const float* q,
+                  const float* l, int64_t n, int32_t d, int32_t k, double gamma, int32_t m,
+                  int32_t prec, double* out, float* lse_out, float* logjoint_out, void* ws,
+                  size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
+
+/*
+ * Reverse pass: seed * grad f, added (+=) into d_alpha [K], d_mu [K][D],
+ * d_q [K][D], d_l [K][T] (grad f x = transpose (linearize f x) 1.0, Sec. 5.2;
+ * seed = 1 gives the gradient). Optionally writes *out = f (nullable).
+ * If logjoint_in [K][N] and lse_in [N] (both from gmm_objective on the same
+ * inputs) are given, they are reused; if both are NULL the log-joint is
+ * recomputed in the workspace, in chunks as large as the workspace allows.
+ * Giving exactly one of them is GPA_ERR_ARG.
+ * The reads of alpha_k, mu_k, Q_k inside the loop over points become
+ * regular segmented reductions indexed by the component (Sec. 6.1.3),
+ * accumulated per (component group, point chunk) and combined in a fixed order
+ * (run-to-run deterministic).
+ */
+GPA_API int gmm_vjp(const float* x, const float* alpha, const float* mu, const float* q, const float* l,
+            int64_t n, int32_t d, int32_t k, double gamma, int32_t m, int32_t prec,
+            const float* logjoint_in, const float* lse_in, double seed, float* d_alpha,
+            float* d_mu, float* d_q, float* d_l, double* out, void* ws, size_t ws_bytes,
+            int32_t* dev_status, gpa_stream_t stream);
+
+/* ========================================================================= */
+/* Camera reprojection (bundle adjustment residual)                          */
+/* ========================================================================= */
+/*
+ * cams [C][11]  camera j = [w(3) Rodrigues rotation, c(3) centre, f focal,
+ *                pp(2) principal point, kappa(2) radial distortion]
+ * pts  [P][3]   3-D points
+ * obs  [M][2]   int32 (camera index, point index) per observation
+ * tgt  [M][2]   observed 2-D positions
+ * Per observation: u = X - c, Y = R(w) u, p = (Y_0, Y_1) / Y_2, rho = |p|^2,
+ * L = 1 + kappa_0 rho + kappa_1 rho^2, res = f L p + pp - tgt.
+ * R(w) = exp([w]x) (rotation by |w| about w/|w|); the rotation of each camera
+ * is expanded once per call in float64 and carried as a float32 hi/lo pair so
+ * that Y_2 keeps its relative accuracy for points close to the image plane.
+ * Supported: 1 <= C, P <= 2^31 - 1, 1 <= M <= 2^31 - 1. Alignment: obs 8-byte,
+ * tgt / res / w 8-byte, others 4-byte.
+ */
+
+/* Workspace for reproj_residual / reproj_vjp (the expanded cameras). */
+GPA_API size_t gpa_reproj_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs);
+
+/* res [M][2] = projection - target. Observations whose indices fall outside
+ * their index sets get NaN residuals and set GPA_ERR_INDEX. */
+GPA_API int reproj_residual(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
+                    int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, void* ws,
+                    size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
+
+/*
+ * VJP of the residual with cotangent w [M][2]: d_cams[c] += J_cam^T w_j and
+ * d_pts[p] += J_pt^T w_j over all observations j with obs[j] = (c, p): the
+ * transpose of the gathers cams.(obs.j.0), pts.(obs.j.1) is an irregular
+ * segmented reduction (histogram pattern, Sec. 6.1.3; LetIndexingTranspose,
+ * Fig. "transpose"). strat selects how the Accum is carried out; SORT needs
+ * `plan` from gpa_obs_plan_build on the same obs (nullable otherwise).
+ * Atomic strategies give float32 sums whose rounding depends on the order.
+ */
+GPA_API int reproj_vjp(const float* cams, const float* pts, const int32_t* obs, const float* w,
+               int32_t n_cams, int32_t n_pts, int64_t n_obs, float* d_cams, float* d_pts,
+               int32_t strat, const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
+               gpa_stream_t stream);
+
+/* Fused residual + VJP in one pass over the observations: res as
+ * reproj_residual, then d_cams / d_pts += J^T (wscale * res) (the Gauss-Newton
+ * gradient of wscale * |res|^2 / 2 when wscale = 1). */
+GPA_API int reproj_residual_vjp(const float* cams, const float* pts, const int32_t* obs,
+                        const float* tgt, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                        float wscale, float* res, float* d_cams, float* d_pts, int32_t strat,
+                        const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
+                        gpa_stream_t stream);
+
+/* ========================================================================= */
+/* Index preparation and the generic Accum scatter                           */
+/* ========================================================================= */
+/*
+ * An index plan: the stable sort of element ids by a data-derived key
+ * (keys from `obs` column 0, i.e. the camera, for the reprojection; the
+ * scatter indices for accum_scatter_add). Index validity is checked here, where
+ * indices are made from data (Sec. 6.3): elements whose key is outside
+ * [0, n_keys) (or, for observations, whose point is outside [0, n_pts)) set
+ * GPA_ERR_INDEX and are placed after all valid elements.
+ * Plan layout (in `plan`, 256-byte aligned, size from the query):
+ *   int64 header[4] = {n_elems, n_keys, n_valid (written on device), reserved}
+ *   int32 perm[n_elems]         element ids in key order (stable)
+ *   int32 key_sorted[n_elems]   keys in that order (n_keys for invalid ones)
+ *   int32 aux_sorted[n_elems]   second index in that order (point ids; 0 for scatter)
+ *   int32 seg_off[n_keys + 1]   start of each key's run; seg_off[n_keys] = n_valid
+ * The integer contents are bit-exact with a stable counting sort.
+ */
+GPA_API size_t gpa_plan_bytes(int64_t n_elems, int32_t n_keys);
+GPA_API size_t gpa_plan_workspace_bytes(int64_t n_elems, int32_t n_keys);
+
+/* Plan over observations keyed by camera (obs [M][2]); checks both indices. */
+GPA_API int gpa_obs_plan_build(const int32_t* obs, int64_t n_obs, int32_t n_cams, int32_t n_pts,
+                       void* plan, size_t plan_bytes, void* ws, size_t ws_bytes,
+                       int32_t* dev_status, gpa_stream_t stream);
+
+/* Plan over plain indices idx [M] with n_keys buckets. */
+GPA_API int gpa_index_plan_build(const int32_t* idx, int64_t m, int32_t n_keys, void* plan,
+                         size_t plan_bytes, void* ws, size_t ws_bytes, int32_t* dev_status,
+                         gpa_stream_t stream);
+
+/*
+ * acc[idx[j]][c] += vals[j][c] for j < m, c < w (hist!(x.i) += v, Sec. 2.3.3,
+ * Sec. 6.1.2). dtype 0 = float32 values and accumulator, 1 = int32 (exact,
+ * wrapping on overflow). Indices outside [0, n_buckets) set GPA_ERR_INDEX and
+ * are skipped. SORT needs `plan` from gpa_index_plan_build on the same idx.
+ * 1 <= w <= 64. Alignment: 4-byte.
+ */
+GPA_API int accum_scatter_add(const int32_t* idx, const void* vals, int64_t m, int32_t w, int32_t dtype,
+                      void* acc, int32_t n_buckets, int32_t strat, const void* plan,
+                      int32_t* dev_status, gpa_stream_t stream);
+
+/* ========================================================================= */
+/* Tracing                                                                   */
+/* ========================================================================= */
+/* Enable (1) or disable (0) per-launch timing: while enabled, every kernel the
+ * library launches is bracketed by two CUDA events on its stream (events are
+ * created once and reused; no device memory is allocated). Process-wide. */
+GPA_API void gpa_trace_enable(int on);
+
+/* Resolve the recorded launches (waits for the last one), write one line
+ * "name launches total_ms" per kernel name into buf (host memory, len bytes,
+ * NUL-terminated, truncated if short), forget them, and return the length the
+ * full text needs. */
+GPA_API int gpa_trace_summary(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPA_H */

@@ -1,0 +1,336 @@
+"""ctypes binding of libgpa (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: it checks tensor dtypes / devices / contiguity, passes
+raw device pointers and the current CUDA stream, allocates the workspace the
+library's size query asks for (through torch, as plain device memory), and
+raises ``GpaError`` on a nonzero status. There is no CPU fallback: if the
+library or a CUDA device is missing, calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpa.so")
+
+PREC_FP32, PREC_BF16_TC = 0, 1
+SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_WARPAGG, SCATTER_SORT = 0, 1, 2, 3
+STRATEGIES = {"auto": 0, "atomic": 1, "warpagg": 2, "sort": 3}
+ERR_ARG, ERR_INDEX, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_ALIGN = 1, 2, 3, 4, 5, 6, 7
+
+
+class GpaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (code {code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = C.c_void_p
+_I64, _I32, _D, _F, _SZ = C.c_int64, C.c_int32, C.c_double, C.c_float, C.c_size_t
+
+_SIGS = {
+    "gpa_status_string": ([_I32], C.c_char_p),
+    "gpa_version": ([], _I32),
+    "gpa_gmm_workspace_bytes": ([_I64, _I32, _I32, _I32, _I64], _SZ),
+    "gmm_objective": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P, _P], _I32),
+    "gmm_vjp": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _P, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P, _P],
+                _I32),
+    "gpa_reproj_workspace_bytes": ([_I32, _I32, _I64], _SZ),
+    "reproj_residual": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
+    "reproj_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
+    "reproj_residual_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _F, _P, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
+    "gpa_plan_bytes": ([_I64, _I32], _SZ),
+    "gpa_plan_workspace_bytes": ([_I64, _I32], _SZ),
+    "gpa_obs_plan_build": ([_P, _I64, _I32, _I32, _P, _SZ, _P, _SZ, _P, _P], _I32),
+    "gpa_index_plan_build": ([_P, _I64, _I32, _P, _SZ, _P, _SZ, _P, _P], _I32),
+    "accum_scatter_add": ([_P, _P, _I64, _I32, _I32, _P, _I32, _I32, _P, _P, _P], _I32),
+    "gpa_trace_enable": ([_I32], None),
+    "gpa_trace_summary": ([C.c_char_p, _SZ], _I32),
+}
+
+
+def load():
+    """Load libgpa.so (built in-tree by ``paper_2104_05372_b300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libgpa.so not found at {LIB_PATH}; run "
+                                   "`python -m paper_2104_05372_b300.build` first")
+            lib = C.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def gpa_trace_enable(on: bool = True):
+    load().gpa_trace_enable(1 if on else 0)
+
+
+def gpa_trace_summary():
+    """{kernel name: (launches, total_ms)} since the last summary."""
+    lib = load()
+    need = lib.gpa_trace_summary(None, 0)
+    buf = C.create_string_buffer(need + 1)
+    lib.gpa_trace_summary(buf, need + 1)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def status_string(code: int) -> str:
+    return load().gpa_status_string(int(code)).decode()
+
+
+def version() -> int:
+    return int(load().gpa_version())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ok(code, where):
+    if code != 0:
+        raise GpaError(int(code), where)
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    """Device scratch buffer of at least nbytes (256-byte aligned by the allocator)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------------------
+# GMM
+# ---------------------------------------------------------------------------
+def gpa_gmm_workspace_bytes(n, d, k, prec=PREC_FP32, logjoint_points=0) -> int:
+    return int(load().gpa_gmm_workspace_bytes(int(n), int(d), int(k), int(prec), int(logjoint_points)))
+
+
+def _gmm_params(x, alpha, mu, q, l):
+    _check(x, torch.float32, "x")
+    n, d = x.shape
+    k = alpha.shape[0]
+    t = d * (d - 1) // 2
+    _check(alpha, torch.float32, "alpha", (k,))
+    _check(mu, torch.float32, "mu", (k, d))
+    _check(q, torch.float32, "q", (k, d))
+    _check(l, torch.float32, "l", (k, t))
+    return n, d, k
+
+
+def gmm_objective(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, out=None, lse_out=None,
+                  logjoint_out=None, ws=None, status=None, stream=None):
+    """Objective f into ``out`` (device float64 [1]); returns ``out``."""
+    n, d, k = _gmm_params(x, alpha, mu, q, l)
+    dev = x.device
+    out = torch.empty(1, dtype=torch.float64, device=dev) if out is None else _check(out, torch.float64, "out")
+    if lse_out is not None:
+        _check(lse_out, torch.float32, "lse_out", (n,))
+    if logjoint_out is not None:
+        _check(logjoint_out, torch.float32, "logjoint_out", (k, n))
+    nb = gpa_gmm_workspace_bytes(n, d, k, prec, 128)
+    if ws is None:
+        ws = workspace(nb, dev)
+    rc = load().gmm_objective(_ptr(x), _ptr(alpha), _ptr(mu), _ptr(q), _ptr(l), n, d, k, float(gamma), int(m),
+                              int(prec), _ptr(out), _ptr(lse_out), _ptr(logjoint_out), _ptr(ws), ws.numel(),
+                              _ptr(status), _stream(stream))
+    _ok(rc, "gmm_objective")
+    return out
+
+
+def gmm_vjp(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, logjoint_in=None, lse_in=None, seed=1.0,
+            d_alpha=None, d_mu=None, d_q=None, d_l=None, out=None, ws=None, logjoint_points=0, status=None,
+            stream=None):
+    """seed * grad f added into (d_alpha, d_mu, d_q, d_l) (zeros if not given); returns them."""
+    n, d, k = _gmm_params(x, alpha, mu, q, l)
+    dev = x.device
+    t = d * (d - 1) // 2
+    d_alpha = torch.zeros(k, dtype=torch.float32, device=dev) if d_alpha is None else d_alpha
+    d_mu = torch.zeros(k, d, dtype=torch.float32, device=dev) if d_mu is None else d_mu
+    d_q = torch.zeros(k, d, dtype=torch.float32, device=dev) if d_q is None else d_q
+    d_l = torch.zeros(k, t, dtype=torch.float32, device=dev) if d_l is None else d_l
+    _check(d_alpha, torch.float32, "d_alpha", (k,))
+    _check(d_mu, torch.float32, "d_mu", (k, d))
+    _check(d_q, torch.float32, "d_q", (k, d))
+    _check(d_l, torch.float32, "d_l", (k, t))
+    if logjoint_in is not None:
+        _check(logjoint_in, torch.float32, "logjoint_in", (k, n))
+    if lse_in is not None:
+        _check(lse_in, torch.float32, "lse_in", (n,))
+    if out is not None:
+        _check(out, torch.float64, "out")
+    if ws is None:
+        lp = 128 if logjoint_in is not None else logjoint_points
+        ws = workspace(gpa_gmm_workspace_bytes(n, d, k, prec, lp), dev)
+    rc = load().gmm_vjp(_ptr(x), _ptr(alpha), _ptr(mu), _ptr(q), _ptr(l), n, d, k, float(gamma), int(m), int(prec),
+                        _ptr(logjoint_in), _ptr(lse_in), float(seed), _ptr(d_alpha), _ptr(d_mu), _ptr(d_q),
+                        _ptr(d_l), _ptr(out), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "gmm_vjp")
+    return d_alpha, d_mu, d_q, d_l
+
+
+# ---------------------------------------------------------------------------
+# Reprojection
+# ---------------------------------------------------------------------------
+def gpa_reproj_workspace_bytes(n_cams, n_pts, n_obs) -> int:
+    return int(load().gpa_reproj_workspace_bytes(int(n_cams), int(n_pts), int(n_obs)))
+
+
+def _reproj_params(cams, pts, obs):
+    _check(cams, torch.float32, "cams")
+    _check(pts, torch.float32, "pts")
+    _check(obs, torch.int32, "obs")
+    if cams.dim() != 2 or cams.shape[1] != 11:
+        raise ValueError("cams must be [C, 11]")
+    if pts.dim() != 2 or pts.shape[1] != 3:
+        raise ValueError("pts must be [P, 3]")
+    if obs.dim() != 2 or obs.shape[1] != 2:
+        raise ValueError("obs must be [M, 2]")
+    return cams.shape[0], pts.shape[0], obs.shape[0]
+
+
+def reproj_residual(cams, pts, obs, tgt, res=None, ws=None, status=None, stream=None):
+    nc, npt, no = _reproj_params(cams, pts, obs)
+    _check(tgt, torch.float32, "tgt", (no, 2))
+    res = torch.empty(no, 2, dtype=torch.float32, device=cams.device) if res is None else res
+    _check(res, torch.float32, "res", (no, 2))
+    ws = workspace(gpa_reproj_workspace_bytes(nc, npt, no), cams.device) if ws is None else ws
+    rc = load().reproj_residual(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, _ptr(res), _ptr(ws),
+                                ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "reproj_residual")
+    return res
+
+
+def reproj_vjp(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=None, ws=None, status=None,
+               stream=None):
+    nc, npt, no = _reproj_params(cams, pts, obs)
+    _check(w, torch.float32, "w", (no, 2))
+    d_cams = torch.zeros(nc, 11, dtype=torch.float32, device=cams.device) if d_cams is None else d_cams
+    d_pts = torch.zeros(npt, 3, dtype=torch.float32, device=cams.device) if d_pts is None else d_pts
+    _check(d_cams, torch.float32, "d_cams", (nc, 11))
+    _check(d_pts, torch.float32, "d_pts", (npt, 3))
+    ws = workspace(gpa_reproj_workspace_bytes(nc, npt, no), cams.device) if ws is None else ws
+    st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
+    rc = load().reproj_vjp(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(w), nc, npt, no, _ptr(d_cams), _ptr(d_pts), st,
+                           _ptr(plan), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "reproj_vjp")
+    return d_cams, d_pts
+
+
+def reproj_residual_vjp(cams, pts, obs, tgt, wscale=1.0, res=None, d_cams=None, d_pts=None, strat="auto",
+                        plan=None, ws=None, status=None, stream=None):
+    nc, npt, no = _reproj_params(cams, pts, obs)
+    _check(tgt, torch.float32, "tgt", (no, 2))
+    res = torch.empty(no, 2, dtype=torch.float32, device=cams.device) if res is None else res
+    d_cams = torch.zeros(nc, 11, dtype=torch.float32, device=cams.device) if d_cams is None else d_cams
+    d_pts = torch.zeros(npt, 3, dtype=torch.float32, device=cams.device) if d_pts is None else d_pts
+    ws = workspace(gpa_reproj_workspace_bytes(nc, npt, no), cams.device) if ws is None else ws
+    st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
+    rc = load().reproj_residual_vjp(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, float(wscale),
+                                    _ptr(res), _ptr(d_cams), _ptr(d_pts), st, _ptr(plan), _ptr(ws), ws.numel(),
+                                    _ptr(status), _stream(stream))
+    _ok(rc, "reproj_residual_vjp")
+    return res, d_cams, d_pts
+
+
+# ---------------------------------------------------------------------------
+# Plans and the generic scatter
+# ---------------------------------------------------------------------------
+def gpa_plan_bytes(n, n_keys) -> int:
+    return int(load().gpa_plan_bytes(int(n), int(n_keys)))
+
+
+def gpa_plan_workspace_bytes(n, n_keys) -> int:
+    return int(load().gpa_plan_workspace_bytes(int(n), int(n_keys)))
+
+
+def gpa_obs_plan_build(obs, n_cams, n_pts, plan=None, ws=None, status=None, stream=None):
+    _check(obs, torch.int32, "obs")
+    no = obs.shape[0]
+    plan = workspace(gpa_plan_bytes(no, n_cams), obs.device) if plan is None else plan
+    ws = workspace(gpa_plan_workspace_bytes(no, n_cams), obs.device) if ws is None else ws
+    rc = load().gpa_obs_plan_build(_ptr(obs), no, int(n_cams), int(n_pts), _ptr(plan), plan.numel(), _ptr(ws),
+                                   ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "gpa_obs_plan_build")
+    return plan
+
+
+def gpa_index_plan_build(idx, n_keys, plan=None, ws=None, status=None, stream=None):
+    _check(idx, torch.int32, "idx")
+    m = idx.shape[0]
+    plan = workspace(gpa_plan_bytes(m, n_keys), idx.device) if plan is None else plan
+    ws = workspace(gpa_plan_workspace_bytes(m, n_keys), idx.device) if ws is None else ws
+    rc = load().gpa_index_plan_build(_ptr(idx), m, int(n_keys), _ptr(plan), plan.numel(), _ptr(ws), ws.numel(),
+                                     _ptr(status), _stream(stream))
+    _ok(rc, "gpa_index_plan_build")
+    return plan
+
+
+def plan_arrays(plan, n, n_keys):
+    """Views (header, perm, key_sorted, aux_sorted, seg_off) into a plan buffer."""
+    def a256(v):
+        return (v + 255) & ~255
+    off = 256
+    hdr = plan[:32].view(torch.int64)
+    arrs = []
+    for _ in range(3):
+        arrs.append(plan[off:off + 4 * n].view(torch.int32))
+        off += a256(4 * n)
+    seg = plan[off:off + 4 * (n_keys + 1)].view(torch.int32)
+    return hdr, arrs[0], arrs[1], arrs[2], seg
+
+
+def accum_scatter_add(idx, vals, acc, strat="auto", plan=None, status=None, stream=None):
+    _check(idx, torch.int32, "idx")
+    m = idx.shape[0]
+    if vals.dtype not in (torch.float32, torch.int32) or acc.dtype != vals.dtype:
+        raise TypeError("vals and acc must both be float32 or both int32")
+    _check(vals, vals.dtype, "vals")
+    _check(acc, acc.dtype, "acc")
+    w = 1 if vals.dim() == 1 else vals.shape[1]
+    if vals.shape[0] != m:
+        raise ValueError("vals must have one row per index")
+    nb = acc.shape[0]
+    st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
+    dtype = 0 if vals.dtype == torch.float32 else 1
+    rc = load().accum_scatter_add(_ptr(idx), _ptr(vals), m, w, dtype, _ptr(acc), nb, st, _ptr(plan), _ptr(status),
+                                  _stream(stream))
+    _ok(rc, "accum_scatter_add")
+    return acc

@@ -1,0 +1,59 @@
+// Internal interface between the GMM C-ABI entry points and the FP32 and
+// tensor-core implementations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace gpa {
+
+constexpr int kGmmMaxChunks = 64;  // point chunks of the backward grid (partials)
+
+struct GmmArgs {
+    const float *x, *alpha, *mu, *q, *l;
+    int64_t n;
+    int d, k;
+    double gamma;
+    int m;
+    double seed;
+    double* out;
+    float* lse_out;
+    float* lj_out;
+    const float* lj_in;
+    const float* lse_in;
+    float *d_alpha, *d_mu, *d_q, *d_l;
+    int32_t* status;
+};
+
+// Workspace layout (byte offsets, 256-byte aligned) of the FP32 path.
+struct GmmLayout {
+    int dp;              // padded dimension (16, 32, 64, 128)
+    int64_t ntiles;      // 128-point tiles over N
+    int nchunk_max;
+    size_t off_rec;      // K staged records: Qt[DP][DP], b[DP], cst, pad (float)
+    size_t off_scal;     // float64 scalars: [0] logsumexp(alpha)
+    size_t off_lpk;      // float64 log-prior per component
+    size_t off_fwd;      // float64 per-tile sums of lse
+    size_t off_bS;       // float partial S blocks [chunk][K][NBLK][64]
+    size_t off_bM;       // float partial m, R     [chunk][K][DP+1]
+    size_t fixed;        // bytes before the log-joint area
+    int64_t lj_points;   // points per log-joint chunk (0: none)
+    size_t off_lse;      // float lse of the current chunk
+    size_t off_lj;       // float log-joint [K][lj_points]
+    size_t total;
+};
+
+int gmm_dp(int d);
+GmmLayout gmm_layout(int64_t n, int d, int k, int64_t lj_points);
+int64_t gmm_lj_points_for(size_t ws_bytes, const GmmLayout& fixed, int64_t n, int k);
+int gmm_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s);
+int gmm_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s);
+
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulate) path.
+bool gmm_tc_supported(int d);
+size_t gmm_tc_extra_bytes(int64_t n, int d, int k);
+int gmm_tc_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s);
+int gmm_tc_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s);
+
+}  // namespace gpa

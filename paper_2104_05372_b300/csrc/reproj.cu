@@ -1,0 +1,438 @@
+// Camera reprojection residual and its VJP with Accum scatter into per-camera
+// and per-point cotangents (bundle-adjustment objective), FP32 on CUDA cores.
+//
+// Per observation j with (c, p) = obs[j]:
+//   u = X_p - c_c, Y = R(w_c) u, p = Y_xy / Y_z, rho = |p|^2,
+//   L = 1 + k1 rho + k2 rho^2, res_j = f L p + pp - t_j.
+// The rotation of each camera is expanded once per call in float64 (A4's
+// parameter expansion): R as a float32 hi/lo pair, plus the Jacobian factor
+// J_r(w) = I - (1-cos t)/t^2 [w]x + (t - sin t)/t^3 [w]x^2 (t = |w|), for which
+// d(R u)/dw = -[R u]x J_r^T. Y_z is evaluated with error-free transformations
+// (u exact as a hi/lo pair, products via FMA, sums via TwoSum), so points close
+// to the image plane keep the accuracy of the float64 oracle.
+//
+// VJP (A5): the reads cams.(obs.j.0), pts.(obs.j.1) transpose to accumulations
+// into d_cams!(obs.j.0) and d_pts!(obs.j.1) (LetIndexingTranspose) -- an
+// irregular segmented reduction (histogram pattern, Sec. 6.1.3). Strategies:
+//   ATOMIC  one red.global.add per value, observations in their own order;
+//   WARPAGG lanes of a warp with the same camera / point combine first;
+//   SORT    observations in camera-sorted order from a plan: runs of equal
+//           cameras are summed with a segmented warp scan, one atomic per run.
+// No observation stores its Jacobian: the projection is recomputed from the
+// gathered parameters (only non-linear steps keep their inputs, Sec. 5.3.2).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "accum.cuh"
+#include "common.cuh"
+#include "plan_internal.cuh"
+#include "trace.cuh"
+
+namespace gpa {
+
+constexpr int kCamRec = 36;  // floats per expanded camera
+// layout: [0..8] R hi (row-major), [9..17] R lo, [18..20] c, [21] f, [22..23] pp,
+//         [24..25] kappa, [26..34] J_r (row-major), [35] pad
+
+__global__ void __launch_bounds__(128) cam_expand_kernel(const float* __restrict__ cams, int n_cams,
+                                                         float* __restrict__ rec) {
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= n_cams) return;
+    const float* c = cams + (size_t)ci * 11;
+    const double w0 = c[0], w1 = c[1], w2 = c[2];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double R[9], A, B;
+    if (th2 > 1e-16) {
+        const double th = sqrt(th2);
+        const double k0 = w0 / th, k1 = w1 / th, k2 = w2 / th;
+        double st, ct;
+        sincos(th, &st, &ct);
+        const double omc = 1.0 - ct;
+        R[0] = ct + omc * k0 * k0;      R[1] = -st * k2 + omc * k0 * k1; R[2] = st * k1 + omc * k0 * k2;
+        R[3] = st * k2 + omc * k1 * k0; R[4] = ct + omc * k1 * k1;      R[5] = -st * k0 + omc * k1 * k2;
+        R[6] = -st * k1 + omc * k2 * k0; R[7] = st * k0 + omc * k2 * k1; R[8] = ct + omc * k2 * k2;
+        if (th < 1e-3) {  // series of (1-cos t)/t^2 and (t-sin t)/t^3
+            A = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+            B = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+        } else {
+            A = omc / th2;
+            B = (th - st) / (th2 * th);
+        }
+    } else {  // first order: R = I + [w]x
+        R[0] = 1.0; R[1] = -w2; R[2] = w1;
+        R[3] = w2;  R[4] = 1.0; R[5] = -w0;
+        R[6] = -w1; R[7] = w0;  R[8] = 1.0;
+        A = 0.5;
+        B = 1.0 / 6.0;
+    }
+    // [w]x and [w]x^2
+    const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+    double W2[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int t = 0; t < 3; ++t) s += W[i * 3 + t] * W[t * 3 + j];
+            W2[i * 3 + j] = s;
+        }
+    float* o = rec + (size_t)ci * kCamRec;
+    for (int i = 0; i < 9; ++i) {
+        const float hi = (float)R[i];
+        o[i] = hi;
+        o[9 + i] = (float)(R[i] - (double)hi);
+        o[26 + i] = (float)(((i % 4) == 0 ? 1.0 : 0.0) - A * W[i] + B * W2[i]);
+    }
+    o[18] = c[3]; o[19] = c[4]; o[20] = c[5];
+    o[21] = c[6]; o[22] = c[7]; o[23] = c[8];
+    o[24] = c[9]; o[25] = c[10]; o[35] = 0.f;
+}
+
+// ---- error-free transformations ---------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct Proj {
+    float Y[3];   // rotated point (Y[2] compensated)
+    float p[2];   // normalised image coordinates
+    float rho, L;
+    float out[2]; // f L p + pp
+};
+
+// Projection of point X by the expanded camera rc.
+__device__ __forceinline__ Proj project(const float* __restrict__ rc, float X0, float X1, float X2) {
+    Proj P;
+    float u[3], ue[3];
+    two_sum(X0, -__ldg(rc + 18), u[0], ue[0]);
+    two_sum(X1, -__ldg(rc + 19), u[1], ue[1]);
+    two_sum(X2, -__ldg(rc + 20), u[2], ue[2]);
+    float Rh[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rh[i] = __ldg(rc + i);
+    P.Y[0] = fmaf(Rh[0], u[0], fmaf(Rh[1], u[1], Rh[2] * u[2]));
+    P.Y[1] = fmaf(Rh[3], u[0], fmaf(Rh[4], u[1], Rh[5] * u[2]));
+    {
+        float pr[3], pe[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            pr[j] = __fmul_rn(Rh[6 + j], u[j]);
+            pe[j] = fmaf(Rh[6 + j], u[j], -pr[j]);
+        }
+        float s1, t1, s2, t2;
+        two_sum(pr[0], pr[1], s1, t1);
+        two_sum(s1, pr[2], s2, t2);
+        float corr = t1 + t2 + pe[0] + pe[1] + pe[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) corr = fmaf(__ldg(rc + 15 + j), u[j], fmaf(Rh[6 + j], ue[j], corr));
+        P.Y[2] = s2 + corr;
+    }
+    P.p[0] = P.Y[0] / P.Y[2];
+    P.p[1] = P.Y[1] / P.Y[2];
+    P.rho = P.p[0] * P.p[0] + P.p[1] * P.p[1];
+    const float k1 = __ldg(rc + 24), k2 = __ldg(rc + 25), f = __ldg(rc + 21);
+    P.L = 1.f + k1 * P.rho + k2 * P.rho * P.rho;
+    P.out[0] = f * P.L * P.p[0] + __ldg(rc + 22);
+    P.out[1] = f * P.L * P.p[1] + __ldg(rc + 23);
+    return P;
+}
+
+// Cotangents of the 11 camera parameters and 3 point coordinates for a
+// cotangent (w0, w1) of the projection.
+__device__ __forceinline__ void project_vjp(const float* __restrict__ rc, const Proj& P, float w0, float w1,
+                                            float (&gc)[11], float (&gp)[3]) {
+    const float f = __ldg(rc + 21), k1 = __ldg(rc + 24), k2 = __ldg(rc + 25);
+    const float pw = P.p[0] * w0 + P.p[1] * w1;
+    const float dL = f * pw;
+    const float drho = dL * (k1 + 2.f * k2 * P.rho);
+    const float fl = f * P.L;
+    const float dp0 = fl * w0 + 2.f * drho * P.p[0];
+    const float dp1 = fl * w1 + 2.f * drho * P.p[1];
+    const float inv = 1.f / P.Y[2];
+    const float yb0 = dp0 * inv, yb1 = dp1 * inv;
+    const float yb2 = -(dp0 * P.p[0] + dp1 * P.p[1]) * inv;
+    // d X = R^T ybar
+    float dX[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        dX[j] = __ldg(rc + j) * yb0 + __ldg(rc + 3 + j) * yb1 + __ldg(rc + 6 + j) * yb2;
+    // d w = J_r (Y x ybar)
+    const float cx = P.Y[1] * yb2 - P.Y[2] * yb1;
+    const float cy = P.Y[2] * yb0 - P.Y[0] * yb2;
+    const float cz = P.Y[0] * yb1 - P.Y[1] * yb0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        gc[i] = __ldg(rc + 26 + 3 * i) * cx + __ldg(rc + 27 + 3 * i) * cy + __ldg(rc + 28 + 3 * i) * cz;
+    gc[3] = -dX[0]; gc[4] = -dX[1]; gc[5] = -dX[2];
+    gc[6] = P.L * pw;
+    gc[7] = w0; gc[8] = w1;
+    gc[9] = dL * P.rho;
+    gc[10] = dL * P.rho * P.rho;
+    gp[0] = dX[0]; gp[1] = dX[1]; gp[2] = dX[2];
+}
+
+__global__ void __launch_bounds__(256) reproj_residual_kernel(
+    const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
+    const float2* __restrict__ tgt, int n_cams, int n_pts, int64_t n_obs, float2* __restrict__ res,
+    int32_t* __restrict__ status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_obs; j += stride) {
+        const int2 o = __ldg(obs + j);
+        if (o.x < 0 || o.x >= n_cams || o.y < 0 || o.y >= n_pts) {
+            res[j] = make_float2(NAN, NAN);
+            report(status, GPA_ERR_INDEX);
+            continue;
+        }
+        const float* rc = rec + (size_t)o.x * kCamRec;
+        const float* X = pts + (size_t)o.y * 3;
+        const Proj P = project(rc, __ldg(X), __ldg(X + 1), __ldg(X + 2));
+        const float2 t = __ldg(tgt + j);
+        res[j] = make_float2(P.out[0] - t.x, P.out[1] - t.y);
+    }
+}
+
+// VJP over observations; FUSED also writes res and uses w = wscale * res.
+template <int STRAT, bool FUSED>
+__global__ void __launch_bounds__(256) reproj_vjp_kernel(
+    const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
+    const float2* __restrict__ wv, const float2* __restrict__ tgt, float wscale, int n_cams, int n_pts,
+    int64_t n_obs, const int32_t* __restrict__ perm, const int32_t* __restrict__ key_s,
+    const int32_t* __restrict__ aux_s, float* __restrict__ d_cams, float* __restrict__ d_pts,
+    float2* __restrict__ res, int32_t* __restrict__ status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    // trip count is uniform over the block so that every lane reaches the shuffles
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_obs; base += stride) {
+        const int64_t pos = base + threadIdx.x;
+        bool valid = pos < n_obs;
+        int64_t e = pos;  // element id
+        int ci = -1, pi = -1;
+        if (valid) {
+            if (STRAT == GPA_SCATTER_SORT) {
+                e = __ldg(perm + pos);
+                ci = __ldg(key_s + pos);
+                pi = __ldg(aux_s + pos);
+                if (e < 0 || e >= n_obs) ci = -1;  // not a plan of these observations
+            } else {
+                const int2 o = __ldg(obs + pos);
+                ci = o.x;
+                pi = o.y;
+            }
+            if (ci < 0 || ci >= n_cams || pi < 0 || pi >= n_pts) {
+                if (FUSED) res[e] = make_float2(NAN, NAN);
+                report(status, GPA_ERR_INDEX);
+                valid = false;
+            }
+        }
+        float gc[11], gp[3];
+#pragma unroll
+        for (int i = 0; i < 11; ++i) gc[i] = 0.f;
+        gp[0] = gp[1] = gp[2] = 0.f;
+        if (valid) {
+            const float* rc = rec + (size_t)ci * kCamRec;
+            const float* X = pts + (size_t)pi * 3;
+            const Proj P = project(rc, __ldg(X), __ldg(X + 1), __ldg(X + 2));
+            float w0, w1;
+            if (FUSED) {
+                const float2 t = __ldg(tgt + e);
+                const float r0 = P.out[0] - t.x, r1 = P.out[1] - t.y;
+                res[e] = make_float2(r0, r1);
+                w0 = wscale * r0;
+                w1 = wscale * r1;
+            } else {
+                const float2 w = __ldg(wv + e);
+                w0 = w.x;
+                w1 = w.y;
+            }
+            project_vjp(rc, P, w0, w1, gc, gp);
+        }
+        if (STRAT == GPA_SCATTER_ATOMIC) {
+            if (valid) {
+                float* dc = d_cams + (size_t)ci * 11;
+#pragma unroll
+                for (int i = 0; i < 11; ++i) red_add(dc + i, gc[i]);
+                float* dp = d_pts + (size_t)pi * 3;
+                red_add(dp, gp[0]); red_add(dp + 1, gp[1]); red_add(dp + 2, gp[2]);
+            }
+        } else if (STRAT == GPA_SCATTER_WARPAGG) {
+            const int ck = valid ? ci : -1 - lane;
+            const unsigned gcm = __match_any_sync(0xffffffffu, ck);
+            if (__any_sync(0xffffffffu, __popc(gcm) > 1)) {
+#pragma unroll
+                for (int i = 0; i < 11; ++i) gc[i] = group_sum(gc[i], gcm);
+            }
+            if (valid && (__ffs(gcm) - 1) == lane) {
+                float* dc = d_cams + (size_t)ci * 11;
+#pragma unroll
+                for (int i = 0; i < 11; ++i) red_add(dc + i, gc[i]);
+            }
+            const int pk = valid ? pi : -1 - lane;
+            const unsigned gpm = __match_any_sync(0xffffffffu, pk);
+            if (__any_sync(0xffffffffu, __popc(gpm) > 1)) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) gp[i] = group_sum(gp[i], gpm);
+            }
+            if (valid && (__ffs(gpm) - 1) == lane) {
+                float* dp = d_pts + (size_t)pi * 3;
+                red_add(dp, gp[0]); red_add(dp + 1, gp[1]); red_add(dp + 2, gp[2]);
+            }
+        } else {  // SORT: runs of equal cameras in lane order
+            const int ck = valid ? ci : -1 - lane;
+#pragma unroll
+            for (int i = 0; i < 11; ++i) gc[i] = run_scan(gc[i], ck);
+            const bool last = run_end(ck);
+            if (valid && last) {
+                float* dc = d_cams + (size_t)ci * 11;
+#pragma unroll
+                for (int i = 0; i < 11; ++i) red_add(dc + i, gc[i]);
+            }
+            if (valid) {
+                float* dp = d_pts + (size_t)pi * 3;
+                red_add(dp, gp[0]); red_add(dp + 1, gp[1]); red_add(dp + 2, gp[2]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+static unsigned obs_grid(int64_t n_obs) {
+    const int64_t want = (n_obs + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    return (unsigned)(want < cap ? want : cap);
+}
+
+static int expand_cams(const float* cams, int n_cams, float* rec, cudaStream_t s) {
+    GPA_LAUNCH("cam_expand", s, cam_expand_kernel<<<(n_cams + 127) / 128, 128, 0, s>>>(cams, n_cams, rec));
+    return GPA_OK;
+}
+
+template <int STRAT, bool FUSED>
+static int launch_vjp(const float* rec, const float* pts, const int32_t* obs, const float* w, const float* tgt,
+                      float wscale, int n_cams, int n_pts, int64_t n_obs, const PlanView& pv, float* d_cams,
+                      float* d_pts, float* res, int32_t* status, cudaStream_t s) {
+    GPA_LAUNCH(FUSED ? "reproj_residual_vjp" : "reproj_vjp", s,
+               reproj_vjp_kernel<STRAT, FUSED><<<obs_grid(n_obs), 256, 0, s>>>(
+                   rec, pts, (const int2*)obs, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts,
+                   n_obs, pv.perm, pv.key_sorted, pv.aux_sorted, d_cams, d_pts, (float2*)res, status));
+    return GPA_OK;
+}
+
+template <bool FUSED>
+static int dispatch_vjp(int strat, const float* rec, const float* pts, const int32_t* obs, const float* w,
+                        const float* tgt, float wscale, int n_cams, int n_pts, int64_t n_obs,
+                        const PlanView& pv, float* d_cams, float* d_pts, float* res, int32_t* status,
+                        cudaStream_t s) {
+    switch (strat) {
+        case GPA_SCATTER_ATOMIC:
+            return launch_vjp<GPA_SCATTER_ATOMIC, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs,
+                                                        pv, d_cams, d_pts, res, status, s);
+        case GPA_SCATTER_WARPAGG:
+            return launch_vjp<GPA_SCATTER_WARPAGG, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs,
+                                                         pv, d_cams, d_pts, res, status, s);
+        case GPA_SCATTER_SORT:
+            return launch_vjp<GPA_SCATTER_SORT, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs, pv,
+                                                      d_cams, d_pts, res, status, s);
+    }
+    return GPA_ERR_ARG;
+}
+
+}  // namespace gpa
+
+using namespace gpa;
+
+static bool al(const void* p, uintptr_t a) { return (((uintptr_t)p) & (a - 1)) == 0; }
+
+extern "C" size_t gpa_reproj_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs) {
+    (void)n_pts;
+    (void)n_obs;
+    if (n_cams < 1) return 0;
+    return ((sizeof(float) * (size_t)n_cams * kCamRec + 255) & ~(size_t)255) + 256;
+}
+
+static int reproj_check(const float* cams, const float* pts, const int32_t* obs, int32_t n_cams,
+                        int32_t n_pts, int64_t n_obs, void* ws, size_t ws_bytes) {
+    if (!cams || !pts || !obs || !ws) return GPA_ERR_ARG;
+    if (n_cams < 1 || n_pts < 1 || n_obs < 1 || n_obs > INT32_MAX) return GPA_ERR_ARG;
+    if (!al(obs, 8) || !al(cams, 4) || !al(pts, 4) || !al(ws, 256)) return GPA_ERR_ALIGN;
+    if (ws_bytes < gpa_reproj_workspace_bytes(n_cams, n_pts, n_obs)) return GPA_ERR_WORKSPACE;
+    return GPA_OK;
+}
+
+extern "C" int reproj_residual(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
+                               int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, void* ws,
+                               size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
+    int rc = reproj_check(cams, pts, obs, n_cams, n_pts, n_obs, ws, ws_bytes);
+    if (rc) return rc;
+    if (!tgt || !res) return GPA_ERR_ARG;
+    if (!al(tgt, 8) || !al(res, 8)) return GPA_ERR_ALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rec = (float*)ws;
+    rc = expand_cams(cams, n_cams, rec, s);
+    if (rc) return rc;
+    GPA_LAUNCH("reproj_residual", s,
+               reproj_residual_kernel<<<obs_grid(n_obs), 256, 0, s>>>(rec, pts, (const int2*)obs,
+                                                                      (const float2*)tgt, n_cams, n_pts, n_obs,
+                                                                      (float2*)res, dev_status));
+    return GPA_OK;
+}
+
+static int resolve_strat(int strat, const void* plan) {
+    if (strat == GPA_SCATTER_AUTO) return plan ? GPA_SCATTER_SORT : GPA_SCATTER_ATOMIC;
+    return strat;
+}
+
+extern "C" int reproj_vjp(const float* cams, const float* pts, const int32_t* obs, const float* w,
+                          int32_t n_cams, int32_t n_pts, int64_t n_obs, float* d_cams, float* d_pts,
+                          int32_t strat, const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
+                          gpa_stream_t stream) {
+    int rc = reproj_check(cams, pts, obs, n_cams, n_pts, n_obs, ws, ws_bytes);
+    if (rc) return rc;
+    if (!w || !d_cams || !d_pts) return GPA_ERR_ARG;
+    if (!al(w, 8)) return GPA_ERR_ALIGN;
+    strat = resolve_strat(strat, plan);
+    if (strat < GPA_SCATTER_ATOMIC || strat > GPA_SCATTER_SORT) return GPA_ERR_ARG;
+    PlanView pv{};
+    if (strat == GPA_SCATTER_SORT) {
+        if (!plan) return GPA_ERR_ARG;
+        pv = plan_view(plan, n_obs, n_cams);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rec = (float*)ws;
+    rc = expand_cams(cams, n_cams, rec, s);
+    if (rc) return rc;
+    return dispatch_vjp<false>(strat, rec, pts, obs, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
+                               nullptr, dev_status, s);
+}
+
+extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
+                                   int32_t n_cams, int32_t n_pts, int64_t n_obs, float wscale, float* res,
+                                   float* d_cams, float* d_pts, int32_t strat, const void* plan, void* ws,
+                                   size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
+    int rc = reproj_check(cams, pts, obs, n_cams, n_pts, n_obs, ws, ws_bytes);
+    if (rc) return rc;
+    if (!tgt || !res || !d_cams || !d_pts) return GPA_ERR_ARG;
+    if (!al(tgt, 8) || !al(res, 8)) return GPA_ERR_ALIGN;
+    strat = resolve_strat(strat, plan);
+    if (strat < GPA_SCATTER_ATOMIC || strat > GPA_SCATTER_SORT) return GPA_ERR_ARG;
+    PlanView pv{};
+    if (strat == GPA_SCATTER_SORT) {
+        if (!plan) return GPA_ERR_ARG;
+        pv = plan_view(plan, n_obs, n_cams);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rec = (float*)ws;
+    rc = expand_cams(cams, n_cams, rec, s);
+    if (rc) return rc;
+    return dispatch_vjp<true>(strat, rec, pts, obs, nullptr, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams,
+                              d_pts, res, dev_status, s);
+}

@@ -1,0 +1,87 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and host-side argument checks reject bad calls before any
+CUDA work is enqueued."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gpa.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"GPA_API\s+(?:const\s+)?\w+\*?\s+\*?(\w+)\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_05372_b300 import build
+    build.build()
+    from paper_2104_05372_b300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("gmm_objective", "gmm_vjp", "reproj_residual", "reproj_vjp", "accum_scatter_add"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2104_05372_b300 import _lib
+    assert sorted(_lib.exported_symbols()) == _declared()
+
+
+def test_status_strings(lib):
+    from paper_2104_05372_b300 import _lib
+    for code in range(8):
+        assert _lib.status_string(code).startswith("GPA_")
+    assert _lib.version() >= 100
+
+
+def test_workspace_queries(lib):
+    from paper_2104_05372_b300 import _lib
+    small = _lib.gpa_gmm_workspace_bytes(1000, 10, 5, 0, 128)
+    full = _lib.gpa_gmm_workspace_bytes(1000, 10, 5, 0, 0)
+    assert 0 < small < full
+    assert _lib.gpa_gmm_workspace_bytes(0, 10, 5, 0, 0) == 0
+    assert _lib.gpa_gmm_workspace_bytes(10, 129, 5, 0, 0) == 0
+    assert _lib.gpa_reproj_workspace_bytes(8192, 500000, 4000000) >= 8192 * 36 * 4
+    assert _lib.gpa_plan_bytes(100, 10) >= 256 + 3 * 400 + 44
+    assert _lib.gpa_plan_workspace_bytes(0, 10) == 0
+
+
+def test_host_argument_errors_return_before_any_launch(lib):
+    fake = C.c_void_p(256)  # never dereferenced: every call below fails its host checks
+    # null x
+    assert lib.gmm_objective(None, fake, fake, fake, fake, 10, 3, 2, 1.0, 0, 0, fake, None, None, fake, 1 << 20,
+                             None, None) == 1
+    # D out of range
+    assert lib.gmm_objective(fake, fake, fake, fake, fake, 10, 129, 2, 1.0, 0, 0, fake, None, None, fake, 1 << 20,
+                             None, None) == 1
+    # gamma <= 0
+    assert lib.gmm_vjp(fake, fake, fake, fake, fake, 10, 3, 2, 0.0, 0, 0, None, None, 1.0, fake, fake, fake, fake,
+                       None, fake, 1 << 20, None, None) == 1
+    # workspace too small
+    assert lib.gmm_objective(fake, fake, fake, fake, fake, 10, 3, 2, 1.0, 0, 0, fake, None, None, fake, 16,
+                             None, None) == 4
+    # misaligned workspace
+    assert lib.gmm_objective(fake, fake, fake, fake, fake, 10, 3, 2, 1.0, 0, 0, fake, None, None, C.c_void_p(260),
+                             1 << 20, None, None) == 7
+    # reprojection: non-positive sizes, bad strategy, SORT without a plan
+    assert lib.reproj_residual(fake, fake, fake, fake, 0, 1, 1, fake, fake, 1 << 20, None, None) == 1
+    assert lib.reproj_vjp(fake, fake, fake, fake, 2, 2, 2, fake, fake, 9, None, fake, 1 << 20, None, None) == 1
+    assert lib.reproj_vjp(fake, fake, fake, fake, 2, 2, 2, fake, fake, 3, None, fake, 1 << 20, None, None) == 1
+    # scatter: w out of range, bad dtype
+    assert lib.accum_scatter_add(fake, fake, 10, 65, 0, fake, 4, 1, None, None, None) == 1
+    assert lib.accum_scatter_add(fake, fake, 10, 1, 2, fake, 4, 1, None, None, None) == 1
+    # plans: workspace too small
+    assert lib.gpa_index_plan_build(fake, 100, 10, fake, 16, fake, 1 << 20, None, None) == 4

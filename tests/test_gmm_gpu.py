@@ -1,0 +1,179 @@
+"""GPU parity of the GMM objective and gradient (FP32 path) against the FP64 oracle.
+
+Objective: relative error <= 1e-5. Gradient: normwise relative error per
+parameter block (alpha, mu, q, l) <= 1e-4. Per-point statistics (lse, log-joint)
+elementwise. Shapes span several tiles with ragged tails and every padded
+dimension class (D <= 16, 32, 64, 128).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import TOL_GRAD_FP32, TOL_OBJ_FP32, gmm_dev, host, rel_norm, status
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_forward(g, prec=0):
+    import paper_2104_05372_b300 as gpa
+    x, a, mu, q, l = gmm_dev(g)
+    lse = torch.empty(g.n, device="cuda")
+    lj = torch.empty(g.k, g.n, device="cuda")
+    st = status()
+    out = gpa.gmm_objective(x, a, mu, q, l, g.gamma, g.m, prec, lse_out=lse, logjoint_out=lj, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    return float(out.item()), host(lse), host(lj), (x, a, mu, q, l, lse, lj)
+
+
+def _gpu_grad(g, prec=0, stored=True, logjoint_points=0, seed=1.0):
+    import paper_2104_05372_b300 as gpa
+    f, lse, lj, (x, a, mu, q, l, lse_t, lj_t) = _gpu_forward(g, prec)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = status()
+    grads = gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, prec, logjoint_in=lj_t if stored else None,
+                        lse_in=lse_t if stored else None, seed=seed, out=out,
+                        logjoint_points=logjoint_points, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    return f, float(out.item()), [host(t) for t in grads], lse, lj
+
+
+def _check_grad(got, ref, tol=TOL_GRAD_FP32):
+    for name, gb, rb in zip(("alpha", "mu", "q", "l"), got, ref):
+        if rb.size == 0:
+            continue
+        err = rel_norm(gb, rb)
+        assert err <= tol, (name, err)
+
+
+SHAPES = [
+    (1, 1, 1, 1.0, 0),
+    (127, 3, 2, 1.0, 0),
+    (129, 16, 9, 0.7, 2),
+    (300, 17, 33, 1.3, 1),
+    (1000, 10, 5, 1.0, 0),       # the small workload
+    (1000, 32, 17, 1.0, 0),
+    (2500, 64, 20, 1.0, 3),
+    (777, 100, 7, 1.0, 0),
+    (640, 128, 5, 2.0, 0),
+    (5000, 8, 130, 1.0, 0),
+]
+
+
+@pytest.mark.parametrize("n,d,k,gamma,m", SHAPES)
+def test_objective_and_gradient_match_oracle(n, d, k, gamma, m):
+    g = synth.gmm_inputs(n, d, k, seed=n * 31 + d * 7 + k, gamma=gamma, m=m)
+    f_ref, lse_ref = oracle.gmm_objective(g, want_lse=True)
+    _, *gref = oracle.gmm_grad(g)
+    f, f2, grads, lse, lj = _gpu_grad(g)
+    assert abs(f - f_ref) <= TOL_OBJ_FP32 * abs(f_ref), (f, f_ref)
+    assert abs(f2 - f_ref) <= TOL_OBJ_FP32 * abs(f_ref), (f2, f_ref)
+    assert np.allclose(lse, lse_ref, rtol=1e-5, atol=1e-4)
+    s_ref, _ = oracle.gmm_logjoint_at(g, np.arange(g.n))
+    assert np.allclose(lj.T, s_ref, rtol=1e-5, atol=2e-4)
+    _check_grad(grads, gref)
+
+
+def test_recompute_mode_matches_oracle_and_stored_mode():
+    """Log-joint recomputed in chunks of 256 points (memory budget) inside gmm_vjp."""
+    g = synth.gmm_inputs(3000, 24, 11, seed=5)
+    _, *gref = oracle.gmm_grad(g)
+    f_ref = oracle.gmm_objective(g)
+    _, f_stored, g_stored, _, _ = _gpu_grad(g, stored=True)
+    _, f_rec, g_rec, _, _ = _gpu_grad(g, stored=False, logjoint_points=256)
+    assert abs(f_rec - f_ref) <= TOL_OBJ_FP32 * abs(f_ref)
+    _check_grad(g_rec, gref)
+    for a, b in zip(g_stored, g_rec):
+        assert rel_norm(a, b) <= 1e-5
+
+
+def test_seed_scales_and_outputs_accumulate():
+    """seed multiplies every term; d_* are += (Accum), so two calls double them."""
+    import paper_2104_05372_b300 as gpa
+    g = synth.gmm_inputs(700, 12, 6, seed=9, gamma=1.4, m=1)
+    _, *gref = oracle.gmm_grad(g, seed=-0.75)
+    x, a, mu, q, l = gmm_dev(g)
+    bufs = gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, seed=-0.75)
+    gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, seed=-0.75, d_alpha=bufs[0], d_mu=bufs[1], d_q=bufs[2], d_l=bufs[3])
+    torch.cuda.synchronize()
+    _check_grad([host(t) / 2.0 for t in bufs], gref)
+
+
+def test_gradient_is_deterministic_run_to_run():
+    import paper_2104_05372_b300 as gpa
+    g = synth.gmm_inputs(4000, 40, 23, seed=2)
+    x, a, mu, q, l = gmm_dev(g)
+    r1 = [host(t) for t in gpa.gmm_vjp(x, a, mu, q, l)]
+    r2 = [host(t) for t in gpa.gmm_vjp(x, a, mu, q, l)]
+    for u, v in zip(r1, r2):
+        assert np.array_equal(u, v)
+
+
+def test_large_workload_slice_matches_oracle():
+    """D=64, K=200 as in the large workload, N = 2^14 + 37 points (many tiles, ragged)."""
+    g = synth.gmm_inputs((1 << 14) + 37, 64, 200, seed=1)
+    f_ref, *gref = oracle.gmm_grad(g)
+    f, f2, grads, _, _ = _gpu_grad(g)
+    assert abs(f - f_ref) <= TOL_OBJ_FP32 * abs(f_ref)
+    assert abs(f2 - f_ref) <= TOL_OBJ_FP32 * abs(f_ref)
+    _check_grad(grads, gref)
+
+
+@pytest.mark.slow
+def test_full_size_sampled_statistics_and_accum_invariance():
+    """N=2^20, D=64, K=200 in the benchmark's launch configuration: sampled
+    per-point statistics against the oracle one by one, and the gradient's
+    invariance under a permutation and a partition of the points (Accum
+    updates are associative, Sec. 2.3.2)."""
+    import paper_2104_05372_b300 as gpa
+    g = synth.gmm_inputs(1 << 20, 64, 200, seed=0)
+    f, lse, lj, (x, a, mu, q, l, lse_t, lj_t) = _gpu_forward(g)
+    idx = np.random.default_rng(0).choice(g.n, 4096, replace=False)
+    idx[:2] = [0, g.n - 1]
+    s_ref, lse_ref = oracle.gmm_logjoint_at(g, idx)
+    assert np.allclose(lse[idx], lse_ref, rtol=1e-5, atol=1e-4)
+    assert np.allclose(lj[:, idx].T, s_ref, rtol=1e-5, atol=2e-4)
+    full = [host(t) for t in gpa.gmm_vjp(x, a, mu, q, l)]
+    perm = torch.from_numpy(np.random.default_rng(1).permutation(g.n)).cuda()
+    permuted = [host(t) for t in gpa.gmm_vjp(x[perm].contiguous(), a, mu, q, l)]
+    for u, v in zip(full, permuted):
+        assert rel_norm(v, u) <= 2e-5
+    h = g.n // 3
+    pa = [host(t) for t in gpa.gmm_vjp(x[:h].contiguous(), a, mu, q, l)]
+    pb = [host(t) for t in gpa.gmm_vjp(x[h:].contiguous(), a, mu, q, l)]
+    # the prior's gradient is counted once per call: remove one copy
+    prior_q = g.m - g.gamma ** 2 * np.exp(2.0 * g.q.astype(np.float64))
+    prior_l = -g.gamma ** 2 * g.l.astype(np.float64)
+    summed = [pa[0] + pb[0], pa[1] + pb[1], pa[2] + pb[2] - prior_q, pa[3] + pb[3] - prior_l]
+    for u, v in zip(full, summed):
+        assert rel_norm(v, u) <= 2e-5
+
+
+def test_host_errors_enqueue_nothing():
+    import paper_2104_05372_b300 as gpa
+    g = synth.gmm_inputs(100, 4, 3, seed=0)
+    x, a, mu, q, l = gmm_dev(g)
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gpa.GpaError) as e:
+        gpa.gmm_objective(x, a, mu, q, l, ws=small)
+    assert e.value.code == 4  # GPA_ERR_WORKSPACE
+    with pytest.raises(gpa.GpaError) as e:
+        gpa.gmm_vjp(x, a, mu, q, l, logjoint_in=torch.empty(3, 100, device="cuda"))
+    assert e.value.code == 1  # exactly one of logjoint_in / lse_in
+
+
+def test_autograd_function_matches_oracle_both_budgets():
+    from paper_2104_05372_b300.autograd import gmm_objective
+    g = synth.gmm_inputs(1500, 20, 9, seed=4, gamma=0.9, m=2)
+    f_ref, *gref = oracle.gmm_grad(g)
+    for budget in (None, 4096):  # stored log-joint / recomputed in 128-point chunks
+        x, a, mu, q, l = gmm_dev(g)
+        for t in (a, mu, q, l):
+            t.requires_grad_(True)
+        f = gmm_objective(x, a, mu, q, l, g.gamma, g.m, budget_bytes=budget)
+        (2.0 * f).backward()
+        assert abs(float(f.item()) - f_ref) <= TOL_OBJ_FP32 * abs(f_ref)
+        _check_grad([host(t.grad) / 2.0 for t in (a, mu, q, l)], gref)

@@ -1,0 +1,95 @@
+"""GPU parity of accum_scatter_add (every strategy) and of index plans.
+
+int32 values: bit-exact against the oracle (exact int64 sums). float32 values:
+per bucket within the summation bound (n_b - 1) u sum_j |v_j| (u = 2^-24) plus
+the final rounding, checked against the oracle's float64 sums.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import dev, host, status
+
+pytestmark = pytest.mark.gpu
+STRATS = ["atomic", "warpagg", "sort"]
+
+
+def _run(idx, vals, nb, strat):
+    import paper_2104_05372_b300 as gpa
+    idx_d = dev(idx)
+    vals_d = dev(vals)
+    acc = torch.zeros((nb,) + vals.shape[1:], dtype=vals_d.dtype, device="cuda")
+    plan = gpa.gpa_index_plan_build(idx_d, nb) if strat == "sort" else None
+    st = status()
+    gpa.accum_scatter_add(idx_d, vals_d, acc, strat=strat, plan=plan, status=st)
+    torch.cuda.synchronize()
+    return host(acc), int(st.item())
+
+
+@pytest.mark.parametrize("strat", STRATS)
+@pytest.mark.parametrize("m,w,nb,skew", [(1, 1, 1, 0.0), (5, 1, 4, 0.0), (100000, 1, 1000, 0.0),
+                                         (100000, 3, 50, 1.5), (33333, 11, 7, 0.0), (4096, 64, 1, 0.0)])
+def test_int32_histogram_bit_exact(strat, m, w, nb, skew):
+    idx, vals = synth.scatter_inputs(m, w, nb, "i32", seed=m + w, skew=skew)
+    ref, bad = oracle.scatter_add(idx, vals, nb)
+    got, st = _run(idx, vals, nb, strat)
+    assert bad == 0 and st == 0
+    assert np.array_equal(got.reshape(nb, w).astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("strat", STRATS)
+@pytest.mark.parametrize("m,w,nb,skew", [(100000, 1, 1000, 0.0), (200000, 4, 300, 1.2), (50000, 14, 3, 0.0)])
+def test_float_scatter_within_summation_bound(strat, m, w, nb, skew):
+    idx, vals = synth.scatter_inputs(m, w, nb, "f32", seed=7 + w, skew=skew)
+    ref, _ = oracle.scatter_add(idx, vals, nb)
+    got, st = _run(idx, vals, nb, strat)
+    assert st == 0
+    nbk = np.bincount(idx, minlength=nb).astype(np.float64)[:, None]
+    absum, _ = oracle.scatter_add(idx, np.abs(vals), nb)
+    bound = (np.maximum(nbk - 1, 0) * 2.0 ** -24) * absum + 2.0 ** -24 * np.abs(ref) + 1e-30
+    assert np.all(np.abs(got.reshape(nb, w) - ref) <= bound)
+
+
+def test_paper_histogram_example():
+    # hist!(x.i) += 1 over x = [2, 0, 2, 3, 2], 4 bins -> [1, 0, 3, 1]
+    for strat in STRATS:
+        got, _ = _run(np.array([2, 0, 2, 3, 2], np.int32), np.ones(5, np.int32), 4, strat)
+        assert got.tolist() == [1, 0, 3, 1]
+
+
+def test_invalid_indices_skipped_and_reported():
+    idx = np.array([0, 7, -1, 2, 2, 3], np.int32)
+    vals = np.arange(1, 7, dtype=np.int32)
+    for strat in STRATS:
+        got, st = _run(idx, vals, 4, strat)
+        assert st == 2
+        assert got.tolist() == [1, 0, 4 + 5, 6]
+
+
+def test_index_plan_bit_exact():
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300._lib import plan_arrays
+    for m, nk in [(1, 1), (1000, 7), (123457, 70000), (300000, 3)]:
+        idx, _ = synth.scatter_inputs(m, 1, nk, "i32", seed=m, skew=0.8 if nk > 10 else 0.0)
+        plan = gpa.gpa_index_plan_build(dev(idx), nk)
+        hdr, perm, keys, _, seg = (host(t) for t in plan_arrays(plan, m, nk))
+        perm_ref, seg_ref, _ = oracle.stable_sort_by_key(idx, nk)
+        assert hdr[2] == m
+        assert np.array_equal(perm, perm_ref)
+        assert np.array_equal(keys, idx[perm_ref])
+        assert np.array_equal(seg, seg_ref.astype(np.int32))
+
+
+def test_partition_invariance_bit_exact_int32():
+    """Accum: splitting the updates into shards and adding the shard sums
+    gives the same histogram (Sec. 2.3.2)."""
+    import paper_2104_05372_b300 as gpa
+    idx, vals = synth.scatter_inputs(200000, 2, 500, "i32", seed=11, skew=1.0)
+    whole, _ = _run(idx, vals, 500, "atomic")
+    acc = torch.zeros(500, 2, dtype=torch.int32, device="cuda")
+    cuts = [0, 12345, 100000, 177777, 200000]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        gpa.accum_scatter_add(dev(idx[a:b]), dev(vals[a:b]), acc, strat="warpagg")
+    assert np.array_equal(host(acc), whole)
