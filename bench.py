@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gmm-n", type=int, default=GMM_N,
+                    help="points of the GMM batch (smaller only for profiling captures)")
     return ap.parse_args()
 
 
@@ -151,6 +153,8 @@ def traffic_record(kernel: str):
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
+    global GMM_N
+    GMM_N = args.gmm_n
     import torch
     rank, world, local = dist_info()
     if world > 1:

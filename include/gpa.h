@@ -244,10 +244,11 @@ GPA_API int accum_scatter_add(const int32_t* idx, const void* vals, int64_t m, i
  * created once and reused; no device memory is allocated). Process-wide. */
 GPA_API void gpa_trace_enable(int on);
 
-/* Resolve the recorded launches (waits for the last one), write one line
- * "name launches total_ms" per kernel name into buf (host memory, len bytes,
- * NUL-terminated, truncated if short), forget them, and return the length the
- * full text needs. */
+/* Resolve the recorded launches (waits for the last one) and return the length
+ * of the text "name launches total_ms\n" (one line per kernel name). If buf
+ * (host memory) holds more than that many bytes, the text is copied into it
+ * NUL-terminated and the records are forgotten; otherwise (buf NULL or too
+ * short) nothing is copied and the records are kept. */
 GPA_API int gpa_trace_summary(char* buf, size_t len);
 
 #ifdef __cplusplus

@@ -53,6 +53,15 @@ struct Fwd {
         sizeof(float) * (size_t)(DP * XST + 2 * NS * REC + 2 * NS * NWC * TP + 2 * NS * TP) + 64;
 };
 
+// Word offset of element c inside a point row of the backward tile: the two
+// 16-byte halves of each 8-float chunk swap places when bit 2 of the chunk index
+// is set, so that the chunks 8a.. read by the lanes of a warp spread over all
+// 32 banks.
+__host__ __device__ __forceinline__ int bwd_swz(int c) {
+    const int a = c >> 3, h = (c >> 2) & 1;
+    return (a << 3) + ((h ^ ((a >> 2) & 1)) << 2) + (c & 3);
+}
+
 template <int DP>
 struct Bwd {
     static constexpr int NB = DP / 8;
@@ -376,7 +385,7 @@ __global__ void __launch_bounds__(256) gmm_objective_finalize_kernel(
 // grid (component groups, point chunks). Diagonal-block threads fill warps of
 // their own (they also accumulate m and R); off-diagonal threads fill the rest.
 template <int DP>
-__global__ void __launch_bounds__(Bwd<DP>::THREADS) __maxnreg__(DP == 64 ? 112 : 168)
+__global__ void __launch_bounds__(Bwd<DP>::THREADS) __maxnreg__(DP == 64 ? 96 : 168)
     gmm_bwd_kernel(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
@@ -429,7 +438,7 @@ __global__ void __launch_bounds__(Bwd<DP>::THREADS) __maxnreg__(DP == 64 ? 112 :
         __syncthreads();
         for (int e = tid; e < nv * d; e += C::THREADS) {
             const int p = e / d, c = e - p * d;
-            Xs[p * XST + c] = __ldg(x + (p0 + p) * d + c);
+            Xs[p * XST + bwd_swz(c)] = __ldg(x + (p0 + p) * d + c);
         }
         for (int e = tid; e < GC * TPB; e += C::THREADS) {
             const int kc = e / TPB, p = e % TPB;
@@ -440,13 +449,15 @@ __global__ void __launch_bounds__(Bwd<DP>::THREADS) __maxnreg__(DP == 64 ? 112 :
         }
         __syncthreads();
         if (!active) continue;
+        // halves of the chunks in swizzled order (see bwd_swz)
         const float* xa = Xs + 8 * a;
         const float* xb = Xs + 8 * b;
+        const int ha = ((a >> 2) & 1) << 2, hb = ((b >> 2) & 1) << 2;
         if (diag) {
 #pragma unroll 2
             for (int p = 0; p < TPB; ++p) {
-                const float4 a0 = *reinterpret_cast<const float4*>(xa + p * XST);
-                const float4 a1 = *reinterpret_cast<const float4*>(xa + p * XST + 4);
+                const float4 a0 = *reinterpret_cast<const float4*>(xa + p * XST + ha);
+                const float4 a1 = *reinterpret_cast<const float4*>(xa + p * XST + (4 ^ ha));
                 const float rr = rs[p * GC + kk];
                 const float xv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                 float ya[8];
@@ -463,13 +474,13 @@ __global__ void __launch_bounds__(Bwd<DP>::THREADS) __maxnreg__(DP == 64 ? 112 :
         } else {
 #pragma unroll 1
             for (int p = 0; p < TPB; ++p) {
-                const float4 b0 = *reinterpret_cast<const float4*>(xb + p * XST);
-                const float4 b1 = *reinterpret_cast<const float4*>(xb + p * XST + 4);
+                const float4 b0 = *reinterpret_cast<const float4*>(xb + p * XST + hb);
+                const float4 b1 = *reinterpret_cast<const float4*>(xb + p * XST + (4 ^ hb));
                 const float rr = rs[p * GC + kk];
                 const float yv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float4 av = *reinterpret_cast<const float4*>(xa + p * XST + 4 * h);
+                    const float4 av = *reinterpret_cast<const float4*>(xa + p * XST + ((4 * h) ^ ha));
                     const float xv[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {

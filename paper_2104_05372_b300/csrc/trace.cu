@@ -76,20 +76,20 @@ extern "C" int gpa_trace_summary(char* buf, size_t len) {
                 break;
             }
         if (!found) agg.push_back({r.name, 1, (double)ms});
-        g_pool.push_back(r.a);
-        g_pool.push_back(r.b);
     }
-    g_recs.clear();
     std::string out;
     char line[256];
     for (const Agg& a : agg) {
         snprintf(line, sizeof line, "%s %ld %.6f\n", a.name.c_str(), a.count, a.ms);
         out += line;
     }
-    if (buf && len > 0) {
-        const size_t n = out.size() < len - 1 ? out.size() : len - 1;
-        memcpy(buf, out.data(), n);
-        buf[n] = '\0';
+    if (!buf || len <= out.size()) return (int)out.size();  // size query: keep the records
+    memcpy(buf, out.data(), out.size());
+    buf[out.size()] = '\0';
+    for (const Rec& r : g_recs) {
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
     }
+    g_recs.clear();
     return (int)out.size();
 }

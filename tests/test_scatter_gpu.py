@@ -21,8 +21,9 @@ def _run(idx, vals, nb, strat):
     idx_d = dev(idx)
     vals_d = dev(vals)
     acc = torch.zeros((nb,) + vals.shape[1:], dtype=vals_d.dtype, device="cuda")
-    plan = gpa.gpa_index_plan_build(idx_d, nb) if strat == "sort" else None
     st = status()
+    # with SORT, invalid indices are reported where the plan is built
+    plan = gpa.gpa_index_plan_build(idx_d, nb, status=st) if strat == "sort" else None
     gpa.accum_scatter_add(idx_d, vals_d, acc, strat=strat, plan=plan, status=st)
     torch.cuda.synchronize()
     return host(acc), int(st.item())
