@@ -125,27 +125,34 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_record(kernel: str):
-    """(bytes per launch, note) from the committed ncu summary, if it still
-    matches the kernel source; else (None, why)."""
+KERNEL_SOURCES = {"gmm": ("gmm.cu", "gmm_internal.cuh", "common.cuh"),
+                  "reproj": ("reproj.cu", "accum.cuh", "plan_internal.cuh", "common.cuh")}
+
+
+def source_digest(kernel: str) -> str:
+    """sha256 (16 hex) of the source files that define a kernel family."""
     import hashlib
+    src = os.path.join(ROOT, "paper_2104_05372_b300", "csrc")
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel.split("_")[0]]:
+        h.update(open(os.path.join(src, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel: str):
+    """(DRAM bytes per launch, note) from the committed ncu summary, if it still
+    matches the kernel's source; else (None, why)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None, "no ncu capture committed"
-    src = os.path.join(ROOT, "paper_2104_05372_b300", "csrc")
-    h = hashlib.sha256()
-    for name in sorted(os.listdir(src)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(src, name), "rb").read())
-    digest = h.hexdigest()[:16]
     for line in open(p):
         if line.startswith("#") or not line.strip():
             continue
         parts = line.split()
         if parts[0] == kernel:
-            if parts[1] != digest:
+            if parts[1] != source_digest(kernel):
                 return None, "kernel source changed since the ncu capture"
-            return float(parts[2]), "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
+            return float(parts[2]), " ".join(parts[3:]) or "ncu dram bytes read + write per launch"
     return None, "kernel not in the ncu summary"
 
 
