@@ -194,6 +194,28 @@ GPA_API int reproj_residual_vjp(const float* cams, const float* pts, const int32
                         const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
                         gpa_stream_t stream);
 
+/*
+ * Same result as reproj_vjp, for callers that cannot give the library a
+ * workspace: code whose device memory is owned by another allocator (a host
+ * framework's caching pool, a plugin or extension host) that forbids or cannot
+ * afford a cudaMalloc on its call path, or code whose device-memory budget is
+ * fixed at start-up. The paper has no counterpart; it is an interface choice.
+ * The only scratch, the expanded cameras, lives in a fixed array in device
+ * memory owned by the library (GPA_NOALLOC_MAX_CAMS cameras, 2.25 MiB on every
+ * GPU that loads the library, held until the process exits); the call itself
+ * allocates nothing. More cameras than that return GPA_ERR_WORKSPACE and
+ * enqueue nothing. The first call on a device looks up the array's device
+ * address for that device (with it current); make that first call before any
+ * stream capture. Every call shares the array and it keeps the last call's
+ * contents (each call rewrites the records it reads): calls that overlap on the
+ * GPU, on any streams, race. Arguments, strategies and Accum (+=) semantics
+ * are those of reproj_vjp.
+ */
+#define GPA_NOALLOC_MAX_CAMS 16384
+GPA_API int reproj_vjp_noalloc(const float* cams, const float* pts, const int32_t* obs, const float* w,
+                               int32_t n_cams, int32_t n_pts, int64_t n_obs, float* d_cams, float* d_pts,
+                               int32_t strat, const void* plan, int32_t* dev_status, gpa_stream_t stream);
+
 /* ========================================================================= */
 /* Index preparation and the generic Accum scatter                           */
 /* ========================================================================= */

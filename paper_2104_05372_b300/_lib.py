@@ -47,6 +47,7 @@ _SIGS = {
     "reproj_residual": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
     "reproj_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "reproj_residual_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _F, _P, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
+    "reproj_vjp_noalloc": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _P], _I32),
     "gpa_plan_bytes": ([_I64, _I32], _SZ),
     "gpa_plan_workspace_bytes": ([_I64, _I32], _SZ),
     "gpa_obs_plan_build": ([_P, _I64, _I32, _I32, _P, _SZ, _P, _SZ, _P, _P], _I32),
@@ -251,6 +252,23 @@ def reproj_vjp(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=No
     rc = load().reproj_vjp(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(w), nc, npt, no, _ptr(d_cams), _ptr(d_pts), st,
                            _ptr(plan), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "reproj_vjp")
+    return d_cams, d_pts
+
+
+def reproj_vjp_noalloc(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=None, status=None,
+                       stream=None):
+    """reproj_vjp without a workspace: the camera scratch is the library's own
+    fixed device array (at most GPA_NOALLOC_MAX_CAMS = 16384 cameras)."""
+    nc, npt, no = _reproj_params(cams, pts, obs)
+    _check(w, torch.float32, "w", (no, 2))
+    d_cams = torch.zeros(nc, 11, dtype=torch.float32, device=cams.device) if d_cams is None else d_cams
+    d_pts = torch.zeros(npt, 3, dtype=torch.float32, device=cams.device) if d_pts is None else d_pts
+    _check(d_cams, torch.float32, "d_cams", (nc, 11))
+    _check(d_pts, torch.float32, "d_pts", (npt, 3))
+    st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
+    rc = load().reproj_vjp_noalloc(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(w), nc, npt, no, _ptr(d_cams), _ptr(d_pts),
+                                   st, _ptr(plan), _ptr(status), _stream(stream))
+    _ok(rc, "reproj_vjp_noalloc")
     return d_cams, d_pts
 
 

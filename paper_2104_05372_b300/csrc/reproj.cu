@@ -436,3 +436,87 @@ extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const in
     return dispatch_vjp<true>(strat, rec, pts, obs, nullptr, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams,
                               d_pts, res, dev_status, s);
 }
+
+// ---------------------------------------------------------------------------
+// reproj_vjp_noalloc: reproj_vjp whose only scratch (the expanded cameras) lives
+// in a fixed array in device memory that the library owns, for callers that
+// cannot hand the library a workspace.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace gpa {
+// Largest camera count the built-in scratch holds (36 floats per camera,
+// 2.25 MiB per GPU that loads the library, kept until the process exits).
+constexpr int kNoAllocMaxCams = 16384;
+static __device__ __align__(256) float g_cam_scratch[kNoAllocMaxCams * kCamRec];
+
+constexpr int kNoAllocMaxDevices = 256;
+static float* g_cam_scratch_addr[kNoAllocMaxDevices];  // device address, per device
+static std::mutex g_cam_scratch_mu;
+
+// Device address of g_cam_scratch on the current device. In host code the
+// array's name only stands in for the symbol, so its address is looked up once
+// per device, with that device current.
+static int cam_scratch_address(float** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GPA_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GPA_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_cam_scratch_mu);
+    if (!g_cam_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_cam_scratch) != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            return GPA_ERR_CUDA;
+        }
+        g_cam_scratch_addr[dev] = static_cast<float*>(p);
+    }
+    *out = g_cam_scratch_addr[dev];
+    return GPA_OK;
+}
+}  // namespace gpa
+
+extern "C" int reproj_vjp_noalloc(const float* cams, const float* pts, const int32_t* obs, const float* w,
+                                  int32_t n_cams, int32_t n_pts, int64_t n_obs, float* d_cams, float* d_pts,
+                                  int32_t strat, const void* plan, int32_t* dev_status, gpa_stream_t stream) {
+    if (!cams || !pts || !obs || !w || !d_cams || !d_pts) return GPA_ERR_ARG;
+    if (n_cams < 1 || n_pts < 1 || n_obs < 1 || n_obs > INT32_MAX) return GPA_ERR_ARG;
+    if (n_cams > kNoAllocMaxCams) return GPA_ERR_WORKSPACE;  // more cameras than the built-in scratch holds
+    if (!al(obs, 8) || !al(w, 8) || !al(cams, 4) || !al(pts, 4)) return GPA_ERR_ALIGN;
+    strat = resolve_strat(strat, plan);
+    if (strat < GPA_SCATTER_ATOMIC || strat > GPA_SCATTER_SORT) return GPA_ERR_ARG;
+    PlanView pv{};
+    if (strat == GPA_SCATTER_SORT) {
+        if (!plan) return GPA_ERR_ARG;
+        pv = plan_view(plan, n_obs, n_cams);
+    }
+    float* rec = nullptr;
+    int rc = cam_scratch_address(&rec);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // every record the VJP reads is rewritten here first: nothing needs clearing
+    cam_expand_kernel<<<(n_cams + 127) / 128, 128, 0, s>>>(cams, n_cams, rec);
+    GPA_LAUNCH_CHECK();
+    const unsigned grid = obs_grid(n_obs);
+    switch (strat) {
+        case GPA_SCATTER_ATOMIC:
+            reproj_vjp_kernel<GPA_SCATTER_ATOMIC, false><<<grid, 256, 0, s>>>(
+                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, pv.perm,
+                pv.key_sorted, pv.aux_sorted, d_cams, d_pts, nullptr, dev_status);
+            break;
+        case GPA_SCATTER_WARPAGG:
+            reproj_vjp_kernel<GPA_SCATTER_WARPAGG, false><<<grid, 256, 0, s>>>(
+                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, pv.perm,
+                pv.key_sorted, pv.aux_sorted, d_cams, d_pts, nullptr, dev_status);
+            break;
+        default:
+            reproj_vjp_kernel<GPA_SCATTER_SORT, false><<<grid, 256, 0, s>>>(
+                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, pv.perm,
+                pv.key_sorted, pv.aux_sorted, d_cams, d_pts, nullptr, dev_status);
+            break;
+    }
+    GPA_LAUNCH_CHECK();
+    return GPA_OK;
+}
