@@ -73,6 +73,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_
     }
 }
 
+// Warp-uniform variant: every lane polls, the warp leaves together (all lanes
+// see the phase complete, or all give up after kWaitLimitNs by lane 0's clock).
+// Use it wherever the warp runs .sync.aligned instructions or __syncwarp next.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int32_t* status) {
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        int late = (globaltimer_ns() - t0 > kWaitLimitNs) ? 1 : 0;
+        late = __shfl_sync(0xffffffffu, late, 0);
+        if (late) {
+            if ((threadIdx.x & 31) == 0) report(status, GPA_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
 // 1-D bulk copy global -> shared through the TMA engine; completion is
 // signalled on `bar` as transaction bytes. dst, src 16-byte aligned, bytes a
 // multiple of 16.

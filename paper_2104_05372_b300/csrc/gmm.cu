@@ -518,7 +518,9 @@ __global__ void __launch_bounds__(256) gmm_finalize_kernel(
     const float* __restrict__ l, int d, int k, int64_t n, double gamma, int m, double seed,
     const float* __restrict__ partS, const float* __restrict__ partM, int nchunks,
     const double* __restrict__ scal, float* __restrict__ d_alpha, float* __restrict__ d_mu,
-    float* __restrict__ d_q, float* __restrict__ d_l) {
+    float* __restrict__ d_q, float* __restrict__ d_l, int centered) {
+    // centered: the partials hold sum r (x - mu)(x - mu)^T and sum r (x - mu)
+    // (tensor-core path) instead of the raw moments S and m.
     constexpr int NBLK = Bwd<DP>::NBLK;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double* Sd = reinterpret_cast<double*>(smem_raw);  // [NBLK*64]
@@ -558,7 +560,7 @@ __global__ void __launch_bounds__(256) gmm_finalize_kernel(
         if (a < d) {
             const int A = a >> 3, B = b >> 3;
             const double S = Sd[(A * (A + 1) / 2 + B) * 64 + (a & 7) * 8 + (b & 7)];
-            c = S - mud[a] * md[b] - md[a] * mud[b] + R * mud[a] * mud[b];
+            c = centered ? S : S - mud[a] * md[b] - md[a] * mud[b] + R * mud[a] * mud[b];
         }
         Cf[a * DP + b] = (float)c;
         Cf[b * DP + a] = (float)c;
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(256) gmm_finalize_kernel(
     for (int r = tid; r < DP; r += 256) {
         double v = 0.0;
         if (r < d)
-            for (int j = 0; j <= r; ++j) v += (double)Qf[r * DP + j] * (md[j] - R * mud[j]);
+            for (int j = 0; j <= r; ++j) v += (double)Qf[r * DP + j] * (centered ? md[j] : md[j] - R * mud[j]);
         vd[r] = v;
     }
     __syncthreads();
@@ -725,7 +727,8 @@ static int launch_bwd(const GmmArgs& A, const GmmLayout& L, char* ws, const floa
 }
 
 template <int DP>
-static int launch_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, cudaStream_t s) {
+static int launch_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, cudaStream_t s,
+                           int centered = 0) {
     constexpr int NBLK = Bwd<DP>::NBLK;
     const size_t smem = sizeof(double) * (NBLK * 64 + 3 * DP + 1) + sizeof(float) * 2 * DP * DP + 64;
     auto kern = gmm_finalize_kernel<DP>;
@@ -733,7 +736,8 @@ static int launch_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int n
     GPA_LAUNCH("gmm_finalize", s,
                kern<<<A.k, 256, smem, s>>>(A.alpha, A.mu, A.q, A.l, A.d, A.k, A.n, A.gamma, A.m, A.seed,
                                            (const float*)(ws + L.off_bS), (const float*)(ws + L.off_bM), nchunks,
-                                           (const double*)(ws + L.off_scal), A.d_alpha, A.d_mu, A.d_q, A.d_l));
+                                           (const double*)(ws + L.off_scal), A.d_alpha, A.d_mu, A.d_q, A.d_l,
+                                           centered));
     return GPA_OK;
 }
 
@@ -793,6 +797,39 @@ static int vjp_impl(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t
     if (A.out) return launch_objective(A, L, ws, s);
     return GPA_OK;
 }
+
+// Stage launchers shared with the tensor-core path (dispatch on L.dp).
+int gmm_run_prep(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s) {
+    switch (L.dp) {
+        case 16: return launch_prep<16>(A, L, ws, s);
+        case 32: return launch_prep<32>(A, L, ws, s);
+        case 64: return launch_prep<64>(A, L, ws, s);
+        case 128: return launch_prep<128>(A, L, ws, s);
+    }
+    return GPA_ERR_UNSUPPORTED;
+}
+
+int gmm_run_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, int centered, cudaStream_t s) {
+    switch (L.dp) {
+        case 16: return launch_finalize<16>(A, L, ws, nchunks, s, centered);
+        case 32: return launch_finalize<32>(A, L, ws, nchunks, s, centered);
+        case 64: return launch_finalize<64>(A, L, ws, nchunks, s, centered);
+        case 128: return launch_finalize<128>(A, L, ws, nchunks, s, centered);
+    }
+    return GPA_ERR_UNSUPPORTED;
+}
+
+int gmm_run_objective(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s) {
+    return launch_objective(A, L, ws, s);
+}
+
+int gmm_run_lse_sum(const float* lse, int64_t n, const GmmLayout& L, char* ws, cudaStream_t s) {
+    GPA_LAUNCH("gmm_lse_sum",
+               s, gmm_lse_sum_kernel<<<(unsigned)L.ntiles, 128, 0, s>>>(lse, n, (double*)(ws + L.off_fwd)));
+    return GPA_OK;
+}
+
+int gmm_bwd_partial_entries(int dp) { return nblk_of(dp) * 64; }
 
 int gmm_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s) {
     switch (L.dp) {
@@ -873,7 +910,7 @@ extern "C" int gmm_vjp(const float* x, const float* alpha, const float* mu, cons
     if (((uintptr_t)ws) & 255) return GPA_ERR_ALIGN;
     GmmLayout L = gmm_layout(n, d, k, 0);
     if (ws_bytes < L.total) return GPA_ERR_WORKSPACE;
-    if (!logjoint_in) {
+    if (!logjoint_in && prec == GPA_PREC_FP32) {  // the tensor-core path sizes its own chunks
         const int64_t P = gmm_lj_points_for(ws_bytes, L, n, k);
         if (P < 128) return GPA_ERR_WORKSPACE;
         L = gmm_layout(n, d, k, P);

@@ -50,6 +50,13 @@ int64_t gmm_lj_points_for(size_t ws_bytes, const GmmLayout& fixed, int64_t n, in
 int gmm_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s);
 int gmm_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s);
 
+// Stages shared by both paths.
+int gmm_run_prep(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s);
+int gmm_run_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, int centered, cudaStream_t s);
+int gmm_run_objective(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s);
+int gmm_run_lse_sum(const float* lse, int64_t n, const GmmLayout& L, char* ws, cudaStream_t s);
+int gmm_bwd_partial_entries(int dp);  // floats of partial S per (chunk, component)
+
 // Tensor-core (tcgen05, BF16 operands, FP32 accumulate) path.
 bool gmm_tc_supported(int d);
 size_t gmm_tc_extra_bytes(int64_t n, int d, int k);

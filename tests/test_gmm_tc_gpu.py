@@ -1,0 +1,93 @@
+"""GPU parity of the tensor-core GMM path (GPA_PREC_BF16_TC: BF16 operands,
+FP32 accumulation in tensor memory) against the FP64 oracle.
+
+Stated bound for BF16-contraction results: relative 3e-3 (objective; per-point
+statistics; gradients normwise per parameter block). The measured errors are
+printed per output (pytest -s shows them).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import TOL_BF16, gmm_dev, host, rel_norm, status
+
+pytestmark = pytest.mark.gpu
+PREC = 1  # GPA_PREC_BF16_TC
+
+
+def _run(g, stored=True, logjoint_points=0):
+    import paper_2104_05372_b300 as gpa
+    x, a, mu, q, l = gmm_dev(g)
+    lse = torch.empty(g.n, device="cuda")
+    lj = torch.empty(g.k, g.n, device="cuda")
+    st = status()
+    f = gpa.gmm_objective(x, a, mu, q, l, g.gamma, g.m, PREC, lse_out=lse, logjoint_out=lj, status=st)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    grads = gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, PREC, logjoint_in=lj if stored else None,
+                        lse_in=lse if stored else None, out=out, logjoint_points=logjoint_points, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    return float(f.item()), float(out.item()), host(lse), host(lj), [host(t) for t in grads]
+
+
+def _errors(g, f, f2, lse, grads, f_ref, lse_ref, gref):
+    e = {"objective": abs(f - f_ref) / abs(f_ref), "objective_vjp": abs(f2 - f_ref) / abs(f_ref),
+         "lse_max": float(np.max(np.abs(lse - lse_ref) / np.abs(lse_ref)))}
+    for name, gb, rb in zip(("alpha", "mu", "q", "l"), grads, gref):
+        e["grad_" + name] = rel_norm(gb, rb)
+    print(f"\nBF16 tensor-core path N={g.n} D={g.d} K={g.k}: " +
+          ", ".join(f"{k}={v:.2e}" for k, v in e.items()))
+    return e
+
+
+@pytest.mark.parametrize("n,d,k", [(300, 65, 3), (1000, 100, 7), (5000, 128, 33), ((1 << 13) + 37, 128, 256)])
+def test_tc_path_matches_oracle(n, d, k):
+    g = synth.gmm_inputs(n, d, k, seed=n + d + k)
+    f_ref, lse_ref = oracle.gmm_objective(g, want_lse=True)
+    _, *gref = oracle.gmm_grad(g)
+    f, f2, lse, lj, grads = _run(g)
+    e = _errors(g, f, f2, lse, grads, f_ref, lse_ref, gref)
+    for name, v in e.items():
+        assert v <= TOL_BF16, (name, v)
+
+
+def test_tc_recompute_mode_matches_stored_mode():
+    g = synth.gmm_inputs(3000, 128, 20, seed=3)
+    _, *gref = oracle.gmm_grad(g)
+    _, _, _, _, g_st = _run(g, stored=True)
+    _, f2, _, _, g_rc = _run(g, stored=False, logjoint_points=256)
+    for a, b, r in zip(g_st, g_rc, gref):
+        assert rel_norm(b, r) <= TOL_BF16
+        assert rel_norm(a, b) <= 1e-5
+
+
+def test_tc_rejects_small_dimensions():
+    import paper_2104_05372_b300 as gpa
+    g = synth.gmm_inputs(100, 32, 3, seed=1)
+    x, a, mu, q, l = gmm_dev(g)
+    with pytest.raises(gpa.GpaError) as e:
+        gpa.gmm_objective(x, a, mu, q, l, prec=PREC)
+    assert e.value.code == 6  # GPA_ERR_UNSUPPORTED
+
+
+@pytest.mark.slow
+def test_tc_full_size_sampled_statistics():
+    """N=2^20, D=128, K=256: sampled per-point statistics vs the oracle, and the
+    gradient's invariance under a permutation of the points."""
+    import paper_2104_05372_b300 as gpa
+    g = synth.gmm_inputs(1 << 20, 128, 256, seed=0)
+    x, a, mu, q, l = gmm_dev(g)
+    lse = torch.empty(g.n, device="cuda")
+    gpa.gmm_objective(x, a, mu, q, l, prec=PREC, lse_out=lse)
+    idx = np.random.default_rng(0).choice(g.n, 2048, replace=False)
+    _, lse_ref = oracle.gmm_logjoint_at(g, idx)
+    err = np.max(np.abs(host(lse)[idx] - lse_ref) / np.abs(lse_ref))
+    print(f"\nBF16 full size: max relative lse error over 2048 sampled points {err:.2e}")
+    assert err <= TOL_BF16
+    full = [host(t) for t in gpa.gmm_vjp(x, a, mu, q, l, prec=PREC)]
+    perm = torch.from_numpy(np.random.default_rng(1).permutation(g.n)).cuda()
+    pm = [host(t) for t in gpa.gmm_vjp(x[perm].contiguous(), a, mu, q, l, prec=PREC)]
+    for u, v in zip(full, pm):
+        assert rel_norm(v, u) <= 1e-4
