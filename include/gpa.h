@@ -144,6 +144,49 @@ GPA_API int gmm_vjp(const float* x, const float* alpha, const float* mu, const f
             float* d_mu, float* d_q, float* d_l, double* out, void* ws, size_t ws_bytes,
             int32_t* dev_status, gpa_stream_t stream);
 
+/* ------------------------------------------------------------------------- */
+/* Batched GMM: many instances of uneven N, D, K in persistent kernels        */
+/* ------------------------------------------------------------------------- */
+/* One mixture instance (all pointers device memory; layouts as for gmm_vjp). */
+typedef struct {
+    const float *x, *alpha, *mu, *q, *l;
+    float *d_alpha, *d_mu, *d_q, *d_l; /* += seed * gradient */
+    double* out;                       /* objective f, nullable */
+    int64_t n;
+    int32_t d, k;
+    double gamma;
+    int32_t m;
+    double seed;
+} gpa_gmm_instance;
+
+/* Workspace for gmm_batched_prepare / gmm_batched_vjp over these instances
+ * (host array). chunk_points: points per backward work item (>= 64; larger
+ * values mean fewer partial sums, smaller values more parallelism). 0 on bad
+ * arguments. */
+GPA_API size_t gpa_gmm_batched_workspace_bytes(const gpa_gmm_instance* inst, int32_t n_inst,
+                                               int64_t chunk_points);
+
+/* Build the work lists (one item per (instance, component) for parameter
+ * expansion and finalize, per (instance, 128-point tile) for the forward pass,
+ * per (instance, component group, point chunk) for the backward Accum; forward
+ * and backward lists in longest-first order) and copy them with the instance
+ * descriptors into ws. Synchronises `stream` before returning. Call it once per
+ * set of instances (pointers, shapes, seeds), before gmm_batched_vjp. */
+GPA_API int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
+                                void* ws, size_t ws_bytes, gpa_stream_t stream);
+
+/* Objective and seed * gradient of every prepared instance: per padded
+ * dimension class (D <= 16, 32, 64, 128) four persistent kernels whose CTAs
+ * pull work items from an atomic counter (flattened loops, Sec. 6.1.1), plus
+ * two memsets. Enqueues device work only, so the call can be captured in a
+ * CUDA graph and replayed while the inputs live at the same addresses.
+ * ctas_per_sm caps resident CTAs per SM (0 = as many as fit). `inst`,
+ * n_inst, chunk_points must equal the gmm_batched_prepare arguments. FP32
+ * CUDA-core arithmetic, deterministic like gmm_vjp. */
+GPA_API int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
+                            int32_t ctas_per_sm, void* ws, size_t ws_bytes, int32_t* dev_status,
+                            gpa_stream_t stream);
+
 /* ========================================================================= */
 /* Camera reprojection (bundle adjustment residual)                          */
 /* ========================================================================= */

@@ -53,6 +53,9 @@ _SIGS = {
     "gpa_obs_plan_build": ([_P, _I64, _I32, _I32, _P, _SZ, _P, _SZ, _P, _P], _I32),
     "gpa_index_plan_build": ([_P, _I64, _I32, _P, _SZ, _P, _SZ, _P, _P], _I32),
     "accum_scatter_add": ([_P, _P, _I64, _I32, _I32, _P, _I32, _I32, _P, _P, _P], _I32),
+    "gpa_gmm_batched_workspace_bytes": ([_P, _I32, _I64], _SZ),
+    "gmm_batched_prepare": ([_P, _I32, _I64, _P, _SZ, _P], _I32),
+    "gmm_batched_vjp": ([_P, _I32, _I64, _I32, _P, _SZ, _P, _P], _I32),
     "gpa_trace_enable": ([_I32], None),
     "gpa_trace_summary": ([C.c_char_p, _SZ], _I32),
 }
@@ -205,6 +208,67 @@ def gmm_vjp(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, logjoint_in=None
                         _ptr(d_l), _ptr(out), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "gmm_vjp")
     return d_alpha, d_mu, d_q, d_l
+
+
+class GmmInstance(C.Structure):
+    """C layout of gpa_gmm_instance (include/gpa.h)."""
+    _fields_ = [("x", C.c_void_p), ("alpha", C.c_void_p), ("mu", C.c_void_p), ("q", C.c_void_p),
+                ("l", C.c_void_p), ("d_alpha", C.c_void_p), ("d_mu", C.c_void_p), ("d_q", C.c_void_p),
+                ("d_l", C.c_void_p), ("out", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("k", C.c_int32),
+                ("gamma", C.c_double), ("m", C.c_int32), ("seed", C.c_double)]
+
+
+class GmmBatch:
+    """Device tensors and descriptors of a batch of GMM instances.
+
+    instances: list of dicts with keys x, alpha, mu, q, l (device float32
+    tensors) and optionally gamma, m, seed. Gradient buffers (zeros) and a
+    float64 objective per instance are allocated here.
+    """
+
+    def __init__(self, instances, chunk_points=4096):
+        self.chunk_points = int(chunk_points)
+        self.tensors = []
+        arr = (GmmInstance * len(instances))()
+        for i, inst in enumerate(instances):
+            n, d, k = _gmm_params(inst["x"], inst["alpha"], inst["mu"], inst["q"], inst["l"])
+            dev = inst["x"].device
+            t = d * (d - 1) // 2
+            g = [torch.zeros(k, device=dev), torch.zeros(k, d, device=dev), torch.zeros(k, d, device=dev),
+                 torch.zeros(k, t, device=dev)]
+            out = torch.zeros(1, dtype=torch.float64, device=dev)
+            self.tensors.append((inst, g, out))
+            arr[i] = GmmInstance(inst["x"].data_ptr(), inst["alpha"].data_ptr(), inst["mu"].data_ptr(),
+                                 inst["q"].data_ptr(), inst["l"].data_ptr() if t > 0 else 0,
+                                 g[0].data_ptr(), g[1].data_ptr(), g[2].data_ptr(), g[3].data_ptr() if t > 0 else 0,
+                                 out.data_ptr(), n, d, k, float(inst.get("gamma", 1.0)), int(inst.get("m", 0)),
+                                 float(inst.get("seed", 1.0)))
+        self.desc = arr
+        self.n_inst = len(instances)
+        nb = int(load().gpa_gmm_batched_workspace_bytes(C.byref(arr), self.n_inst, self.chunk_points))
+        if nb == 0:
+            raise GpaError(ERR_ARG, "gpa_gmm_batched_workspace_bytes")
+        self.ws = workspace(nb, instances[0]["x"].device)
+
+    def prepare(self, stream=None):
+        rc = load().gmm_batched_prepare(C.byref(self.desc), self.n_inst, self.chunk_points, _ptr(self.ws),
+                                        self.ws.numel(), _stream(stream))
+        _ok(rc, "gmm_batched_prepare")
+
+    def run(self, ctas_per_sm=0, status=None, stream=None):
+        rc = load().gmm_batched_vjp(C.byref(self.desc), self.n_inst, self.chunk_points, int(ctas_per_sm),
+                                    _ptr(self.ws), self.ws.numel(), _ptr(status), _stream(stream))
+        _ok(rc, "gmm_batched_vjp")
+
+    def zero_grads(self):
+        for _, g, out in self.tensors:
+            for t in g:
+                t.zero_()
+            out.zero_()
+
+    def results(self):
+        """[(objective, (d_alpha, d_mu, d_q, d_l))] per instance (device tensors)."""
+        return [(out, tuple(g)) for _, g, out in self.tensors]
 
 
 # ---------------------------------------------------------------------------

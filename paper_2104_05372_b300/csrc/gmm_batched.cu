@@ -1,0 +1,357 @@
+// Batched GMM objective + gradient (A8): many mixture instances of uneven N, D
+// and K in a handful of persistent kernels, meant to be captured once in a CUDA
+// graph and replayed.
+//
+// The host turns the instances into work lists, one per (padded dimension,
+// phase): parameter expansion (instance, component), forward (instance,
+// 128-point tile), backward Accum (instance, component group, point chunk),
+// finalize (instance, component, plus one objective item per instance).
+// Forward and backward items are sorted by estimated cost, largest first
+// (longest-processing-time order), so that the long items start early and the
+// short ones fill the tail. Persistent CTAs pull item indices from an atomic
+// counter and run the same per-block bodies as the per-call kernels
+// (gmm_kernels.cuh): flattening the nested loops over instances, tiles and
+// components into one parallel loop (Sec. 6.1.1).
+//
+// gmm_batched_prepare writes the descriptors and work lists into the workspace
+// (one host-to-device copy, then a stream synchronisation); gmm_batched_vjp only
+// enqueues memsets and kernels, so it can be captured in a graph.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "gmm_internal.cuh"
+#include "gmm_kernels.cuh"
+#include "trace.cuh"
+
+namespace gpa {
+namespace {
+
+struct BInst {
+    const float *x, *alpha, *mu, *q, *l;
+    float *d_alpha, *d_mu, *d_q, *d_l;
+    double* out;
+    float *rec, *bS, *bM, *lj, *lse;
+    double *scal, *lpk, *fwd;
+    int64_t n, tiles_per_chunk;
+    double gamma, seed;
+    int d, k, m, dp, nchunks, ntiles128;
+};
+
+struct BItem {
+    int inst, a, b, pad;
+};
+
+constexpr int kClasses = 4;  // padded dimension 16, 32, 64, 128
+constexpr int kPhases = 4;   // prep, forward, backward, finalize
+int class_of(int dp) { return dp == 16 ? 0 : dp == 32 ? 1 : dp == 64 ? 2 : 3; }
+int dp_of_class(int c) { return 16 << c; }
+
+size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int nblk(int dp) { return (dp / 8) * (dp / 8 + 1) / 2; }
+int gc_of(int dp) { return dp == 16 ? 32 : dp == 32 ? 16 : dp == 64 ? 8 : 2; }
+
+struct Plan {
+    std::vector<BInst> inst;
+    std::vector<BItem> items[kClasses][kPhases];
+    size_t off_desc, off_items[kClasses][kPhases], off_counters, off_partials, partial_bytes, off_regions, total;
+};
+
+// Deterministic plan: workspace offsets are relative (base = 0) until bound.
+bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, char* base, Plan& P) {
+    P.inst.resize(n_inst);
+    size_t off = 256;  // header
+    P.off_desc = off;
+    off = a256(off + sizeof(BInst) * (size_t)n_inst);
+    // item lists
+    for (int i = 0; i < n_inst; ++i) {
+        const gpa_gmm_instance& I = in[i];
+        if (I.n < 1 || I.d < 1 || I.d > 128 || I.k < 1 || I.k > 4096 || !(I.gamma > 0.0)) return false;
+        const int dp = gmm_dp(I.d), c = class_of(dp);
+        BInst& B = P.inst[i];
+        B.n = I.n;
+        B.d = I.d;
+        B.k = I.k;
+        B.m = I.m;
+        B.dp = dp;
+        B.gamma = I.gamma;
+        B.seed = I.seed;
+        B.ntiles128 = (int)((I.n + 127) / 128);
+        const int64_t ntiles64 = (I.n + 63) / 64;
+        int nch = (int)((I.n + chunk_points - 1) / chunk_points);
+        nch = std::max(1, std::min(nch, kGmmMaxChunks));
+        nch = (int)std::min<int64_t>(nch, ntiles64);
+        B.tiles_per_chunk = (ntiles64 + nch - 1) / nch;
+        B.nchunks = (int)((ntiles64 + B.tiles_per_chunk - 1) / B.tiles_per_chunk);
+        const int groups = (I.k + gc_of(dp) - 1) / gc_of(dp);
+        for (int kk = 0; kk < I.k; ++kk) P.items[c][0].push_back({i, kk, 0, 0});
+        for (int t = 0; t < B.ntiles128; ++t) P.items[c][1].push_back({i, t, 0, 0});
+        for (int g = 0; g < groups; ++g)
+            for (int ch = 0; ch < B.nchunks; ++ch) P.items[c][2].push_back({i, g, ch, 0});
+        for (int kk = 0; kk < I.k; ++kk) P.items[c][3].push_back({i, kk, 0, 0});
+        P.items[c][3].push_back({i, -1, 0, 0});  // objective
+    }
+    // longest-processing-time order for the forward and backward lists
+    for (int c = 0; c < kClasses; ++c) {
+        auto cost_f = [&](const BItem& w) { return (double)P.inst[w.inst].k; };
+        auto cost_b = [&](const BItem& w) {
+            const BInst& B = P.inst[w.inst];
+            const int64_t ntiles64 = (B.n + 63) / 64;
+            const int64_t t0 = (int64_t)w.b * B.tiles_per_chunk;
+            return (double)std::max<int64_t>(0, std::min<int64_t>(ntiles64, t0 + B.tiles_per_chunk) - t0);
+        };
+        std::stable_sort(P.items[c][1].begin(), P.items[c][1].end(),
+                         [&](const BItem& u, const BItem& v) { return cost_f(u) > cost_f(v); });
+        std::stable_sort(P.items[c][2].begin(), P.items[c][2].end(),
+                         [&](const BItem& u, const BItem& v) { return cost_b(u) > cost_b(v); });
+    }
+    for (int c = 0; c < kClasses; ++c)
+        for (int ph = 0; ph < kPhases; ++ph) {
+            P.off_items[c][ph] = off;
+            off = a256(off + sizeof(BItem) * P.items[c][ph].size());
+        }
+    P.off_counters = off;
+    off = a256(off + sizeof(int) * kClasses * kPhases);
+    // Accum partials of every instance, contiguous so that one memset clears them
+    P.off_partials = off;
+    for (int i = 0; i < n_inst; ++i) {
+        BInst& B = P.inst[i];
+        B.bS = (float*)(base + off);
+        off = a256(off + sizeof(float) * (size_t)B.nchunks * B.k * nblk(B.dp) * 64);
+        B.bM = (float*)(base + off);
+        off = a256(off + sizeof(float) * (size_t)B.nchunks * B.k * (B.dp + 1));
+    }
+    P.partial_bytes = off - P.off_partials;
+    P.off_regions = off;
+    for (int i = 0; i < n_inst; ++i) {
+        BInst& B = P.inst[i];
+        const gpa_gmm_instance& I = in[i];
+        B.x = I.x; B.alpha = I.alpha; B.mu = I.mu; B.q = I.q; B.l = I.l;
+        B.d_alpha = I.d_alpha; B.d_mu = I.d_mu; B.d_q = I.d_q; B.d_l = I.d_l; B.out = I.out;
+        B.rec = (float*)(base + off);  off = a256(off + sizeof(float) * (size_t)B.k * (B.dp * B.dp + B.dp + 4));
+        B.scal = (double*)(base + off); off = a256(off + sizeof(double) * 8);
+        B.lpk = (double*)(base + off);  off = a256(off + sizeof(double) * (size_t)B.k);
+        B.fwd = (double*)(base + off);  off = a256(off + sizeof(double) * (size_t)B.ntiles128);
+        B.lse = (float*)(base + off);   off = a256(off + sizeof(float) * (size_t)B.n);
+        B.lj = (float*)(base + off);    off = a256(off + sizeof(float) * (size_t)B.n * B.k);
+    }
+    P.total = off;
+    return true;
+}
+
+// ---- persistent kernels -----------------------------------------------------------
+__device__ __forceinline__ int next_item(int* counter) {
+    __shared__ int s_item;
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    return it;
+}
+
+template <int DP>
+__global__ void __launch_bounds__(128) batched_prep_kernel(const BInst* __restrict__ inst,
+                                                           const BItem* __restrict__ items, int n_items,
+                                                           int* counter) {
+    for (;;) {
+        const int it = next_item(counter);
+        if (it >= n_items) break;
+        const BItem w = items[it];
+        const BInst& B = inst[w.inst];
+        gmm_prep_kernel_body<DP>(B.alpha, B.mu, B.q, B.l, B.d, B.k, B.gamma, B.m, B.rec, B.lpk, B.scal,
+                                 (unsigned)w.a);
+        __syncthreads();
+    }
+}
+
+template <int DP>
+__global__ void __launch_bounds__(256, (DP <= 64 ? 2 : 1))
+    batched_fwd_kernel(const BInst* __restrict__ inst, const BItem* __restrict__ items, int n_items, int* counter,
+                       int32_t* status) {
+    for (;;) {
+        const int it = next_item(counter);
+        if (it >= n_items) break;
+        const BItem w = items[it];
+        const BInst& B = inst[w.inst];
+        gmm_fwd_kernel_body<DP>(B.x, B.n, B.d, B.k, B.rec, B.lj, B.n, B.lse, B.fwd, 0, status, (unsigned)w.a);
+        __syncthreads();
+    }
+}
+
+template <int DP>
+__global__ void __launch_bounds__(Bwd<DP>::THREADS) __maxnreg__(DP == 64 ? 96 : 168)
+    batched_bwd_kernel(const BInst* __restrict__ inst, const BItem* __restrict__ items, int n_items,
+                       int* counter) {
+    for (;;) {
+        const int it = next_item(counter);
+        if (it >= n_items) break;
+        const BItem w = items[it];
+        const BInst& B = inst[w.inst];
+        gmm_bwd_kernel_body<DP>(B.x, B.n, B.d, B.k, B.lj, B.n, B.lse, (float)B.seed, B.tiles_per_chunk, B.bS, B.bM,
+                                (unsigned)w.a, (unsigned)w.b);
+        __syncthreads();
+    }
+}
+
+template <int DP>
+__global__ void __launch_bounds__(256) batched_fin_kernel(const BInst* __restrict__ inst,
+                                                          const BItem* __restrict__ items, int n_items,
+                                                          int* counter) {
+    for (;;) {
+        const int it = next_item(counter);
+        if (it >= n_items) break;
+        const BItem w = items[it];
+        const BInst& B = inst[w.inst];
+        if (w.a < 0) {
+            if (B.out) gmm_objective_finalize_kernel_body(B.fwd, B.ntiles128, B.lpk, B.k, B.scal, B.n, B.d, B.out, 0u);
+        } else {
+            gmm_finalize_kernel_body<DP>(B.alpha, B.mu, B.q, B.l, B.d, B.k, B.n, B.gamma, B.m, B.seed, B.bS, B.bM,
+                                         B.nchunks, B.scal, B.d_alpha, B.d_mu, B.d_q, B.d_l, 0, (unsigned)w.a);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- host -------------------------------------------------------------------------
+template <typename K>
+bool smem_attr(K kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return true;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
+
+int sms() {
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+template <typename K>
+unsigned persistent_grid(K kern, int threads, size_t smem, int n_items, int ctas_per_sm) {
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    occ = std::max(1, occ);
+    if (ctas_per_sm > 0) occ = std::min(occ, ctas_per_sm);
+    return (unsigned)std::max(1, std::min(n_items, sms() * occ));
+}
+
+template <int DP>
+int run_class(const Plan& P, char* ws, int c, int ctas_per_sm, int32_t* status, cudaStream_t s) {
+    const BInst* inst = (const BInst*)(ws + P.off_desc);
+    int* counters = (int*)(ws + P.off_counters);
+    const BItem* it[kPhases];
+    int n[kPhases];
+    for (int ph = 0; ph < kPhases; ++ph) {
+        it[ph] = (const BItem*)(ws + P.off_items[c][ph]);
+        n[ph] = (int)P.items[c][ph].size();
+    }
+    if (n[1] == 0) return GPA_OK;
+    {
+        auto k = batched_prep_kernel<DP>;
+        const unsigned g = persistent_grid(k, 128, 0, n[0], 0);
+        GPA_LAUNCH("gmm_batched_prep", s, k<<<g, 128, 0, s>>>(inst, it[0], n[0], counters + c * kPhases + 0));
+    }
+    {
+        auto k = batched_fwd_kernel<DP>;
+        if (!smem_attr(k, Fwd<DP>::SMEM)) return GPA_ERR_CUDA;
+        const unsigned g = persistent_grid(k, Fwd<DP>::THREADS, Fwd<DP>::SMEM, n[1], ctas_per_sm);
+        GPA_LAUNCH("gmm_batched_fwd", s,
+                   k<<<g, Fwd<DP>::THREADS, Fwd<DP>::SMEM, s>>>(inst, it[1], n[1], counters + c * kPhases + 1,
+                                                               status));
+    }
+    {
+        auto k = batched_bwd_kernel<DP>;
+        if (!smem_attr(k, Bwd<DP>::SMEM)) return GPA_ERR_CUDA;
+        const unsigned g = persistent_grid(k, Bwd<DP>::THREADS, Bwd<DP>::SMEM, n[2], ctas_per_sm);
+        GPA_LAUNCH("gmm_batched_bwd", s,
+                   k<<<g, Bwd<DP>::THREADS, Bwd<DP>::SMEM, s>>>(inst, it[2], n[2], counters + c * kPhases + 2));
+    }
+    {
+        constexpr int NB = (DP / 8) * (DP / 8 + 1) / 2;
+        const size_t smem = sizeof(double) * (NB * 64 + 3 * DP + 1) + sizeof(float) * 2 * DP * DP + 64;
+        auto k = batched_fin_kernel<DP>;
+        if (!smem_attr(k, smem)) return GPA_ERR_CUDA;
+        const unsigned g = persistent_grid(k, 256, smem, n[3], 0);
+        GPA_LAUNCH("gmm_batched_finalize", s,
+                   k<<<g, 256, smem, s>>>(inst, it[3], n[3], counters + c * kPhases + 3));
+    }
+    return GPA_OK;
+}
+
+int check_instances(const gpa_gmm_instance* in, int n_inst) {
+    if (!in || n_inst < 1 || n_inst > (1 << 20)) return GPA_ERR_ARG;
+    for (int i = 0; i < n_inst; ++i) {
+        const gpa_gmm_instance& I = in[i];
+        if (!I.x || !I.alpha || !I.mu || !I.q || (I.d > 1 && !I.l) || !I.d_alpha || !I.d_mu || !I.d_q ||
+            (I.d > 1 && !I.d_l))
+            return GPA_ERR_ARG;
+        if (I.n < 1 || I.n > INT32_MAX || I.d < 1 || I.d > 128 || I.k < 1 || I.k > 4096 || !(I.gamma > 0.0))
+            return GPA_ERR_ARG;
+    }
+    return GPA_OK;
+}
+
+}  // namespace
+}  // namespace gpa
+
+using namespace gpa;
+
+extern "C" size_t gpa_gmm_batched_workspace_bytes(const gpa_gmm_instance* inst, int32_t n_inst,
+                                                  int64_t chunk_points) {
+    if (check_instances(inst, n_inst) || chunk_points < 64) return 0;
+    Plan P;
+    if (!make_plan(inst, n_inst, chunk_points, nullptr, P)) return 0;
+    return P.total + 256;
+}
+
+extern "C" int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points, void* ws,
+                                   size_t ws_bytes, gpa_stream_t stream) {
+    int rc = check_instances(inst, n_inst);
+    if (rc) return rc;
+    if (!ws || chunk_points < 64) return GPA_ERR_ARG;
+    if (((uintptr_t)ws) & 255) return GPA_ERR_ALIGN;
+    Plan P;
+    if (!make_plan(inst, n_inst, chunk_points, (char*)ws, P)) return GPA_ERR_ARG;
+    if (ws_bytes < P.total) return GPA_ERR_WORKSPACE;
+    // host image of descriptors and work lists, copied in one transfer
+    std::vector<char> img(P.off_regions, 0);
+    memcpy(img.data() + P.off_desc, P.inst.data(), sizeof(BInst) * P.inst.size());
+    for (int c = 0; c < kClasses; ++c)
+        for (int ph = 0; ph < kPhases; ++ph)
+            if (!P.items[c][ph].empty())
+                memcpy(img.data() + P.off_items[c][ph], P.items[c][ph].data(),
+                       sizeof(BItem) * P.items[c][ph].size());
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(ws, img.data(), P.off_partials, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GPA_ERR_CUDA;
+    }
+    return GPA_OK;
+}
+
+extern "C" int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
+                               int32_t ctas_per_sm, void* ws, size_t ws_bytes, int32_t* dev_status,
+                               gpa_stream_t stream) {
+    int rc = check_instances(inst, n_inst);
+    if (rc) return rc;
+    if (!ws || chunk_points < 64 || ctas_per_sm < 0) return GPA_ERR_ARG;
+    if (((uintptr_t)ws) & 255) return GPA_ERR_ALIGN;
+    Plan P;
+    if (!make_plan(inst, n_inst, chunk_points, (char*)ws, P)) return GPA_ERR_ARG;
+    if (ws_bytes < P.total) return GPA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync((char*)ws + P.off_counters, 0, sizeof(int) * kClasses * kPhases, s) != cudaSuccess ||
+        cudaMemsetAsync((char*)ws + P.off_partials, 0, P.partial_bytes, s) != cudaSuccess)
+        return GPA_ERR_CUDA;
+    if ((rc = run_class<16>(P, (char*)ws, 0, ctas_per_sm, dev_status, s))) return rc;
+    if ((rc = run_class<32>(P, (char*)ws, 1, ctas_per_sm, dev_status, s))) return rc;
+    if ((rc = run_class<64>(P, (char*)ws, 2, ctas_per_sm, dev_status, s))) return rc;
+    if ((rc = run_class<128>(P, (char*)ws, 3, ctas_per_sm, dev_status, s))) return rc;
+    return GPA_OK;
+}

@@ -1,0 +1,113 @@
+"""GPU parity of the batched GMM path (persistent work-queue kernels) against
+the FP64 oracle, per instance, plus its CUDA-graph replay and the autotuner."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import TOL_GRAD_FP32, TOL_OBJ_FP32, host, rel_norm, status
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(1, 1, 1), (130, 3, 4), (1000, 8, 9), (3000, 16, 40), (777, 20, 5), (2500, 32, 17), (64, 64, 2),
+          (4100, 64, 33), (900, 100, 3), (129, 128, 7), (50, 5, 120), (2049, 12, 1)]
+
+
+def _instances(shapes, seed=0):
+    gs = [synth.gmm_inputs(n, d, k, seed=seed + 17 * i, gamma=1.0 + 0.1 * (i % 3), m=i % 2)
+          for i, (n, d, k) in enumerate(shapes)]
+    inst = [dict(x=torch.from_numpy(g.x).cuda(), alpha=torch.from_numpy(g.alpha).cuda(),
+                 mu=torch.from_numpy(g.mu).cuda(), q=torch.from_numpy(g.q).cuda(),
+                 l=torch.from_numpy(g.l).cuda(), gamma=g.gamma, m=g.m, seed=1.0 if i % 4 else -0.5)
+            for i, g in enumerate(gs)]
+    return gs, inst
+
+
+def _check(gs, inst, batch, which=None):
+    res = batch.results()
+    for i in (range(len(gs)) if which is None else which):
+        g = gs[i]
+        f_ref, *gref = oracle.gmm_grad(g, seed=inst[i]["seed"])
+        f_ref0 = oracle.gmm_objective(g)
+        out, grads = res[i]
+        assert abs(float(out.item()) - f_ref0) <= TOL_OBJ_FP32 * abs(f_ref0), (i, float(out.item()), f_ref0)
+        for name, gb, rb in zip(("alpha", "mu", "q", "l"), grads, gref):
+            if rb.size:
+                assert rel_norm(host(gb), rb) <= TOL_GRAD_FP32, (i, name)
+
+
+@pytest.mark.parametrize("chunk", [64, 1024])
+def test_batched_matches_oracle_per_instance(chunk):
+    from paper_2104_05372_b300._lib import GmmBatch
+    gs, inst = _instances(SHAPES)
+    b = GmmBatch(inst, chunk_points=chunk)
+    b.prepare()
+    st = status()
+    b.run(status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    _check(gs, inst, b)
+
+
+def test_batched_equals_per_instance_calls():
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300._lib import GmmBatch
+    gs, inst = _instances(SHAPES[:8], seed=5)
+    b = GmmBatch(inst, chunk_points=2048)
+    b.prepare()
+    b.run(ctas_per_sm=1)
+    for (out, grads), i in zip(b.results(), inst):
+        single = gpa.gmm_vjp(i["x"], i["alpha"], i["mu"], i["q"], i["l"], i["gamma"], i["m"], seed=i["seed"])
+        for u, v in zip(grads, single):
+            if u.numel():
+                assert rel_norm(host(u), host(v)) <= 1e-5
+
+
+def test_graph_capture_and_replay():
+    from paper_2104_05372_b300._lib import GmmBatch
+    gs, inst = _instances(SHAPES[:6], seed=9)
+    b = GmmBatch(inst, chunk_points=1024)
+    b.prepare()
+    b.run()  # warm-up outside the capture
+    torch.cuda.synchronize()
+    ref = [(float(o.item()), [host(t).copy() for t in g]) for o, g in b.results()]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.run()
+    for _ in range(2):
+        b.zero_grads()
+        graph.replay()
+    torch.cuda.synchronize()
+    for (o, g), (fo, fg) in zip(b.results(), ref):
+        assert float(o.item()) == fo
+        for u, v in zip(g, fg):
+            assert np.array_equal(host(u), v)
+
+
+def test_autotuner_picks_and_caches(tmp_path):
+    from paper_2104_05372_b300 import autotune
+    _, inst = _instances(SHAPES[:5], seed=3)
+    path = str(tmp_path / "tune.json")
+    r1 = autotune.tune_batched(inst, chunks=(256, 4096), ctas=(0,), reps=1, cache_path=path)
+    assert r1["chunk_points"] in (256, 4096) and len(r1["table"]) == 2
+    r2 = autotune.tune_batched(inst, chunks=(256, 4096), ctas=(0,), reps=1, cache_path=path)
+    assert r2 == r1
+
+
+@pytest.mark.slow
+def test_full_batched_workload_sampled_instances():
+    """512 instances with the batched workload's shape law; 12 sampled instances
+    compared with the oracle."""
+    from paper_2104_05372_b300._lib import GmmBatch
+    shapes = synth.batched_shapes(512, seed=0)
+    gs = synth.batched_inputs(shapes, seed=0)
+    inst = [dict(x=torch.from_numpy(g.x).cuda(), alpha=torch.from_numpy(g.alpha).cuda(),
+                 mu=torch.from_numpy(g.mu).cuda(), q=torch.from_numpy(g.q).cuda(),
+                 l=torch.from_numpy(g.l).cuda(), gamma=g.gamma, m=g.m, seed=1.0) for g in gs]
+    b = GmmBatch(inst, chunk_points=4096)
+    b.prepare()
+    b.run()
+    torch.cuda.synchronize()
+    which = sorted(set(np.random.default_rng(0).choice(512, 12, replace=False).tolist()))
+    _check(gs, inst, b, which=which)
