@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--tc-only", action="store_true",
                     help="only the tensor-core precision form (profiling captures)")
     ap.add_argument("--tc-n", type=int, default=1 << 20, help="points of the tensor-core workload")
+    ap.add_argument("--batched-only", action="store_true", help="only the batched workload")
     return ap.parse_args()
 
 
@@ -166,6 +167,13 @@ def run_ours(args):
     global GMM_N
     GMM_N = args.gmm_n
     import torch
+    if args.batched_only:
+        torch.cuda.set_device(0)
+        import paper_2104_05372_b300 as gpa
+        from paper_2104_05372_b300 import _lib
+        dev = torch.device("cuda", 0)
+        print(json.dumps(run_batched(args, gpa, _lib, dev, torch.cuda.current_stream(dev), 0)))
+        return
     if args.tc_only:
         torch.cuda.set_device(0)
         import paper_2104_05372_b300 as gpa
@@ -263,6 +271,7 @@ def run_ours(args):
     if not args.no_secondary:
         result["secondary"] = run_reproj(args, gpa, _lib, dev, stream, rank)
         result["precision_form"] = run_gmm_tc(args, gpa, _lib, dev, stream, rank)
+        result["batched"] = run_batched(args, gpa, _lib, dev, stream, rank)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -426,6 +435,66 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, fp32_steps=1):
                      "note": "achieved counts D^2 + 3D flops per (point, component); executed counts every "
                              "MMA (dense 128x128 tiles, 3 passes in the forward)"},
     }
+
+
+def run_batched(args, gpa, _lib, dev, stream, rank):
+    """Batched workload: 512 instances (N log-uniform in [1e3, 2e5], D in
+    {8,16,32,64}, K log-uniform in [4,128]) in one CUDA-graph replay of the
+    persistent kernels (autotuned work-item size), against a loop of
+    per-instance gmm_vjp calls on the plain path."""
+    import torch
+    import synth
+    from paper_2104_05372_b300 import autotune
+    shapes = synth.batched_shapes(512, seed=0)
+    gs = synth.batched_inputs(shapes, seed=5000 + rank)
+    inst = [dict(x=torch.from_numpy(g.x).to(dev), alpha=torch.from_numpy(g.alpha).to(dev),
+                 mu=torch.from_numpy(g.mu).to(dev), q=torch.from_numpy(g.q).to(dev),
+                 l=torch.from_numpy(g.l).to(dev), gamma=g.gamma, m=g.m, seed=1.0) for g in gs]
+    tune = autotune.tune_batched(inst, reps=2)
+    b = _lib.GmmBatch(inst, chunk_points=tune["chunk_points"])
+    b.prepare()
+    cps = tune["ctas_per_sm"]
+    b.zero_grads()
+    b.run(cps)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.zero_grads()
+        b.run(cps)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_b = e0.elapsed_time(e1) / args.steps
+    # plain path: one gmm_vjp call per instance (its own workspace, allocated beforehand)
+    wss = [_lib.workspace(gpa.gpa_gmm_workspace_bytes(g.n, g.d, g.k, 0, 0), dev) for g in gs]
+    grads = [gpa.gmm_vjp(i["x"], i["alpha"], i["mu"], i["q"], i["l"], i["gamma"], i["m"], ws=w)
+             for i, w in zip(inst, wss)]
+
+    def loop():
+        for i, w, gr in zip(inst, wss, grads):
+            gpa.gmm_vjp(i["x"], i["alpha"], i["mu"], i["q"], i["l"], i["gamma"], i["m"], d_alpha=gr[0],
+                        d_mu=gr[1], d_q=gr[2], d_l=gr[3], ws=w)
+    loop()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    reps = max(1, args.steps // 2)
+    for _ in range(reps):
+        loop()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_loop = e0.elapsed_time(e1) / reps
+    del wss
+    return {"workload": "512 GMM instances, N log-uniform [1e3,2e5], D in {8,16,32,64}, K log-uniform [4,128], FP32",
+            "metric": METRIC, "unit": UNIT, "pairs": b.pairs, "value": b.pairs / (ms_b / 1e3), "ms_per_step": ms_b,
+            "per_instance_launches": {"value": b.pairs / (ms_loop / 1e3), "ms_per_step": ms_loop},
+            "speedup_vs_per_instance": ms_loop / ms_b, "autotune": {k: tune[k] for k in
+                                                                      ("chunk_points", "ctas_per_sm", "ms")}}
 
 
 # ---------------------------------------------------------------------------

@@ -228,27 +228,35 @@ class GmmBatch:
 
     def __init__(self, instances, chunk_points=4096):
         self.chunk_points = int(chunk_points)
+        dev = instances[0]["x"].device
+        shapes = [_gmm_params(i["x"], i["alpha"], i["mu"], i["q"], i["l"]) for i in instances]
+        # every gradient and objective of the batch in one buffer: one memset clears them
+        sizes = [k + 2 * k * d + k * (d * (d - 1) // 2) for n, d, k in shapes]
+        self.flat = torch.zeros(sum(sizes), dtype=torch.float32, device=dev)
+        self.outs = torch.zeros(len(instances), dtype=torch.float64, device=dev)
         self.tensors = []
         arr = (GmmInstance * len(instances))()
-        for i, inst in enumerate(instances):
-            n, d, k = _gmm_params(inst["x"], inst["alpha"], inst["mu"], inst["q"], inst["l"])
-            dev = inst["x"].device
+        off = 0
+        for i, (inst, (n, d, k)) in enumerate(zip(instances, shapes)):
             t = d * (d - 1) // 2
-            g = [torch.zeros(k, device=dev), torch.zeros(k, d, device=dev), torch.zeros(k, d, device=dev),
-                 torch.zeros(k, t, device=dev)]
-            out = torch.zeros(1, dtype=torch.float64, device=dev)
-            self.tensors.append((inst, g, out))
+            parts = []
+            for numel, shape in ((k, (k,)), (k * d, (k, d)), (k * d, (k, d)), (k * t, (k, t))):
+                parts.append(self.flat[off:off + numel].view(shape))
+                off += numel
+            out = self.outs[i:i + 1]
+            self.tensors.append((inst, parts, out))
             arr[i] = GmmInstance(inst["x"].data_ptr(), inst["alpha"].data_ptr(), inst["mu"].data_ptr(),
                                  inst["q"].data_ptr(), inst["l"].data_ptr() if t > 0 else 0,
-                                 g[0].data_ptr(), g[1].data_ptr(), g[2].data_ptr(), g[3].data_ptr() if t > 0 else 0,
-                                 out.data_ptr(), n, d, k, float(inst.get("gamma", 1.0)), int(inst.get("m", 0)),
-                                 float(inst.get("seed", 1.0)))
+                                 parts[0].data_ptr(), parts[1].data_ptr(), parts[2].data_ptr(),
+                                 parts[3].data_ptr() if t > 0 else 0, out.data_ptr(), n, d, k,
+                                 float(inst.get("gamma", 1.0)), int(inst.get("m", 0)), float(inst.get("seed", 1.0)))
         self.desc = arr
         self.n_inst = len(instances)
+        self.pairs = sum(n * k for n, d, k in shapes)
         nb = int(load().gpa_gmm_batched_workspace_bytes(C.byref(arr), self.n_inst, self.chunk_points))
         if nb == 0:
             raise GpaError(ERR_ARG, "gpa_gmm_batched_workspace_bytes")
-        self.ws = workspace(nb, instances[0]["x"].device)
+        self.ws = workspace(nb, dev)
 
     def prepare(self, stream=None):
         rc = load().gmm_batched_prepare(C.byref(self.desc), self.n_inst, self.chunk_points, _ptr(self.ws),
@@ -261,10 +269,8 @@ class GmmBatch:
         _ok(rc, "gmm_batched_vjp")
 
     def zero_grads(self):
-        for _, g, out in self.tensors:
-            for t in g:
-                t.zero_()
-            out.zero_()
+        self.flat.zero_()
+        self.outs.zero_()
 
     def results(self):
         """[(objective, (d_alpha, d_mu, d_q, d_l))] per instance (device tensors)."""
