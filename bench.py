@@ -59,6 +59,7 @@ def parse():
                     help="only the tensor-core precision form (profiling captures)")
     ap.add_argument("--tc-n", type=int, default=1 << 20, help="points of the tensor-core workload")
     ap.add_argument("--batched-only", action="store_true", help="only the batched workload")
+    ap.add_argument("--reproj-only", action="store_true", help="only the reprojection workload")
     return ap.parse_args()
 
 
@@ -167,6 +168,13 @@ def run_ours(args):
     global GMM_N
     GMM_N = args.gmm_n
     import torch
+    if args.reproj_only:
+        torch.cuda.set_device(0)
+        import paper_2104_05372_b300 as gpa
+        from paper_2104_05372_b300 import _lib
+        dev = torch.device("cuda", 0)
+        print(json.dumps(run_reproj(args, gpa, _lib, dev, torch.cuda.current_stream(dev), 0)))
+        return
     if args.batched_only:
         torch.cuda.set_device(0)
         import paper_2104_05372_b300 as gpa

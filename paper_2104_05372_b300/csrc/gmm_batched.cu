@@ -54,6 +54,9 @@ int dp_of_class(int c) { return 16 << c; }
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 int nblk(int dp) { return (dp / 8) * (dp / 8 + 1) / 2; }
+int bwd_tpb(int dp) {
+    return dp == 16 ? Bwd<16>::TPB : dp == 32 ? Bwd<32>::TPB : dp == 64 ? Bwd<64>::TPB : Bwd<128>::TPB;
+}
 int gc_of(int dp) { return dp == 16 ? 32 : dp == 32 ? 16 : dp == 64 ? 8 : 2; }
 
 struct Plan {
@@ -82,7 +85,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
         B.gamma = I.gamma;
         B.seed = I.seed;
         B.ntiles128 = (int)((I.n + 127) / 128);
-        const int64_t ntiles64 = (I.n + 63) / 64;
+        const int64_t ntiles64 = (I.n + bwd_tpb(dp) - 1) / bwd_tpb(dp);  // backward tiles
         int nch = (int)((I.n + chunk_points - 1) / chunk_points);
         nch = std::max(1, std::min(nch, kGmmMaxChunks));
         nch = (int)std::min<int64_t>(nch, ntiles64);
@@ -101,7 +104,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
         auto cost_f = [&](const BItem& w) { return (double)P.inst[w.inst].k; };
         auto cost_b = [&](const BItem& w) {
             const BInst& B = P.inst[w.inst];
-            const int64_t ntiles64 = (B.n + 63) / 64;
+            const int64_t ntiles64 = (B.n + bwd_tpb(B.dp) - 1) / bwd_tpb(B.dp);
             const int64_t t0 = (int64_t)w.b * B.tiles_per_chunk;
             return (double)std::max<int64_t>(0, std::min<int64_t>(ntiles64, t0 + B.tiles_per_chunk) - t0);
         };

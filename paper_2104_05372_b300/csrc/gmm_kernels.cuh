@@ -45,9 +45,10 @@ struct Bwd {
     static constexpr int NDIAG_T = GC * NB;            // threads on diagonal blocks
     static constexpr int NOFF_T = GC * NOFF;           // threads on off-diagonal blocks
     static constexpr int THREADS = ((NDIAG_T + NOFF_T + 31) / 32) * 32;
-    static constexpr int TPB = 64;                     // points per tile
+    static constexpr int TPB = 128;                    // points per tile
     static constexpr int XST = DP + 4;                 // row stride of Xs[p][c]
-    static constexpr size_t SMEM = sizeof(float) * (size_t)(TPB * XST + TPB * GC);
+    // double-buffered: point tiles, raw log-joint and lse, and the cotangents r
+    static constexpr size_t SMEM = sizeof(float) * (size_t)(2 * TPB * XST + 2 * GC * TPB + 2 * TPB + 2 * TPB * GC);
 };
 
 // ---------------------------------------------------------------------------
@@ -395,8 +396,10 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
     using C = Bwd<DP>;
     constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, NB = C::NB, NBLK = C::NBLK;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float* Xs = reinterpret_cast<float*>(smem_raw);  // [TPB][XST]
-    float* rs = Xs + TPB * XST;                       // [TPB][GC]
+    float* Xs = reinterpret_cast<float*>(smem_raw);  // [2][TPB][XST]
+    float* rawlj = Xs + 2 * TPB * XST;                // [2][GC][TPB]
+    float* rawlse = rawlj + 2 * GC * TPB;             // [2][TPB]
+    float* rs = rawlse + 2 * TPB;                     // [2][TPB][GC]
     const int tid = threadIdx.x;
     const int kg0 = bx * GC;
     const int64_t ntiles = (n + TPB - 1) / TPB;
@@ -422,7 +425,40 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
     }
     const bool active = (tid < C::NDIAG_T + C::NOFF_T) && (kg0 + kk < k);
 
-    for (int e = tid; e < TPB * XST; e += C::THREADS) Xs[e] = 0.f;
+    // asynchronous copies of tile t into buffer buf (no registers involved)
+    auto issue = [&](int64_t t, int buf) {
+        const int64_t p0 = t * TPB;
+        const int nv = (int)min64(TPB, n - p0);
+        float* X = Xs + buf * TPB * XST;
+        for (int e = tid; e < nv * d; e += C::THREADS) {
+            const int p = e / d, c = e - p * d;
+            cp_async4(X + p * XST + bwd_swz(c), x + (p0 + p) * d + c);
+        }
+        float* L = rawlj + buf * GC * TPB;
+        for (int e = tid; e < GC * TPB; e += C::THREADS) {
+            const int kc = e / TPB, p = e % TPB;
+            if (p < nv && kg0 + kc < k) cp_async4(L + e, lj + (int64_t)(kg0 + kc) * lj_ld + p0 + p);
+        }
+        float* S = rawlse + buf * TPB;
+        for (int p = tid; p < nv; p += C::THREADS) cp_async4(S + p, lse + p0 + p);
+    };
+    // cotangents r = seed exp(s - lse) of tile t from buffer buf; 0 on the ragged tail
+    auto make_r = [&](int64_t t, int buf) {
+        const int64_t p0 = t * TPB;
+        const int nv = (int)min64(TPB, n - p0);
+        const float* L = rawlj + buf * GC * TPB;
+        const float* S = rawlse + buf * TPB;
+        float* R = rs + buf * TPB * GC;
+        for (int e = tid; e < GC * TPB; e += C::THREADS) {
+            const int kc = e / TPB, p = e % TPB;
+            float r = 0.f;
+            if (p < nv && kg0 + kc < k) r = seed * expf(L[e] - S[p]);
+            R[p * GC + kc] = r;
+        }
+    };
+
+    for (int e = tid; e < 2 * TPB * XST; e += C::THREADS) Xs[e] = 0.f;
+    __syncthreads();
 
     float acc[8][8];
     float macc[8];
@@ -434,65 +470,70 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
     }
 
+    // pipeline: tile t+1 in shared memory and tile t+2 in flight while t is accumulated
+    if (t_begin < t_end) issue(t_begin, 0);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (t_begin < t_end) make_r(t_begin, 0);
+    if (t_begin + 1 < t_end) issue(t_begin + 1, 1);
+    cp_async_commit();
+    __syncthreads();
+
     for (int64_t t = t_begin; t < t_end; ++t) {
-        const int64_t p0 = t * TPB;
-        const int nv = (int)min64(TPB, n - p0);
-        __syncthreads();
-        for (int e = tid; e < nv * d; e += C::THREADS) {
-            const int p = e / d, c = e - p * d;
-            Xs[p * XST + bwd_swz(c)] = __ldg(x + (p0 + p) * d + c);
-        }
-        for (int e = tid; e < GC * TPB; e += C::THREADS) {
-            const int kc = e / TPB, p = e % TPB;
-            float r = 0.f;
-            if (p < nv && kg0 + kc < k)
-                r = seed * expf(__ldg(lj + (int64_t)(kg0 + kc) * lj_ld + p0 + p) - __ldg(lse + p0 + p));
-            rs[p * GC + kc] = r;
-        }
-        __syncthreads();
-        if (!active) continue;
-        // halves of the chunks in swizzled order (see bwd_swz)
-        const float* xa = Xs + 8 * a;
-        const float* xb = Xs + 8 * b;
-        const int ha = ((a >> 2) & 1) << 2, hb = ((b >> 2) & 1) << 2;
-        if (diag) {
+        const int buf = (int)((t - t_begin) & 1);
+        if (active) {
+            const float* Xb = Xs + buf * TPB * XST;
+            const float* rb = rs + buf * TPB * GC;
+            // halves of the chunks in swizzled order (see bwd_swz)
+            const float* xa = Xb + 8 * a;
+            const float* xb = Xb + 8 * b;
+            const int ha = ((a >> 2) & 1) << 2, hb = ((b >> 2) & 1) << 2;
+            if (diag) {
 #pragma unroll 2
-            for (int p = 0; p < TPB; ++p) {
-                const float4 a0 = *reinterpret_cast<const float4*>(xa + p * XST + ha);
-                const float4 a1 = *reinterpret_cast<const float4*>(xa + p * XST + (4 ^ ha));
-                const float rr = rs[p * GC + kk];
-                const float xv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                float ya[8];
+                for (int p = 0; p < TPB; ++p) {
+                    const float4 a0 = *reinterpret_cast<const float4*>(xa + p * XST + ha);
+                    const float4 a1 = *reinterpret_cast<const float4*>(xa + p * XST + (4 ^ ha));
+                    const float rr = rb[p * GC + kk];
+                    const float xv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    float ya[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) ya[i] = rr * xv[i];
+                    for (int i = 0; i < 8; ++i) ya[i] = rr * xv[i];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    macc[i] += ya[i];
+                    for (int i = 0; i < 8; ++i) {
+                        macc[i] += ya[i];
 #pragma unroll
-                    for (int j = 0; j <= i; ++j) acc[i][j] = fmaf(ya[i], xv[j], acc[i][j]);
+                        for (int j = 0; j <= i; ++j) acc[i][j] = fmaf(ya[i], xv[j], acc[i][j]);
+                    }
+                    racc += rr;
                 }
-                racc += rr;
-            }
-        } else {
+            } else {
 #pragma unroll 1
-            for (int p = 0; p < TPB; ++p) {
-                const float4 b0 = *reinterpret_cast<const float4*>(xb + p * XST + hb);
-                const float4 b1 = *reinterpret_cast<const float4*>(xb + p * XST + (4 ^ hb));
-                const float rr = rs[p * GC + kk];
-                const float yv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                for (int p = 0; p < TPB; ++p) {
+                    const float4 b0 = *reinterpret_cast<const float4*>(xb + p * XST + hb);
+                    const float4 b1 = *reinterpret_cast<const float4*>(xb + p * XST + (4 ^ hb));
+                    const float rr = rb[p * GC + kk];
+                    const float yv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float4 av = *reinterpret_cast<const float4*>(xa + p * XST + ((4 * h) ^ ha));
-                    const float xv[4] = {av.x, av.y, av.z, av.w};
+                    for (int h = 0; h < 2; ++h) {
+                        const float4 av = *reinterpret_cast<const float4*>(xa + p * XST + ((4 * h) ^ ha));
+                        const float xv[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float ya = rr * xv[i];
+                        for (int i = 0; i < 4; ++i) {
+                            const float ya = rr * xv[i];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[4 * h + i][j] = fmaf(ya, yv[j], acc[4 * h + i][j]);
+                            for (int j = 0; j < 8; ++j) acc[4 * h + i][j] = fmaf(ya, yv[j], acc[4 * h + i][j]);
+                        }
                     }
                 }
             }
         }
+        cp_async_wait_all();  // this thread's copies of tile t+1 have landed
+        __syncthreads();      // every thread's, and nobody reads buffer `buf` any more
+        if (t + 1 < t_end) make_r(t + 1, buf ^ 1);
+        if (t + 2 < t_end) issue(t + 2, buf);
+        cp_async_commit();
+        __syncthreads();      // r of tile t+1 complete
     }
     if (!active) return;
     const int kg = kg0 + kk;
