@@ -244,7 +244,7 @@ GPA_API int reproj_residual_vjp(const float* cams, const float* pts, const int32
  * afford a cudaMalloc on its call path, or code whose device-memory budget is
  * fixed at start-up. The paper has no counterpart; it is an interface choice.
  * The only scratch, the expanded cameras, lives in a fixed array in device
- * memory owned by the library (GPA_NOALLOC_MAX_CAMS cameras, 2.25 MiB on every
+ * memory owned by the library (GPA_NOALLOC_MAX_CAMS cameras, 2 MiB on every
  * GPU that loads the library, held until the process exits); the call itself
  * allocates nothing. More cameras than that return GPA_ERR_WORKSPACE and
  * enqueue nothing. The first call on a device looks up the array's device

@@ -49,7 +49,6 @@ struct BItem {
 constexpr int kClasses = 4;  // padded dimension 16, 32, 64, 128
 constexpr int kPhases = 4;   // prep, forward, backward, finalize
 int class_of(int dp) { return dp == 16 ? 0 : dp == 32 ? 1 : dp == 64 ? 2 : 3; }
-int dp_of_class(int c) { return 16 << c; }
 
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 

@@ -31,9 +31,11 @@
 
 namespace gpa {
 
-constexpr int kCamRec = 36;  // floats per expanded camera
-// layout: [0..8] R hi (row-major), [9..17] R lo, [18..20] c, [21] f, [22..23] pp,
-//         [24..25] kappa, [26..34] J_r (row-major), [35] pad
+constexpr int kCamRec = 32;  // floats per expanded camera: one 128-byte line
+// layout: [0..8] R hi (row-major), [9..11] R lo of the depth row, [12..14] c, [15] f,
+//         [16..17] pp, [18..19] kappa, [20..28] J_r (row-major), [29..31] pad.
+// The residual reads the first 20 floats only.
+constexpr int kCamResid = 20;
 
 __global__ void __launch_bounds__(128) cam_expand_kernel(const float* __restrict__ cams, int n_cams,
                                                          float* __restrict__ rec) {
@@ -79,12 +81,13 @@ __global__ void __launch_bounds__(128) cam_expand_kernel(const float* __restrict
     for (int i = 0; i < 9; ++i) {
         const float hi = (float)R[i];
         o[i] = hi;
-        o[9 + i] = (float)(R[i] - (double)hi);
-        o[26 + i] = (float)(((i % 4) == 0 ? 1.0 : 0.0) - A * W[i] + B * W2[i]);
+        if (i >= 6) o[9 + (i - 6)] = (float)(R[i] - (double)hi);
+        o[20 + i] = (float)(((i % 4) == 0 ? 1.0 : 0.0) - A * W[i] + B * W2[i]);
     }
-    o[18] = c[3]; o[19] = c[4]; o[20] = c[5];
-    o[21] = c[6]; o[22] = c[7]; o[23] = c[8];
-    o[24] = c[9]; o[25] = c[10]; o[35] = 0.f;
+    o[12] = c[3]; o[13] = c[4]; o[14] = c[5];
+    o[15] = c[6]; o[16] = c[7]; o[17] = c[8];
+    o[18] = c[9]; o[19] = c[10];
+    o[29] = 0.f; o[30] = 0.f; o[31] = 0.f;
 }
 
 // ---- error-free transformations ---------------------------------------------
@@ -94,6 +97,35 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// The first NF floats of the record of camera ci, with 16-byte loads (records
+// are 128 B apart and the workspace is 256-byte aligned).
+template <int NF>
+__device__ __forceinline__ void load_cam(const float* __restrict__ rec, int ci, float (&cam)[kCamRec]) {
+    const float4* p = reinterpret_cast<const float4*>(rec + (size_t)ci * kCamRec);
+#pragma unroll
+    for (int i = 0; i < NF / 4; ++i) {
+        const float4 v = __ldg(p + i);
+        cam[4 * i] = v.x;
+        cam[4 * i + 1] = v.y;
+        cam[4 * i + 2] = v.z;
+        cam[4 * i + 3] = v.w;
+    }
+}
+
+// d_pts[pi][0..2] += g with one 8-byte vector reduction and one scalar one: row
+// pi starts 12*pi bytes in, 8-byte aligned for even pi (pair first) and 4 bytes
+// off for odd pi (scalar first).
+__device__ __forceinline__ void red_add_point(float* __restrict__ d_pts, int pi, const float (&g)[3]) {
+    float* dp = d_pts + (size_t)pi * 3;
+    if ((pi & 1) == 0) {
+        atomicAdd(reinterpret_cast<float2*>(dp), make_float2(g[0], g[1]));
+        atomicAdd(dp + 2, g[2]);
+    } else {
+        atomicAdd(dp, g[0]);
+        atomicAdd(reinterpret_cast<float2*>(dp + 1), make_float2(g[1], g[2]));
+    }
+}
+
 struct Proj {
     float Y[3];   // rotated point (Y[2] compensated)
     float p[2];   // normalised image coordinates
@@ -101,16 +133,16 @@ struct Proj {
     float out[2]; // f L p + pp
 };
 
-// Projection of point X by the expanded camera rc.
+// Projection of point X by the expanded camera rc (a register copy of the record).
 __device__ __forceinline__ Proj project(const float* __restrict__ rc, float X0, float X1, float X2) {
     Proj P;
     float u[3], ue[3];
-    two_sum(X0, -__ldg(rc + 18), u[0], ue[0]);
-    two_sum(X1, -__ldg(rc + 19), u[1], ue[1]);
-    two_sum(X2, -__ldg(rc + 20), u[2], ue[2]);
+    two_sum(X0, -rc[12], u[0], ue[0]);
+    two_sum(X1, -rc[13], u[1], ue[1]);
+    two_sum(X2, -rc[14], u[2], ue[2]);
     float Rh[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Rh[i] = __ldg(rc + i);
+    for (int i = 0; i < 9; ++i) Rh[i] = rc[i];
     P.Y[0] = fmaf(Rh[0], u[0], fmaf(Rh[1], u[1], Rh[2] * u[2]));
     P.Y[1] = fmaf(Rh[3], u[0], fmaf(Rh[4], u[1], Rh[5] * u[2]));
     {
@@ -125,16 +157,16 @@ __device__ __forceinline__ Proj project(const float* __restrict__ rc, float X0, 
         two_sum(s1, pr[2], s2, t2);
         float corr = t1 + t2 + pe[0] + pe[1] + pe[2];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) corr = fmaf(__ldg(rc + 15 + j), u[j], fmaf(Rh[6 + j], ue[j], corr));
+        for (int j = 0; j < 3; ++j) corr = fmaf(rc[9 + j], u[j], fmaf(Rh[6 + j], ue[j], corr));
         P.Y[2] = s2 + corr;
     }
     P.p[0] = P.Y[0] / P.Y[2];
     P.p[1] = P.Y[1] / P.Y[2];
     P.rho = P.p[0] * P.p[0] + P.p[1] * P.p[1];
-    const float k1 = __ldg(rc + 24), k2 = __ldg(rc + 25), f = __ldg(rc + 21);
+    const float k1 = rc[18], k2 = rc[19], f = rc[15];
     P.L = 1.f + k1 * P.rho + k2 * P.rho * P.rho;
-    P.out[0] = f * P.L * P.p[0] + __ldg(rc + 22);
-    P.out[1] = f * P.L * P.p[1] + __ldg(rc + 23);
+    P.out[0] = f * P.L * P.p[0] + rc[16];
+    P.out[1] = f * P.L * P.p[1] + rc[17];
     return P;
 }
 
@@ -142,7 +174,7 @@ __device__ __forceinline__ Proj project(const float* __restrict__ rc, float X0, 
 // cotangent (w0, w1) of the projection.
 __device__ __forceinline__ void project_vjp(const float* __restrict__ rc, const Proj& P, float w0, float w1,
                                             float (&gc)[11], float (&gp)[3]) {
-    const float f = __ldg(rc + 21), k1 = __ldg(rc + 24), k2 = __ldg(rc + 25);
+    const float f = rc[15], k1 = rc[18], k2 = rc[19];
     const float pw = P.p[0] * w0 + P.p[1] * w1;
     const float dL = f * pw;
     const float drho = dL * (k1 + 2.f * k2 * P.rho);
@@ -156,14 +188,14 @@ __device__ __forceinline__ void project_vjp(const float* __restrict__ rc, const 
     float dX[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-        dX[j] = __ldg(rc + j) * yb0 + __ldg(rc + 3 + j) * yb1 + __ldg(rc + 6 + j) * yb2;
+        dX[j] = rc[j] * yb0 + rc[3 + j] * yb1 + rc[6 + j] * yb2;
     // d w = J_r (Y x ybar)
     const float cx = P.Y[1] * yb2 - P.Y[2] * yb1;
     const float cy = P.Y[2] * yb0 - P.Y[0] * yb2;
     const float cz = P.Y[0] * yb1 - P.Y[1] * yb0;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        gc[i] = __ldg(rc + 26 + 3 * i) * cx + __ldg(rc + 27 + 3 * i) * cy + __ldg(rc + 28 + 3 * i) * cz;
+        gc[i] = rc[20 + 3 * i] * cx + rc[21 + 3 * i] * cy + rc[22 + 3 * i] * cz;
     gc[3] = -dX[0]; gc[4] = -dX[1]; gc[5] = -dX[2];
     gc[6] = P.L * pw;
     gc[7] = w0; gc[8] = w1;
@@ -184,7 +216,8 @@ __global__ void __launch_bounds__(256) reproj_residual_kernel(
             report(status, GPA_ERR_INDEX);
             continue;
         }
-        const float* rc = rec + (size_t)o.x * kCamRec;
+        float rc[kCamRec];
+        load_cam<kCamResid>(rec, o.x, rc);
         const float* X = pts + (size_t)o.y * 3;
         const Proj P = project(rc, __ldg(X), __ldg(X + 1), __ldg(X + 2));
         const float2 t = __ldg(tgt + j);
@@ -230,7 +263,8 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
         for (int i = 0; i < 11; ++i) gc[i] = 0.f;
         gp[0] = gp[1] = gp[2] = 0.f;
         if (valid) {
-            const float* rc = rec + (size_t)ci * kCamRec;
+            float rc[kCamRec];
+            load_cam<kCamRec>(rec, ci, rc);
             const float* X = pts + (size_t)pi * 3;
             const Proj P = project(rc, __ldg(X), __ldg(X + 1), __ldg(X + 2));
             float w0, w1;
@@ -252,8 +286,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
                 float* dc = d_cams + (size_t)ci * 11;
 #pragma unroll
                 for (int i = 0; i < 11; ++i) red_add(dc + i, gc[i]);
-                float* dp = d_pts + (size_t)pi * 3;
-                red_add(dp, gp[0]); red_add(dp + 1, gp[1]); red_add(dp + 2, gp[2]);
+                red_add_point(d_pts, pi, gp);
             }
         } else if (STRAT == GPA_SCATTER_WARPAGG) {
             const int ck = valid ? ci : -1 - lane;
@@ -273,10 +306,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
 #pragma unroll
                 for (int i = 0; i < 3; ++i) gp[i] = group_sum(gp[i], gpm);
             }
-            if (valid && (__ffs(gpm) - 1) == lane) {
-                float* dp = d_pts + (size_t)pi * 3;
-                red_add(dp, gp[0]); red_add(dp + 1, gp[1]); red_add(dp + 2, gp[2]);
-            }
+            if (valid && (__ffs(gpm) - 1) == lane) red_add_point(d_pts, pi, gp);
         } else {  // SORT: runs of equal cameras in lane order
             const int ck = valid ? ci : -1 - lane;
 #pragma unroll
@@ -287,10 +317,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
 #pragma unroll
                 for (int i = 0; i < 11; ++i) red_add(dc + i, gc[i]);
             }
-            if (valid) {
-                float* dp = d_pts + (size_t)pi * 3;
-                red_add(dp, gp[0]); red_add(dp + 1, gp[1]); red_add(dp + 2, gp[2]);
-            }
+            if (valid) red_add_point(d_pts, pi, gp);
         }
     }
 }
@@ -445,8 +472,8 @@ extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const in
 #include <mutex>
 
 namespace gpa {
-// Largest camera count the built-in scratch holds (36 floats per camera,
-// 2.25 MiB per GPU that loads the library, kept until the process exits).
+// Largest camera count the built-in scratch holds (32 floats per camera,
+// 2 MiB per GPU that loads the library, kept until the process exits).
 constexpr int kNoAllocMaxCams = 16384;
 static __device__ __align__(256) float g_cam_scratch[kNoAllocMaxCams * kCamRec];
 
