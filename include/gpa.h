@@ -228,6 +228,15 @@ GPA_API int reproj_vjp(const float* cams, const float* pts, const int32_t* obs, 
                int32_t strat, const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
                gpa_stream_t stream);
 
+/* JVP of the residual (forward mode, linearize, Sec. 5.1): jv [M][2] =
+ * J_cam(j) v_cams[c] + J_pt(j) v_pts[p] for each observation j = (c, p), with
+ * tangents v_cams [C][11] and v_pts [P][3] laid out like cams and pts.
+ * Out-of-range observations get NaN and set GPA_ERR_INDEX. Workspace as for
+ * reproj_residual. */
+GPA_API int reproj_jvp(const float* cams, const float* pts, const int32_t* obs, const float* v_cams,
+                       const float* v_pts, int32_t n_cams, int32_t n_pts, int64_t n_obs, float* jv, void* ws,
+                       size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
+
 /* Fused residual + VJP in one pass over the observations: res as
  * reproj_residual, then d_cams / d_pts += J^T (wscale * res) (the Gauss-Newton
  * gradient of wscale * |res|^2 / 2 when wscale = 1). */

@@ -47,6 +47,7 @@ _SIGS = {
     "reproj_residual": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
     "reproj_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "reproj_residual_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _F, _P, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
+    "reproj_jvp": ([_P, _P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
     "reproj_vjp_noalloc": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _P], _I32),
     "gpa_plan_bytes": ([_I64, _I32], _SZ),
     "gpa_plan_workspace_bytes": ([_I64, _I32], _SZ),
@@ -323,6 +324,20 @@ def reproj_vjp(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=No
                            _ptr(plan), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "reproj_vjp")
     return d_cams, d_pts
+
+
+def reproj_jvp(cams, pts, obs, v_cams, v_pts, jv=None, ws=None, status=None, stream=None):
+    """J v per observation [M, 2] for tangents v_cams [C, 11], v_pts [P, 3]."""
+    nc, npt, no = _reproj_params(cams, pts, obs)
+    _check(v_cams, torch.float32, "v_cams", (nc, 11))
+    _check(v_pts, torch.float32, "v_pts", (npt, 3))
+    jv = torch.empty(no, 2, dtype=torch.float32, device=cams.device) if jv is None else jv
+    _check(jv, torch.float32, "jv", (no, 2))
+    ws = workspace(gpa_reproj_workspace_bytes(nc, npt, no), cams.device) if ws is None else ws
+    rc = load().reproj_jvp(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(v_cams), _ptr(v_pts), nc, npt, no, _ptr(jv),
+                           _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "reproj_jvp")
+    return jv
 
 
 def reproj_vjp_noalloc(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=None, status=None,

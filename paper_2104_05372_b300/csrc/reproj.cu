@@ -204,6 +204,60 @@ __device__ __forceinline__ void project_vjp(const float* __restrict__ rc, const 
     gp[0] = dX[0]; gp[1] = dX[1]; gp[2] = dX[2];
 }
 
+// Tangent of the projection for tangents (vc[0..10]) of the camera and (vx) of
+// the point (linearize, Sec. 5.1): Ydot = R (Xdot - cdot) + (J_r^T wdot) x Y,
+// pdot = (Ydot_xy - p Ydot_z) / Y_z, rhodot = 2 p.pdot,
+// Ldot = k1dot rho + k1 rhodot + k2dot rho^2 + 2 k2 rho rhodot,
+// out_dot = fdot L p + f Ldot p + f L pdot + ppdot.
+__device__ __forceinline__ void project_jvp(const float* __restrict__ rc, const Proj& P, const float (&vc)[11],
+                                            const float (&vx)[3], float (&jv)[2]) {
+    const float f = rc[15], k1 = rc[18], k2 = rc[19];
+    float v[3];  // J_r^T wdot
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = rc[20 + a] * vc[0] + rc[23 + a] * vc[1] + rc[26 + a] * vc[2];
+    const float du[3] = {vx[0] - vc[3], vx[1] - vc[4], vx[2] - vc[5]};
+    float Yd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Yd[i] = rc[3 * i] * du[0] + rc[3 * i + 1] * du[1] + rc[3 * i + 2] * du[2];
+    Yd[0] += v[1] * P.Y[2] - v[2] * P.Y[1];
+    Yd[1] += v[2] * P.Y[0] - v[0] * P.Y[2];
+    Yd[2] += v[0] * P.Y[1] - v[1] * P.Y[0];
+    const float inv = 1.f / P.Y[2];
+    const float pd0 = (Yd[0] - P.p[0] * Yd[2]) * inv, pd1 = (Yd[1] - P.p[1] * Yd[2]) * inv;
+    const float rhod = 2.f * (P.p[0] * pd0 + P.p[1] * pd1);
+    const float Ld = vc[9] * P.rho + k1 * rhod + vc[10] * P.rho * P.rho + 2.f * k2 * P.rho * rhod;
+    const float fL = f * P.L, c0 = vc[6] * P.L + f * Ld;
+    jv[0] = c0 * P.p[0] + fL * pd0 + vc[7];
+    jv[1] = c0 * P.p[1] + fL * pd1 + vc[8];
+}
+
+__global__ void __launch_bounds__(256) reproj_jvp_kernel(const float* __restrict__ rec, const float* __restrict__ pts,
+                                                         const int2* __restrict__ obs, const float* __restrict__ v_cams,
+                                                         const float* __restrict__ v_pts, int n_cams, int n_pts,
+                                                         int64_t n_obs, float2* __restrict__ jv_out,
+                                                         int32_t* __restrict__ status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_obs; j += stride) {
+        const int2 o = __ldg(obs + j);
+        if (o.x < 0 || o.x >= n_cams || o.y < 0 || o.y >= n_pts) {
+            jv_out[j] = make_float2(NAN, NAN);
+            report(status, GPA_ERR_INDEX);
+            continue;
+        }
+        float rc[kCamRec];
+        load_cam<kCamRec>(rec, o.x, rc);
+        const float* X = pts + (size_t)o.y * 3;
+        const Proj P = project(rc, __ldg(X), __ldg(X + 1), __ldg(X + 2));
+        float vc[11], vx[3], jv[2];
+#pragma unroll
+        for (int i = 0; i < 11; ++i) vc[i] = __ldg(v_cams + (size_t)o.x * 11 + i);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) vx[i] = __ldg(v_pts + (size_t)o.y * 3 + i);
+        project_jvp(rc, P, vc, vx, jv);
+        jv_out[j] = make_float2(jv[0], jv[1]);
+    }
+}
+
 __global__ void __launch_bounds__(256) reproj_residual_kernel(
     const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
     const float2* __restrict__ tgt, int n_cams, int n_pts, int64_t n_obs, float2* __restrict__ res,
@@ -439,6 +493,23 @@ extern "C" int reproj_vjp(const float* cams, const float* pts, const int32_t* ob
     if (rc) return rc;
     return dispatch_vjp<false>(strat, rec, pts, obs, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
                                nullptr, dev_status, s);
+}
+
+extern "C" int reproj_jvp(const float* cams, const float* pts, const int32_t* obs, const float* v_cams,
+                          const float* v_pts, int32_t n_cams, int32_t n_pts, int64_t n_obs, float* jv, void* ws,
+                          size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
+    int rc = reproj_check(cams, pts, obs, n_cams, n_pts, n_obs, ws, ws_bytes);
+    if (rc) return rc;
+    if (!v_cams || !v_pts || !jv) return GPA_ERR_ARG;
+    if (!al(jv, 8) || !al(v_cams, 4) || !al(v_pts, 4)) return GPA_ERR_ALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rec = (float*)ws;
+    rc = expand_cams(cams, n_cams, rec, s);
+    if (rc) return rc;
+    GPA_LAUNCH("reproj_jvp", s,
+               reproj_jvp_kernel<<<obs_grid(n_obs), 256, 0, s>>>(rec, pts, (const int2*)obs, v_cams, v_pts, n_cams,
+                                                                 n_pts, n_obs, (float2*)jv, dev_status));
+    return GPA_OK;
 }
 
 extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const int32_t* obs, const float* tgt,

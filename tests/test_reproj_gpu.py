@@ -188,3 +188,38 @@ def test_autograd_reprojection():
     dcm_ref, dpt_ref, _ = oracle.reproj_vjp(r)
     assert rel_norm(host(cams.grad), dcm_ref) <= TOL_GRAD_FP32
     assert rel_norm(host(pts.grad), dpt_ref) <= TOL_GRAD_FP32
+
+
+@pytest.mark.parametrize("n_cams,n_pts,n_obs", [(1, 1, 1), (50, 300, 20000), (200, 5000, 100003)])
+def test_jvp_matches_oracle(n_cams, n_pts, n_obs):
+    """Forward mode (linearize) on the GPU against the oracle's dual numbers."""
+    import paper_2104_05372_b300 as gpa
+    r = synth.reproj_inputs(n_cams, n_pts, n_obs, seed=n_obs + 7)
+    if n_obs > 1000:
+        _near_plane(r)
+    vc, vp = synth.reproj_tangents(n_cams, n_pts, seed=4)
+    ref, _ = oracle.reproj_jvp(r, vc, vp)
+    cams, pts, obs, _, _ = _dev_inputs(r)
+    st = status()
+    jv = host(gpa.reproj_jvp(cams, pts, obs, dev(vc.astype(np.float32)), dev(vp.astype(np.float32)), status=st))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    # the oracle used float64 tangents; the GPU their float32 rounding
+    ref32, _ = oracle.reproj_jvp(r, vc.astype(np.float32).astype(np.float64), vp.astype(np.float32).astype(np.float64))
+    assert rel_norm(jv, ref32) <= 1e-5
+
+
+def test_dot_product_adjoint_entirely_on_gpu():
+    """<J v, w> with the GPU JVP equals <v, J^T w> with the GPU VJP."""
+    import paper_2104_05372_b300 as gpa
+    r = synth.reproj_inputs(64, 2000, 50000, seed=13)
+    cams, pts, obs, _, w = _dev_inputs(r)
+    dcm, dpt = gpa.reproj_vjp(cams, pts, obs, w)
+    for s in range(4):
+        vc, vp = synth.reproj_tangents(r.n_cams, r.n_pts, seed=200 + s)
+        vc32, vp32 = vc.astype(np.float32), vp.astype(np.float32)
+        jv = host(gpa.reproj_jvp(cams, pts, obs, dev(vc32), dev(vp32))).astype(np.float64)
+        lhs = np.sum(jv * r.w.astype(np.float64))
+        rhs = np.sum(host(dcm).astype(np.float64) * vc32) + np.sum(host(dpt).astype(np.float64) * vp32)
+        scale = np.sqrt(np.sum(jv ** 2) * np.sum(r.w.astype(np.float64) ** 2))
+        assert abs(lhs - rhs) <= 1e-5 * scale, (lhs, rhs)
