@@ -33,7 +33,8 @@
  *           GPA_PREC_FP32 computes every product and sum in float32 (sums over
  *           points in float64 where stated); GPA_PREC_BF16_TC runs the dense
  *           contractions on the tensor cores with bfloat16 operands and float32
- *           accumulation.
+ *           accumulation (GMM only, for 32 < D <= 128; other D return
+ *           GPA_ERR_UNSUPPORTED).
  */
 #ifndef GPA_H
 #define GPA_H

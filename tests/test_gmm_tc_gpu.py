@@ -42,7 +42,9 @@ def _errors(g, f, f2, lse, grads, f_ref, lse_ref, gref):
     return e
 
 
-@pytest.mark.parametrize("n,d,k", [(300, 65, 3), (1000, 100, 7), (5000, 128, 33), ((1 << 13) + 37, 128, 256)])
+@pytest.mark.parametrize("n,d,k", [(300, 33, 3), (1000, 40, 7), (5000, 64, 33), (2000, 64, 1),
+                                   (300, 65, 3), (1000, 100, 7), (5000, 128, 33),
+                                   ((1 << 13) + 37, 128, 256), ((1 << 13) + 37, 64, 255)])
 def test_tc_path_matches_oracle(n, d, k):
     g = synth.gmm_inputs(n, d, k, seed=n + d + k)
     f_ref, lse_ref = oracle.gmm_objective(g, want_lse=True)
@@ -53,8 +55,9 @@ def test_tc_path_matches_oracle(n, d, k):
         assert v <= TOL_BF16, (name, v)
 
 
-def test_tc_recompute_mode_matches_stored_mode():
-    g = synth.gmm_inputs(3000, 128, 20, seed=3)
+@pytest.mark.parametrize("d", [48, 128])
+def test_tc_recompute_mode_matches_stored_mode(d):
+    g = synth.gmm_inputs(3000, d, 21, seed=3)
     _, *gref = oracle.gmm_grad(g)
     _, _, _, _, g_st = _run(g, stored=True)
     _, f2, _, _, g_rc = _run(g, stored=False, logjoint_points=256)
