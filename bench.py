@@ -4,15 +4,18 @@
 One step = one pass of the hot path over one batch of synthetic input: the GMM
 objective and its gradient for N = 2^20 points, D = 64, K = 200 components
 (parameter expansion, forward log-joint + logsumexp, backward Accum of the
-weighted moments, finalize) through the C ABI (gmm_vjp with the log-joint
-recomputed in the workspace). The reprojection VJP on 8192 cameras, 500 000
-points and 4 000 000 observations is measured in the same run and reported in
-the "secondary" block.
+weighted moments, finalize) through the C ABI (gmm_vjp_partial with the
+log-joint recomputed in the workspace, then gmm_vjp_finalize). The
+reprojection VJP on 8192 cameras, 500 000 points and 4 000 000 observations,
+the tensor-core form and the batched form are measured in the same run and
+reported in their own blocks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0). Under torchrun every rank processes its own batch
-(weak scaling, no collective on the data path); timing is the max over ranks.
+Prints one JSON line (rank 0). Under torchrun each rank holds its own 2^20
+points of one data set of N x 2^20 points (weak scaling) and the ranks sum
+their exchange vectors with one all-reduce per step; timing is the max over
+ranks. The other blocks run per rank without a collective.
 """
 from __future__ import annotations
 
@@ -58,6 +61,9 @@ def parse():
     ap.add_argument("--tc-only", action="store_true",
                     help="only the tensor-core precision form (profiling captures)")
     ap.add_argument("--tc-n", type=int, default=1 << 20, help="points of the tensor-core workload")
+    ap.add_argument("--tc-d", type=int, default=128, help="dimension of the --tc-only workload")
+    ap.add_argument("--tc-k", type=int, default=256, help="components of the --tc-only workload")
+    ap.add_argument("--tc-fp32-steps", type=int, default=0, help="--tc-only: also time the FP32 path")
     ap.add_argument("--batched-only", action="store_true", help="only the batched workload")
     ap.add_argument("--reproj-only", action="store_true", help="only the reprojection workload")
     return ap.parse_args()
@@ -187,7 +193,8 @@ def run_ours(args):
         import paper_2104_05372_b300 as gpa
         from paper_2104_05372_b300 import _lib
         dev = torch.device("cuda", 0)
-        print(json.dumps(run_gmm_tc(args, gpa, _lib, dev, torch.cuda.current_stream(dev), 0, fp32_steps=0)))
+        print(json.dumps(run_gmm_tc(args, gpa, _lib, dev, torch.cuda.current_stream(dev), 0, d=args.tc_d,
+                                    k=args.tc_k, fp32_steps=args.tc_fp32_steps)))
         return
     rank, world, local = dist_info()
     if world > 1:
@@ -207,12 +214,16 @@ def run_ours(args):
              torch.zeros(GMM_K, GMM_D, device=dev), torch.zeros(GMM_K, t, device=dev)]
     out = torch.zeros(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # points sharded over ranks (this rank's 2^20 points), parameters replicated;
+    # one all-reduce of the exchange vector per step when world > 1
+    exch = torch.empty(gpa.gpa_gmm_exchange_len(GMM_D, GMM_K), dtype=torch.float64, device=dev)
+    n_total = GMM_N * world
 
     def step():
         for gb in grads:
             gb.zero_()
-        gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, logjoint_in=None, lse_in=None, seed=1.0, d_alpha=grads[0],
-                    d_mu=grads[1], d_q=grads[2], d_l=grads[3], out=out, ws=ws)
+        gpa.data_parallel.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, seed=1.0, n_total=n_total, d_alpha=grads[0],
+                                  d_mu=grads[1], d_q=grads[2], d_l=grads[3], out=out, ws=ws, exch=exch)
 
     def barrier():
         if world > 1:
@@ -264,7 +275,7 @@ def run_ours(args):
                             for k, (c, v) in trace.items()}}
 
     # end to end: host buffers, copies inside the timed region
-    e2e = run_e2e(args, gpa, _lib, g, dev, ws, stream)
+    e2e = run_e2e(args, gpa, _lib, g, dev, ws, stream, exch, n_total)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -272,13 +283,17 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "GMM objective+gradient, N=2^20 points, D=64, K=200, gamma=1, m=0, FP32 "
                                "(log-joint recomputed in the workspace)",
-                   "N": GMM_N, "D": GMM_D, "K": GMM_K, "parallelism": f"replica x{world}",
+                   "N": GMM_N, "D": GMM_D, "K": GMM_K, "N_total": n_total, "parallelism": f"dp{world}",
+                   "sharding": "points split across ranks (N per rank), parameters replicated, one all-reduce "
+                               f"(sum) of the {exch.numel() * 8 / 1e6:.2f} MB float64 exchange vector per "
+                               "step when n_gpus > 1",
                    "l2": "inputs larger than L2 (x is 256 MiB, log-joint 800 MiB)"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
     }
     if not args.no_secondary:
         result["secondary"] = run_reproj(args, gpa, _lib, dev, stream, rank)
-        result["precision_form"] = run_gmm_tc(args, gpa, _lib, dev, stream, rank)
+        result["precision_form"] = [run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=GMM_D, k=GMM_K),
+                                    run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256)]
         result["batched"] = run_batched(args, gpa, _lib, dev, stream, rank)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
@@ -289,7 +304,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, gpa, _lib, g, dev, ws, stream):
+def run_e2e(args, gpa, _lib, g, dev, ws, stream, exch, n_total):
     import torch
     host = [torch.from_numpy(t).pin_memory() for t in (g.x, g.alpha, g.mu, g.q, g.l)]
     dbuf = [torch.empty(t.shape, dtype=t.dtype, device=dev) for t in host]
@@ -305,8 +320,8 @@ def run_e2e(args, gpa, _lib, g, dev, ws, stream):
             d_.copy_(h_, non_blocking=True)
         for gb in grads:
             gb.zero_()
-        gpa.gmm_vjp(*dbuf, g.gamma, g.m, seed=1.0, d_alpha=grads[0], d_mu=grads[1], d_q=grads[2], d_l=grads[3],
-                    out=out, ws=ws)
+        gpa.data_parallel.gmm_vjp(*dbuf, g.gamma, g.m, seed=1.0, n_total=n_total, d_alpha=grads[0],
+                                  d_mu=grads[1], d_q=grads[2], d_l=grads[3], out=out, ws=ws, exch=exch)
         for h_, d_ in zip(hgrads, grads):
             h_.copy_(d_, non_blocking=True)
         hout.copy_(out, non_blocking=True)
@@ -380,13 +395,13 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
     return out
 
 
-def run_gmm_tc(args, gpa, _lib, dev, stream, rank, fp32_steps=1):
-    """Precision form: N=2^20, D=128, K=256 with the contractions on the tensor
-    cores (split-BF16 forward, BF16 backward, FP32 accumulate), beside the
-    plain FP32 CUDA-core path on the same shape."""
+def run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256, fp32_steps=1):
+    """Precision form: N=2^20 points, D x K as given, with the contractions on
+    the tensor cores (split-BF16 forward, BF16 backward, FP32 accumulate),
+    beside the plain FP32 CUDA-core path on the same shape."""
     import torch
     import synth
-    n, d, k = args.tc_n, 128, 256
+    n = args.tc_n
     g = synth.gmm_inputs(n, d, k, seed=4000 + rank)
     x, a, mu, q, l = (torch.from_numpy(t_).to(dev) for t_ in (g.x, g.alpha, g.mu, g.q, g.l))
     t = d * (d - 1) // 2
@@ -428,10 +443,15 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, fp32_steps=1):
     fwd_ms, bwd_ms = fwd[1] / fwd[0], bwd[1] / bwd[0]
     dom, dom_ms = ("gmm_tc_fwd", fwd_ms) if fwd_ms >= bwd_ms else ("gmm_tc_bwd", bwd_ms)
     alg = (d * d + 3 * d) * pairs / (dom_ms / 1e3) / 1e12  # algorithmic flops of the dominant kernel
-    dense = (3 if dom == "gmm_tc_fwd" else 1) * 2 * d * d * pairs / (dom_ms / 1e3) / 1e12
+    tdp = 64 if d <= 64 else 128
+    # executed MMA flops per (point, component): forward 3 passes of 2 TDP^2;
+    # backward one 128 x 128 block per 128 / TDP components over the points
+    per_pair = 3 * 2 * tdp * tdp if dom == "gmm_tc_fwd" else 2 * 128 * tdp
+    dense = per_pair * pairs / (dom_ms / 1e3) / 1e12
     return {
-        "workload": "GMM objective+gradient, N=2^20, D=128, K=256, tensor cores (split-BF16 forward, BF16 "
+        "workload": f"GMM objective+gradient, N={n}, D={d}, K={k}, tensor cores (split-BF16 forward, BF16 "
                     "backward, FP32 accumulate)",
+        "N": n, "D": d, "K": k,
         "metric": METRIC, "unit": UNIT, "value": pairs / (ms_tc / 1e3), "ms_per_step": ms_tc, "dtype": "bf16",
         "plain_fp32_same_shape": {"value": pairs / (ms_fp32 / 1e3), "ms_per_step": ms_fp32},
         "speedup_vs_plain_fp32": ms_fp32 / ms_tc,
@@ -441,7 +461,7 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, fp32_steps=1):
                      "executed_mma_tflops": round(dense, 1),
                      "executed_frac": round(dense / peaks["bf16_tflops"], 4), "peak_source": src,
                      "note": "achieved counts D^2 + 3D flops per (point, component); executed counts every "
-                             "MMA (dense 128x128 tiles, 3 passes in the forward)"},
+                             "MMA (128x128 tiles of the padded dimension, 3 passes in the forward)"},
     }
 
 

@@ -146,6 +146,48 @@ GPA_API int gmm_vjp(const float* x, const float* alpha, const float* mu, const f
             int32_t* dev_status, gpa_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
+/* Data-parallel GMM gradient: points sharded over ranks                      */
+/* ------------------------------------------------------------------------- */
+/*
+ * The Accum sums of the reverse pass are associative (Sec. 2.3.2: partial sums
+ * over any partition of the points combine by addition), so the gradient over
+ * points split across ranks is: each rank runs gmm_vjp_partial on its shard,
+ * the ranks add their exchange vectors (one all-reduce, sum), and each rank
+ * runs gmm_vjp_finalize on the sum. Parameters are replicated; per-point
+ * statistics never leave their rank.
+ *
+ * Exchange vector: float64, gpa_gmm_exchange_len(d, k) entries; per component
+ * the sums [S (lower 8x8 blocks of the padded dimension) | m | R] of the
+ * reverse pass (raw moments for GPA_PREC_FP32, moments centred on mu_k for
+ * GPA_PREC_BF16_TC: every rank must use the same prec), then the sum over
+ * the shard's points of logsumexp_k s_ik. Its layout is internal; only its
+ * length and its additivity are part of the interface.
+ */
+GPA_API int64_t gpa_gmm_exchange_len(int32_t d, int32_t k); /* 0 on bad arguments */
+
+/* Shard half: arguments as gmm_vjp for this rank's n points (logjoint_in /
+ * lse_in of the shard, or both NULL); writes (=) the exchange vector exch
+ * (device, 8-byte aligned). seed scales every term as in gmm_vjp. Workspace:
+ * gpa_gmm_workspace_bytes(n, d, k, prec, .) of the shard. */
+GPA_API int gmm_vjp_partial(const float* x, const float* alpha, const float* mu, const float* q,
+                            const float* l, int64_t n, int32_t d, int32_t k, double gamma, int32_t m,
+                            int32_t prec, const float* logjoint_in, const float* lse_in, double seed,
+                            double* exch, void* ws, size_t ws_bytes, int32_t* dev_status,
+                            gpa_stream_t stream);
+
+/* Combine half: exch = the sum over all shards of their exchange vectors (same
+ * seed and prec on every rank), n_total = the sum of the shards' n. Adds (+=)
+ * seed * grad f of the whole data set to d_alpha, d_mu, d_q, d_l and writes
+ * *out = f (nullable), exactly as one gmm_vjp over all points would (up to
+ * the order of the float64 sums). Any workspace that serves gmm_vjp_partial
+ * for the same d, k serves this call. */
+GPA_API int gmm_vjp_finalize(const float* alpha, const float* mu, const float* q, const float* l,
+                             int64_t n_total, int32_t d, int32_t k, double gamma, int32_t m, int32_t prec,
+                             double seed, const double* exch, float* d_alpha, float* d_mu, float* d_q,
+                             float* d_l, double* out, void* ws, size_t ws_bytes, int32_t* dev_status,
+                             gpa_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
 /* Batched GMM: many instances of uneven N, D, K in persistent kernels        */
 /* ------------------------------------------------------------------------- */
 /* One mixture instance (all pointers device memory; layouts as for gmm_vjp). */

@@ -60,6 +60,11 @@ def _load():
             lib.oracle_gmm_objective.restype = D
             lib.oracle_gmm_logjoint_at.argtypes = [f32p] * 5 + [I32, I32, i64p, I64, vp, f64p]
             lib.oracle_gmm_grad.argtypes = [f32p] * 5 + [I64, I32, I32, D, I32, D] + [f64p] * 4
+            lib.oracle_gmm_accum.argtypes = [f32p] * 5 + [I64, I32, I32, D] + [f64p] * 3
+            lib.oracle_gmm_accum.restype = D
+            lib.oracle_gmm_finish.argtypes = [f32p] * 3 + [I64, I32, I32, D, I32, D] + [f64p] * 3 + [D] + \
+                [f64p] * 4
+            lib.oracle_gmm_finish.restype = D
             lib.oracle_gmm_grad.restype = D
             lib.oracle_gmm_jvp.argtypes = [f32p] * 5 + [I64, I32, I32, D, I32] + [f64p] * 4 + [vp]
             lib.oracle_gmm_jvp.restype = D
@@ -118,6 +123,30 @@ def gmm_grad(g, seed: float = 1.0):
     t = g.d * (g.d - 1) // 2
     da = np.empty(g.k); dm = np.empty((g.k, g.d)); dq = np.empty((g.k, g.d)); dl = np.empty((g.k, t))
     f = lib.oracle_gmm_grad(*_gmm_args(g), g.n, g.d, g.k, g.gamma, g.m, float(seed), da, dm, dq, dl)
+    return f, da, dm, dq, dl
+
+
+def gmm_accum(g, seed: float = 1.0):
+    """Accum sums of the gradient over the points of g, packed into one float64
+    vector [A (K) | MU (K*D) | QB (K*D*D) | sum of logsumexp]: additive over any
+    partition of the points."""
+    lib = _load()
+    a = np.empty(g.k); mu = np.empty((g.k, g.d)); qb = np.empty((g.k, g.d, g.d))
+    sl = lib.oracle_gmm_accum(*_gmm_args(g), g.n, g.d, g.k, float(seed), a, mu, qb)
+    return np.concatenate([a, mu.ravel(), qb.ravel(), [sl]])
+
+
+def gmm_finish(g, n_total: int, sums, seed: float = 1.0):
+    """(f, d_alpha, d_mu, d_q, d_l) from Accum sums (gmm_accum's layout) over
+    n_total points; only the parameters of g are read."""
+    lib = _load()
+    k, d = g.k, g.d
+    t = d * (d - 1) // 2
+    sums = np.ascontiguousarray(sums, np.float64)
+    a = sums[:k].copy(); mu = sums[k:k + k * d].copy(); qb = sums[k + k * d:k + k * d + k * d * d].copy()
+    da = np.empty(k); dm = np.empty((k, d)); dq = np.empty((k, d)); dl = np.empty((k, t))
+    f = lib.oracle_gmm_finish(_c(g.alpha, np.float32), _c(g.q, np.float32), _c(g.l, np.float32), int(n_total), d, k,
+                              g.gamma, g.m, float(seed), a, mu, qb, float(sums[-1]), da, dm, dq, dl)
     return f, da, dm, dq, dl
 
 

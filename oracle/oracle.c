@@ -195,15 +195,22 @@ void oracle_gmm_logjoint_at(const float* x, const float* alpha, const float* mu,
  * into their cotangent slots (LetIndexingTranspose), kept thread-private and
  * combined at the end (Accum, Sec. 2.3.2).
  */
-double oracle_gmm_grad(const float* x, const float* alpha, const float* mu, const float* q,
-                       const float* l, int64_t n, int d, int k, double gamma, int m, double seed,
-                       double* d_alpha, double* d_mu, double* d_q, double* d_l) {
-    const int t = d * (d - 1) / 2;
+/*
+ * The Accum half of the gradient over the n points given: the cotangent
+ * accumulations A_k = sum_i r_ik, MU_k = -sum_i Q_k^T zbar_ik and
+ * QB_k = sum_i zbar_ik (x_i - mu_k)^T (lower triangle, zbar = -r z), with
+ * r_ik = seed * softmax_k(s_i.)_k. Returns sum_i logsumexp_k s_ik. These sums
+ * are additive over any partition of the points (Sec. 2.3.2), which is what
+ * the data-parallel form relies on.
+ */
+double oracle_gmm_accum(const float* x, const float* alpha, const float* mu, const float* q,
+                        const float* l, int64_t n, int d, int k, double seed,
+                        double* A, double* MU, double* QB) {
     double* Q = (double*)malloc(sizeof(double) * (size_t)k * d * d);
     gmm_expand_q(q, l, d, k, Q);
-    double* A = (double*)calloc((size_t)k, sizeof(double));
-    double* MU = (double*)calloc((size_t)k * d, sizeof(double));
-    double* QB = (double*)calloc((size_t)k * d * d, sizeof(double));
+    memset(A, 0, sizeof(double) * (size_t)k);
+    memset(MU, 0, sizeof(double) * (size_t)k * d);
+    memset(QB, 0, sizeof(double) * (size_t)k * d * d);
     double ll = 0.0;
 #pragma omp parallel reduction(+ : ll)
     {
@@ -244,9 +251,24 @@ double oracle_gmm_grad(const float* x, const float* alpha, const float* mu, cons
         }
         free(a_p); free(mu_p); free(qb_p); free(s); free(xc); free(z); free(zbar);
     }
+    free(Q);
+    return ll;
+}
+
+/*
+ * The rest of the gradient from Accum sums taken over all n_total points: the
+ * cotangents of the terms outside the loop over points (-N logsumexp(alpha)
+ * and the prior) and the chain through Q_k = (exp(q_k) on the diagonal, l_k
+ * below it). Returns f, given sum_lse = sum_i logsumexp_k s_ik.
+ */
+double oracle_gmm_finish(const float* alpha, const float* q, const float* l, int64_t n_total, int d, int k,
+                         double gamma, int m, double seed, const double* A, const double* MU,
+                         const double* QB, double sum_lse, double* d_alpha, double* d_mu, double* d_q,
+                         double* d_l) {
+    const int t = d * (d - 1) / 2;
     /* -N logsumexp(alpha): cotangent -seed N softmax(alpha). */
     const double la = alpha_lse(alpha, k);
-    for (int kk = 0; kk < k; ++kk) d_alpha[kk] = A[kk] - seed * (double)n * exp((double)alpha[kk] - la);
+    for (int kk = 0; kk < k; ++kk) d_alpha[kk] = A[kk] - seed * (double)n_total * exp((double)alpha[kk] - la);
     for (int kk = 0; kk < k; ++kk) {
         for (int r = 0; r < d; ++r) {
             const double qv = q[kk * d + r];
@@ -262,9 +284,21 @@ double oracle_gmm_grad(const float* x, const float* alpha, const float* mu, cons
                 d_l[j] = QB[(size_t)kk * d * d + r * d + c] - seed * gamma * gamma * (double)l[j];
             }
     }
-    free(A); free(MU); free(QB); free(Q);
-    ll -= (double)n * la + 0.5 * (double)n * d * log(2.0 * M_PI);
+    const double ll = sum_lse - ((double)n_total * la + 0.5 * (double)n_total * d * log(2.0 * M_PI));
     return ll + gmm_log_prior(q, l, d, k, gamma, m);
+}
+
+double oracle_gmm_grad(const float* x, const float* alpha, const float* mu, const float* q,
+                       const float* l, int64_t n, int d, int k, double gamma, int m, double seed,
+                       double* d_alpha, double* d_mu, double* d_q, double* d_l) {
+    double* A = (double*)malloc(sizeof(double) * (size_t)k);
+    double* MU = (double*)malloc(sizeof(double) * (size_t)k * d);
+    double* QB = (double*)malloc(sizeof(double) * (size_t)k * d * d);
+    const double sum_lse = oracle_gmm_accum(x, alpha, mu, q, l, n, d, k, seed, A, MU, QB);
+    const double f = oracle_gmm_finish(alpha, q, l, n, d, k, gamma, m, seed, A, MU, QB, sum_lse, d_alpha, d_mu,
+                                       d_q, d_l);
+    free(A); free(MU); free(QB);
+    return f;
 }
 
 /*

@@ -43,6 +43,10 @@ _SIGS = {
     "gmm_objective": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P, _P], _I32),
     "gmm_vjp": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _P, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P, _P],
                 _I32),
+    "gpa_gmm_exchange_len": ([_I32, _I32], _I64),
+    "gmm_vjp_partial": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _P, _P, _D, _P, _P, _SZ, _P, _P], _I32),
+    "gmm_vjp_finalize": ([_P] * 4 + [_I64, _I32, _I32, _D, _I32, _I32, _D, _P, _P, _P, _P, _P, _P, _P, _SZ, _P,
+                                     _P], _I32),
     "gpa_reproj_workspace_bytes": ([_I32, _I32, _I64], _SZ),
     "reproj_residual": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
     "reproj_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
@@ -208,6 +212,63 @@ def gmm_vjp(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, logjoint_in=None
                         _ptr(logjoint_in), _ptr(lse_in), float(seed), _ptr(d_alpha), _ptr(d_mu), _ptr(d_q),
                         _ptr(d_l), _ptr(out), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "gmm_vjp")
+    return d_alpha, d_mu, d_q, d_l
+
+
+def gpa_gmm_exchange_len(d, k) -> int:
+    return int(load().gpa_gmm_exchange_len(int(d), int(k)))
+
+
+def gmm_vjp_partial(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, logjoint_in=None, lse_in=None,
+                    seed=1.0, exch=None, ws=None, logjoint_points=0, status=None, stream=None):
+    """Exchange vector (device float64) of this shard of points; returns it."""
+    n, d, k = _gmm_params(x, alpha, mu, q, l)
+    dev = x.device
+    e = gpa_gmm_exchange_len(d, k)
+    exch = torch.empty(e, dtype=torch.float64, device=dev) if exch is None else _check(exch, torch.float64,
+                                                                                        "exch", (e,))
+    if logjoint_in is not None:
+        _check(logjoint_in, torch.float32, "logjoint_in", (k, n))
+    if lse_in is not None:
+        _check(lse_in, torch.float32, "lse_in", (n,))
+    if ws is None:
+        lp = 128 if logjoint_in is not None else logjoint_points
+        ws = workspace(gpa_gmm_workspace_bytes(n, d, k, prec, lp), dev)
+    rc = load().gmm_vjp_partial(_ptr(x), _ptr(alpha), _ptr(mu), _ptr(q), _ptr(l), n, d, k, float(gamma), int(m),
+                                int(prec), _ptr(logjoint_in), _ptr(lse_in), float(seed), _ptr(exch), _ptr(ws),
+                                ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "gmm_vjp_partial")
+    return exch
+
+
+def gmm_vjp_finalize(alpha, mu, q, l, n_total, exch, gamma=1.0, m=0, prec=PREC_FP32, seed=1.0, d_alpha=None,
+                     d_mu=None, d_q=None, d_l=None, out=None, ws=None, status=None, stream=None):
+    """seed * grad f over all shards added into (d_alpha, d_mu, d_q, d_l) from
+    the summed exchange vector; returns them."""
+    k, d = mu.shape
+    t = d * (d - 1) // 2
+    dev = mu.device
+    _check(alpha, torch.float32, "alpha", (k,))
+    _check(mu, torch.float32, "mu", (k, d))
+    _check(q, torch.float32, "q", (k, d))
+    _check(l, torch.float32, "l", (k, t))
+    _check(exch, torch.float64, "exch", (gpa_gmm_exchange_len(d, k),))
+    d_alpha = torch.zeros(k, dtype=torch.float32, device=dev) if d_alpha is None else d_alpha
+    d_mu = torch.zeros(k, d, dtype=torch.float32, device=dev) if d_mu is None else d_mu
+    d_q = torch.zeros(k, d, dtype=torch.float32, device=dev) if d_q is None else d_q
+    d_l = torch.zeros(k, t, dtype=torch.float32, device=dev) if d_l is None else d_l
+    _check(d_alpha, torch.float32, "d_alpha", (k,))
+    _check(d_mu, torch.float32, "d_mu", (k, d))
+    _check(d_q, torch.float32, "d_q", (k, d))
+    _check(d_l, torch.float32, "d_l", (k, t))
+    if out is not None:
+        _check(out, torch.float64, "out")
+    if ws is None:
+        ws = workspace(gpa_gmm_workspace_bytes(1, d, k, prec, 128), dev)
+    rc = load().gmm_vjp_finalize(_ptr(alpha), _ptr(mu), _ptr(q), _ptr(l), int(n_total), d, k, float(gamma), int(m),
+                                 int(prec), float(seed), _ptr(exch), _ptr(d_alpha), _ptr(d_mu), _ptr(d_q),
+                                 _ptr(d_l), _ptr(out), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "gmm_vjp_finalize")
     return d_alpha, d_mu, d_q, d_l
 
 

@@ -178,7 +178,17 @@ static int launch_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int n
                kern<<<A.k, 256, smem, s>>>(A.alpha, A.mu, A.q, A.l, A.d, A.k, A.n, A.gamma, A.m, A.seed,
                                            (const float*)(ws + L.off_bS), (const float*)(ws + L.off_bM), nchunks,
                                            (const double*)(ws + L.off_scal), A.d_alpha, A.d_mu, A.d_q, A.d_l,
-                                           centered));
+                                           centered, A.exch_in));
+    return GPA_OK;
+}
+
+template <int DP>
+static int launch_exchange(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, cudaStream_t s) {
+    GPA_LAUNCH("gmm_exchange", s,
+               gmm_exchange_kernel<DP><<<A.k + 1, 256, 0, s>>>((const float*)(ws + L.off_bS),
+                                                               (const float*)(ws + L.off_bM), nchunks, A.k,
+                                                               (const double*)(ws + L.off_fwd), L.ntiles,
+                                                               A.exch_out));
     return GPA_OK;
 }
 
@@ -213,7 +223,7 @@ static int vjp_impl(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t
     if (A.lj_in) {
         rc = launch_bwd<DP>(A, L, ws, A.x, A.n, A.lj_in, A.n, A.lse_in, nchunks, s);
         if (rc) return rc;
-        if (A.out) {
+        if (A.out || A.exch_out) {
             GPA_LAUNCH("gmm_lse_sum", s,
                        gmm_lse_sum_kernel<<<(unsigned)L.ntiles, 128, 0, s>>>(A.lse_in, A.n,
                                                                             (double*)(ws + L.off_fwd)));
@@ -233,6 +243,7 @@ static int vjp_impl(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t
             if (rc) return rc;
         }
     }
+    if (A.exch_out) return launch_exchange<DP>(A, L, ws, nchunks, s);
     rc = launch_finalize<DP>(A, L, ws, nchunks, s);
     if (rc) return rc;
     if (A.out) return launch_objective(A, L, ws, s);
@@ -271,6 +282,38 @@ int gmm_run_lse_sum(const float* lse, int64_t n, const GmmLayout& L, char* ws, c
 }
 
 int gmm_bwd_partial_entries(int dp) { return nblk_of(dp) * 64; }
+
+int64_t gmm_exchange_len(int d, int k) {
+    const int dp = gmm_dp(d);
+    return (int64_t)k * (gmm_bwd_partial_entries(dp) + dp + 1) + 1;
+}
+
+int gmm_run_exchange(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, cudaStream_t s) {
+    switch (L.dp) {
+        case 16: return launch_exchange<16>(A, L, ws, nchunks, s);
+        case 32: return launch_exchange<32>(A, L, ws, nchunks, s);
+        case 64: return launch_exchange<64>(A, L, ws, nchunks, s);
+        case 128: return launch_exchange<128>(A, L, ws, nchunks, s);
+    }
+    return GPA_ERR_UNSUPPORTED;
+}
+
+// Finish the reverse pass from an exchange vector summed over shards: the
+// gradient from its Accum sums, the objective from its sum of logsumexp.
+static int finalize_from_exchange(const GmmArgs& A, const GmmLayout& L, char* ws, int centered, cudaStream_t s) {
+    int rc = gmm_run_prep(A, L, ws, s);
+    if (rc) return rc;
+    if ((rc = gmm_run_finalize(A, L, ws, 1, centered, s))) return rc;
+    if (!A.out) return GPA_OK;
+    const int dp = gmm_dp(A.d);
+    const int64_t E = gmm_bwd_partial_entries(dp) + dp + 1;
+    GPA_LAUNCH("gmm_objective_finalize", s,
+               gmm_objective_finalize_kernel<<<1, 256, 0, s>>>(A.exch_in + (size_t)A.k * E, 1,
+                                                               (const double*)(ws + L.off_lpk), A.k,
+                                                               (const double*)(ws + L.off_scal), A.n, A.d,
+                                                               A.out));
+    return GPA_OK;
+}
 
 int gmm_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s) {
     switch (L.dp) {
@@ -339,14 +382,11 @@ extern "C" int gmm_objective(const float* x, const float* alpha, const float* mu
     return gmm_objective_run(A, L, (char*)ws, (cudaStream_t)stream);
 }
 
-extern "C" int gmm_vjp(const float* x, const float* alpha, const float* mu, const float* q, const float* l,
-                       int64_t n, int32_t d, int32_t k, double gamma, int32_t m, int32_t prec,
-                       const float* logjoint_in, const float* lse_in, double seed, float* d_alpha,
-                       float* d_mu, float* d_q, float* d_l, double* out, void* ws, size_t ws_bytes,
-                       int32_t* dev_status, gpa_stream_t stream) {
-    int rc = gmm_check(x, alpha, mu, q, l, n, d, k, gamma, prec);
-    if (rc) return rc;
-    if (!d_alpha || !d_mu || !d_q || (d > 1 && !d_l) || !ws) return GPA_ERR_ARG;
+static int vjp_body(const float* x, const float* alpha, const float* mu, const float* q, const float* l,
+                    int64_t n, int32_t d, int32_t k, double gamma, int32_t m, int32_t prec,
+                    const float* logjoint_in, const float* lse_in, double seed, float* d_alpha, float* d_mu,
+                    float* d_q, float* d_l, double* out, double* exch, void* ws, size_t ws_bytes,
+                    int32_t* dev_status, gpa_stream_t stream) {
     if ((logjoint_in == nullptr) != (lse_in == nullptr)) return GPA_ERR_ARG;
     if (((uintptr_t)ws) & 255) return GPA_ERR_ALIGN;
     GmmLayout L = gmm_layout(n, d, k, 0);
@@ -360,7 +400,57 @@ extern "C" int gmm_vjp(const float* x, const float* alpha, const float* mu, cons
     GmmArgs A{};
     A.x = x; A.alpha = alpha; A.mu = mu; A.q = q; A.l = l; A.n = n; A.d = d; A.k = k;
     A.gamma = gamma; A.m = m; A.out = out; A.lj_in = logjoint_in; A.lse_in = lse_in; A.seed = seed;
-    A.d_alpha = d_alpha; A.d_mu = d_mu; A.d_q = d_q; A.d_l = d_l; A.status = dev_status;
+    A.d_alpha = d_alpha; A.d_mu = d_mu; A.d_q = d_q; A.d_l = d_l; A.status = dev_status; A.exch_out = exch;
     if (prec == GPA_PREC_BF16_TC) return gmm_tc_vjp_run(A, L, (char*)ws, ws_bytes, (cudaStream_t)stream);
     return gmm_vjp_run(A, L, (char*)ws, (cudaStream_t)stream);
+}
+
+extern "C" int gmm_vjp(const float* x, const float* alpha, const float* mu, const float* q, const float* l,
+                       int64_t n, int32_t d, int32_t k, double gamma, int32_t m, int32_t prec,
+                       const float* logjoint_in, const float* lse_in, double seed, float* d_alpha,
+                       float* d_mu, float* d_q, float* d_l, double* out, void* ws, size_t ws_bytes,
+                       int32_t* dev_status, gpa_stream_t stream) {
+    int rc = gmm_check(x, alpha, mu, q, l, n, d, k, gamma, prec);
+    if (rc) return rc;
+    if (!d_alpha || !d_mu || !d_q || (d > 1 && !d_l) || !ws) return GPA_ERR_ARG;
+    return vjp_body(x, alpha, mu, q, l, n, d, k, gamma, m, prec, logjoint_in, lse_in, seed, d_alpha, d_mu, d_q,
+                    d_l, out, nullptr, ws, ws_bytes, dev_status, stream);
+}
+
+extern "C" int64_t gpa_gmm_exchange_len(int32_t d, int32_t k) {
+    if (d < 1 || d > 128 || k < 1 || k > 4096) return 0;
+    return gmm_exchange_len(d, k);
+}
+
+extern "C" int gmm_vjp_partial(const float* x, const float* alpha, const float* mu, const float* q,
+                               const float* l, int64_t n, int32_t d, int32_t k, double gamma, int32_t m,
+                               int32_t prec, const float* logjoint_in, const float* lse_in, double seed,
+                               double* exch, void* ws, size_t ws_bytes, int32_t* dev_status,
+                               gpa_stream_t stream) {
+    int rc = gmm_check(x, alpha, mu, q, l, n, d, k, gamma, prec);
+    if (rc) return rc;
+    if (!exch || !ws) return GPA_ERR_ARG;
+    if (((uintptr_t)exch) & 7) return GPA_ERR_ALIGN;
+    return vjp_body(x, alpha, mu, q, l, n, d, k, gamma, m, prec, logjoint_in, lse_in, seed, nullptr, nullptr,
+                    nullptr, nullptr, nullptr, exch, ws, ws_bytes, dev_status, stream);
+}
+
+extern "C" int gmm_vjp_finalize(const float* alpha, const float* mu, const float* q, const float* l,
+                                int64_t n_total, int32_t d, int32_t k, double gamma, int32_t m, int32_t prec,
+                                double seed, const double* exch, float* d_alpha, float* d_mu, float* d_q,
+                                float* d_l, double* out, void* ws, size_t ws_bytes, int32_t* dev_status,
+                                gpa_stream_t stream) {
+    if (!alpha || !mu || !q || (d > 1 && !l) || !exch || !ws) return GPA_ERR_ARG;
+    if (n_total < 1 || d < 1 || d > 128 || k < 1 || k > 4096 || !(gamma > 0.0)) return GPA_ERR_ARG;
+    if (prec != GPA_PREC_FP32 && prec != GPA_PREC_BF16_TC) return GPA_ERR_ARG;
+    if (prec == GPA_PREC_BF16_TC && !gmm_tc_supported(d)) return GPA_ERR_UNSUPPORTED;
+    if (!d_alpha || !d_mu || !d_q || (d > 1 && !d_l)) return GPA_ERR_ARG;
+    if ((((uintptr_t)ws) & 255) || (((uintptr_t)exch) & 7)) return GPA_ERR_ALIGN;
+    const GmmLayout L = gmm_layout(1, d, k, 0);
+    if (ws_bytes < L.off_fwd) return GPA_ERR_WORKSPACE;  // records, scalars, log-prior
+    GmmArgs A{};
+    A.alpha = alpha; A.mu = mu; A.q = q; A.l = l; A.n = n_total; A.d = d; A.k = k; A.gamma = gamma; A.m = m;
+    A.seed = seed; A.out = out; A.d_alpha = d_alpha; A.d_mu = d_mu; A.d_q = d_q; A.d_l = d_l;
+    A.status = dev_status; A.exch_in = exch;
+    return finalize_from_exchange(A, L, (char*)ws, prec == GPA_PREC_BF16_TC ? 1 : 0, (cudaStream_t)stream);
 }

@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(256) batched_fin_kernel(const BInst* __restric
             if (B.out) gmm_objective_finalize_kernel_body(B.fwd, B.ntiles128, B.lpk, B.k, B.scal, B.n, B.d, B.out, 0u);
         } else {
             gmm_finalize_kernel_body<DP>(B.alpha, B.mu, B.q, B.l, B.d, B.k, B.n, B.gamma, B.m, B.seed, B.bS, B.bM,
-                                         B.nchunks, B.scal, B.d_alpha, B.d_mu, B.d_q, B.d_l, 0, (unsigned)w.a);
+                                         B.nchunks, B.scal, B.d_alpha, B.d_mu, B.d_q, B.d_l, 0, nullptr,
+                                         (unsigned)w.a);
         }
         __syncthreads();
     }

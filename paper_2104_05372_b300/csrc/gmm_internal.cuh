@@ -24,6 +24,8 @@ struct GmmArgs {
     const float* lse_in;
     float *d_alpha, *d_mu, *d_q, *d_l;
     int32_t* status;
+    double* exch_out;        // reverse pass: write the shard's exchange vector instead of finishing
+    const double* exch_in;   // finish from a (summed) exchange vector
 };
 
 // Workspace layout (byte offsets, 256-byte aligned) of the FP32 path.
@@ -56,6 +58,8 @@ int gmm_run_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks
 int gmm_run_objective(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s);
 int gmm_run_lse_sum(const float* lse, int64_t n, const GmmLayout& L, char* ws, cudaStream_t s);
 int gmm_bwd_partial_entries(int dp);  // floats of partial S per (chunk, component)
+int64_t gmm_exchange_len(int d, int k);  // doubles of the exchange vector
+int gmm_run_exchange(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, cudaStream_t s);
 
 // Tensor-core (tcgen05, BF16 operands, FP32 accumulate) path.
 bool gmm_tc_supported(int d);

@@ -570,10 +570,14 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
     const float* __restrict__ l, int d, int k, int64_t n, double gamma, int m, double seed,
     const float* __restrict__ partS, const float* __restrict__ partM, int nchunks,
     const double* __restrict__ scal, float* __restrict__ d_alpha, float* __restrict__ d_mu,
-    float* __restrict__ d_q, float* __restrict__ d_l, int centered, unsigned bx) {
+    float* __restrict__ d_q, float* __restrict__ d_l, int centered, const double* __restrict__ exch,
+    unsigned bx) {
     // centered: the partials hold sum r (x - mu)(x - mu)^T and sum r (x - mu)
     // (tensor-core path) instead of the raw moments S and m.
+    // exch: when given, the sums come from an exchange vector (float64, already
+    // combined over chunks and shards) instead of the chunk partials.
     constexpr int NBLK = Bwd<DP>::NBLK;
+    constexpr int E = NBLK * 64 + DP + 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double* Sd = reinterpret_cast<double*>(smem_raw);  // [NBLK*64]
     double* md = Sd + NBLK * 64;                         // [DP+1]
@@ -586,15 +590,20 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
     const float* qk = q + (size_t)kk * d;
     const float* lk = l + (size_t)kk * t;
 
-    for (int e = tid; e < NBLK * 64; e += 256) {
-        double s = 0.0;
-        for (int c = 0; c < nchunks; ++c) s += partS[((int64_t)c * k + kk) * NBLK * 64 + e];
-        Sd[e] = s;
-    }
-    for (int e = tid; e < DP + 1; e += 256) {
-        double s = 0.0;
-        for (int c = 0; c < nchunks; ++c) s += partM[((int64_t)c * k + kk) * (DP + 1) + e];
-        md[e] = s;
+    if (exch) {
+        for (int e = tid; e < NBLK * 64; e += 256) Sd[e] = exch[(size_t)kk * E + e];
+        for (int e = tid; e < DP + 1; e += 256) md[e] = exch[(size_t)kk * E + NBLK * 64 + e];
+    } else {
+        for (int e = tid; e < NBLK * 64; e += 256) {
+            double s = 0.0;
+            for (int c = 0; c < nchunks; ++c) s += partS[((int64_t)c * k + kk) * NBLK * 64 + e];
+            Sd[e] = s;
+        }
+        for (int e = tid; e < DP + 1; e += 256) {
+            double s = 0.0;
+            for (int c = 0; c < nchunks; ++c) s += partM[((int64_t)c * k + kk) * (DP + 1) + e];
+            md[e] = s;
+        }
     }
     for (int e = tid; e < DP * DP; e += 256) {
         const int r = e / DP, c = e % DP;
@@ -655,8 +664,45 @@ __global__ void __launch_bounds__(256) gmm_finalize_kernel(
     const float* __restrict__ l, int d, int k, int64_t n, double gamma, int m, double seed,
     const float* __restrict__ partS, const float* __restrict__ partM, int nchunks,
     const double* __restrict__ scal, float* __restrict__ d_alpha, float* __restrict__ d_mu,
-    float* __restrict__ d_q, float* __restrict__ d_l, int centered) {
-    gmm_finalize_kernel_body<DP>(alpha, mu, q, l, d, k, n, gamma, m, seed, partS, partM, nchunks, scal, d_alpha, d_mu, d_q, d_l, centered, blockIdx.x);
+    float* __restrict__ d_q, float* __restrict__ d_l, int centered, const double* __restrict__ exch) {
+    gmm_finalize_kernel_body<DP>(alpha, mu, q, l, d, k, n, gamma, m, seed, partS, partM, nchunks, scal, d_alpha,
+                                 d_mu, d_q, d_l, centered, exch, blockIdx.x);
+}
+
+// Exchange vector of one shard of points: per component the chunk partial sums
+// [S blocks | m | R] combined in chunk order in float64, then the sum of the
+// shard's per-point logsumexp (tile partials in tile order). Sums of these
+// vectors over shards are the Accum sums of all points (Sec. 2.3.2).
+template <int DP>
+__global__ void __launch_bounds__(256) gmm_exchange_kernel(const float* __restrict__ partS,
+                                                           const float* __restrict__ partM, int nchunks, int k,
+                                                           const double* __restrict__ fwd_part, int64_t ntiles,
+                                                           double* __restrict__ exch) {
+    constexpr int NS = Bwd<DP>::NBLK * 64, E = NS + DP + 1;
+    const int kk = blockIdx.x;
+    if (kk < k) {
+        for (int e = threadIdx.x; e < NS; e += 256) {
+            double s = 0.0;
+            for (int c = 0; c < nchunks; ++c) s += partS[((int64_t)c * k + kk) * NS + e];
+            exch[(size_t)kk * E + e] = s;
+        }
+        for (int e = threadIdx.x; e < DP + 1; e += 256) {
+            double s = 0.0;
+            for (int c = 0; c < nchunks; ++c) s += partM[((int64_t)c * k + kk) * (DP + 1) + e];
+            exch[(size_t)kk * E + NS + e] = s;
+        }
+        return;
+    }
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t t = threadIdx.x; t < ntiles; t += 256) s += fwd_part[t];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) exch[(size_t)k * E] = sh[0];
 }
 
 

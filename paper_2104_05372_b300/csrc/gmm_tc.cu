@@ -674,7 +674,7 @@ int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cud
     if ((rc = convert_inputs<TDP>(A, L, T, ws, s))) return rc;
     if (A.lj_in) {
         if ((rc = launch_tc_bwd<TDP>(A, L, ws, 0, A.n, A.lj_in, A.n, A.lse_in, nchunks, s))) return rc;
-        if (A.out && (rc = gmm_run_lse_sum(A.lse_in, A.n, L, ws, s))) return rc;
+        if ((A.out || A.exch_out) && (rc = gmm_run_lse_sum(A.lse_in, A.n, L, ws, s))) return rc;
     } else {
         // log-joint chunk after the tensor-core area, as large as the workspace allows
         const size_t avail = ws_bytes > T.fixed + 2048 ? ws_bytes - T.fixed - 2048 : 0;
@@ -691,6 +691,7 @@ int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cud
             if ((rc = launch_tc_bwd<TDP>(A, L, ws, c0, nl, lj, P, lse, nchunks, s))) return rc;
         }
     }
+    if (A.exch_out) return gmm_run_exchange(A, L, ws, nchunks, s);
     if ((rc = gmm_run_finalize(A, L, ws, nchunks, 1, s))) return rc;
     if (A.out) return gmm_run_objective(A, L, ws, s);
     return GPA_OK;
