@@ -60,8 +60,12 @@ struct Tc {
     static constexpr uint32_t TAIL = (TDP + 4) * 4;      // b_k, constant, pad
 };
 
+// The dynamic shared array advanced to the next 1024-byte boundary (the
+// 128-byte swizzle atoms need it). The offset is added to the shared array
+// itself, so that the compiler keeps the pointer in the shared address space
+// and accesses through it stay shared-memory instructions.
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
-    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
+    return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
 }
 
 // ---- forward ------------------------------------------------------------------
@@ -258,26 +262,36 @@ __global__ void __launch_bounds__(192, 1)
 
 // ---- backward -----------------------------------------------------------------
 constexpr int BSLOT = 4;                        // 128-row blocks per CTA (4 x 128 TMEM columns)
-constexpr int BPROD = 256;                      // producer threads (8 warps)
+constexpr int BPROD = 512;                      // producer threads (16 warps, a quarter of the points each)
 constexpr int BTHREADS = BPROD + 32;            // + the MMA warp
 template <int TDP>
 struct BwdSm {
     static constexpr int BGC = BSLOT * Tc<TDP>::CPR;                // components per CTA
-    static constexpr uint32_t U = 0;                                // [BSLOT] tiles of 32 KB
-    static constexpr uint32_t SR = U + BSLOT * 2 * ATOM;            // sqrt(r) [BGC][TM] float
+    static constexpr int NUB = TDP == 128 ? 2 : 4;                  // U buffers (cycled over the 4 blocks)
+    static constexpr uint32_t U = 0;                                // [NUB] tiles of 32 KB
+    static constexpr uint32_t XS = U + NUB * 2 * ATOM;              // point tiles [2][TM][d] float
+    static constexpr uint32_t LJ = XS + 2 * TM * TDP * 4;           // log-joint [2][BGC][TM] float
+    static constexpr uint32_t LS = LJ + 2 * BGC * TM * 4;           // lse [2][TM] float
+    static constexpr uint32_t SR = LS + 2 * TM * 4;                 // sqrt(r) [BGC][TM] float
     static constexpr uint32_t MU = SR + BGC * TM * 4;               // mu [BSLOT][128] float
-    static constexpr uint32_t MRED = MU + BSLOT * 128 * 4;          // m' halves [BSLOT][128] float
-    static constexpr uint32_t RSUM = MRED + BSLOT * 128 * 4;        // R per component [BGC] float
-    static constexpr uint32_t BAR = RSUM + BGC * 4;                 // u_full[4], u_empty[4], done
+    static constexpr uint32_t MRED = MU + BSLOT * 128 * 4;          // m' of quarters 1..3 [3][BSLOT][128] float
+    static constexpr uint32_t RSUM = MRED + 3 * BSLOT * 128 * 4;    // R per component [BGC] float
+    static constexpr uint32_t BAR = RSUM + BGC * 4;                 // u_full[NUB], u_empty[NUB], done
     static constexpr uint32_t TMEMP = BAR + 16 * 8;
     static constexpr uint32_t FLAG = TMEMP + 8;  // abort flag, then the producers' decision slot
     static constexpr uint32_t END = FLAG + 8;
     static constexpr size_t SMEM = END + 1024;
+    static_assert(SMEM <= 227 * 1024, "backward shared memory");
 };
 
 __device__ __forceinline__ void producers_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(BPROD) : "memory");
 }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <int TDP>
 __global__ void __launch_bounds__(BTHREADS, 1)
@@ -287,15 +301,18 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                       int nblk64, int32_t* __restrict__ status) {
     using T = Tc<TDP>;
     using S = BwdSm<TDP>;
-    constexpr int BGC = S::BGC;
+    constexpr int BGC = S::BGC, NUB = S::NUB;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::BAR);
     uint64_t* u_full = bars;
-    uint64_t* u_empty = bars + BSLOT;
-    uint64_t* done = bars + 2 * BSLOT;
+    uint64_t* u_empty = bars + NUB;
+    uint64_t* done = bars + 2 * NUB;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sm + S::TMEMP);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + S::FLAG);
+    float* xs = reinterpret_cast<float*>(sm + S::XS);
+    float* ljs = reinterpret_cast<float*>(sm + S::LJ);
+    float* lss = reinterpret_cast<float*>(sm + S::LS);
     float* sr = reinterpret_cast<float*>(sm + S::SR);
     float* mus = reinterpret_cast<float*>(sm + S::MU);
     float* mred = reinterpret_cast<float*>(sm + S::MRED);
@@ -308,7 +325,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     const int64_t t_end = min64(ntiles, t_begin + tiles_per_chunk);
 
     if (tid == 0) {
-        for (int c = 0; c < BSLOT; ++c) {
+        for (int c = 0; c < NUB; ++c) {
             mbar_init(&u_full[c], BPROD / 32);
             mbar_init(&u_empty[c], 1);
         }
@@ -333,24 +350,27 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     const uint32_t tmem = *tmem_holder;
 
     if (warp == BPROD / 32) {
-        // MMA issuer
+        // MMA issuer: block c of tile `it` uses U buffer c % NUB, its use number
+        // u = it * (BSLOT / NUB) + c / NUB giving the barrier phases
         if (lane == 0) {
             bool ok = true;
             int it = 0;
             for (int64_t t = t_begin; ok && t < t_end; ++t, ++it) {
                 for (int c = 0; c < BSLOT; ++c) {
-                    if (!mbar_wait(&u_full[c], (uint32_t)it & 1u, status)) {
+                    const int b = c % NUB;
+                    const uint32_t use = (uint32_t)(it * (BSLOT / NUB) + c / NUB);
+                    if (!mbar_wait(&u_full[b], use & 1u, status)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t ua = smem_u32(sm + S::U + c * 2 * ATOM);
+                    const uint32_t ua = smem_u32(sm + S::U + b * 2 * ATOM);
 #pragma unroll
                     for (int j = 0; j < TM / 16; ++j) {
                         const uint64_t dsc = tc::desc_sw128(ua + (uint32_t)(j >> 2) * ATOM + (uint32_t)(j & 3) * 32u);
                         tc::mma_bf16(tmem + (uint32_t)(c * 128), dsc, dsc, IDESC, (it > 0 || j > 0) ? 1u : 0u);
                     }
-                    tc::mma_commit(&u_empty[c]);
+                    tc::mma_commit(&u_empty[b]);
                 }
             }
             if (!ok) *abort_flag = 1;
@@ -359,10 +379,29 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         __syncwarp();
     } else {
         // producers: thread owns row a' of every block (component a'/TDP of the
-        // block, dimension a'%TDP) and half of the tile's points
+        // block, dimension a'%TDP) and a quarter of the tile's points. Tile t+1
+        // (points, log-joint, lse) is copied into shared memory while tile t is built.
         const int ar = tid & 127;
         const int jr = ar / TDP, a = ar % TDP;
-        const int half = tid >> 7;
+        const int qp = tid >> 7;  // points 32 qp .. 32 qp + 31 of the tile
+        const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+        auto issue = [&](int64_t t, int buf) {
+            const int64_t p0 = t * TM;
+            const int nv = (int)min64(TM, n - p0);
+            float* X = xs + buf * TM * TDP;
+            const float* src = x + p0 * d;
+            if (vec) {
+                for (int e = tid; e < nv * d / 4; e += BPROD) cp_async16(X + 4 * e, src + 4 * e);
+            } else {
+                for (int e = tid; e < nv * d; e += BPROD) cp_async4(X + e, src + e);
+            }
+            float* L = ljs + buf * BGC * TM;
+            for (int e = tid; e < BGC * TM; e += BPROD) {
+                const int c = e / TM, p = e % TM;
+                if (p < nv && kg0 + c < k) cp_async4(L + e, lj + (int64_t)(kg0 + c) * lj_ld + p0 + p);
+            }
+            for (int p = tid; p < nv; p += BPROD) cp_async4(lss + buf * TM + p, lse + p0 + p);
+        };
         float macc[BSLOT];
 #pragma unroll
         for (int c = 0; c < BSLOT; ++c) macc[c] = 0.f;
@@ -370,62 +409,89 @@ __global__ void __launch_bounds__(BTHREADS, 1)
 #pragma unroll
         for (int u = 0; u < BGC * TM / BPROD; ++u) racc[u] = 0.f;
         volatile int* decision = abort_flag + 1;  // written by thread 0 before a barrier, read after it
+        if (t_begin < t_end) issue(t_begin, 0);
+        cp_async_commit();
         int it = 0;
         for (int64_t t = t_begin; t < t_end; ++t, ++it) {
+            const int buf = it & 1;
             const int64_t p0 = t * TM;
-            // x values of this thread: points p0 + half*64 + 0..63, dimension a
-            float xv[64];
-#pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const int64_t p = p0 + half * 64 + j;
-                xv[j] = (p < n && a < d) ? __ldg(x + p * d + a) : 0.f;
-            }
+            // buffer buf ^ 1 was last read in the previous tile, before the barrier that ended it
+            if (t + 1 < t_end) issue(t + 1, buf ^ 1);
+            cp_async_commit();
+            cp_async_wait_one();  // this thread's copies of tile t have landed
             if (tid == 0) *decision = *abort_flag;
-            producers_sync();  // previous tile's sqrt(r) no longer read; decision published
+            producers_sync();     // every thread's copies of tile t are visible; decision published
             if (*decision) break;  // uniform over all producer threads
+            const float* X = xs + buf * TM * TDP;
+            const float* L = ljs + buf * BGC * TM;
+            const float* Ls = lss + buf * TM;
 #pragma unroll
             for (int u = 0; u < BGC * TM / BPROD; ++u) {
                 const int e = tid + u * BPROD;
                 const int c = e / TM, p = e % TM;
                 float v = 0.f;
-                if (p0 + p < n && kg0 + c < k)
-                    v = expf(0.5f * (__ldg(lj + (int64_t)(kg0 + c) * lj_ld + p0 + p) - __ldg(lse + p0 + p)));
+                if (p0 + p < n && kg0 + c < k) v = expf(0.5f * (L[e] - Ls[p]));
                 sr[e] = v;
                 racc[u] += v * v;
             }
-            producers_sync();
+            // x values of this thread: points p0 + 32 qp + 0..31, dimension a (0 past
+            // the end), as pairs of consecutive points
+            f2_t xv[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int p = qp * 32 + 2 * j;
+                xv[j] = f2_pack((p0 + p < n && a < d) ? X[p * d + a] : 0.f,
+                                (p0 + p + 1 < n && a < d) ? X[(p + 1) * d + a] : 0.f);
+            }
+            producers_sync();     // sqrt(r) of tile t complete
 #pragma unroll 1
             for (int c = 0; c < BSLOT; ++c) {
-                if (!mbar_wait_warp(&u_empty[c], ((uint32_t)it & 1u) ^ 1u, status)) {
+                const int b = c % NUB;
+                const uint32_t use = (uint32_t)(it * (BSLOT / NUB) + c / NUB);
+                if (!mbar_wait_warp(&u_empty[b], (use & 1u) ^ 1u, status)) {
                     *abort_flag = 1;  // skip the work; the next decision point stops every warp
                     continue;
                 }
-                uint8_t* ut = sm + S::U + c * 2 * ATOM + half * ATOM;
-                const float* src = sr + (c * T::CPR + jr) * TM + half * 64;
-                const float mc = mus[c * 128 + ar];
-                float mloc = 0.f;
+                // points 32 qp .. +31 are chunks 4 (qp & 1) .. +3 of K atom qp >> 1
+                uint8_t* ut = sm + S::U + b * 2 * ATOM + (qp >> 1) * ATOM;
+                const float4* src = reinterpret_cast<const float4*>(sr + (c * T::CPR + jr) * TM + qp * 32);
+                const f2_t mc = f2_bcast(mus[c * 128 + ar]);
+                // u = sqrt(r) (x - mu) for two points per packed op; m' += sqrt(r) u in
+                // four independent partial sums (no serial chain through the slot)
+                f2_t mq[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < 4; ++j) {
+                    const float4 sa = src[2 * j], sb = src[2 * j + 1];
+                    const f2_t sp[4] = {f2_pack(sa.x, sa.y), f2_pack(sa.z, sa.w), f2_pack(sb.x, sb.y),
+                                        f2_pack(sb.z, sb.w)};
                     uint32_t w4[4];
 #pragma unroll
-                    for (int i = 0; i < 8; i += 2) {
-                        const float s0 = src[j * 8 + i], s1 = src[j * 8 + i + 1];
-                        const float u0 = s0 * (xv[j * 8 + i] - mc), u1 = s1 * (xv[j * 8 + i + 1] - mc);
-                        mloc = fmaf(s0, u0, fmaf(s1, u1, mloc));
-                        w4[i >> 1] = tc::pack_bf16x2(u0, u1);
+                    for (int i = 0; i < 4; ++i) {
+                        const f2_t u = f2_mul(sp[i], f2_sub(xv[4 * j + i], mc));
+                        mq[i] = f2_fma(sp[i], u, mq[i]);
+                        const float2 uf = f2_unpack(u);
+                        w4[i] = tc::pack_bf16x2(uf.x, uf.y);
                     }
-                    *reinterpret_cast<uint4*>(ut + tc::sw128_offset((uint32_t)ar, (uint32_t)j)) =
+                    *reinterpret_cast<uint4*>(ut + tc::sw128_offset((uint32_t)ar, (uint32_t)(4 * (qp & 1) + j))) =
                         make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                }
+                float mloc = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 v = f2_unpack(mq[i]);
+                    mloc += v.x + v.y;
                 }
                 macc[c] += mloc;
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&u_full[c]);
+                if (lane == 0) tc::mbar_arrive(&u_full[b]);
             }
+            producers_sync();     // tile t's shared buffers (points, sqrt(r)) no longer read
         }
-        // m' halves
-        if (half == 1)
-            for (int c = 0; c < BSLOT; ++c) mred[c * 128 + ar] = macc[c];
+        cp_async_wait_all();  // no copy may land after the block exits
+        // m' of quarters 1..3 for quarter 0 to add
+        if (qp > 0)
+            for (int c = 0; c < BSLOT; ++c) mred[(qp - 1) * BSLOT * 128 + c * 128 + ar] = macc[c];
         // R per component
 #pragma unroll
         for (int u = 0; u < BGC * TM / BPROD; ++u) {
@@ -434,16 +500,17 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         }
         producers_sync();
         const int64_t cbase = (int64_t)blockIdx.y * k;
-        if (half == 0) {
+        if (qp == 0) {
             for (int c = 0; c < BSLOT; ++c) {
                 const int kg = kg0 + c * T::CPR + jr;
                 if (kg >= k) continue;
                 float* M = partM + (cbase + kg) * (TDP + 1);
-                M[a] += seed * (macc[c] + mred[c * 128 + ar]);
+                const float* mr = mred + c * 128 + ar;
+                M[a] += seed * (macc[c] + mr[0] + mr[BSLOT * 128] + mr[2 * BSLOT * 128]);
                 if (a == 0) M[TDP] += seed * rsum[c * T::CPR + jr];
             }
         }
-        // accumulators: warp w reads TMEM lanes of its quarter for blocks w/4 and w/4 + 2;
+        // accumulators: warp w reads TMEM lanes of its quarter w % 4 for block w / 4;
         // row a' = lane index, the component's columns are [jr*TDP, jr*TDP + TDP)
         const bool fin = mbar_wait_warp(done, 0, status);
         if (!fin) *abort_flag = 1;
@@ -454,10 +521,9 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             const int qtr = warp & 3;
             const int row = qtr * 32 + lane;      // row a' of the block
             const int jw = row / TDP, aw = row % TDP;  // the same jw for the whole warp
-            for (int cc = 0; cc < 2; ++cc) {
-                const int c = (warp >> 2) + 2 * cc;
-                const int kg = kg0 + c * T::CPR + jw;
-                if (kg >= k) continue;
+            const int c = warp >> 2;
+            const int kg = kg0 + c * T::CPR + jw;
+            if (kg < k) {
                 float* Sp = partS + (cbase + kg) * (int64_t)nblk64;
 #pragma unroll 1
                 for (int ch = 0; ch < TDP / 32; ++ch) {
