@@ -267,10 +267,10 @@ constexpr int BTHREADS = BPROD + 32;            // + the MMA warp
 template <int TDP>
 struct BwdSm {
     static constexpr int BGC = BSLOT * Tc<TDP>::CPR;                // components per CTA
-    static constexpr int NUB = TDP == 128 ? 2 : 4;                  // U buffers (cycled over the 4 blocks)
+    static constexpr int NUB = 4;                                   // U buffers (cycled over the 4 blocks)
     static constexpr uint32_t U = 0;                                // [NUB] tiles of 32 KB
-    static constexpr uint32_t XS = U + NUB * 2 * ATOM;              // point tiles [2][TM][d] float
-    static constexpr uint32_t LJ = XS + 2 * TM * TDP * 4;           // log-joint [2][BGC][TM] float
+    static constexpr uint32_t XS = U + NUB * 2 * ATOM;              // point tile [TM][d] float
+    static constexpr uint32_t LJ = XS + TM * TDP * 4;               // log-joint [2][BGC][TM] float
     static constexpr uint32_t LS = LJ + 2 * BGC * TM * 4;           // lse [2][TM] float
     static constexpr uint32_t SR = LS + 2 * TM * 4;                 // sqrt(r) [BGC][TM] float
     static constexpr uint32_t MU = SR + BGC * TM * 4;               // mu [BSLOT][128] float
@@ -291,7 +291,6 @@ __device__ __forceinline__ void producers_sync() {
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <int TDP>
 __global__ void __launch_bounds__(BTHREADS, 1)
@@ -380,7 +379,9 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     } else {
         // producers: thread owns row a' of every block (component a'/TDP of the
         // block, dimension a'%TDP) and a quarter of the tile's points. Tile t+1
-        // (points, log-joint, lse) is copied into shared memory while tile t is built.
+        // (points, log-joint, lse) is copied into shared memory while tile t is
+        // built: the point tile has one buffer, free once every thread holds its
+        // column of it in registers.
         const int ar = tid & 127;
         const int jr = ar / TDP, a = ar % TDP;
         const int qp = tid >> 7;  // points 32 qp .. 32 qp + 31 of the tile
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         auto issue = [&](int64_t t, int buf) {
             const int64_t p0 = t * TM;
             const int nv = (int)min64(TM, n - p0);
-            float* X = xs + buf * TM * TDP;
+            float* X = xs;
             const float* src = x + p0 * d;
             if (vec) {
                 for (int e = tid; e < nv * d / 4; e += BPROD) cp_async16(X + 4 * e, src + 4 * e);
@@ -415,14 +416,13 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         for (int64_t t = t_begin; t < t_end; ++t, ++it) {
             const int buf = it & 1;
             const int64_t p0 = t * TM;
-            // buffer buf ^ 1 was last read in the previous tile, before the barrier that ended it
-            if (t + 1 < t_end) issue(t + 1, buf ^ 1);
-            cp_async_commit();
-            cp_async_wait_one();  // this thread's copies of tile t have landed
+            cp_async_wait_all();  // this thread's copies of tile t have landed
             if (tid == 0) *decision = *abort_flag;
-            producers_sync();     // every thread's copies of tile t are visible; decision published
+            // every thread's copies of tile t are visible, every thread is done with
+            // tile t-1 (its sqrt(r) may be overwritten); decision published
+            producers_sync();
             if (*decision) break;  // uniform over all producer threads
-            const float* X = xs + buf * TM * TDP;
+            const float* X = xs;
             const float* L = ljs + buf * BGC * TM;
             const float* Ls = lss + buf * TM;
 #pragma unroll
@@ -443,7 +443,9 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 xv[j] = f2_pack((p0 + p < n && a < d) ? X[p * d + a] : 0.f,
                                 (p0 + p + 1 < n && a < d) ? X[(p + 1) * d + a] : 0.f);
             }
-            producers_sync();     // sqrt(r) of tile t complete
+            producers_sync();     // sqrt(r) of tile t complete, the point tile read by all
+            if (t + 1 < t_end) issue(t + 1, buf ^ 1);  // log-joint buffer buf ^ 1 last read in tile t-1
+            cp_async_commit();
 #pragma unroll 1
             for (int c = 0; c < BSLOT; ++c) {
                 const int b = c % NUB;
@@ -486,7 +488,6 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&u_full[b]);
             }
-            producers_sync();     // tile t's shared buffers (points, sqrt(r)) no longer read
         }
         cp_async_wait_all();  // no copy may land after the block exits
         // m' of quarters 1..3 for quarter 0 to add
