@@ -145,6 +145,25 @@ GPA_API int gmm_vjp(const float* x, const float* alpha, const float* mu, const f
             float* d_mu, float* d_q, float* d_l, double* out, void* ws, size_t ws_bytes,
             int32_t* dev_status, gpa_stream_t stream);
 
+/*
+ * Forward-mode directional derivative (linearize, Sec. 5.1):
+ * *df_out = df(theta)[v] = d/de f(theta + e v) at e = 0 for the direction
+ * v = (v_alpha [K], v_mu [K][D], v_q [K][D], v_l [K][T]) (device float32, the
+ * parameters' layouts). The tangents ride along the forward pass point by
+ * point: z_ik and its tangent Qd_k (x_i - mu_k) - Q_k v_mu_k, s_ik and its
+ * tangent, and an online logsumexp over k with its tangent. Optional outputs:
+ * *f_out = f (device float64, nullable) and lse_dot_out [N] (device float32,
+ * nullable) = the tangent of logsumexp_k s_ik per point. FP32 arithmetic, sums
+ * over points in float64 per 128-point tile in a fixed order.
+ * <grad f, v> (gmm_vjp) equals df[v] (Sec. 5.2) up to rounding.
+ */
+GPA_API size_t gpa_gmm_jvp_workspace_bytes(int64_t n, int32_t d, int32_t k); /* 0 on bad arguments */
+GPA_API int gmm_jvp(const float* x, const float* alpha, const float* mu, const float* q, const float* l,
+                    int64_t n, int32_t d, int32_t k, double gamma, int32_t m, const float* v_alpha,
+                    const float* v_mu, const float* v_q, const float* v_l, double* df_out, double* f_out,
+                    float* lse_dot_out, void* ws, size_t ws_bytes, int32_t* dev_status,
+                    gpa_stream_t stream);
+
 /* ------------------------------------------------------------------------- */
 /* Data-parallel GMM gradient: points sharded over ranks                      */
 /* ------------------------------------------------------------------------- */

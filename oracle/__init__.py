@@ -66,7 +66,7 @@ def _load():
                 [f64p] * 4
             lib.oracle_gmm_finish.restype = D
             lib.oracle_gmm_grad.restype = D
-            lib.oracle_gmm_jvp.argtypes = [f32p] * 5 + [I64, I32, I32, D, I32] + [f64p] * 4 + [vp]
+            lib.oracle_gmm_jvp.argtypes = [f32p] * 5 + [I64, I32, I32, D, I32] + [f64p] * 4 + [vp, vp]
             lib.oracle_gmm_jvp.restype = D
             lib.oracle_reproj_residual.argtypes = [f32p, f32p, i32p, f32p, I32, I32, I64, f64p]
             lib.oracle_reproj_residual.restype = I64
@@ -150,14 +150,15 @@ def gmm_finish(g, n_total: int, sums, seed: float = 1.0):
     return f, da, dm, dq, dl
 
 
-def gmm_jvp(g, va, vm, vq, vl):
-    """(df[v], f)."""
+def gmm_jvp(g, va, vm, vq, vl, want_lse_dot: bool = False):
+    """(df[v], f), and the per-point tangent of logsumexp_k s_ik when asked."""
     lib = _load()
     fo = C.c_double()
+    ld = np.empty(g.n, np.float64) if want_lse_dot else None
     df = lib.oracle_gmm_jvp(*_gmm_args(g), g.n, g.d, g.k, g.gamma, g.m, _c(va, np.float64),
                             _c(vm, np.float64), _c(vq, np.float64), _c(vl, np.float64),
-                            C.addressof(fo))
-    return df, fo.value
+                            C.addressof(fo), None if ld is None else ld.ctypes.data)
+    return (df, fo.value, ld) if want_lse_dot else (df, fo.value)
 
 
 def reproj_residual(r):

@@ -304,12 +304,13 @@ double oracle_gmm_grad(const float* x, const float* alpha, const float* mu, cons
 /*
  * Directional derivative df(theta)[v] by forward mode (linearize, Sec. 5.1)
  * (parity pinned: central finite differences along v, tests). Returns df; the
- * objective goes to *f_out when given.
+ * objective goes to *f_out and the per-point tangent of logsumexp_k s_ik to
+ * lse_dot_out when given.
  */
 double oracle_gmm_jvp(const float* x, const float* alpha, const float* mu, const float* q,
                       const float* l, int64_t n, int d, int k, double gamma, int m,
                       const double* v_alpha, const double* v_mu, const double* v_q,
-                      const double* v_l, double* f_out) {
+                      const double* v_l, double* f_out, double* lse_dot_out /* n, nullable */) {
     const int t = d * (d - 1) / 2;
     double* Q = (double*)malloc(sizeof(double) * (size_t)k * d * d);
     double* QD = (double*)calloc((size_t)k * d * d, sizeof(double)); /* tangent of Q */
@@ -352,6 +353,7 @@ double oracle_gmm_jvp(const float* x, const float* alpha, const float* mu, const
             ll += lse;
             double dd = 0.0;
             for (int kk = 0; kk < k; ++kk) dd += exp(s[kk] - lse) * sd[kk];
+            if (lse_dot_out) lse_dot_out[i] = dd; /* tangent of logsumexp_k s_ik */
             tot += dd;
         }
         free(s); free(sd); free(xc);

@@ -43,6 +43,8 @@ _SIGS = {
     "gmm_objective": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P, _P], _I32),
     "gmm_vjp": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _P, _P, _D, _P, _P, _P, _P, _P, _P, _SZ, _P, _P],
                 _I32),
+    "gpa_gmm_jvp_workspace_bytes": ([_I64, _I32, _I32], _SZ),
+    "gmm_jvp": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32] + [_P] * 4 + [_P, _P, _P, _P, _SZ, _P, _P], _I32),
     "gpa_gmm_exchange_len": ([_I32, _I32], _I64),
     "gmm_vjp_partial": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _P, _P, _D, _P, _P, _SZ, _P, _P], _I32),
     "gmm_vjp_finalize": ([_P] * 4 + [_I64, _I32, _I32, _D, _I32, _I32, _D, _P, _P, _P, _P, _P, _P, _P, _SZ, _P,
@@ -213,6 +215,31 @@ def gmm_vjp(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, logjoint_in=None
                         _ptr(d_l), _ptr(out), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "gmm_vjp")
     return d_alpha, d_mu, d_q, d_l
+
+
+def gmm_jvp(x, alpha, mu, q, l, v_alpha, v_mu, v_q, v_l, gamma=1.0, m=0, df_out=None, f_out=None,
+            lse_dot_out=None, ws=None, status=None, stream=None):
+    """Directional derivative df[v] into ``df_out`` (device float64 [1]); returns it."""
+    n, d, k = _gmm_params(x, alpha, mu, q, l)
+    t = d * (d - 1) // 2
+    dev = x.device
+    _check(v_alpha, torch.float32, "v_alpha", (k,))
+    _check(v_mu, torch.float32, "v_mu", (k, d))
+    _check(v_q, torch.float32, "v_q", (k, d))
+    _check(v_l, torch.float32, "v_l", (k, t))
+    df_out = torch.empty(1, dtype=torch.float64, device=dev) if df_out is None else _check(df_out, torch.float64,
+                                                                                          "df_out")
+    if f_out is not None:
+        _check(f_out, torch.float64, "f_out")
+    if lse_dot_out is not None:
+        _check(lse_dot_out, torch.float32, "lse_dot_out", (n,))
+    if ws is None:
+        ws = workspace(int(load().gpa_gmm_jvp_workspace_bytes(n, d, k)), dev)
+    rc = load().gmm_jvp(_ptr(x), _ptr(alpha), _ptr(mu), _ptr(q), _ptr(l), n, d, k, float(gamma), int(m),
+                        _ptr(v_alpha), _ptr(v_mu), _ptr(v_q), _ptr(v_l), _ptr(df_out), _ptr(f_out),
+                        _ptr(lse_dot_out), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "gmm_jvp")
+    return df_out
 
 
 def gpa_gmm_exchange_len(d, k) -> int:

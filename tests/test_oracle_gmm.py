@@ -157,9 +157,24 @@ def test_jvp_matches_central_difference_along_direction():
         return (fp - fm) / (2 * step)
 
     fd = (4.0 * central(h / 2) - central(h)) / 3.0
-    df, f = oracle.gmm_jvp(g, *vs)
+    df, f, lse_dot = oracle.gmm_jvp(g, *vs, want_lse_dot=True)
     assert abs(f - oracle.gmm_objective(g)) < 1e-9 * abs(f)
     assert abs(df - fd) <= 1e-8 * abs(fd), (df, fd)
+
+    # per point: the tangent of logsumexp_k s_ik against the same differences
+    def central_lse(step):
+        for b, v in zip(blocks, vs):
+            setattr(g, b, (saved[b] + step * v).astype(np.float32))
+        lp = oracle.gmm_objective(g, want_lse=True)[1]
+        for b, v in zip(blocks, vs):
+            setattr(g, b, (saved[b] - step * v).astype(np.float32))
+        lm = oracle.gmm_objective(g, want_lse=True)[1]
+        for b in blocks:
+            setattr(g, b, saved[b])
+        return (lp - lm) / (2 * step)
+
+    fd_lse = (4.0 * central_lse(h / 2) - central_lse(h)) / 3.0
+    assert np.max(np.abs(lse_dot - fd_lse)) <= 1e-7 * np.max(np.abs(fd_lse))
 
 
 def test_dot_product_reverse_equals_forward():
