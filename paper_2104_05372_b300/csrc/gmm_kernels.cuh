@@ -54,11 +54,6 @@ struct Bwd {
 // ---------------------------------------------------------------------------
 // A0: parameter expansion (one CTA per component)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double log_mvgamma(int dd, double a) {
-    double s = 0.25 * dd * (dd - 1) * log(3.14159265358979323846);
-    for (int j = 1; j <= dd; ++j) s += lgamma(a + 0.5 * (1 - j));
-    return s;
-}
 
 template <int DP>
 __device__ __forceinline__ void gmm_prep_kernel_body(const float* __restrict__ alpha,
@@ -84,52 +79,73 @@ __device__ __forceinline__ void gmm_prep_kernel_body(const float* __restrict__ a
         const int c = e / DP, r = e % DP;
         R[e] = Qrc(r, c);  // transposed: Qt[c][r]
     }
-    for (int r = threadIdx.x; r < DP; r += blockDim.x) {
+    // b = Q mu: one warp per row, lanes over the row's columns (coalesced reads of l)
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < DP; r += nw) {
         double s = 0.0;
         if (r < d)
-            for (int c = 0; c <= r; ++c) s += (double)Qrc(r, c) * (double)muk[c];
-        R[DP * DP + r] = (float)s;
+            for (int c = lane; c <= r; c += 32) s += (double)Qrc(r, c) * (double)muk[c];
+        s = warp_sum(s);
+        if (lane == 0) R[DP * DP + r] = (float)s;
     }
     // log-prior of this component and the constant alpha_k + sum_d q_kd
-    double sq = 0.0, fro = 0.0;
+    const double nn = (double)(d + m + 1);
+    double sq = 0.0, fro = 0.0, lg = 0.0;
     for (int r = threadIdx.x; r < d; r += blockDim.x) {
         const double qv = qk[r];
         sq += qv;
         fro += exp(2.0 * qv);
+        lg += lgamma(0.5 * nn + 0.5 * (double)(-r));  // log Gamma_D(n/2) term j = r + 1
     }
     for (int j = threadIdx.x; j < t; j += blockDim.x) {
         const double lv = lk[j];
         fro += lv * lv;
     }
-    __shared__ double red[2][8];  // up to 256 threads
+    // logsumexp(alpha) (used once, by component 0's block)
+    double amax = -INFINITY;
+    if (kk == 0)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) amax = fmax(amax, (double)alpha[i]);
+    __shared__ double red[4][8];  // up to 256 threads
     sq = warp_sum(sq);
     fro = warp_sum(fro);
-    if ((threadIdx.x & 31) == 0) {
+    lg = warp_sum(lg);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) {
         red[0][threadIdx.x >> 5] = sq;
         red[1][threadIdx.x >> 5] = fro;
+        red[2][threadIdx.x >> 5] = lg;
+        red[3][threadIdx.x >> 5] = amax;
     }
+    __syncthreads();
+    double mx = -INFINITY;
+    for (int w = 0; w < nw; ++w) mx = fmax(mx, red[3][w]);
+    double ae = 0.0;
+    if (kk == 0)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) ae += exp((double)alpha[i] - mx);
+    ae = warp_sum(ae);
+    __syncthreads();  // everyone has read red[3]
+    if (lane == 0) red[3][threadIdx.x >> 5] = ae;
     __syncthreads();
     if (threadIdx.x == 0) {
         sq = 0.0;
         fro = 0.0;
-        for (unsigned w = 0; w < blockDim.x / 32; ++w) {
+        lg = 0.0;
+        ae = 0.0;
+        for (int w = 0; w < nw; ++w) {
             sq += red[0][w];
             fro += red[1][w];
+            lg += red[2][w];
+            ae += red[3][w];
         }
         R[DP * DP + DP] = (float)((double)alpha[kk] + sq);
         R[DP * DP + DP + 1] = 0.f;
         R[DP * DP + DP + 2] = 0.f;
         R[DP * DP + DP + 3] = 0.f;
-        const double nn = (double)(d + m + 1);
-        const double cw = nn * d * log(gamma) - 0.5 * nn * d * log(2.0) - log_mvgamma(d, 0.5 * nn);
+        const double log_mvg = 0.25 * d * (d - 1) * log(3.14159265358979323846) + lg;
+        const double cw = nn * d * log(gamma) - 0.5 * nn * d * log(2.0) - log_mvg;
         lpk[kk] = (double)m * sq - 0.5 * gamma * gamma * fro + cw;
-        if (kk == 0) {
-            double mx = -INFINITY;
-            for (int i = 0; i < k; ++i) mx = fmax(mx, (double)alpha[i]);
-            double s = 0.0;
-            for (int i = 0; i < k; ++i) s += exp((double)alpha[i] - mx);
-            scal[0] = mx + log(s);
-        }
+        if (kk == 0) scal[0] = mx + log(ae);
     }
 }
 
