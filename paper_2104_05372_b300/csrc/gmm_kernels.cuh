@@ -441,8 +441,14 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
     }
     const bool active = (tid < C::NDIAG_T + C::NOFF_T) && (kg0 + kk < k);
 
-    // asynchronous copies of tile t into buffer buf (no registers involved)
-    auto issue = [&](int64_t t, int buf) {
+    // Pipeline. The diagonal-block threads (whole warps, NDIAG_T of them) do
+    // less arithmetic per point than the off-diagonal ones, so they also carry
+    // the per-tile side work while the others accumulate: they copy the next
+    // tile's log-joint and lse columns (cp.async, so their own wait covers
+    // them) and turn them into the cotangents r. Every thread copies its share
+    // of the next point tile. One block barrier per tile.
+    constexpr int ND = C::NDIAG_T;
+    auto issue_x = [&](int64_t t, int buf) {
         const int64_t p0 = t * TPB;
         const int nv = (int)min64(TPB, n - p0);
         float* X = Xs + buf * TPB * XST;
@@ -450,28 +456,33 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
             const int p = e / d, c = e - p * d;
             cp_async4(X + p * XST + bwd_swz(c), x + (p0 + p) * d + c);
         }
+    };
+    auto issue_lj = [&](int64_t t, int buf) {  // diagonal threads only
+        const int64_t p0 = t * TPB;
+        const int nv = (int)min64(TPB, n - p0);
         float* L = rawlj + buf * GC * TPB;
-        for (int e = tid; e < GC * TPB; e += C::THREADS) {
+        for (int e = tid; e < GC * TPB; e += ND) {
             const int kc = e / TPB, p = e % TPB;
             if (p < nv && kg0 + kc < k) cp_async4(L + e, lj + (int64_t)(kg0 + kc) * lj_ld + p0 + p);
         }
         float* S = rawlse + buf * TPB;
-        for (int p = tid; p < nv; p += C::THREADS) cp_async4(S + p, lse + p0 + p);
+        for (int p = tid; p < nv; p += ND) cp_async4(S + p, lse + p0 + p);
     };
     // cotangents r = seed exp(s - lse) of tile t from buffer buf; 0 on the ragged tail
-    auto make_r = [&](int64_t t, int buf) {
+    auto make_r = [&](int64_t t, int buf) {  // diagonal threads only
         const int64_t p0 = t * TPB;
         const int nv = (int)min64(TPB, n - p0);
         const float* L = rawlj + buf * GC * TPB;
         const float* S = rawlse + buf * TPB;
         float* R = rs + buf * TPB * GC;
-        for (int e = tid; e < GC * TPB; e += C::THREADS) {
+        for (int e = tid; e < GC * TPB; e += ND) {
             const int kc = e / TPB, p = e % TPB;
             float r = 0.f;
             if (p < nv && kg0 + kc < k) r = seed * expf(L[e] - S[p]);
             R[p * GC + kc] = r;
         }
     };
+    auto diag_sync = [] { asm volatile("bar.sync 2, %0;" ::"n"(ND) : "memory"); };
 
     for (int e = tid; e < 2 * TPB * XST; e += C::THREADS) Xs[e] = 0.f;
     __syncthreads();
@@ -486,13 +497,19 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
     }
 
-    // pipeline: tile t+1 in shared memory and tile t+2 in flight while t is accumulated
-    if (t_begin < t_end) issue(t_begin, 0);
+    // prologue: tile t_begin in shared memory with its r, tile t_begin+1 in flight
+    if (t_begin < t_end) {
+        issue_x(t_begin, 0);
+        if (diag) issue_lj(t_begin, 0);
+    }
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    if (t_begin < t_end) make_r(t_begin, 0);
-    if (t_begin + 1 < t_end) issue(t_begin + 1, 1);
+    if (diag && t_begin < t_end) make_r(t_begin, 0);
+    if (t_begin + 1 < t_end) {
+        issue_x(t_begin + 1, 1);
+        if (diag) issue_lj(t_begin + 1, 1);
+    }
     cp_async_commit();
     __syncthreads();
 
@@ -506,7 +523,7 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
             const float* xb = Xb + 8 * b;
             const int ha = ((a >> 2) & 1) << 2, hb = ((b >> 2) & 1) << 2;
             if (diag) {
-#pragma unroll 2
+#pragma unroll 1
                 for (int p = 0; p < TPB; ++p) {
                     const float4 a0 = *reinterpret_cast<const float4*>(xa + p * XST + ha);
                     const float4 a1 = *reinterpret_cast<const float4*>(xa + p * XST + (4 ^ ha));
@@ -545,11 +562,16 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
             }
         }
         cp_async_wait_all();  // this thread's copies of tile t+1 have landed
-        __syncthreads();      // every thread's, and nobody reads buffer `buf` any more
-        if (t + 1 < t_end) make_r(t + 1, buf ^ 1);
-        if (t + 2 < t_end) issue(t + 2, buf);
+        if (diag && t + 1 < t_end) {
+            diag_sync();          // every diagonal thread's log-joint copies of tile t+1 are visible
+            make_r(t + 1, buf ^ 1);
+        }
+        __syncthreads();      // tile t+1 and its r complete; nobody reads buffer `buf` any more
+        if (t + 2 < t_end) {
+            issue_x(t + 2, buf);
+            if (diag) issue_lj(t + 2, buf);
+        }
         cp_async_commit();
-        __syncthreads();      // r of tile t+1 complete
     }
     if (!active) return;
     const int kg = kg0 + kk;
