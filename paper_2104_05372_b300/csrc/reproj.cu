@@ -99,25 +99,54 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 // The first NF floats of the record of camera ci, with 16-byte loads (records
 // are 128 B apart and the workspace is 256-byte aligned).
+// The first NF floats of camera ci's record (128-byte aligned) in 32-byte loads:
+// one sector per lane per load instruction (16-byte loads would fetch every
+// sector of a gathered record twice).
 template <int NF>
 __device__ __forceinline__ void load_cam(const float* __restrict__ rec, int ci, float (&cam)[kCamRec]) {
-    const float4* p = reinterpret_cast<const float4*>(rec + (size_t)ci * kCamRec);
+    const float* p = rec + (size_t)ci * kCamRec;
 #pragma unroll
-    for (int i = 0; i < NF / 4; ++i) {
-        const float4 v = __ldg(p + i);
-        cam[4 * i] = v.x;
-        cam[4 * i + 1] = v.y;
-        cam[4 * i + 2] = v.z;
-        cam[4 * i + 3] = v.w;
-    }
+    for (int i = 0; i < (NF + 7) / 8; ++i)
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(cam[8 * i]), "=f"(cam[8 * i + 1]), "=f"(cam[8 * i + 2]), "=f"(cam[8 * i + 3]),
+              "=f"(cam[8 * i + 4]), "=f"(cam[8 * i + 5]), "=f"(cam[8 * i + 6]), "=f"(cam[8 * i + 7])
+            : "l"(p + 8 * i));
 }
 
 // d_pts[pi][0..2] += g with one 8-byte vector reduction and one scalar one: row
 // pi starts 12*pi bytes in, 8-byte aligned for even pi (pair first) and 4 bytes
 // off for odd pi (scalar first).
-__device__ __forceinline__ void red_add_point(float* __restrict__ d_pts, int pi, const float (&g)[3]) {
+// Point pi of a [P][3] array: one float2 and one float load when the array is
+// 8-byte aligned (which half is 8-byte aligned follows the parity of pi),
+// three float loads otherwise.
+__device__ __forceinline__ void load_point(const float* __restrict__ pts, int pi, bool al8, float& X0, float& X1,
+                                           float& X2) {
+    const float* X = pts + (size_t)pi * 3;
+    if (!al8) {
+        X0 = __ldg(X);
+        X1 = __ldg(X + 1);
+        X2 = __ldg(X + 2);
+    } else if ((pi & 1) == 0) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(X));
+        X0 = v.x;
+        X1 = v.y;
+        X2 = __ldg(X + 2);
+    } else {
+        X0 = __ldg(X);
+        const float2 v = __ldg(reinterpret_cast<const float2*>(X + 1));
+        X1 = v.x;
+        X2 = v.y;
+    }
+}
+
+// d_pts[pi] += g directly: float2 + float atomics when d_pts is 8-byte aligned.
+__device__ __forceinline__ void red_add_point(float* __restrict__ d_pts, int pi, const float (&g)[3], bool al8) {
     float* dp = d_pts + (size_t)pi * 3;
-    if ((pi & 1) == 0) {
+    if (!al8) {
+        atomicAdd(dp, g[0]);
+        atomicAdd(dp + 1, g[1]);
+        atomicAdd(dp + 2, g[2]);
+    } else if ((pi & 1) == 0) {
         atomicAdd(reinterpret_cast<float2*>(dp), make_float2(g[0], g[1]));
         atomicAdd(dp + 2, g[2]);
     } else {
@@ -235,7 +264,7 @@ __global__ void __launch_bounds__(256) reproj_jvp_kernel(const float* __restrict
                                                          const int2* __restrict__ obs, const float* __restrict__ v_cams,
                                                          const float* __restrict__ v_pts, int n_cams, int n_pts,
                                                          int64_t n_obs, float2* __restrict__ jv_out,
-                                                         int32_t* __restrict__ status) {
+                                                         int32_t* __restrict__ status, int pts8) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_obs; j += stride) {
         const int2 o = __ldg(obs + j);
@@ -246,8 +275,9 @@ __global__ void __launch_bounds__(256) reproj_jvp_kernel(const float* __restrict
         }
         float rc[kCamRec];
         load_cam<kCamRec>(rec, o.x, rc);
-        const float* X = pts + (size_t)o.y * 3;
-        const Proj P = project(rc, __ldg(X), __ldg(X + 1), __ldg(X + 2));
+        float X0, X1, X2;
+        load_point(pts, o.y, pts8, X0, X1, X2);
+        const Proj P = project(rc, X0, X1, X2);
         float vc[11], vx[3], jv[2];
 #pragma unroll
         for (int i = 0; i < 11; ++i) vc[i] = __ldg(v_cams + (size_t)o.x * 11 + i);
@@ -261,7 +291,7 @@ __global__ void __launch_bounds__(256) reproj_jvp_kernel(const float* __restrict
 __global__ void __launch_bounds__(256) reproj_residual_kernel(
     const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
     const float2* __restrict__ tgt, int n_cams, int n_pts, int64_t n_obs, float2* __restrict__ res,
-    int32_t* __restrict__ status) {
+    int32_t* __restrict__ status, int pts8) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_obs; j += stride) {
         const int2 o = __ldg(obs + j);
@@ -272,8 +302,9 @@ __global__ void __launch_bounds__(256) reproj_residual_kernel(
         }
         float rc[kCamRec];
         load_cam<kCamResid>(rec, o.x, rc);
-        const float* X = pts + (size_t)o.y * 3;
-        const Proj P = project(rc, __ldg(X), __ldg(X + 1), __ldg(X + 2));
+        float X0, X1, X2;
+        load_point(pts, o.y, pts8, X0, X1, X2);
+        const Proj P = project(rc, X0, X1, X2);
         const float2 t = __ldg(tgt + j);
         res[j] = make_float2(P.out[0] - t.x, P.out[1] - t.y);
     }
@@ -284,9 +315,11 @@ template <int STRAT, bool FUSED>
 __global__ void __launch_bounds__(256) reproj_vjp_kernel(
     const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
     const float2* __restrict__ wv, const float2* __restrict__ tgt, float wscale, int n_cams, int n_pts,
-    int64_t n_obs, const int32_t* __restrict__ perm, const int32_t* __restrict__ key_s,
-    const int32_t* __restrict__ aux_s, float* __restrict__ d_cams, float* __restrict__ d_pts,
-    float2* __restrict__ res, int32_t* __restrict__ status) {
+    int64_t n_obs, float* __restrict__ d_cams, float* __restrict__ d_pts,
+    float4* __restrict__ d_pts4, float2* __restrict__ res, int32_t* __restrict__ status, int pts8, int dpts8) {
+    static_assert(STRAT == GPA_SCATTER_ATOMIC || STRAT == GPA_SCATTER_WARPAGG, "SORT has its own kernel");
+    // point cotangents: into the 16-byte padded accumulators d_pts4 (one vector
+    // atomic per observation) when given, else straight into d_pts
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     // trip count is uniform over the block so that every lane reaches the shuffles
@@ -296,16 +329,9 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
         int64_t e = pos;  // element id
         int ci = -1, pi = -1;
         if (valid) {
-            if (STRAT == GPA_SCATTER_SORT) {
-                e = __ldg(perm + pos);
-                ci = __ldg(key_s + pos);
-                pi = __ldg(aux_s + pos);
-                if (e < 0 || e >= n_obs) ci = -1;  // not a plan of these observations
-            } else {
-                const int2 o = __ldg(obs + pos);
-                ci = o.x;
-                pi = o.y;
-            }
+            const int2 o = __ldg(obs + pos);
+            ci = o.x;
+            pi = o.y;
             if (ci < 0 || ci >= n_cams || pi < 0 || pi >= n_pts) {
                 if (FUSED) res[e] = make_float2(NAN, NAN);
                 report(status, GPA_ERR_INDEX);
@@ -319,8 +345,9 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
         if (valid) {
             float rc[kCamRec];
             load_cam<kCamRec>(rec, ci, rc);
-            const float* X = pts + (size_t)pi * 3;
-            const Proj P = project(rc, __ldg(X), __ldg(X + 1), __ldg(X + 2));
+            float X0, X1, X2;
+            load_point(pts, pi, pts8, X0, X1, X2);
+            const Proj P = project(rc, X0, X1, X2);
             float w0, w1;
             if (FUSED) {
                 const float2 t = __ldg(tgt + e);
@@ -340,7 +367,10 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
                 float* dc = d_cams + (size_t)ci * 11;
 #pragma unroll
                 for (int i = 0; i < 11; ++i) red_add(dc + i, gc[i]);
-                red_add_point(d_pts, pi, gp);
+                if (d_pts4)
+                    atomicAdd(d_pts4 + pi, make_float4(gp[0], gp[1], gp[2], 0.f));
+                else
+                    red_add_point(d_pts, pi, gp, dpts8);
             }
         } else if (STRAT == GPA_SCATTER_WARPAGG) {
             const int ck = valid ? ci : -1 - lane;
@@ -360,19 +390,149 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
 #pragma unroll
                 for (int i = 0; i < 3; ++i) gp[i] = group_sum(gp[i], gpm);
             }
-            if (valid && (__ffs(gpm) - 1) == lane) red_add_point(d_pts, pi, gp);
-        } else {  // SORT: runs of equal cameras in lane order
-            const int ck = valid ? ci : -1 - lane;
-#pragma unroll
-            for (int i = 0; i < 11; ++i) gc[i] = run_scan(gc[i], ck);
-            const bool last = run_end(ck);
-            if (valid && last) {
-                float* dc = d_cams + (size_t)ci * 11;
-#pragma unroll
-                for (int i = 0; i < 11; ++i) red_add(dc + i, gc[i]);
+            if (valid && (__ffs(gpm) - 1) == lane) {
+                if (d_pts4)
+                    atomicAdd(d_pts4 + pi, make_float4(gp[0], gp[1], gp[2], 0.f));
+                else
+                    red_add_point(d_pts, pi, gp, dpts8);
             }
-            if (valid) red_add_point(d_pts, pi, gp);
         }
+    }
+}
+
+// SORT strategy: observations in the plan's camera-sorted order, kOpt
+// consecutive ones per thread. A thread keeps its camera's expanded record and
+// its partial camera cotangent in registers while the camera repeats (a camera
+// owns about M / C consecutive observations), adds a finished run with 11
+// atomics when its camera changes, and at the end of its chunk the lanes of a
+// warp merge their last runs (cameras are non-decreasing across lanes) with one
+// segmented scan, whose last lane per camera adds the sum. Point cotangents go
+// out per observation (points are in random order).
+constexpr int kOpt = 8;
+
+// Inclusive scan of v over runs of equal keys in lane order, 11 values at once
+// (the run predicates are computed once).
+__device__ __forceinline__ void seg_scan11(float (&v)[11], int key) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int kk = __shfl_up_sync(0xffffffffu, key, off);
+        const bool take = lane >= off && kk == key;
+#pragma unroll
+        for (int i = 0; i < 11; ++i) {
+            const float t = __shfl_up_sync(0xffffffffu, v[i], off);
+            if (take) v[i] += t;
+        }
+    }
+}
+
+template <bool FUSED>
+__global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
+    const float* __restrict__ rec, const float* __restrict__ pts, const float2* __restrict__ wv,
+    const float2* __restrict__ tgt, float wscale, int n_cams, int n_pts, int64_t n_obs,
+    const int32_t* __restrict__ perm, const int32_t* __restrict__ key_s, const int32_t* __restrict__ aux_s,
+    float* __restrict__ d_cams, float* __restrict__ d_pts, float4* __restrict__ d_pts4, float2* __restrict__ res,
+    int32_t* __restrict__ status, int pts8, int dpts8) {
+    const int lane = threadIdx.x & 31;
+    const int64_t chunk = (int64_t)blockDim.x * kOpt;
+    // trip count is uniform over the block so that every lane reaches the shuffles
+    for (int64_t base = (int64_t)blockIdx.x * chunk; base < n_obs; base += (int64_t)gridDim.x * chunk) {
+        const int64_t pos0 = base + (int64_t)threadIdx.x * kOpt;
+        int ev[kOpt], cv[kOpt], pv[kOpt];
+        if (pos0 + kOpt <= n_obs) {  // plan arrays are 256-byte aligned, pos0 a multiple of 8
+#pragma unroll
+            for (int h = 0; h < kOpt / 4; ++h) {
+                const int4 e4 = __ldg(reinterpret_cast<const int4*>(perm + pos0) + h);
+                const int4 c4 = __ldg(reinterpret_cast<const int4*>(key_s + pos0) + h);
+                const int4 p4 = __ldg(reinterpret_cast<const int4*>(aux_s + pos0) + h);
+                ev[4 * h] = e4.x; ev[4 * h + 1] = e4.y; ev[4 * h + 2] = e4.z; ev[4 * h + 3] = e4.w;
+                cv[4 * h] = c4.x; cv[4 * h + 1] = c4.y; cv[4 * h + 2] = c4.z; cv[4 * h + 3] = c4.w;
+                pv[4 * h] = p4.x; pv[4 * h + 1] = p4.y; pv[4 * h + 2] = p4.z; pv[4 * h + 3] = p4.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kOpt; ++i) {
+                const bool in = pos0 + i < n_obs;
+                ev[i] = in ? __ldg(perm + pos0 + i) : -1;
+                cv[i] = in ? __ldg(key_s + pos0 + i) : -1;
+                pv[i] = in ? __ldg(aux_s + pos0 + i) : -1;
+            }
+        }
+        float gc[11];
+#pragma unroll
+        for (int i = 0; i < 11; ++i) gc[i] = 0.f;
+        int cur = -1, rcam = -1;
+        float rc[kCamRec];
+#pragma unroll
+        for (int i = 0; i < kOpt; ++i) {
+            if (pos0 + i >= n_obs) break;
+            const int e = ev[i], ci = cv[i], pi = pv[i];
+            const bool e_ok = e >= 0 && e < n_obs;
+            if (!e_ok || ci < 0 || ci >= n_cams || pi < 0 || pi >= n_pts) {
+                if (FUSED && e_ok) res[e] = make_float2(NAN, NAN);
+                report(status, GPA_ERR_INDEX);
+                continue;
+            }
+            if (ci != cur) {
+                if (cur >= 0) {
+                    float* dc = d_cams + (size_t)cur * 11;
+#pragma unroll
+                    for (int j = 0; j < 11; ++j) {
+                        red_add(dc + j, gc[j]);
+                        gc[j] = 0.f;
+                    }
+                }
+                cur = ci;
+            }
+            if (ci != rcam) {
+                load_cam<kCamRec>(rec, ci, rc);
+                rcam = ci;
+            }
+            float X0, X1, X2;
+            load_point(pts, pi, pts8, X0, X1, X2);
+            const Proj P = project(rc, X0, X1, X2);
+            float w0, w1;
+            if (FUSED) {
+                const float2 t = __ldg(tgt + e);
+                const float r0 = P.out[0] - t.x, r1 = P.out[1] - t.y;
+                res[e] = make_float2(r0, r1);
+                w0 = wscale * r0;
+                w1 = wscale * r1;
+            } else {
+                const float2 w = __ldg(wv + e);
+                w0 = w.x;
+                w1 = w.y;
+            }
+            float gl[11], gp[3];
+            project_vjp(rc, P, w0, w1, gl, gp);
+#pragma unroll
+            for (int j = 0; j < 11; ++j) gc[j] += gl[j];
+            if (d_pts4)
+                atomicAdd(d_pts4 + pi, make_float4(gp[0], gp[1], gp[2], 0.f));
+            else
+                red_add_point(d_pts, pi, gp, dpts8);
+        }
+        const int ck = cur >= 0 ? cur : -1 - lane;
+        seg_scan11(gc, ck);
+        const bool last = run_end(ck);  // a shuffle: every lane evaluates it
+        if (cur >= 0 && last) {
+            float* dc = d_cams + (size_t)cur * 11;
+#pragma unroll
+            for (int j = 0; j < 11; ++j) red_add(dc + j, gc[j]);
+        }
+    }
+}
+
+// d_pts[p] += acc[p].xyz (the padded accumulators of one VJP call).
+__global__ void __launch_bounds__(256) pts4_add_kernel(const float4* __restrict__ acc, int n_pts,
+                                                       float* __restrict__ d_pts) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pts; p += stride) {
+        const float4 v = acc[p];
+        float* dp = d_pts + p * 3;
+        dp[0] += v.x;
+        dp[1] += v.y;
+        dp[2] += v.z;
     }
 }
 
@@ -397,34 +557,61 @@ static int expand_cams(const float* cams, int n_cams, float* rec, cudaStream_t s
     return GPA_OK;
 }
 
+static bool al_dev(const void* p, uintptr_t a) { return (((uintptr_t)p) & (a - 1)) == 0; }
+
 template <int STRAT, bool FUSED>
 static int launch_vjp(const float* rec, const float* pts, const int32_t* obs, const float* w, const float* tgt,
                       float wscale, int n_cams, int n_pts, int64_t n_obs, const PlanView& pv, float* d_cams,
-                      float* d_pts, float* res, int32_t* status, cudaStream_t s) {
+                      float* d_pts, float4* d_pts4, float* res, int32_t* status, cudaStream_t s) {
     GPA_LAUNCH(FUSED ? "reproj_residual_vjp" : "reproj_vjp", s,
                reproj_vjp_kernel<STRAT, FUSED><<<obs_grid(n_obs), 256, 0, s>>>(
                    rec, pts, (const int2*)obs, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts,
-                   n_obs, pv.perm, pv.key_sorted, pv.aux_sorted, d_cams, d_pts, (float2*)res, status));
+                   n_obs, d_cams, d_pts, d_pts4, (float2*)res, status, al_dev(pts, 8) ? 1 : 0,
+                   al_dev(d_pts, 8) ? 1 : 0));
     return GPA_OK;
 }
 
 template <bool FUSED>
+static int launch_vjp_sorted(const float* rec, const float* pts, const float* w, const float* tgt, float wscale,
+                             int n_cams, int n_pts, int64_t n_obs, const PlanView& pv, float* d_cams, float* d_pts,
+                             float4* d_pts4, float* res, int32_t* status, cudaStream_t s) {
+    const int64_t want = (n_obs + 256 * kOpt - 1) / (256 * kOpt), cap = (int64_t)sm_count() * 8;
+    GPA_LAUNCH(FUSED ? "reproj_residual_vjp" : "reproj_vjp", s,
+               reproj_vjp_sorted_kernel<FUSED><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
+                   rec, pts, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts, n_obs, pv.perm,
+                   pv.key_sorted, pv.aux_sorted, d_cams, d_pts, d_pts4, (float2*)res, status, al_dev(pts, 8) ? 1 : 0,
+                   al_dev(d_pts, 8) ? 1 : 0));
+    return GPA_OK;
+}
+
+// d_pts4: padded point accumulators in the workspace (zeroed here, added into
+// d_pts after the scatter), or null to scatter into d_pts directly.
+template <bool FUSED>
 static int dispatch_vjp(int strat, const float* rec, const float* pts, const int32_t* obs, const float* w,
                         const float* tgt, float wscale, int n_cams, int n_pts, int64_t n_obs,
-                        const PlanView& pv, float* d_cams, float* d_pts, float* res, int32_t* status,
-                        cudaStream_t s) {
+                        const PlanView& pv, float* d_cams, float* d_pts, float4* d_pts4, float* res,
+                        int32_t* status, cudaStream_t s) {
+    if (d_pts4 && cudaMemsetAsync(d_pts4, 0, sizeof(float4) * (size_t)n_pts, s) != cudaSuccess) return GPA_ERR_CUDA;
+    int rc = GPA_ERR_ARG;
     switch (strat) {
         case GPA_SCATTER_ATOMIC:
-            return launch_vjp<GPA_SCATTER_ATOMIC, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs,
-                                                        pv, d_cams, d_pts, res, status, s);
+            rc = launch_vjp<GPA_SCATTER_ATOMIC, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs, pv,
+                                                      d_cams, d_pts, d_pts4, res, status, s);
+            break;
         case GPA_SCATTER_WARPAGG:
-            return launch_vjp<GPA_SCATTER_WARPAGG, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs,
-                                                         pv, d_cams, d_pts, res, status, s);
+            rc = launch_vjp<GPA_SCATTER_WARPAGG, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs, pv,
+                                                       d_cams, d_pts, d_pts4, res, status, s);
+            break;
         case GPA_SCATTER_SORT:
-            return launch_vjp<GPA_SCATTER_SORT, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs, pv,
-                                                      d_cams, d_pts, res, status, s);
+            rc = launch_vjp_sorted<FUSED>(rec, pts, w, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams, d_pts, d_pts4,
+                                          res, status, s);
+            break;
     }
-    return GPA_ERR_ARG;
+    if (rc || !d_pts4) return rc;
+    const int64_t want = (n_pts + 255) / 256, cap = (int64_t)sm_count() * 8;
+    GPA_LAUNCH("reproj_pts_add", s,
+               pts4_add_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(d_pts4, n_pts, d_pts));
+    return GPA_OK;
 }
 
 }  // namespace gpa
@@ -433,12 +620,16 @@ using namespace gpa;
 
 static bool al(const void* p, uintptr_t a) { return (((uintptr_t)p) & (a - 1)) == 0; }
 
+// Workspace: expanded cameras, then the padded point accumulators of the VJP.
+static size_t cam_area(int32_t n_cams) { return (sizeof(float) * (size_t)n_cams * kCamRec + 255) & ~(size_t)255; }
+
 extern "C" size_t gpa_reproj_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs) {
-    (void)n_pts;
     (void)n_obs;
-    if (n_cams < 1) return 0;
-    return ((sizeof(float) * (size_t)n_cams * kCamRec + 255) & ~(size_t)255) + 256;
+    if (n_cams < 1 || n_pts < 1) return 0;
+    return cam_area(n_cams) + ((sizeof(float4) * (size_t)n_pts + 255) & ~(size_t)255);
 }
+
+static float4* pts_acc(void* ws, int32_t n_cams) { return (float4*)((char*)ws + cam_area(n_cams)); }
 
 static int reproj_check(const float* cams, const float* pts, const int32_t* obs, int32_t n_cams,
                         int32_t n_pts, int64_t n_obs, void* ws, size_t ws_bytes) {
@@ -463,7 +654,7 @@ extern "C" int reproj_residual(const float* cams, const float* pts, const int32_
     GPA_LAUNCH("reproj_residual", s,
                reproj_residual_kernel<<<obs_grid(n_obs), 256, 0, s>>>(rec, pts, (const int2*)obs,
                                                                       (const float2*)tgt, n_cams, n_pts, n_obs,
-                                                                      (float2*)res, dev_status));
+                                                                      (float2*)res, dev_status, al(pts, 8) ? 1 : 0));
     return GPA_OK;
 }
 
@@ -492,7 +683,7 @@ extern "C" int reproj_vjp(const float* cams, const float* pts, const int32_t* ob
     rc = expand_cams(cams, n_cams, rec, s);
     if (rc) return rc;
     return dispatch_vjp<false>(strat, rec, pts, obs, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
-                               nullptr, dev_status, s);
+                               pts_acc(ws, n_cams), nullptr, dev_status, s);
 }
 
 extern "C" int reproj_jvp(const float* cams, const float* pts, const int32_t* obs, const float* v_cams,
@@ -508,7 +699,8 @@ extern "C" int reproj_jvp(const float* cams, const float* pts, const int32_t* ob
     if (rc) return rc;
     GPA_LAUNCH("reproj_jvp", s,
                reproj_jvp_kernel<<<obs_grid(n_obs), 256, 0, s>>>(rec, pts, (const int2*)obs, v_cams, v_pts, n_cams,
-                                                                 n_pts, n_obs, (float2*)jv, dev_status));
+                                                                 n_pts, n_obs, (float2*)jv, dev_status,
+                                                                 al(pts, 8) ? 1 : 0));
     return GPA_OK;
 }
 
@@ -532,7 +724,7 @@ extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const in
     rc = expand_cams(cams, n_cams, rec, s);
     if (rc) return rc;
     return dispatch_vjp<true>(strat, rec, pts, obs, nullptr, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams,
-                              d_pts, res, dev_status, s);
+                              d_pts, pts_acc(ws, n_cams), res, dev_status, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -598,22 +790,21 @@ extern "C" int reproj_vjp_noalloc(const float* cams, const float* pts, const int
     cam_expand_kernel<<<(n_cams + 127) / 128, 128, 0, s>>>(cams, n_cams, rec);
     GPA_LAUNCH_CHECK();
     const unsigned grid = obs_grid(n_obs);
+    const int p8 = al(pts, 8) ? 1 : 0, dp8 = al(d_pts, 8) ? 1 : 0;  // no padded accumulators: direct atomics
     switch (strat) {
         case GPA_SCATTER_ATOMIC:
             reproj_vjp_kernel<GPA_SCATTER_ATOMIC, false><<<grid, 256, 0, s>>>(
-                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, pv.perm,
-                pv.key_sorted, pv.aux_sorted, d_cams, d_pts, nullptr, dev_status);
+                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, d_cams, d_pts,
+                nullptr, nullptr, dev_status, p8, dp8);
             break;
         case GPA_SCATTER_WARPAGG:
             reproj_vjp_kernel<GPA_SCATTER_WARPAGG, false><<<grid, 256, 0, s>>>(
-                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, pv.perm,
-                pv.key_sorted, pv.aux_sorted, d_cams, d_pts, nullptr, dev_status);
+                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, d_cams, d_pts,
+                nullptr, nullptr, dev_status, p8, dp8);
             break;
         default:
-            reproj_vjp_kernel<GPA_SCATTER_SORT, false><<<grid, 256, 0, s>>>(
-                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, pv.perm,
-                pv.key_sorted, pv.aux_sorted, d_cams, d_pts, nullptr, dev_status);
-            break;
+            return launch_vjp_sorted<false>(rec, pts, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
+                                            nullptr, nullptr, dev_status, s);
     }
     GPA_LAUNCH_CHECK();
     return GPA_OK;

@@ -223,3 +223,40 @@ def test_dot_product_adjoint_entirely_on_gpu():
         rhs = np.sum(host(dcm).astype(np.float64) * vc32) + np.sum(host(dpt).astype(np.float64) * vp32)
         scale = np.sqrt(np.sum(jv ** 2) * np.sum(r.w.astype(np.float64) ** 2))
         assert abs(lhs - rhs) <= 1e-5 * scale, (lhs, rhs)
+
+
+def _offset4(a):
+    """A device copy of float32 array a whose data pointer is 4 mod 8 bytes:
+    4-byte aligned as the header allows, but not 8-byte aligned."""
+    buf = torch.zeros(a.size + 1, dtype=torch.float32, device="cuda")
+    t = buf[1:].view(*a.shape)
+    t.copy_(torch.from_numpy(np.ascontiguousarray(a, np.float32)))
+    assert t.data_ptr() % 8 == 4
+    return t
+
+
+@pytest.mark.parametrize("strat", STRATS)
+def test_point_arrays_aligned_to_four_bytes_only(strat):
+    """pts and d_pts at 4 mod 8 bytes: every entry point takes its 4-byte paths."""
+    import paper_2104_05372_b300 as gpa
+    r = synth.reproj_inputs(40, 1001, 20000, seed=77)
+    dcm_ref, dpt_ref, _ = oracle.reproj_vjp(r)
+    res_ref, _ = oracle.reproj_residual(r)
+    cams, _, obs, tgt, w = _dev_inputs(r)
+    pts = _offset4(r.pts)
+    plan = gpa.gpa_obs_plan_build(obs, r.n_cams, r.n_pts) if strat == "sort" else None
+    st = status()
+    res = host(gpa.reproj_residual(cams, pts, obs, tgt, status=st))
+    d_pts = _offset4(np.zeros((r.n_pts, 3), np.float32))
+    dcm, dpt = gpa.reproj_vjp(cams, pts, obs, w, d_pts=d_pts, strat=strat, plan=plan, status=st)
+    d_pts2 = _offset4(np.zeros((r.n_pts, 3), np.float32))
+    dcm2, dpt2 = gpa._lib.reproj_vjp_noalloc(cams, pts, obs, w, d_pts=d_pts2, strat=strat, plan=plan, status=st)
+    vc, vp = synth.reproj_tangents(r.n_cams, r.n_pts, seed=5)
+    jv = host(gpa.reproj_jvp(cams, pts, obs, dev(vc.astype(np.float32)), _offset4(vp), status=st))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert rel_norm(res, res_ref) <= 1e-5
+    for a, b in ((dcm, dcm_ref), (dpt, dpt_ref), (dcm2, dcm_ref), (dpt2, dpt_ref)):
+        assert rel_norm(host(a), b) <= TOL_GRAD_FP32
+    ref32, _ = oracle.reproj_jvp(r, vc.astype(np.float32).astype(np.float64), vp.astype(np.float32).astype(np.float64))
+    assert rel_norm(jv, ref32) <= 1e-5
