@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--tc-fp32-steps", type=int, default=0, help="--tc-only: also time the FP32 path")
     ap.add_argument("--batched-only", action="store_true", help="only the batched workload")
     ap.add_argument("--reproj-only", action="store_true", help="only the reprojection workload")
+    ap.add_argument("--scatter-only", action="store_true", help="only the generic scatter workloads")
     return ap.parse_args()
 
 
@@ -181,6 +182,13 @@ def run_ours(args):
         dev = torch.device("cuda", 0)
         print(json.dumps(run_reproj(args, gpa, _lib, dev, torch.cuda.current_stream(dev), 0)))
         return
+    if args.scatter_only:
+        torch.cuda.set_device(0)
+        import paper_2104_05372_b300 as gpa
+        from paper_2104_05372_b300 import _lib
+        dev = torch.device("cuda", 0)
+        print(json.dumps(run_scatter(args, gpa, _lib, dev, torch.cuda.current_stream(dev), 0)))
+        return
     if args.batched_only:
         torch.cuda.set_device(0)
         import paper_2104_05372_b300 as gpa
@@ -295,6 +303,7 @@ def run_ours(args):
         result["precision_form"] = [run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=GMM_D, k=GMM_K),
                                     run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256)]
         result["batched"] = run_batched(args, gpa, _lib, dev, stream, rank)
+        result["scatter"] = run_scatter(args, gpa, _lib, dev, stream, rank)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -392,6 +401,57 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
     out["roofline"] = {"bound": "hbm", "achieved": out[f"vjp_{best}"]["hbm_gbs_algorithmic"],
                        "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": out[f"vjp_{best}"]["frac"],
                        "peak_source": src, "bytes_per_obs": BYTES_PER_OBS_VJP}
+    return out
+
+
+def run_scatter(args, gpa, _lib, dev, stream, rank):
+    """Generic Accum scatter (accum_scatter_add) on the reduction patterns of
+    Sec. 6.1.3, each with its specialised strategy beside the generic ones:
+    complete (one bucket), few buckets (histogram), regular segmented
+    (idx = j // 488, runs in order), irregular (500k buckets). Roofline: HBM on
+    algorithmic bytes (indices and values read once; the accumulator's
+    read-modify-write once)."""
+    import torch
+    import synth
+    peaks, src = measured_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / args.steps
+
+    cases = [("complete", 1 << 24, 1, 1, "f32", None, ("smem", "atomic", "warpagg")),
+             ("histogram_256", 1 << 24, 1, 256, "i32", None, ("smem", "warpagg", "atomic")),
+             ("regular_segmented", 4_000_000, 11, 8197, "f32", 488, ("runs", "warpagg", "atomic")),
+             ("irregular_500k", 4_000_000, 3, 500_000, "f32", None, ("sort", "warpagg", "atomic"))]
+    out = {"metric": "elements/s", "l2": "flushed between timed iterations", "peak_gbs": peaks["hbm_gbs"],
+           "peak_source": src}
+    for name, m, w, nb, dt, seg, strats in cases:
+        idx, vals = synth.scatter_inputs(m, w, nb, dt, seed=6000 + rank)
+        if seg:
+            idx = (np.arange(m) // seg).astype(np.int32)
+        idx_d, vals_d = torch.from_numpy(idx).to(dev), torch.from_numpy(vals).to(dev)
+        acc = torch.zeros((nb, w), dtype=vals_d.dtype, device=dev)
+        plan = gpa.gpa_index_plan_build(idx_d, nb) if "sort" in strats else None
+        alg = m * (4 + 4 * w) + 2 * 4 * nb * w
+        row = {"m": m, "w": w, "buckets": nb, "dtype": dt, "algorithmic_bytes": alg}
+        for st in strats:
+            ms = timed(lambda: gpa.accum_scatter_add(idx_d, vals_d, acc, strat=st, plan=plan))
+            gbs = alg / (ms / 1e3) / 1e9
+            row[st] = {"ms": round(ms, 4), "elements_per_s": m / (ms / 1e3), "gbs": round(gbs, 1),
+                       "frac": round(gbs / peaks["hbm_gbs"], 4)}
+        out[name] = row
     return out
 
 

@@ -68,10 +68,16 @@ typedef enum {
 typedef enum { GPA_PREC_FP32 = 0, GPA_PREC_BF16_TC = 1 } gpa_prec;
 
 typedef enum {
-    GPA_SCATTER_AUTO = 0,    /* SORT when a plan is given, else ATOMIC */
+    GPA_SCATTER_AUTO = 0,    /* SORT when a plan is given, else SMEM when the buckets fit, else ATOMIC */
     GPA_SCATTER_ATOMIC = 1,  /* one red.global.add per element */
     GPA_SCATTER_WARPAGG = 2, /* lanes of a warp with equal keys combine first */
-    GPA_SCATTER_SORT = 3     /* key-sorted order from a plan, segmented warp sums */
+    GPA_SCATTER_SORT = 3,    /* key-sorted order from a plan, segmented warp sums */
+    GPA_SCATTER_SMEM = 4,    /* accum_scatter_add only: per-CTA copy of the buckets in shared
+                                memory (n_buckets * w <= 24576), one global add per touched
+                                entry; one bucket of width 1 is a complete reduction (trees) */
+    GPA_SCATTER_RUNS = 5     /* accum_scatter_add only: equal indices adjacent in input order
+                                (regular segmented, e.g. idx = j / L): segmented warp sums, no
+                                plan; correct for any order */
 } gpa_scatter;
 
 /* Human-readable name of a gpa_status value (static string, never NULL). */
@@ -366,7 +372,10 @@ GPA_API int gpa_index_plan_build(const int32_t* idx, int64_t m, int32_t n_keys, 
  * Sec. 6.1.2). dtype 0 = float32 values and accumulator, 1 = int32 (exact,
  * wrapping on overflow). Indices outside [0, n_buckets) set GPA_ERR_INDEX and
  * are skipped. SORT needs `plan` from gpa_index_plan_build on the same idx.
- * 1 <= w <= 64. Alignment: 4-byte.
+ * The strategies follow the reduction patterns of Sec. 6.1.3: complete (one
+ * bucket: SMEM's tree), regular segmented (RUNS), irregular (ATOMIC, WARPAGG,
+ * SORT; SMEM when the buckets are few). SMEM with more than 24576 entries is
+ * GPA_ERR_UNSUPPORTED. 1 <= w <= 64. Alignment: 4-byte.
  */
 GPA_API int accum_scatter_add(const int32_t* idx, const void* vals, int64_t m, int32_t w, int32_t dtype,
                       void* acc, int32_t n_buckets, int32_t strat, const void* plan,

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libgpa.so")
 
 PREC_FP32, PREC_BF16_TC = 0, 1
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_WARPAGG, SCATTER_SORT = 0, 1, 2, 3
-STRATEGIES = {"auto": 0, "atomic": 1, "warpagg": 2, "sort": 3}
+STRATEGIES = {"auto": 0, "atomic": 1, "warpagg": 2, "sort": 3, "smem": 4, "runs": 5}
 ERR_ARG, ERR_INDEX, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_ALIGN = 1, 2, 3, 4, 5, 6, 7
 
 

@@ -29,19 +29,32 @@ __device__ __forceinline__ int group_sum(int v, unsigned group) {
     return s;
 }
 
-// Inclusive segmented scan over runs of equal keys in lane order (keys must
-// form contiguous runs, as in a key-sorted sequence). The last lane of each run
-// ends up with the run's total.
-template <typename T>
-__device__ __forceinline__ T run_scan(T v, int key) {
+// First lane of this lane's run: the highest lane <= this one whose key differs
+// from its left neighbour's (a run is a maximal stretch of adjacent equal keys;
+// equal keys further apart are separate runs). All 32 lanes must call it.
+__device__ __forceinline__ int run_head(int key) {
     const unsigned lane = lane_id();
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, lane == 0u || prev != key);
+    return 31 - __clz(starts & (0xffffffffu >> (31u - lane)));
+}
+
+// Inclusive scan of v within this lane's run [head, lane]; the last lane of
+// each run ends up with the run's total. All 32 lanes must call it.
+template <typename T>
+__device__ __forceinline__ T run_scan_head(T v, int head) {
+    const int lane = (int)lane_id();
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const T t = __shfl_up_sync(0xffffffffu, v, off);
-        const int kk = __shfl_up_sync(0xffffffffu, key, off);
-        if (lane >= (unsigned)off && kk == key) v += t;
+        if (lane - off >= head) v += t;
     }
     return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T run_scan(T v, int key) {
+    return run_scan_head(v, run_head(key));
 }
 
 __device__ __forceinline__ bool run_end(int key) {

@@ -411,19 +411,11 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
 constexpr int kOpt = 8;
 
 // Inclusive scan of v over runs of equal keys in lane order, 11 values at once
-// (the run predicates are computed once).
+// (the run head is computed once).
 __device__ __forceinline__ void seg_scan11(float (&v)[11], int key) {
-    const int lane = threadIdx.x & 31;
+    const int head = run_head(key);
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int kk = __shfl_up_sync(0xffffffffu, key, off);
-        const bool take = lane >= off && kk == key;
-#pragma unroll
-        for (int i = 0; i < 11; ++i) {
-            const float t = __shfl_up_sync(0xffffffffu, v[i], off);
-            if (take) v[i] += t;
-        }
-    }
+    for (int i = 0; i < 11; ++i) v[i] = run_scan_head(v[i], head);
 }
 
 template <bool FUSED>

@@ -14,6 +14,7 @@
 //   SORT     key-sorted order from a plan, runs summed by a segmented warp scan.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "accum.cuh"
 #include "common.cuh"
@@ -213,9 +214,143 @@ __global__ void __launch_bounds__(256) scatter_sorted_kernel(const int32_t* __re
         const bool valid = b >= 0 && b < n_buckets;  // invalid elements were reported by the plan
         const int key = valid ? b : -1 - lane;
         const bool last = run_end(key);
+        const int head = run_head(key);
         for (int c = 0; c < w; ++c) {
             T v = valid ? __ldg(vals + e * w + c) : T(0);
-            v = run_scan(v, key);
+            v = run_scan_head(v, head);
+            if (valid && last) atomicAdd(acc + (int64_t)b * w + c, v);
+        }
+    }
+}
+
+// SMEM: every CTA accumulates into its own copy of acc in shared memory (shared
+// atomics, no contention across the GPU), then adds each entry it touched into
+// acc once. For few buckets: n_buckets * w <= kSmemEntries.
+constexpr int kSmemEntries = 24576;  // 96 KB of float / int32: two CTAs per SM
+
+template <typename T>
+__global__ void __launch_bounds__(256) scatter_smem_kernel(const int32_t* __restrict__ idx,
+                                                           const T* __restrict__ vals, int64_t m, int w,
+                                                           T* __restrict__ acc, int n_buckets,
+                                                           int32_t* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* priv = reinterpret_cast<T*>(smem_raw);
+    const int ne = n_buckets * w;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) priv[e] = T(0);
+    __syncthreads();
+    const int64_t total = m * w;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t e0 = 0;
+    if (w == 1 && ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(vals)) & 15) == 0) {
+        // four elements per thread and step, 16-byte loads
+        const int64_t m4 = m / 4;
+        for (int64_t q = t0; q < m4; q += stride) {
+            const int4 b4 = __ldg(reinterpret_cast<const int4*>(idx) + q);
+            const float4 raw = __ldg(reinterpret_cast<const float4*>(vals) + q);
+            const int bs[4] = {b4.x, b4.y, b4.z, b4.w};
+            const float vf[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (bs[u] < 0 || bs[u] >= n_buckets) {
+                    report(status, GPA_ERR_INDEX);
+                    continue;
+                }
+                T v;
+                memcpy(&v, &vf[u], sizeof(T));  // T is float or int32: the same 4 bytes
+                atomicAdd(priv + bs[u], v);
+            }
+        }
+        e0 = m4 * 4;
+    }
+    for (int64_t e = e0 + t0; e < total; e += stride) {
+        const int64_t j = w == 1 ? e : e / w;
+        const int c = (int)(e - j * w);
+        const int b = __ldg(idx + j);
+        if (b < 0 || b >= n_buckets) {
+            if (c == 0) report(status, GPA_ERR_INDEX);
+            continue;
+        }
+        atomicAdd(priv + b * w + c, __ldg(vals + e));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const T v = priv[e];
+        if (v != T(0)) atomicAdd(acc + e, v);  // untouched entries add nothing
+    }
+}
+
+// Complete reduction (one bucket, one value per element): per-thread sums, a
+// warp tree, a block tree, one atomic per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) scatter_complete_kernel(const int32_t* __restrict__ idx,
+                                                               const T* __restrict__ vals, int64_t m,
+                                                               T* __restrict__ acc, int32_t* __restrict__ status) {
+    T sum = T(0);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t j0 = 0;
+    if (((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(vals)) & 15) == 0) {
+        const int64_t m4 = m / 4;  // four elements per thread and step, 16-byte loads
+        for (int64_t q = t0; q < m4; q += stride) {
+            const int4 b4 = __ldg(reinterpret_cast<const int4*>(idx) + q);
+            const float4 raw = __ldg(reinterpret_cast<const float4*>(vals) + q);
+            const int bs[4] = {b4.x, b4.y, b4.z, b4.w};
+            const float vf[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (bs[u] != 0) {
+                    report(status, GPA_ERR_INDEX);
+                    continue;
+                }
+                T v;
+                memcpy(&v, &vf[u], sizeof(T));
+                sum += v;
+            }
+        }
+        j0 = m4 * 4;
+    }
+    for (int64_t j = j0 + t0; j < m; j += stride) {
+        if (__ldg(idx + j) != 0) {
+            report(status, GPA_ERR_INDEX);
+            continue;
+        }
+        sum += __ldg(vals + j);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __shared__ T part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T t = T(0);
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += part[i];
+        atomicAdd(acc, t);
+    }
+}
+
+// RUNS: equal indices are adjacent in input order (a regular segmented
+// reduction, e.g. idx = j / L, or any grouped index): runs summed by a
+// segmented warp scan, one atomic per run and warp, no plan. Correct for any
+// index order; efficient when runs are long.
+template <typename T>
+__global__ void __launch_bounds__(256) scatter_runs_kernel(const int32_t* __restrict__ idx,
+                                                           const T* __restrict__ vals, int64_t m, int w,
+                                                           T* __restrict__ acc, int n_buckets,
+                                                           int32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+        const int64_t j = base + threadIdx.x;
+        const int b = j < m ? __ldg(idx + j) : -1;
+        const bool valid = j < m && b >= 0 && b < n_buckets;
+        if (j < m && !valid) report(status, GPA_ERR_INDEX);
+        const int key = valid ? b : -1 - lane;
+        const bool last = run_end(key);
+        const int head = run_head(key);
+        for (int c = 0; c < w; ++c) {
+            T v = valid ? __ldg(vals + j * w + c) : T(0);
+            v = run_scan_head(v, head);
             if (valid && last) atomicAdd(acc + (int64_t)b * w + c, v);
         }
     }
@@ -322,9 +457,66 @@ extern "C" int accum_scatter_add(const int32_t* idx, const void* vals, int64_t m
     if (m < 1 || m > INT32_MAX || w < 1 || w > 64 || n_buckets < 1) return GPA_ERR_ARG;
     if (dtype != 0 && dtype != 1) return GPA_ERR_ARG;
     if ((((uintptr_t)idx) | ((uintptr_t)vals) | ((uintptr_t)acc)) & 3) return GPA_ERR_ALIGN;
-    if (strat == GPA_SCATTER_AUTO) strat = plan ? GPA_SCATTER_SORT : GPA_SCATTER_ATOMIC;
+    const bool few = (int64_t)n_buckets * w <= kSmemEntries;
+    if (strat == GPA_SCATTER_AUTO) strat = plan ? GPA_SCATTER_SORT : few ? GPA_SCATTER_SMEM : GPA_SCATTER_ATOMIC;
     cudaStream_t s = (cudaStream_t)stream;
     switch (strat) {
+        case GPA_SCATTER_SMEM: {
+            if (!few) return GPA_ERR_UNSUPPORTED;
+            if (n_buckets == 1 && w == 1) {  // complete reduction
+                const unsigned g = grid_for((m + 3) / 4);
+                if (dtype == 0)
+                    GPA_LAUNCH("scatter_complete", s,
+                               scatter_complete_kernel<float><<<g, 256, 0, s>>>(idx, (const float*)vals, m,
+                                                                                (float*)acc, dev_status));
+                else
+                    GPA_LAUNCH("scatter_complete", s,
+                               scatter_complete_kernel<int><<<g, 256, 0, s>>>(idx, (const int*)vals, m, (int*)acc,
+                                                                              dev_status));
+                break;
+            }
+            const size_t smem = sizeof(float) * (size_t)n_buckets * w;
+            // enough CTAs to fill the GPU, few enough that flushing stays small against the scatter
+            int64_t per = (int64_t)n_buckets * w * 8;
+            if (per < 4096) per = 4096;
+            const int64_t want = (m * w + per - 1) / per;
+            int dev = 0, sms = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            int per_sm = (int)((200 * 1024) / (smem + 1024));  // CTAs that fit one SM's shared memory
+            per_sm = per_sm < 1 ? 1 : per_sm > 8 ? 8 : per_sm;
+            const unsigned cap = (unsigned)(sms * per_sm);
+            const unsigned g = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+            if (dtype == 0) {
+                auto kern = scatter_smem_kernel<float>;
+                if (smem > 48 * 1024 &&
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                    return GPA_ERR_CUDA;
+                GPA_LAUNCH("scatter_smem", s,
+                           kern<<<g, 256, smem, s>>>(idx, (const float*)vals, m, w, (float*)acc, n_buckets,
+                                                     dev_status));
+            } else {
+                auto kern = scatter_smem_kernel<int>;
+                if (smem > 48 * 1024 &&
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                    return GPA_ERR_CUDA;
+                GPA_LAUNCH("scatter_smem", s,
+                           kern<<<g, 256, smem, s>>>(idx, (const int*)vals, m, w, (int*)acc, n_buckets, dev_status));
+            }
+            break;
+        }
+        case GPA_SCATTER_RUNS: {
+            const unsigned g = grid_for(m);
+            if (dtype == 0)
+                GPA_LAUNCH("scatter_runs", s,
+                           scatter_runs_kernel<float><<<g, 256, 0, s>>>(idx, (const float*)vals, m, w, (float*)acc,
+                                                                        n_buckets, dev_status));
+            else
+                GPA_LAUNCH("scatter_runs", s,
+                           scatter_runs_kernel<int><<<g, 256, 0, s>>>(idx, (const int*)vals, m, w, (int*)acc,
+                                                                      n_buckets, dev_status));
+            break;
+        }
         case GPA_SCATTER_ATOMIC: {
             const unsigned g = grid_for(m * w);
             if (dtype == 0)

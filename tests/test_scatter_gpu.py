@@ -13,7 +13,7 @@ import synth
 from gpu_util import dev, host, status
 
 pytestmark = pytest.mark.gpu
-STRATS = ["atomic", "warpagg", "sort"]
+STRATS = ["atomic", "warpagg", "sort", "smem", "runs"]
 
 
 def _run(idx, vals, nb, strat):
@@ -31,7 +31,8 @@ def _run(idx, vals, nb, strat):
 
 @pytest.mark.parametrize("strat", STRATS)
 @pytest.mark.parametrize("m,w,nb,skew", [(1, 1, 1, 0.0), (5, 1, 4, 0.0), (100000, 1, 1000, 0.0),
-                                         (100000, 3, 50, 1.5), (33333, 11, 7, 0.0), (4096, 64, 1, 0.0)])
+                                         (100000, 3, 50, 1.5), (33333, 11, 7, 0.0), (4096, 64, 1, 0.0),
+                                         (1000003, 1, 1, 0.0), (300000, 2, 12288, 0.5)])
 def test_int32_histogram_bit_exact(strat, m, w, nb, skew):
     idx, vals = synth.scatter_inputs(m, w, nb, "i32", seed=m + w, skew=skew)
     ref, bad = oracle.scatter_add(idx, vals, nb)
@@ -94,3 +95,48 @@ def test_partition_invariance_bit_exact_int32():
     for a, b in zip(cuts[:-1], cuts[1:]):
         gpa.accum_scatter_add(dev(idx[a:b]), dev(vals[a:b]), acc, strat="warpagg")
     assert np.array_equal(host(acc), whole)
+
+
+@pytest.mark.parametrize("dtype", ["i32", "f32"])
+@pytest.mark.parametrize("seg", [1, 7, 256, 5000])
+def test_runs_regular_segmented(dtype, seg):
+    """idx = j // seg: the regular segmented pattern (Sec. 6.1.3) through RUNS,
+    against the oracle (int bit-exact, float within the summation bound)."""
+    m, w = 200003, 3
+    nb = (m + seg - 1) // seg
+    idx = (np.arange(m) // seg).astype(np.int32)
+    _, vals = synth.scatter_inputs(m, w, nb, dtype, seed=seg)
+    ref, _ = oracle.scatter_add(idx, vals, nb)
+    for strat in ("runs", "auto"):
+        got, st = _run(idx, vals, nb, strat)
+        assert st == 0
+        if dtype == "i32":
+            assert np.array_equal(got.reshape(nb, w).astype(np.int64), ref)
+        else:
+            absum, _ = oracle.scatter_add(idx, np.abs(vals), nb)
+            bound = (seg - 1) * 2.0 ** -24 * absum + 2.0 ** -24 * np.abs(ref) + 1e-30
+            assert np.all(np.abs(got.reshape(nb, w) - ref) <= bound)
+
+
+def test_complete_reduction_float_within_bound():
+    """One bucket, width 1: the complete pattern (tree sums, one atomic per CTA)."""
+    m = 3000017
+    idx = np.zeros(m, np.int32)
+    _, vals = synth.scatter_inputs(m, 1, 1, "f32", seed=3)
+    ref, _ = oracle.scatter_add(idx, vals, 1)
+    got, st = _run(idx, vals, 1, "smem")
+    assert st == 0
+    bound = (m - 1) * 2.0 ** -24 * float(np.sum(np.abs(vals.astype(np.float64)))) + 1e-30
+    assert abs(float(got.reshape(-1)[0]) - float(ref.reshape(-1)[0])) <= bound
+
+
+def test_smem_rejects_too_many_buckets_and_auto_falls_back():
+    import paper_2104_05372_b300 as gpa
+    idx, vals = synth.scatter_inputs(1000, 2, 20000, "i32", seed=1)
+    acc = torch.zeros(20000, 2, dtype=torch.int32, device="cuda")
+    with pytest.raises(gpa.GpaError) as e:
+        gpa.accum_scatter_add(dev(idx), dev(vals), acc, strat="smem")
+    assert e.value.code == 6
+    got, st = _run(idx, vals, 20000, "auto")  # 40000 entries: ATOMIC
+    ref, _ = oracle.scatter_add(idx, vals, 20000)
+    assert st == 0 and np.array_equal(got.reshape(20000, 2).astype(np.int64), ref)
