@@ -394,6 +394,18 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
                                                strat="sort", plan=plan, ws=ws))
     out["fused_residual_vjp_sort"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
                                       "hbm_gbs_algorithmic": BYTES_PER_OBS_FUSED * RP_M / (ms / 1e3) / 1e9}
+    # Gauss-Newton blocks (NEXT-2): U, V, g accumulated, W and res written per observation
+    U = torch.zeros(RP_C, 66, device=dev)
+    V = torch.zeros(RP_P, 6, device=dev)
+    W = torch.empty(RP_M, 33, device=dev)
+    gws = _lib.workspace(_lib.load().gpa_reproj_gn_workspace_bytes(RP_C, RP_P, RP_M), dev)
+    ms = timed(lambda: gpa.reproj_normal_eqs(cams, pts, obs, tgt, U=U, V=V, W=W, g_cams=dcm, g_pts=dpt, res=res,
+                                             strat="sort", plan=plan, ws=gws))
+    gn_bytes = 8 + 8 + 8 + 33 * 4  # indices, target, residual, W block
+    out["normal_eqs_sort"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
+                              "hbm_gbs_algorithmic": gn_bytes * RP_M / (ms / 1e3) / 1e9,
+                              "bytes_per_obs": gn_bytes}
+    del U, V, W, gws
     best = max(("sort", "atomic", "warpagg"), key=lambda s_: out[f"vjp_{s_}"]["obs_per_s"])
     out["metric"] = "reproj VJP obs/s"
     out["value"] = out[f"vjp_{best}"]["obs_per_s"]

@@ -296,6 +296,29 @@ GPA_API int reproj_vjp(const float* cams, const float* pts, const int32_t* obs, 
                int32_t strat, const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
                gpa_stream_t stream);
 
+/*
+ * Gauss-Newton normal equations of the residual, the blocks of J^T J and J^T r
+ * for J = d res / d(cams, pts) (each observation's 2 x 14 Jacobian rows, from the
+ * reverse pass with unit cotangents):
+ *   U [C][66]  += sum over the camera's observations of J_c^T J_c (11 x 11,
+ *                 upper triangle packed by rows: (a, b), a <= b)
+ *   V [P][6]   += sum over the point's observations of J_p^T J_p (3 x 3, same packing)
+ *   W [M][33]   = J_c^T J_p of each observation (11 x 3 row-major; nullable)
+ *   g_cams [C][11] += J_c^T r,  g_pts [P][3] += J_p^T r,  res [M][2] = r (nullable)
+ * The camera and point blocks are Accum reductions like the VJP's, with a
+ * 66 + 11 and a 6 + 3 float payload. strat: SORT (camera-sorted runs from
+ * `plan`, gpa_obs_plan_build on the same obs) or ATOMIC (input order); AUTO
+ * picks SORT when a plan is given. Out-of-range observations get NaN in W and
+ * res and set GPA_ERR_INDEX. Workspace: gpa_reproj_gn_workspace_bytes. Sums in
+ * float32, order-dependent. The paper has no counterpart of this call; it is
+ * the consumer of the VJP that a least-squares solver needs.
+ */
+GPA_API size_t gpa_reproj_gn_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs);
+GPA_API int reproj_normal_eqs(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
+                              int32_t n_cams, int32_t n_pts, int64_t n_obs, float* U, float* V, float* W,
+                              float* g_cams, float* g_pts, float* res, int32_t strat, const void* plan,
+                              void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
+
 /* JVP of the residual (forward mode, linearize, Sec. 5.1): jv [M][2] =
  * J_cam(j) v_cams[c] + J_pt(j) v_pts[p] for each observation j = (c, p), with
  * tangents v_cams [C][11] and v_pts [P][3] laid out like cams and pts.

@@ -75,6 +75,8 @@ def _load():
             lib.oracle_reproj_jvp.argtypes = [f32p, f32p, i32p, I32, I32, I64, f64p, f64p, f64p]
             lib.oracle_reproj_jvp.restype = I64
             lib.oracle_reproj_jacobian.argtypes = [f32p, f32p, i32p, I64, f64p]
+            lib.oracle_reproj_normal_eqs.argtypes = [f32p, f32p, i32p, f32p, I32, I32, I64] + [vp] * 6
+            lib.oracle_reproj_normal_eqs.restype = I64
             lib.oracle_scatter_add_f64.argtypes = [i32p, f32p, I64, I32, I32, f64p]
             lib.oracle_scatter_add_f64.restype = I64
             lib.oracle_scatter_add_i64.argtypes = [i32p, i32p, I64, I32, I32, i64p]
@@ -195,6 +197,21 @@ def reproj_jacobian(r):
     lib.oracle_reproj_jacobian(_c(r.cams, np.float32), _c(r.pts, np.float32), _c(r.obs, np.int32),
                                r.n_obs, jac)
     return jac
+
+
+def reproj_normal_eqs(r, want_w: bool = True):
+    """Gauss-Newton blocks (U [C][66], V [P][6], W [M][33] or None, g_cams [C][11],
+    g_pts [P][3], res [M][2], skipped count); U and V are upper triangles packed
+    by rows."""
+    lib = _load()
+    U = np.empty((r.n_cams, 66)); V = np.empty((r.n_pts, 6))
+    W = np.empty((r.n_obs, 33)) if want_w else None
+    gc = np.empty((r.n_cams, 11)); gp = np.empty((r.n_pts, 3)); res = np.empty((r.n_obs, 2))
+    bad = lib.oracle_reproj_normal_eqs(_c(r.cams, np.float32), _c(r.pts, np.float32), _c(r.obs, np.int32),
+                                       _c(r.tgt, np.float32), r.n_cams, r.n_pts, r.n_obs, U.ctypes.data,
+                                       V.ctypes.data, None if W is None else W.ctypes.data, gc.ctypes.data,
+                                       gp.ctypes.data, res.ctypes.data)
+    return U, V, W, gc, gp, res, int(bad)
 
 
 def scatter_add(idx, vals, n_buckets: int):

@@ -525,6 +525,66 @@ int64_t oracle_reproj_jvp(const float* cams, const float* pts, const int32_t* ob
     return bad;
 }
 
+/*
+ * Gauss-Newton normal equations of the reprojection (J = d res / d(cams, pts)):
+ *   U[c] = sum_{j: cam c} J_c^T J_c   (11 x 11, upper triangle packed by rows: 66)
+ *   V[p] = sum_{j: point p} J_p^T J_p (3 x 3, upper triangle packed by rows: 6)
+ *   W[j] = J_c^T J_p of observation j (11 x 3 row-major, nullable)
+ *   g_cams[c] = sum J_c^T r_j, g_pts[p] = sum J_p^T r_j, res[j] = r_j (nullable)
+ * with J_c, J_p the 2 x 11 and 2 x 3 blocks of observation j's Jacobian: the
+ * block rows of J^T J, each an Accum into the camera's or the point's slot.
+ * Outputs are overwritten. Parity pinned: (J^T J) v = J^T (J v) through
+ * oracle_reproj_jvp / oracle_reproj_vjp, and a dense J^T J on tiny inputs
+ * (tests). Returns the number of skipped (out-of-range) observations.
+ */
+int64_t oracle_reproj_normal_eqs(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
+                                 int32_t n_cams, int32_t n_pts, int64_t n_obs, double* U, double* V,
+                                 double* W, double* g_cams, double* g_pts, double* res) {
+    double* Jb = (double*)malloc(sizeof(double) * (size_t)n_obs * 2 * NT);
+    double* rb = (double*)malloc(sizeof(double) * (size_t)n_obs * 2);
+    int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t j = 0; j < n_obs; ++j) {
+        if (!obs_ok(obs, j, n_cams, n_pts)) { ++bad; continue; }
+        double val[2], J[2][NT];
+        obs_jacobian(cams, pts, obs[2 * j], obs[2 * j + 1], val, J);
+        for (int o = 0; o < 2; ++o) {
+            rb[2 * j + o] = val[o] - (double)tgt[2 * j + o];
+            for (int a = 0; a < NT; ++a) Jb[(size_t)j * 2 * NT + o * NT + a] = J[o][a];
+        }
+    }
+    memset(U, 0, sizeof(double) * (size_t)n_cams * 66);
+    memset(V, 0, sizeof(double) * (size_t)n_pts * 6);
+    memset(g_cams, 0, sizeof(double) * (size_t)n_cams * 11);
+    memset(g_pts, 0, sizeof(double) * (size_t)n_pts * 3);
+    for (int64_t j = 0; j < n_obs; ++j) {
+        if (!obs_ok(obs, j, n_cams, n_pts)) {
+            if (res) res[2 * j] = res[2 * j + 1] = NAN;
+            if (W) for (int e = 0; e < 33; ++e) W[(size_t)j * 33 + e] = NAN;
+            continue;
+        }
+        const int32_t ci = obs[2 * j], pi = obs[2 * j + 1];
+        const double* J0 = Jb + (size_t)j * 2 * NT;
+        const double* J1 = J0 + NT;
+        const double r0 = rb[2 * j], r1 = rb[2 * j + 1];
+        int e = 0;
+        for (int a = 0; a < 11; ++a)
+            for (int b = a; b < 11; ++b, ++e) U[(size_t)ci * 66 + e] += J0[a] * J0[b] + J1[a] * J1[b];
+        e = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = a; b < 3; ++b, ++e) V[(size_t)pi * 6 + e] += J0[11 + a] * J0[11 + b] + J1[11 + a] * J1[11 + b];
+        if (W)
+            for (int a = 0; a < 11; ++a)
+                for (int b = 0; b < 3; ++b) W[(size_t)j * 33 + a * 3 + b] = J0[a] * J0[11 + b] + J1[a] * J1[11 + b];
+        for (int a = 0; a < 11; ++a) g_cams[(size_t)ci * 11 + a] += J0[a] * r0 + J1[a] * r1;
+        for (int b = 0; b < 3; ++b) g_pts[(size_t)pi * 3 + b] += J0[11 + b] * r0 + J1[11 + b] * r1;
+        if (res) { res[2 * j] = r0; res[2 * j + 1] = r1; }
+    }
+    free(Jb);
+    free(rb);
+    return bad;
+}
+
 /* Per-observation Jacobian rows (M x 2 x 14), for tests on small inputs. */
 void oracle_reproj_jacobian(const float* cams, const float* pts, const int32_t* obs, int64_t n_obs,
                             double* jac) {

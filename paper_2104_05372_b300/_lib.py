@@ -54,6 +54,8 @@ _SIGS = {
     "reproj_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "reproj_residual_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _F, _P, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "reproj_jvp": ([_P, _P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
+    "gpa_reproj_gn_workspace_bytes": ([_I32, _I32, _I64], _SZ),
+    "reproj_normal_eqs": ([_P] * 4 + [_I32, _I32, _I64] + [_P] * 6 + [_I32, _P, _P, _SZ, _P, _P], _I32),
     "reproj_vjp_noalloc": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _P], _I32),
     "gpa_plan_bytes": ([_I64, _I32], _SZ),
     "gpa_plan_workspace_bytes": ([_I64, _I32], _SZ),
@@ -426,6 +428,35 @@ def reproj_jvp(cams, pts, obs, v_cams, v_pts, jv=None, ws=None, status=None, str
                            _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "reproj_jvp")
     return jv
+
+
+def reproj_normal_eqs(cams, pts, obs, tgt, U=None, V=None, W=None, g_cams=None, g_pts=None, res=None,
+                      want_w=False, want_res=False, strat="auto", plan=None, ws=None, status=None, stream=None):
+    """Gauss-Newton blocks (U, V, W, g_cams, g_pts, res): U, V, g_cams, g_pts
+    accumulate (+=, zeros if not given); W and res are written when given (or
+    asked for with want_w / want_res), else None."""
+    nc, npt, no = _reproj_params(cams, pts, obs)
+    _check(tgt, torch.float32, "tgt", (no, 2))
+    dv = cams.device
+    U = torch.zeros(nc, 66, device=dv) if U is None else _check(U, torch.float32, "U", (nc, 66))
+    V = torch.zeros(npt, 6, device=dv) if V is None else _check(V, torch.float32, "V", (npt, 6))
+    g_cams = torch.zeros(nc, 11, device=dv) if g_cams is None else _check(g_cams, torch.float32, "g_cams", (nc, 11))
+    g_pts = torch.zeros(npt, 3, device=dv) if g_pts is None else _check(g_pts, torch.float32, "g_pts", (npt, 3))
+    if W is None and want_w:
+        W = torch.empty(no, 33, device=dv)
+    if W is not None:
+        _check(W, torch.float32, "W", (no, 33))
+    if res is None and want_res:
+        res = torch.empty(no, 2, device=dv)
+    if res is not None:
+        _check(res, torch.float32, "res", (no, 2))
+    ws = workspace(int(load().gpa_reproj_gn_workspace_bytes(nc, npt, no)), dv) if ws is None else ws
+    st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
+    rc = load().reproj_normal_eqs(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, _ptr(U), _ptr(V),
+                                  _ptr(W), _ptr(g_cams), _ptr(g_pts), _ptr(res), st, _ptr(plan), _ptr(ws),
+                                  ws.numel(), _ptr(status), _stream(stream))
+    _ok(rc, "reproj_normal_eqs")
+    return U, V, W, g_cams, g_pts, res
 
 
 def reproj_vjp_noalloc(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=None, status=None,

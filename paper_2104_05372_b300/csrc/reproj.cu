@@ -515,6 +515,150 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
     }
 }
 
+// Gauss-Newton normal equations (J = d res / d(cams, pts), rows from
+// project_vjp with unit cotangents): per camera U += J_c^T J_c (66, upper
+// triangle by rows) and g_cams += J_c^T r, per point V += J_p^T J_p (6) and
+// g_pts += J_p^T r, per observation W = J_c^T J_p (33) and res. A thread takes
+// kGnOpt consecutive observations (camera-sorted from a plan, or in input
+// order), keeps its camera's 77 sums in registers while the camera repeats and
+// adds them when it changes; the lanes of a warp merge their last runs with one
+// segmented scan. The point's 9 sums go out as three 16-byte atomics into
+// padded accumulators (pacc, [P][3] float4: V[0..5], g[0..2], pad).
+constexpr int kGnOpt = 4;
+
+template <bool SORTED>
+__global__ void __launch_bounds__(128) reproj_gn_kernel(
+    const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
+    const float2* __restrict__ tgt, int n_cams, int n_pts, int64_t n_obs, const int32_t* __restrict__ perm,
+    const int32_t* __restrict__ key_s, const int32_t* __restrict__ aux_s, float* __restrict__ U,
+    float* __restrict__ W, float* __restrict__ g_cams, float4* __restrict__ pacc, float2* __restrict__ res,
+    int32_t* __restrict__ status, int pts8) {
+    const int lane = threadIdx.x & 31;
+    const int64_t chunk = (int64_t)blockDim.x * kGnOpt;
+    for (int64_t base = (int64_t)blockIdx.x * chunk; base < n_obs; base += (int64_t)gridDim.x * chunk) {
+        const int64_t pos0 = base + (int64_t)threadIdx.x * kGnOpt;
+        int ev[kGnOpt], cv[kGnOpt], pv[kGnOpt];
+#pragma unroll
+        for (int i = 0; i < kGnOpt; ++i) {
+            const int64_t pos = pos0 + i;
+            if (pos >= n_obs) {
+                ev[i] = cv[i] = pv[i] = -1;
+            } else if (SORTED) {
+                ev[i] = __ldg(perm + pos);
+                cv[i] = __ldg(key_s + pos);
+                pv[i] = __ldg(aux_s + pos);
+            } else {
+                const int2 o = __ldg(obs + pos);
+                ev[i] = (int)pos;
+                cv[i] = o.x;
+                pv[i] = o.y;
+            }
+        }
+        float ua[66], ga[11];
+#pragma unroll
+        for (int a = 0; a < 66; ++a) ua[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 11; ++a) ga[a] = 0.f;
+        int cur = -1, rcam = -1;
+        float rc[kCamRec];
+#pragma unroll
+        for (int i = 0; i < kGnOpt; ++i) {
+            if (pos0 + i >= n_obs) break;
+            const int e = ev[i], ci = cv[i], pi = pv[i];
+            const bool e_ok = e >= 0 && e < n_obs;
+            if (!e_ok || ci < 0 || ci >= n_cams || pi < 0 || pi >= n_pts) {
+                if (e_ok) {
+                    if (res) res[e] = make_float2(NAN, NAN);
+                    if (W)
+                        for (int a = 0; a < 33; ++a) W[(size_t)e * 33 + a] = NAN;
+                }
+                report(status, GPA_ERR_INDEX);
+                continue;
+            }
+            if (ci != cur) {
+                if (cur >= 0) {
+#pragma unroll
+                    for (int a = 0; a < 66; ++a) {
+                        red_add(U + (size_t)cur * 66 + a, ua[a]);
+                        ua[a] = 0.f;
+                    }
+#pragma unroll
+                    for (int a = 0; a < 11; ++a) {
+                        red_add(g_cams + (size_t)cur * 11 + a, ga[a]);
+                        ga[a] = 0.f;
+                    }
+                }
+                cur = ci;
+            }
+            if (ci != rcam) {
+                load_cam<kCamRec>(rec, ci, rc);
+                rcam = ci;
+            }
+            float X0, X1, X2;
+            load_point(pts, pi, pts8, X0, X1, X2);
+            const Proj P = project(rc, X0, X1, X2);
+            const float2 t = __ldg(tgt + e);
+            const float r0 = P.out[0] - t.x, r1 = P.out[1] - t.y;
+            if (res) res[e] = make_float2(r0, r1);
+            float j0c[11], j0p[3], j1c[11], j1p[3];
+            project_vjp(rc, P, 1.f, 0.f, j0c, j0p);
+            project_vjp(rc, P, 0.f, 1.f, j1c, j1p);
+            int q = 0;
+#pragma unroll
+            for (int a = 0; a < 11; ++a) {
+                ga[a] = fmaf(j0c[a], r0, fmaf(j1c[a], r1, ga[a]));
+#pragma unroll
+                for (int b = a; b < 11; ++b, ++q) ua[q] = fmaf(j0c[a], j0c[b], fmaf(j1c[a], j1c[b], ua[q]));
+            }
+            if (W) {
+                float* Wj = W + (size_t)e * 33;
+#pragma unroll
+                for (int a = 0; a < 11; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) Wj[a * 3 + b] = fmaf(j0c[a], j0p[b], j1c[a] * j1p[b]);
+            }
+            float v[9];
+            q = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = a; b < 3; ++b, ++q) v[q] = fmaf(j0p[a], j0p[b], j1p[a] * j1p[b]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[6 + a] = fmaf(j0p[a], r0, j1p[a] * r1);
+            float4* pa = pacc + (size_t)pi * 3;
+            atomicAdd(pa, make_float4(v[0], v[1], v[2], v[3]));
+            atomicAdd(pa + 1, make_float4(v[4], v[5], v[6], v[7]));
+            atomicAdd(pa + 2, make_float4(v[8], 0.f, 0.f, 0.f));
+        }
+        const int ck = cur >= 0 ? cur : -1 - lane;
+        const int head = run_head(ck);
+        const bool last = run_end(ck);  // shuffles: every lane evaluates them
+#pragma unroll
+        for (int a = 0; a < 66; ++a) ua[a] = run_scan_head(ua[a], head);
+#pragma unroll
+        for (int a = 0; a < 11; ++a) ga[a] = run_scan_head(ga[a], head);
+        if (cur >= 0 && last) {
+#pragma unroll
+            for (int a = 0; a < 66; ++a) red_add(U + (size_t)cur * 66 + a, ua[a]);
+#pragma unroll
+            for (int a = 0; a < 11; ++a) red_add(g_cams + (size_t)cur * 11 + a, ga[a]);
+        }
+    }
+}
+
+// V[p] += pacc[p] (first 6), g_pts[p] += pacc[p] (next 3).
+__global__ void __launch_bounds__(256) gn_points_add_kernel(const float4* __restrict__ pacc, int n_pts,
+                                                            float* __restrict__ V, float* __restrict__ g_pts) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pts; p += stride) {
+        const float4 a = pacc[3 * p], b = pacc[3 * p + 1], c = pacc[3 * p + 2];
+        float* v = V + p * 6;
+        v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w; v[4] += b.x; v[5] += b.y;
+        float* g = g_pts + p * 3;
+        g[0] += b.z; g[1] += b.w; g[2] += c.x;
+    }
+}
+
 // d_pts[p] += acc[p].xyz (the padded accumulators of one VJP call).
 __global__ void __launch_bounds__(256) pts4_add_kernel(const float4* __restrict__ acc, int n_pts,
                                                        float* __restrict__ d_pts) {
@@ -717,6 +861,56 @@ extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const in
     if (rc) return rc;
     return dispatch_vjp<true>(strat, rec, pts, obs, nullptr, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams,
                               d_pts, pts_acc(ws, n_cams), res, dev_status, s);
+}
+
+extern "C" size_t gpa_reproj_gn_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs) {
+    (void)n_obs;
+    if (n_cams < 1 || n_pts < 1) return 0;
+    return cam_area(n_cams) + ((sizeof(float4) * 3 * (size_t)n_pts + 255) & ~(size_t)255);
+}
+
+extern "C" int reproj_normal_eqs(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
+                                 int32_t n_cams, int32_t n_pts, int64_t n_obs, float* U, float* V, float* W,
+                                 float* g_cams, float* g_pts, float* res, int32_t strat, const void* plan,
+                                 void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
+    if (!cams || !pts || !obs || !tgt || !U || !V || !g_cams || !g_pts || !ws) return GPA_ERR_ARG;
+    if (n_cams < 1 || n_pts < 1 || n_obs < 1 || n_obs > INT32_MAX) return GPA_ERR_ARG;
+    if (!al(obs, 8) || !al(tgt, 8) || (res && !al(res, 8)) || !al(ws, 256)) return GPA_ERR_ALIGN;
+    if (!al(cams, 4) || !al(pts, 4) || !al(U, 4) || !al(V, 4) || (W && !al(W, 4)) || !al(g_cams, 4) ||
+        !al(g_pts, 4))
+        return GPA_ERR_ALIGN;
+    if (ws_bytes < gpa_reproj_gn_workspace_bytes(n_cams, n_pts, n_obs)) return GPA_ERR_WORKSPACE;
+    strat = resolve_strat(strat, plan);
+    if (strat != GPA_SCATTER_ATOMIC && strat != GPA_SCATTER_SORT) return GPA_ERR_UNSUPPORTED;
+    PlanView pv{};
+    if (strat == GPA_SCATTER_SORT) {
+        if (!plan) return GPA_ERR_ARG;
+        pv = plan_view(plan, n_obs, n_cams);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rec = (float*)ws;
+    float4* pacc = pts_acc(ws, n_cams);
+    int rc = expand_cams(cams, n_cams, rec, s);
+    if (rc) return rc;
+    if (cudaMemsetAsync(pacc, 0, sizeof(float4) * 3 * (size_t)n_pts, s) != cudaSuccess) return GPA_ERR_CUDA;
+    const int64_t want = (n_obs + 128 * kGnOpt - 1) / (128 * kGnOpt), cap = (int64_t)sm_count() * 12;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    const int p8 = al(pts, 8) ? 1 : 0;
+    if (strat == GPA_SCATTER_SORT)
+        GPA_LAUNCH("reproj_normal_eqs", s,
+                   reproj_gn_kernel<true><<<grid, 128, 0, s>>>(rec, pts, (const int2*)obs, (const float2*)tgt,
+                                                               n_cams, n_pts, n_obs, pv.perm, pv.key_sorted,
+                                                               pv.aux_sorted, U, W, g_cams, pacc, (float2*)res,
+                                                               dev_status, p8));
+    else
+        GPA_LAUNCH("reproj_normal_eqs", s,
+                   reproj_gn_kernel<false><<<grid, 128, 0, s>>>(rec, pts, (const int2*)obs, (const float2*)tgt,
+                                                                n_cams, n_pts, n_obs, nullptr, nullptr, nullptr, U,
+                                                                W, g_cams, pacc, (float2*)res, dev_status, p8));
+    const int64_t pw = (n_pts + 255) / 256, pc = (int64_t)sm_count() * 8;
+    GPA_LAUNCH("reproj_gn_points", s,
+               gn_points_add_kernel<<<(unsigned)(pw < pc ? pw : pc), 256, 0, s>>>(pacc, n_pts, V, g_pts));
+    return GPA_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -145,3 +145,73 @@ def test_out_of_range_observations_are_skipped():
     r2 = synth.ReprojInputs(r.cams, r.pts, r.obs[keep].copy(), r.tgt[keep].copy(), r.w[keep].copy())
     dcm2, dpt2, _ = oracle.reproj_vjp(r2)
     assert np.allclose(dcm, dcm2) and np.allclose(dpt, dpt2)
+
+
+def _unpack_upper(packed, n):
+    """Symmetric n x n blocks from upper triangles packed by rows (last axis)."""
+    iu = np.triu_indices(n)
+    out = np.zeros(packed.shape[:-1] + (n, n))
+    out[..., iu[0], iu[1]] = packed
+    out[..., iu[1], iu[0]] = packed
+    return out
+
+
+def _normal_action(r, U, V, W, vc, vp):
+    """(J^T J) v from the blocks: camera rows U v_c + sum_j W_j v_p, point rows
+    V v_p + sum_j W_j^T v_c."""
+    Uf, Vf = _unpack_upper(U, 11), _unpack_upper(V, 3)
+    ac = np.einsum("cab,cb->ca", Uf, vc)
+    ap = np.einsum("pab,pb->pa", Vf, vp)
+    Wm = W.reshape(-1, 11, 3)
+    ci, pi = r.obs[:, 0], r.obs[:, 1]
+    np.add.at(ac, ci, np.einsum("jab,jb->ja", Wm, vp[pi]))
+    np.add.at(ap, pi, np.einsum("jab,ja->jb", Wm, vc[ci]))
+    return ac, ap
+
+
+def test_normal_equations_act_as_jt_j():
+    """(J^T J) v = J^T (J v) with J v from the forward mode and J^T w from the
+    reverse mode (both pinned by central differences of the residual)."""
+    r = synth.reproj_inputs(12, 90, 700, seed=21)
+    U, V, W, gc, gp, res, bad = oracle.reproj_normal_eqs(r)
+    assert bad == 0
+    for s in range(3):
+        vc, vp = synth.reproj_tangents(r.n_cams, r.n_pts, seed=50 + s)
+        jv, _ = oracle.reproj_jvp(r, vc, vp)
+        # the VJP takes float32 cotangents: J v rounded once, about 6e-8 relative
+        rc, rp, _ = oracle.reproj_vjp(r, w=jv.astype(np.float32))
+        ac, ap = _normal_action(r, U, V, W, vc, vp)
+        assert np.max(np.abs(ac - rc)) <= 1e-6 * np.max(np.abs(ac))
+        assert np.max(np.abs(ap - rp)) <= 1e-6 * np.max(np.abs(ap))
+
+
+def test_normal_equations_match_dense_jt_j_on_tiny_inputs():
+    """Every block against the dense (2M x (11C + 3P)) Jacobian's J^T J and J^T r."""
+    r = synth.reproj_inputs(3, 5, 17, seed=8)
+    U, V, W, gc, gp, res, _ = oracle.reproj_normal_eqs(r)
+    jac = oracle.reproj_jacobian(r)  # (M, 2, 14)
+    nc, npt = r.n_cams, r.n_pts
+    J = np.zeros((2 * r.n_obs, 11 * nc + 3 * npt))
+    for j, (c, p) in enumerate(r.obs):
+        J[2 * j:2 * j + 2, 11 * c:11 * c + 11] = jac[j, :, :11]
+        J[2 * j:2 * j + 2, 11 * nc + 3 * p:11 * nc + 3 * p + 3] = jac[j, :, 11:]
+    H = J.T @ J
+    g = J.T @ res.reshape(-1)
+    Uf, Vf = _unpack_upper(U, 11), _unpack_upper(V, 3)
+    for c in range(nc):
+        assert np.allclose(Uf[c], H[11 * c:11 * c + 11, 11 * c:11 * c + 11], rtol=1e-12, atol=1e-9)
+        assert np.allclose(gc[c], g[11 * c:11 * c + 11], rtol=1e-12, atol=1e-9)
+    for p in range(npt):
+        o = 11 * nc + 3 * p
+        assert np.allclose(Vf[p], H[o:o + 3, o:o + 3], rtol=1e-12, atol=1e-9)
+        assert np.allclose(gp[p], g[o:o + 3], rtol=1e-12, atol=1e-9)
+    # off-diagonal blocks: sums of W over observations of the same (camera, point) pair
+    for c in range(nc):
+        for p in range(npt):
+            o = 11 * nc + 3 * p
+            Wsum = sum(W[j].reshape(11, 3) for j in range(r.n_obs) if tuple(r.obs[j]) == (c, p))
+            assert np.allclose(Wsum if np.ndim(Wsum) else np.zeros((11, 3)), H[11 * c:11 * c + 11, o:o + 3],
+                               rtol=1e-12, atol=1e-9)
+    # the residual agrees with the residual function
+    ref, _ = oracle.reproj_residual(r)
+    assert np.allclose(res, ref, rtol=0, atol=0)
