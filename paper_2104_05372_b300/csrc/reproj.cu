@@ -534,6 +534,7 @@ __global__ void __launch_bounds__(128) reproj_gn_kernel(
     float* __restrict__ W, float* __restrict__ g_cams, float4* __restrict__ pacc, float2* __restrict__ res,
     int32_t* __restrict__ status, int pts8) {
     const int lane = threadIdx.x & 31;
+    __shared__ float wstage[4 * 32 * 33];  // per warp: 32 rows of W, one per lane
     const int64_t chunk = (int64_t)blockDim.x * kGnOpt;
     for (int64_t base = (int64_t)blockIdx.x * chunk; base < n_obs; base += (int64_t)gridDim.x * chunk) {
         const int64_t pos0 = base + (int64_t)threadIdx.x * kGnOpt;
@@ -561,74 +562,88 @@ __global__ void __launch_bounds__(128) reproj_gn_kernel(
         for (int a = 0; a < 11; ++a) ga[a] = 0.f;
         int cur = -1, rcam = -1;
         float rc[kCamRec];
+        float* stage = wstage + (threadIdx.x >> 5) * 32 * 33;  // this warp's W rows
 #pragma unroll
         for (int i = 0; i < kGnOpt; ++i) {
-            if (pos0 + i >= n_obs) break;
+            // no early exits: every lane reaches the warp's W store below
             const int e = ev[i], ci = cv[i], pi = pv[i];
-            const bool e_ok = e >= 0 && e < n_obs;
-            if (!e_ok || ci < 0 || ci >= n_cams || pi < 0 || pi >= n_pts) {
-                if (e_ok) {
-                    if (res) res[e] = make_float2(NAN, NAN);
-                    if (W)
-                        for (int a = 0; a < 33; ++a) W[(size_t)e * 33 + a] = NAN;
-                }
+            const bool active = pos0 + i < n_obs;
+            const bool e_ok = active && e >= 0 && e < n_obs;
+            const bool valid = e_ok && ci >= 0 && ci < n_cams && pi >= 0 && pi < n_pts;
+            if (active && !valid) {
+                if (e_ok && res) res[e] = make_float2(NAN, NAN);
                 report(status, GPA_ERR_INDEX);
-                continue;
             }
-            if (ci != cur) {
-                if (cur >= 0) {
+            if (valid) {
+                if (ci != cur) {
+                    if (cur >= 0) {
 #pragma unroll
-                    for (int a = 0; a < 66; ++a) {
-                        red_add(U + (size_t)cur * 66 + a, ua[a]);
-                        ua[a] = 0.f;
+                        for (int a = 0; a < 66; ++a) {
+                            red_add(U + (size_t)cur * 66 + a, ua[a]);
+                            ua[a] = 0.f;
+                        }
+#pragma unroll
+                        for (int a = 0; a < 11; ++a) {
+                            red_add(g_cams + (size_t)cur * 11 + a, ga[a]);
+                            ga[a] = 0.f;
+                        }
                     }
+                    cur = ci;
+                }
+                if (ci != rcam) {
+                    load_cam<kCamRec>(rec, ci, rc);
+                    rcam = ci;
+                }
+                float X0, X1, X2;
+                load_point(pts, pi, pts8, X0, X1, X2);
+                const Proj P = project(rc, X0, X1, X2);
+                const float2 t = __ldg(tgt + e);
+                const float r0 = P.out[0] - t.x, r1 = P.out[1] - t.y;
+                if (res) res[e] = make_float2(r0, r1);
+                float j0c[11], j0p[3], j1c[11], j1p[3];
+                project_vjp(rc, P, 1.f, 0.f, j0c, j0p);
+                project_vjp(rc, P, 0.f, 1.f, j1c, j1p);
+                int q = 0;
 #pragma unroll
-                    for (int a = 0; a < 11; ++a) {
-                        red_add(g_cams + (size_t)cur * 11 + a, ga[a]);
-                        ga[a] = 0.f;
+                for (int a = 0; a < 11; ++a) {
+                    ga[a] = fmaf(j0c[a], r0, fmaf(j1c[a], r1, ga[a]));
+#pragma unroll
+                    for (int b = a; b < 11; ++b, ++q) ua[q] = fmaf(j0c[a], j0c[b], fmaf(j1c[a], j1c[b], ua[q]));
+                }
+                if (W) {
+#pragma unroll
+                    for (int a = 0; a < 11; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b)
+                            stage[lane * 33 + a * 3 + b] = fmaf(j0c[a], j0p[b], j1c[a] * j1p[b]);
+                }
+                float v[9];
+                q = 0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = a; b < 3; ++b, ++q) v[q] = fmaf(j0p[a], j0p[b], j1p[a] * j1p[b]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) v[6 + a] = fmaf(j0p[a], r0, j1p[a] * r1);
+                float4* pa = pacc + (size_t)pi * 3;
+                atomicAdd(pa, make_float4(v[0], v[1], v[2], v[3]));
+                atomicAdd(pa + 1, make_float4(v[4], v[5], v[6], v[7]));
+                atomicAdd(pa + 2, make_float4(v[8], 0.f, 0.f, 0.f));
+            }
+            if (W) {  // the warp writes its 32 rows, each as contiguous stores (NaN rows for bad indices)
+                const int mode = valid ? 1 : (e_ok ? 2 : 0);
+                __syncwarp();
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int mr = __shfl_sync(0xffffffffu, mode, rr);
+                    const int er = __shfl_sync(0xffffffffu, e, rr);
+                    if (mr) {
+                        float* Wr = W + (size_t)er * 33;
+                        Wr[lane] = mr == 1 ? stage[rr * 33 + lane] : NAN;
+                        if (lane == 0) Wr[32] = mr == 1 ? stage[rr * 33 + 32] : NAN;
                     }
                 }
-                cur = ci;
+                __syncwarp();
             }
-            if (ci != rcam) {
-                load_cam<kCamRec>(rec, ci, rc);
-                rcam = ci;
-            }
-            float X0, X1, X2;
-            load_point(pts, pi, pts8, X0, X1, X2);
-            const Proj P = project(rc, X0, X1, X2);
-            const float2 t = __ldg(tgt + e);
-            const float r0 = P.out[0] - t.x, r1 = P.out[1] - t.y;
-            if (res) res[e] = make_float2(r0, r1);
-            float j0c[11], j0p[3], j1c[11], j1p[3];
-            project_vjp(rc, P, 1.f, 0.f, j0c, j0p);
-            project_vjp(rc, P, 0.f, 1.f, j1c, j1p);
-            int q = 0;
-#pragma unroll
-            for (int a = 0; a < 11; ++a) {
-                ga[a] = fmaf(j0c[a], r0, fmaf(j1c[a], r1, ga[a]));
-#pragma unroll
-                for (int b = a; b < 11; ++b, ++q) ua[q] = fmaf(j0c[a], j0c[b], fmaf(j1c[a], j1c[b], ua[q]));
-            }
-            if (W) {
-                float* Wj = W + (size_t)e * 33;
-#pragma unroll
-                for (int a = 0; a < 11; ++a)
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) Wj[a * 3 + b] = fmaf(j0c[a], j0p[b], j1c[a] * j1p[b]);
-            }
-            float v[9];
-            q = 0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = a; b < 3; ++b, ++q) v[q] = fmaf(j0p[a], j0p[b], j1p[a] * j1p[b]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) v[6 + a] = fmaf(j0p[a], r0, j1p[a] * r1);
-            float4* pa = pacc + (size_t)pi * 3;
-            atomicAdd(pa, make_float4(v[0], v[1], v[2], v[3]));
-            atomicAdd(pa + 1, make_float4(v[4], v[5], v[6], v[7]));
-            atomicAdd(pa + 2, make_float4(v[8], 0.f, 0.f, 0.f));
         }
         const int ck = cur >= 0 ? cur : -1 - lane;
         const int head = run_head(ck);
