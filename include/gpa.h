@@ -225,6 +225,8 @@ typedef struct {
     double gamma;
     int32_t m;
     double seed;
+    int32_t prec; /* GPA_PREC_FP32, or GPA_PREC_BF16_TC for 32 < d <= 128 (the tensor-core
+                     path, run instance by instance in the batch's stream) */
 } gpa_gmm_instance;
 
 /* Workspace for gmm_batched_prepare / gmm_batched_vjp over these instances
@@ -239,7 +241,9 @@ GPA_API size_t gpa_gmm_batched_workspace_bytes(const gpa_gmm_instance* inst, int
  * per (instance, component group, point chunk) for the backward Accum; forward
  * and backward lists in longest-first order) and copy them with the instance
  * descriptors into ws. Synchronises `stream` before returning. Call it once per
- * set of instances (pointers, shapes, seeds), before gmm_batched_vjp. */
+ * set of instances (pointers, shapes, seeds, precisions), before gmm_batched_vjp.
+ * With tensor-core instances it also makes, once per device, the library's own
+ * streams and events over which gmm_batched_vjp spreads them. */
 GPA_API int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
                                 void* ws, size_t ws_bytes, gpa_stream_t stream);
 
@@ -250,7 +254,11 @@ GPA_API int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst, in
  * CUDA graph and replayed while the inputs live at the same addresses.
  * ctas_per_sm caps resident CTAs per SM (0 = as many as fit). `inst`,
  * n_inst, chunk_points must equal the gmm_batched_prepare arguments. FP32
- * CUDA-core arithmetic, deterministic like gmm_vjp. */
+ * CUDA-core arithmetic, deterministic like gmm_vjp. Instances with prec =
+ * GPA_PREC_BF16_TC run the tensor-core path of gmm_vjp instead, spread over 8
+ * library streams forked from `stream` with events and joined back into it
+ * (capturable in the same graph); their R sums use shared-memory float atomics,
+ * so their last bits may differ between runs. */
 GPA_API int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
                             int32_t ctas_per_sm, void* ws, size_t ws_bytes, int32_t* dev_status,
                             gpa_stream_t stream);

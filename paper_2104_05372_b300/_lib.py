@@ -306,15 +306,16 @@ class GmmInstance(C.Structure):
     _fields_ = [("x", C.c_void_p), ("alpha", C.c_void_p), ("mu", C.c_void_p), ("q", C.c_void_p),
                 ("l", C.c_void_p), ("d_alpha", C.c_void_p), ("d_mu", C.c_void_p), ("d_q", C.c_void_p),
                 ("d_l", C.c_void_p), ("out", C.c_void_p), ("n", C.c_int64), ("d", C.c_int32), ("k", C.c_int32),
-                ("gamma", C.c_double), ("m", C.c_int32), ("seed", C.c_double)]
+                ("gamma", C.c_double), ("m", C.c_int32), ("seed", C.c_double), ("prec", C.c_int32)]
 
 
 class GmmBatch:
     """Device tensors and descriptors of a batch of GMM instances.
 
     instances: list of dicts with keys x, alpha, mu, q, l (device float32
-    tensors) and optionally gamma, m, seed. Gradient buffers (zeros) and a
-    float64 objective per instance are allocated here.
+    tensors) and optionally gamma, m, seed, prec (PREC_FP32 or PREC_BF16_TC).
+    Gradient buffers (zeros) and a float64 objective per instance are
+    allocated here.
     """
 
     def __init__(self, instances, chunk_points=4096):
@@ -340,7 +341,8 @@ class GmmBatch:
                                  inst["q"].data_ptr(), inst["l"].data_ptr() if t > 0 else 0,
                                  parts[0].data_ptr(), parts[1].data_ptr(), parts[2].data_ptr(),
                                  parts[3].data_ptr() if t > 0 else 0, out.data_ptr(), n, d, k,
-                                 float(inst.get("gamma", 1.0)), int(inst.get("m", 0)), float(inst.get("seed", 1.0)))
+                                 float(inst.get("gamma", 1.0)), int(inst.get("m", 0)), float(inst.get("seed", 1.0)),
+                                 int(inst.get("prec", PREC_FP32)))
         self.desc = arr
         self.n_inst = len(instances)
         self.pairs = sum(n * k for n, d, k in shapes)

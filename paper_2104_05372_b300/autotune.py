@@ -30,7 +30,8 @@ def _cache_path(path=None):
 
 
 def signature(instances) -> str:
-    shapes = [(int(i["x"].shape[0]), int(i["x"].shape[1]), int(i["alpha"].shape[0])) for i in instances]
+    shapes = [(int(i["x"].shape[0]), int(i["x"].shape[1]), int(i["alpha"].shape[0]), int(i.get("prec", 0)))
+              for i in instances]
     h = hashlib.sha256(json.dumps(shapes).encode()).hexdigest()[:16]
     return f"{torch.cuda.get_device_name(instances[0]['x'].device)}|{len(shapes)}|{h}"
 

@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -61,8 +62,50 @@ int gc_of(int dp) { return dp == 16 ? 32 : dp == 32 ? 16 : dp == 64 ? 8 : 2; }
 struct Plan {
     std::vector<BInst> inst;
     std::vector<BItem> items[kClasses][kPhases];
-    size_t off_desc, off_items[kClasses][kPhases], off_counters, off_partials, partial_bytes, off_regions, total;
+    std::vector<int> tc;  // instances on the tensor-core path, run one after another
+    size_t off_desc, off_items[kClasses][kPhases], off_counters, off_partials, partial_bytes, off_regions;
+    size_t off_tc, tc_bytes, total;
 };
+
+// Workspace of one tensor-core instance: the per-call layout with the whole
+// log-joint resident.
+size_t tc_instance_bytes(const gpa_gmm_instance& I) {
+    return gpa_gmm_workspace_bytes(I.n, I.d, I.k, GPA_PREC_BF16_TC, 0);
+}
+
+// Tensor-core instances run as separate launches; small ones would leave most
+// SMs idle one after another, so they are spread over kTcLanes streams forked
+// from (and joined back into) the caller's stream with events: capturable in
+// the same CUDA graph. The streams and events are the library's, made once per
+// device by gmm_batched_prepare (before any capture) and kept for the process.
+constexpr int kTcLanes = 8;
+constexpr int kTcMaxDevices = 64;
+struct TcLanes {
+    cudaStream_t st[kTcLanes];
+    cudaEvent_t fork, join[kTcLanes];
+    bool ready;
+};
+TcLanes g_tc_lanes[kTcMaxDevices];
+std::mutex g_tc_lanes_mu;
+
+TcLanes* tc_lanes(bool create) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTcMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_tc_lanes_mu);
+    TcLanes& L = g_tc_lanes[dev];
+    if (!L.ready && create) {
+        bool ok = cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; ok && i < kTcLanes; ++i)
+            ok = cudaStreamCreateWithFlags(&L.st[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&L.join[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        L.ready = true;
+    }
+    return L.ready ? &L : nullptr;
+}
 
 // Deterministic plan: workspace offsets are relative (base = 0) until bound.
 bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, char* base, Plan& P) {
@@ -74,6 +117,10 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
     for (int i = 0; i < n_inst; ++i) {
         const gpa_gmm_instance& I = in[i];
         if (I.n < 1 || I.d < 1 || I.d > 128 || I.k < 1 || I.k > 4096 || !(I.gamma > 0.0)) return false;
+        if (I.prec == GPA_PREC_BF16_TC) {
+            P.tc.push_back(i);
+            continue;
+        }
         const int dp = gmm_dp(I.d), c = class_of(dp);
         BInst& B = P.inst[i];
         B.n = I.n;
@@ -122,6 +169,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
     // Accum partials of every instance, contiguous so that one memset clears them
     P.off_partials = off;
     for (int i = 0; i < n_inst; ++i) {
+        if (in[i].prec == GPA_PREC_BF16_TC) continue;
         BInst& B = P.inst[i];
         B.bS = (float*)(base + off);
         off = a256(off + sizeof(float) * (size_t)B.nchunks * B.k * nblk(B.dp) * 64);
@@ -131,6 +179,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
     P.partial_bytes = off - P.off_partials;
     P.off_regions = off;
     for (int i = 0; i < n_inst; ++i) {
+        if (in[i].prec == GPA_PREC_BF16_TC) continue;
         BInst& B = P.inst[i];
         const gpa_gmm_instance& I = in[i];
         B.x = I.x; B.alpha = I.alpha; B.mu = I.mu; B.q = I.q; B.l = I.l;
@@ -142,8 +191,54 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
         B.lse = (float*)(base + off);   off = a256(off + sizeof(float) * (size_t)B.n);
         B.lj = (float*)(base + off);    off = a256(off + sizeof(float) * (size_t)B.n * B.k);
     }
+    // one region per stream lane, each reused by the instances of its lane in turn
+    P.off_tc = off;
+    P.tc_bytes = 0;
+    for (int i : P.tc) P.tc_bytes = std::max(P.tc_bytes, a256(tc_instance_bytes(in[i])));
+    off += P.tc_bytes * (size_t)std::min<int>(kTcLanes, (int)P.tc.size());
     P.total = off;
     return true;
+}
+
+// Fork the lanes from s and enqueue the tensor-core instances on them; the
+// caller enqueues the FP32 classes on s meanwhile and then calls tc_join.
+int tc_fork_and_run(const gpa_gmm_instance* in, const Plan& P, char* ws, int32_t* status, cudaStream_t s) {
+    if (P.tc.empty()) return GPA_OK;
+    TcLanes* T = tc_lanes(false);
+    if (!T) return GPA_ERR_CUDA;  // gmm_batched_prepare makes the lanes
+    const int lanes = std::min<int>(kTcLanes, (int)P.tc.size());
+    if (cudaEventRecord(T->fork, s) != cudaSuccess) return GPA_ERR_CUDA;
+    for (int j = 0; j < lanes; ++j)
+        if (cudaStreamWaitEvent(T->st[j], T->fork, 0) != cudaSuccess) return GPA_ERR_CUDA;
+    // longest instances first, dealt round-robin over the lanes
+    std::vector<int> order(P.tc);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int u, int v) { return in[u].n * in[u].k > in[v].n * in[v].k; });
+    int rc = GPA_OK;
+    for (size_t t = 0; t < order.size() && rc == GPA_OK; ++t) {
+        const int j = (int)(t % lanes);
+        const gpa_gmm_instance& I = in[order[t]];
+        GmmArgs A{};
+        A.x = I.x; A.alpha = I.alpha; A.mu = I.mu; A.q = I.q; A.l = I.l; A.n = I.n; A.d = I.d; A.k = I.k;
+        A.gamma = I.gamma; A.m = I.m; A.seed = I.seed; A.out = I.out; A.status = status;
+        A.d_alpha = I.d_alpha; A.d_mu = I.d_mu; A.d_q = I.d_q; A.d_l = I.d_l;
+        const GmmLayout L = gmm_layout(I.n, I.d, I.k, 0);
+        rc = gmm_tc_vjp_run(A, L, ws + P.off_tc + (size_t)j * P.tc_bytes, P.tc_bytes, T->st[j]);
+    }
+    return rc;
+}
+
+// Join every forked lane back into s (also after an error, so that no lane
+// stays forked, which would leave a graph capture unjoined).
+int tc_join(const Plan& P, cudaStream_t s) {
+    if (P.tc.empty()) return GPA_OK;
+    TcLanes* T = tc_lanes(false);
+    if (!T) return GPA_ERR_CUDA;
+    const int lanes = std::min<int>(kTcLanes, (int)P.tc.size());
+    for (int j = 0; j < lanes; ++j)
+        if (cudaEventRecord(T->join[j], T->st[j]) != cudaSuccess || cudaStreamWaitEvent(s, T->join[j], 0) != cudaSuccess)
+            return GPA_ERR_CUDA;
+    return GPA_OK;
 }
 
 // ---- persistent kernels -----------------------------------------------------------
@@ -295,6 +390,8 @@ int check_instances(const gpa_gmm_instance* in, int n_inst) {
             return GPA_ERR_ARG;
         if (I.n < 1 || I.n > INT32_MAX || I.d < 1 || I.d > 128 || I.k < 1 || I.k > 4096 || !(I.gamma > 0.0))
             return GPA_ERR_ARG;
+        if (I.prec != GPA_PREC_FP32 && I.prec != GPA_PREC_BF16_TC) return GPA_ERR_ARG;
+        if (I.prec == GPA_PREC_BF16_TC && !gmm_tc_supported(I.d)) return GPA_ERR_UNSUPPORTED;
     }
     return GPA_OK;
 }
@@ -321,6 +418,7 @@ extern "C" int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst,
     Plan P;
     if (!make_plan(inst, n_inst, chunk_points, (char*)ws, P)) return GPA_ERR_ARG;
     if (ws_bytes < P.total) return GPA_ERR_WORKSPACE;
+    if (!P.tc.empty() && !tc_lanes(true)) return GPA_ERR_CUDA;
     // host image of descriptors and work lists, copied in one transfer
     std::vector<char> img(P.off_regions, 0);
     memcpy(img.data() + P.off_desc, P.inst.data(), sizeof(BInst) * P.inst.size());
@@ -352,9 +450,12 @@ extern "C" int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int
     if (cudaMemsetAsync((char*)ws + P.off_counters, 0, sizeof(int) * kClasses * kPhases, s) != cudaSuccess ||
         cudaMemsetAsync((char*)ws + P.off_partials, 0, P.partial_bytes, s) != cudaSuccess)
         return GPA_ERR_CUDA;
-    if ((rc = run_class<16>(P, (char*)ws, 0, ctas_per_sm, dev_status, s))) return rc;
-    if ((rc = run_class<32>(P, (char*)ws, 1, ctas_per_sm, dev_status, s))) return rc;
-    if ((rc = run_class<64>(P, (char*)ws, 2, ctas_per_sm, dev_status, s))) return rc;
-    if ((rc = run_class<128>(P, (char*)ws, 3, ctas_per_sm, dev_status, s))) return rc;
-    return GPA_OK;
+    // tensor-core instances on the forked lanes, concurrently with the FP32 classes on s
+    rc = tc_fork_and_run(inst, P, (char*)ws, dev_status, s);
+    if (!rc) rc = run_class<16>(P, (char*)ws, 0, ctas_per_sm, dev_status, s);
+    if (!rc) rc = run_class<32>(P, (char*)ws, 1, ctas_per_sm, dev_status, s);
+    if (!rc) rc = run_class<64>(P, (char*)ws, 2, ctas_per_sm, dev_status, s);
+    if (!rc) rc = run_class<128>(P, (char*)ws, 3, ctas_per_sm, dev_status, s);
+    const int jr = tc_join(P, s);
+    return rc ? rc : jr;
 }

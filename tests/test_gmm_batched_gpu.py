@@ -6,7 +6,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import TOL_GRAD_FP32, TOL_OBJ_FP32, host, rel_norm, status
+from gpu_util import TOL_BF16, TOL_GRAD_FP32, TOL_OBJ_FP32, host, rel_norm, status
 
 pytestmark = pytest.mark.gpu
 
@@ -31,10 +31,12 @@ def _check(gs, inst, batch, which=None):
         f_ref, *gref = oracle.gmm_grad(g, seed=inst[i]["seed"])
         f_ref0 = oracle.gmm_objective(g)
         out, grads = res[i]
-        assert abs(float(out.item()) - f_ref0) <= TOL_OBJ_FP32 * abs(f_ref0), (i, float(out.item()), f_ref0)
+        tc = inst[i].get("prec", 0) == 1
+        tol_f, tol_g = (TOL_BF16, TOL_BF16) if tc else (TOL_OBJ_FP32, TOL_GRAD_FP32)
+        assert abs(float(out.item()) - f_ref0) <= tol_f * abs(f_ref0), (i, float(out.item()), f_ref0)
         for name, gb, rb in zip(("alpha", "mu", "q", "l"), grads, gref):
             if rb.size:
-                assert rel_norm(host(gb), rb) <= TOL_GRAD_FP32, (i, name)
+                assert rel_norm(host(gb), rb) <= tol_g, (i, name)
 
 
 @pytest.mark.parametrize("chunk", [64, 1024])
@@ -97,17 +99,71 @@ def test_autotuner_picks_and_caches(tmp_path):
 
 @pytest.mark.slow
 def test_full_batched_workload_sampled_instances():
-    """512 instances with the batched workload's shape law; 12 sampled instances
-    compared with the oracle."""
+    """512 instances with the batched workload's shape law (D = 64 instances on the
+    tensor cores); 12 sampled instances compared with the oracle."""
     from paper_2104_05372_b300._lib import GmmBatch
     shapes = synth.batched_shapes(512, seed=0)
     gs = synth.batched_inputs(shapes, seed=0)
     inst = [dict(x=torch.from_numpy(g.x).cuda(), alpha=torch.from_numpy(g.alpha).cuda(),
                  mu=torch.from_numpy(g.mu).cuda(), q=torch.from_numpy(g.q).cuda(),
                  l=torch.from_numpy(g.l).cuda(), gamma=g.gamma, m=g.m, seed=1.0) for g in gs]
+    inst = _tensor_cores_where_supported(inst)  # the D = 64 instances: BF16 contraction
     b = GmmBatch(inst, chunk_points=4096)
     b.prepare()
     b.run()
     torch.cuda.synchronize()
     which = sorted(set(np.random.default_rng(0).choice(512, 12, replace=False).tolist()))
     _check(gs, inst, b, which=which)
+
+
+def _tensor_cores_where_supported(inst):
+    for i in inst:
+        if 32 < i["x"].shape[1] <= 128:
+            i["prec"] = 1  # GPA_PREC_BF16_TC
+    return inst
+
+
+def test_mixed_precision_batch_matches_oracle():
+    """Instances with 32 < D <= 128 on the tensor-core path (BF16 bound), the
+    rest on the FP32 persistent kernels, in one batch."""
+    from paper_2104_05372_b300._lib import GmmBatch
+    gs, inst = _instances(SHAPES, seed=21)
+    inst = _tensor_cores_where_supported(inst)
+    assert sum(i.get("prec", 0) for i in inst) == 4
+    b = GmmBatch(inst, chunk_points=1024)
+    b.prepare()
+    st = status()
+    b.run(status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    _check(gs, inst, b)
+
+
+def test_mixed_precision_graph_replay():
+    from paper_2104_05372_b300._lib import GmmBatch
+    gs, inst = _instances(SHAPES[4:10], seed=23)
+    inst = _tensor_cores_where_supported(inst)
+    b = GmmBatch(inst, chunk_points=1024)
+    b.prepare()
+    b.run()
+    torch.cuda.synchronize()
+    ref = [(float(o.item()), [host(t).copy() for t in g]) for o, g in b.results()]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.run()
+    b.zero_grads()
+    graph.replay()
+    torch.cuda.synchronize()
+    for (o, g), (fo, fg) in zip(b.results(), ref):
+        assert abs(float(o.item()) - fo) <= 1e-9 * abs(fo)
+        for u, v in zip(g, fg):
+            assert rel_norm(host(u), v) <= 1e-6
+
+
+def test_tensor_core_instance_outside_its_range_is_rejected():
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300._lib import GmmBatch
+    _, inst = _instances([(100, 32, 3)], seed=1)
+    inst[0]["prec"] = 1
+    with pytest.raises(gpa.GpaError):
+        GmmBatch(inst).prepare()
