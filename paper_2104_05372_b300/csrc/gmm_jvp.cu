@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) gmm_jvp_kernel(const float* __restrict__ 
             const float* Qd = Q + REC;
             const int rb0 = wl, rb1 = C::NB - 1 - wl;
             float zb[4][16];
-            fwd_gemm<DP>(Xs, Q, lane, wl, zb);
+            fwd_gemm_packed<DP>(Xs, Q, lane, wl, zb);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const float b0 = Q[DP * DP + rb0 * 8 + i], b1 = Q[DP * DP + rb1 * 8 + i];
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) gmm_jvp_kernel(const float* __restrict__ 
                 }
             }
             float zd[4][16];
-            fwd_gemm<DP>(Xs, Qd, lane, wl, zd);
+            fwd_gemm_packed<DP>(Xs, Qd, lane, wl, zd);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float s2 = 0.f, sd = 0.f;

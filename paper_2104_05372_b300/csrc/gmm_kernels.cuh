@@ -165,17 +165,22 @@ __global__ void __launch_bounds__(128) gmm_prep_kernel(const float* __restrict__
 // ---------------------------------------------------------------------------
 // Z tile for one component: warp `wl` of the component owns row blocks rb0 = wl
 // and rb1 = NB-1-wl (so every warp does the same work on the triangle), lane
-// owns points 4*lane .. 4*lane+3. Row r needs c <= r only.
+// owns points 4*lane .. 4*lane+3. Row r needs c <= r only. The accumulators
+// are packed float32 pairs along Q's rows: the operand pairs of Q come straight
+// from the 16-byte loads and only the four point values need a broadcast per
+// step, so 32 packed FMAs (each two float32 FMAs, rounded as the scalar
+// instruction would) do the work of 64 scalar ones.
 template <int DP>
-__device__ __forceinline__ void fwd_gemm(const float* __restrict__ Xs, const float* __restrict__ Q,
-                                         int lane, int wl, float (&acc)[4][16]) {
+__device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, const float* __restrict__ Q,
+                                                int lane, int wl, float (&acc)[4][16]) {
     constexpr int NB = Fwd<DP>::NB, XST = Fwd<DP>::XST;
     const int rb0 = wl, rb1 = NB - 1 - wl;
     const int ce0 = 8 * (rb0 + 1), ce1 = 8 * (rb1 + 1);
+    f2_t a2[4][8];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc[j][i] = 0.f;
+        for (int i = 0; i < 8; ++i) a2[j][i] = 0ull;
     const float* xp = Xs + lane * 4;
     const float* qa = Q + rb0 * 8;
     const float* qb = Q + rb1 * 8;
@@ -187,26 +192,38 @@ __device__ __forceinline__ void fwd_gemm(const float* __restrict__ Xs, const flo
         const float4 a1 = *reinterpret_cast<const float4*>(qa + c * DP + 4);
         const float4 b0 = *reinterpret_cast<const float4*>(qb + c * DP);
         const float4 b1 = *reinterpret_cast<const float4*>(qb + c * DP + 4);
+        const f2_t qs[8] = {f2_pack(a0.x, a0.y), f2_pack(a0.z, a0.w), f2_pack(a1.x, a1.y), f2_pack(a1.z, a1.w),
+                            f2_pack(b0.x, b0.y), f2_pack(b0.z, b0.w), f2_pack(b1.x, b1.y), f2_pack(b1.z, b1.w)};
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-        const float qs[16] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
-                              b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 4; ++j) {
+            const f2_t xb = f2_bcast(xs[j]);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[j][i] = fmaf(xs[j], qs[i], acc[j][i]);
+            for (int i = 0; i < 8; ++i) a2[j][i] = f2_fma(xb, qs[i], a2[j][i]);
+        }
     }
 #pragma unroll 2
     for (; c < ce1; ++c) {
         const float4 xv = *reinterpret_cast<const float4*>(xp + c * XST);
         const float4 b0 = *reinterpret_cast<const float4*>(qb + c * DP);
         const float4 b1 = *reinterpret_cast<const float4*>(qb + c * DP + 4);
+        const f2_t qs[4] = {f2_pack(b0.x, b0.y), f2_pack(b0.z, b0.w), f2_pack(b1.x, b1.y), f2_pack(b1.z, b1.w)};
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-        const float qs[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 4; ++j) {
+            const f2_t xb = f2_bcast(xs[j]);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc[j][8 + i] = fmaf(xs[j], qs[i], acc[j][8 + i]);
+            for (int i = 0; i < 4; ++i) a2[j][4 + i] = f2_fma(xb, qs[i], a2[j][4 + i]);
+        }
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float2 v = f2_unpack(a2[j][i]);
+            acc[j][2 * i] = v.x;
+            acc[j][2 * i + 1] = v.y;
+        }
 }
 
 // One CTA per tile of 128 points. x, lj, lse are chunk-local; the objective
@@ -278,7 +295,7 @@ __device__ __forceinline__ void gmm_fwd_kernel_body(const float* __restrict__ x,
         if (kk < k) {
             const float* Q = Qb + (buf * NS + slot) * REC;
             float acc[4][16];
-            fwd_gemm<DP>(Xs, Q, lane, wl, acc);
+            fwd_gemm_packed<DP>(Xs, Q, lane, wl, acc);
             const int rb0 = wl, rb1 = C::NB - 1 - wl;
             float bv[16];
 #pragma unroll
@@ -523,7 +540,7 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
             const float* xb = Xb + 8 * b;
             const int ha = ((a >> 2) & 1) << 2, hb = ((b >> 2) & 1) << 2;
             if (diag) {
-#pragma unroll 1
+#pragma unroll 2
                 for (int p = 0; p < TPB; ++p) {
                     const float4 a0 = *reinterpret_cast<const float4*>(xa + p * XST + ha);
                     const float4 a1 = *reinterpret_cast<const float4*>(xa + p * XST + (4 ^ ha));
