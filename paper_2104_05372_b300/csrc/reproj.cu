@@ -450,6 +450,20 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
                 pv[i] = in ? __ldg(aux_s + pos0 + i) : -1;
             }
         }
+        // the random gathers of every observation of the thread first (points,
+        // cotangents or targets), so that they are in flight together
+        float xq[kOpt][3];
+        float2 wq[kOpt];
+#pragma unroll
+        for (int i = 0; i < kOpt; ++i) {
+            const bool ok = pos0 + i < n_obs && ev[i] >= 0 && ev[i] < n_obs && pv[i] >= 0 && pv[i] < n_pts;
+            xq[i][0] = xq[i][1] = xq[i][2] = 0.f;
+            wq[i] = make_float2(0.f, 0.f);
+            if (ok) {
+                load_point(pts, pv[i], pts8, xq[i][0], xq[i][1], xq[i][2]);
+                wq[i] = __ldg((FUSED ? tgt : wv) + ev[i]);
+            }
+        }
         float gc[11];
 #pragma unroll
         for (int i = 0; i < 11; ++i) gc[i] = 0.f;
@@ -480,20 +494,17 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
                 load_cam<kCamRec>(rec, ci, rc);
                 rcam = ci;
             }
-            float X0, X1, X2;
-            load_point(pts, pi, pts8, X0, X1, X2);
-            const Proj P = project(rc, X0, X1, X2);
+            const Proj P = project(rc, xq[i][0], xq[i][1], xq[i][2]);
             float w0, w1;
             if (FUSED) {
-                const float2 t = __ldg(tgt + e);
+                const float2 t = wq[i];
                 const float r0 = P.out[0] - t.x, r1 = P.out[1] - t.y;
                 res[e] = make_float2(r0, r1);
                 w0 = wscale * r0;
                 w1 = wscale * r1;
             } else {
-                const float2 w = __ldg(wv + e);
-                w0 = w.x;
-                w1 = w.y;
+                w0 = wq[i].x;
+                w1 = wq[i].y;
             }
             float gl[11], gp[3];
             project_vjp(rc, P, w0, w1, gl, gp);
