@@ -191,9 +191,11 @@ GPA_API int gmm_jvp(const float* x, const float* alpha, const float* mu, const f
 GPA_API int64_t gpa_gmm_exchange_len(int32_t d, int32_t k); /* 0 on bad arguments */
 
 /* Shard half: arguments as gmm_vjp for this rank's n points (logjoint_in /
- * lse_in of the shard, or both NULL); writes (=) the exchange vector exch
- * (device, 8-byte aligned). seed scales every term as in gmm_vjp. Workspace:
- * gpa_gmm_workspace_bytes(n, d, k, prec, .) of the shard. */
+ * lse_in of the shard, or both NULL); adds (+=) the shard's exchange vector
+ * into exch (device, 8-byte aligned, zeroed by the caller), so that successive
+ * calls over chunks of the points accumulate them. seed scales every term as
+ * in gmm_vjp. Workspace: gpa_gmm_workspace_bytes(n, d, k, prec, .) of the
+ * shard (or chunk). */
 GPA_API int gmm_vjp_partial(const float* x, const float* alpha, const float* mu, const float* q,
                             const float* l, int64_t n, int32_t d, int32_t k, double gamma, int32_t m,
                             int32_t prec, const float* logjoint_in, const float* lse_in, double seed,

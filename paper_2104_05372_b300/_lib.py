@@ -250,11 +250,12 @@ def gpa_gmm_exchange_len(d, k) -> int:
 
 def gmm_vjp_partial(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, logjoint_in=None, lse_in=None,
                     seed=1.0, exch=None, ws=None, logjoint_points=0, status=None, stream=None):
-    """Exchange vector (device float64) of this shard of points; returns it."""
+    """Exchange vector (device float64) of this shard of points added (+=) into
+    ``exch`` (zeros if not given); returns it."""
     n, d, k = _gmm_params(x, alpha, mu, q, l)
     dev = x.device
     e = gpa_gmm_exchange_len(d, k)
-    exch = torch.empty(e, dtype=torch.float64, device=dev) if exch is None else _check(exch, torch.float64,
+    exch = torch.zeros(e, dtype=torch.float64, device=dev) if exch is None else _check(exch, torch.float64,
                                                                                         "exch", (e,))
     if logjoint_in is not None:
         _check(logjoint_in, torch.float32, "logjoint_in", (k, n))

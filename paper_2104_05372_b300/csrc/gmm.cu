@@ -185,7 +185,8 @@ static int launch_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int n
 template <int DP>
 static int launch_exchange(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, cudaStream_t s) {
     GPA_LAUNCH("gmm_exchange", s,
-               gmm_exchange_kernel<DP><<<A.k + 1, 256, 0, s>>>((const float*)(ws + L.off_bS),
+               gmm_exchange_kernel<DP><<<dim3(A.k + 1, (gmm_bwd_partial_entries(DP) + DP + 1 + 255) / 256), 256, 0,
+                                         s>>>((const float*)(ws + L.off_bS),
                                                                (const float*)(ws + L.off_bM), nchunks, A.k,
                                                                (const double*)(ws + L.off_fwd), L.ntiles,
                                                                A.exch_out));

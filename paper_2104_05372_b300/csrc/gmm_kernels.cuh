@@ -726,28 +726,31 @@ __global__ void __launch_bounds__(256) gmm_finalize_kernel(
 
 // Exchange vector of one shard of points: per component the chunk partial sums
 // [S blocks | m | R] combined in chunk order in float64, then the sum of the
-// shard's per-point logsumexp (tile partials in tile order). Sums of these
-// vectors over shards are the Accum sums of all points (Sec. 2.3.2).
+// shard's per-point logsumexp (tile partials in tile order), added (+=) into
+// exch. Sums of these vectors over shards are the Accum sums of all points
+// (Sec. 2.3.2).
 template <int DP>
 __global__ void __launch_bounds__(256) gmm_exchange_kernel(const float* __restrict__ partS,
                                                            const float* __restrict__ partM, int nchunks, int k,
                                                            const double* __restrict__ fwd_part, int64_t ntiles,
                                                            double* __restrict__ exch) {
+    // grid (k + 1, ceil(E / 256)): one entry per thread, its chunks summed in order
     constexpr int NS = Bwd<DP>::NBLK * 64, E = NS + DP + 1;
     const int kk = blockIdx.x;
     if (kk < k) {
-        for (int e = threadIdx.x; e < NS; e += 256) {
+        const int e = blockIdx.y * 256 + threadIdx.x;
+        if (e < NS) {
             double s = 0.0;
             for (int c = 0; c < nchunks; ++c) s += partS[((int64_t)c * k + kk) * NS + e];
-            exch[(size_t)kk * E + e] = s;
-        }
-        for (int e = threadIdx.x; e < DP + 1; e += 256) {
+            exch[(size_t)kk * E + e] += s;
+        } else if (e < E) {
             double s = 0.0;
-            for (int c = 0; c < nchunks; ++c) s += partM[((int64_t)c * k + kk) * (DP + 1) + e];
-            exch[(size_t)kk * E + NS + e] = s;
+            for (int c = 0; c < nchunks; ++c) s += partM[((int64_t)c * k + kk) * (DP + 1) + (e - NS)];
+            exch[(size_t)kk * E + e] += s;
         }
         return;
     }
+    if (blockIdx.y != 0) return;
     __shared__ double sh[256];
     double s = 0.0;
     for (int64_t t = threadIdx.x; t < ntiles; t += 256) s += fwd_part[t];
@@ -757,7 +760,7 @@ __global__ void __launch_bounds__(256) gmm_exchange_kernel(const float* __restri
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) exch[(size_t)k * E] = sh[0];
+    if (threadIdx.x == 0) exch[(size_t)k * E] += sh[0];
 }
 
 

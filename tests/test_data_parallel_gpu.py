@@ -60,13 +60,13 @@ def test_tensor_core_shards_match_oracle(n, d, k, world):
 
 def test_exchange_vector_is_additive_over_shards():
     """partial(all points) == partial(first half) + partial(second half), up to
-    FP32 rounding of the per-chunk sums."""
+    FP32 rounding of the per-chunk sums; successive calls accumulate (+=)."""
     import paper_2104_05372_b300 as gpa
     g = synth.gmm_inputs(4096, 24, 6, seed=5)
     x, a, mu, q, l = gmm_dev(g)
     full = gpa.gmm_vjp_partial(x, a, mu, q, l, g.gamma, g.m)
-    h = gpa.gmm_vjp_partial(x[:2048].contiguous(), a, mu, q, l, g.gamma, g.m) + \
-        gpa.gmm_vjp_partial(x[2048:].contiguous(), a, mu, q, l, g.gamma, g.m)
+    h = gpa.gmm_vjp_partial(x[:2048].contiguous(), a, mu, q, l, g.gamma, g.m)
+    gpa.gmm_vjp_partial(x[2048:].contiguous(), a, mu, q, l, g.gamma, g.m, exch=h)
     assert rel_norm(host(h), host(full)) <= 1e-5
 
 
@@ -98,3 +98,25 @@ def test_finalize_rejects_bad_arguments():
     with pytest.raises(gpa.GpaError) as e:
         gpa.gmm_vjp_finalize(a, mu, q, l, 100, exch, prec=gpa.PREC_BF16_TC)
     assert e.value.code == 6
+
+
+@pytest.mark.parametrize("n,chunk", [(5000, 1024), (300, 1 << 18), (1 << 15, 4096)])
+def test_streamed_from_host_matches_device_call(n, chunk):
+    """Points in pinned host memory, copied chunk by chunk on a side stream while
+    the previous chunk accumulates: the same gradient and objective as one call
+    on device-resident points (float32 partial sums in another grouping)."""
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300 import data_parallel as dp
+    g = synth.gmm_inputs(n, 24, 7, seed=n)
+    x, a, mu, q, l = gmm_dev(g)
+    out1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    one = [host(t) for t in gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, out=out1)]
+    xh = torch.from_numpy(g.x).pin_memory()
+    out2 = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = status()
+    grads = dp.gmm_vjp_from_host(xh, a, mu, q, l, g.gamma, g.m, chunk_points=chunk, out=out2)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert abs(float(out2.item()) - float(out1.item())) <= 1e-9 * abs(float(out1.item()))
+    for u, v in zip([host(t) for t in grads], one):
+        assert rel_norm(u, v) <= 1e-5
