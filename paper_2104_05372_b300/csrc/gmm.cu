@@ -132,7 +132,10 @@ template <int DP>
 static int bwd_chunks(int k, int64_t ntiles) {
     using C = Bwd<DP>;
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gmm_bwd_kernel<DP>, C::THREADS, C::SMEM);
+    // the dynamic shared-memory limit must be raised before the query, or a
+    // CTA above the 48 KB default reports no residency at all
+    if (set_smem(gmm_bwd_kernel<DP>, C::SMEM))
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gmm_bwd_kernel<DP>, C::THREADS, C::SMEM);
     if (occ < 1) occ = 1;
     const int slots = num_sms() * occ;
     const int groups = (k + C::GC - 1) / C::GC;

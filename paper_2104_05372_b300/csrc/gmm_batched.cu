@@ -57,7 +57,7 @@ int nblk(int dp) { return (dp / 8) * (dp / 8 + 1) / 2; }
 int bwd_tpb(int dp) {
     return dp == 16 ? Bwd<16>::TPB : dp == 32 ? Bwd<32>::TPB : dp == 64 ? Bwd<64>::TPB : Bwd<128>::TPB;
 }
-int gc_of(int dp) { return dp == 16 ? 32 : dp == 32 ? 16 : dp == 64 ? 8 : 2; }
+int gc_of(int dp) { return dp == 16 ? Bwd<16>::GC : dp == 32 ? Bwd<32>::GC : dp == 64 ? Bwd<64>::GC : Bwd<128>::GC; }
 
 struct Plan {
     std::vector<BInst> inst;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256, (DP <= 64 ? 2 : 1))
 }
 
 template <int DP>
-__global__ void __launch_bounds__(Bwd<DP>::THREADS) __maxnreg__(DP == 64 ? 96 : 168)
+__global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
     batched_bwd_kernel(const BInst* __restrict__ inst, const BItem* __restrict__ items, int n_items,
                        int* counter) {
     for (;;) {

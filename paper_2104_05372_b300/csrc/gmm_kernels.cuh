@@ -36,20 +36,63 @@ __host__ __device__ __forceinline__ int bwd_swz(int c) {
     return (a << 3) + ((h ^ ((a >> 2) & 1)) << 2) + (c & 3);
 }
 
+// Backward layout. Every thread owns one full 8x8 block (a, b), a >= b, of one
+// component's S and runs the same instruction stream: diagonal blocks are
+// accumulated in full (their upper halves are dropped at the write-out), and
+// the m and R sums are spread over the threads as MP extra packed FMAs per
+// point each (see bwd_mtask). GC components per CTA.
 template <int DP>
 struct Bwd {
     static constexpr int NB = DP / 8;
-    static constexpr int NOFF = NB * (NB - 1) / 2;     // strictly-lower 8x8 blocks
     static constexpr int NBLK = NB * (NB + 1) / 2;     // lower blocks incl. diagonal
-    static constexpr int GC = DP == 16 ? 32 : DP == 32 ? 16 : DP == 64 ? 8 : 2;  // components per CTA
-    static constexpr int NDIAG_T = GC * NB;            // threads on diagonal blocks
-    static constexpr int NOFF_T = GC * NOFF;           // threads on off-diagonal blocks
-    static constexpr int THREADS = ((NDIAG_T + NOFF_T + 31) / 32) * 32;
-    static constexpr int TPB = 128;                    // points per tile
-    static constexpr int XST = DP + 4;                 // row stride of Xs[p][c]
-    // double-buffered: point tiles, raw log-joint and lse, and the cotangents r
-    static constexpr size_t SMEM = sizeof(float) * (size_t)(2 * TPB * XST + 2 * GC * TPB + 2 * TPB + 2 * TPB * GC);
+    static constexpr int GC = DP == 16 ? 42 : DP == 32 ? 25 : DP == 64 ? 7 : 3;  // components per CTA
+    static constexpr int TPB = DP == 64 ? 128 : DP == 16 ? 32 : 64;  // points per tile
+    static constexpr int MP = NB == 2 ? 3 : NB == 4 ? 2 : 1;  // m / R pairs per thread
+    static constexpr int NACT = GC * NBLK;               // threads with a block
+    static constexpr int THREADS = ((NACT + 31) / 32) * 32;
+    static constexpr int MINB = DP == 16 ? 3 : DP == 128 ? 1 : 2;  // resident CTAs per SM
+    static constexpr int XST = DP + 4;  // row stride of the point tiles; floats DP, DP+1 hold 1.0
+    // point tiles double-buffered; raw log-joint, lse and the cotangents r
+    // triple-buffered
+    static constexpr size_t SMEM = sizeof(float) * (size_t)(2 * TPB * XST + 3 * GC * TPB + 3 * TPB + 3 * TPB * GC);
 };
+
+// The m / R task of slot s of the thread on block (a, b): the natural
+// coordinate index 2j of the pair (m_2j, m_2j+1) it accumulates, DP for R
+// (operand: the constant 1.0 pair at the end of each tile row), or -1 (no task).
+// Each of the 4 NB pairs of m and R goes to exactly one (block, slot) whose
+// row or column chunk holds the pair:
+//   NB >= 8: pair (c, 0) on (c, c); pair (c, s), s = 1..3, on the block of
+//            chunks {c, c + s mod NB}; R on (4, 0);
+//   NB == 4, NB == 2: the tables below.
+template <int NB>
+__host__ __device__ __forceinline__ int bwd_mtask(int a, int b, int s) {
+    if constexpr (NB >= 8) {
+        if (s != 0) return -1;
+        if (a == b) return 8 * a;
+        if (a == 4 && b == 0) return 8 * NB;
+        const int s1 = a - b, s2 = NB - s1;
+        if (s1 <= 3) return 8 * b + 2 * s1;
+        if (s2 <= 3) return 8 * a + 2 * s2;
+        return -1;
+    } else if constexpr (NB == 4) {
+        if (a == b) return s < 2 ? 8 * a + 2 * s : -1;
+        const int blk = a * (a + 1) / 2 + b;  // (1,0)=1 (2,0)=3 (2,1)=4 (3,0)=6 (3,1)=7 (3,2)=8
+        switch (blk) {
+            case 1: return s == 0 ? 4 : s == 1 ? 32 : -1;
+            case 3: return s == 0 ? 6 : s == 1 ? 22 : -1;
+            case 4: return s == 0 ? 12 : -1;
+            case 6: return s == 0 ? 28 : -1;
+            case 7: return s == 0 ? 14 : s == 1 ? 30 : -1;
+            case 8: return s == 0 ? 20 : -1;
+            default: return -1;
+        }
+    } else {
+        static_assert(NB == 2, "padded dimension 16, 32, 64 or 128");
+        if (a == b) return s < 3 ? 8 * a + 2 * s : -1;
+        return s == 0 ? 6 : s == 1 ? 14 : s == 2 ? 16 : -1;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // A0: parameter expansion (one CTA per component)
@@ -176,11 +219,11 @@ __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, co
     constexpr int NB = Fwd<DP>::NB, XST = Fwd<DP>::XST;
     const int rb0 = wl, rb1 = NB - 1 - wl;
     const int ce0 = 8 * (rb0 + 1), ce1 = 8 * (rb1 + 1);
-    f2_t a2[4][8];
+    float2 a2[4][8];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a2[j][i] = 0ull;
+        for (int i = 0; i < 8; ++i) a2[j][i] = make_float2(0.f, 0.f);
     const float* xp = Xs + lane * 4;
     const float* qa = Q + rb0 * 8;
     const float* qb = Q + rb1 * 8;
@@ -192,14 +235,15 @@ __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, co
         const float4 a1 = *reinterpret_cast<const float4*>(qa + c * DP + 4);
         const float4 b0 = *reinterpret_cast<const float4*>(qb + c * DP);
         const float4 b1 = *reinterpret_cast<const float4*>(qb + c * DP + 4);
-        const f2_t qs[8] = {f2_pack(a0.x, a0.y), f2_pack(a0.z, a0.w), f2_pack(a1.x, a1.y), f2_pack(a1.z, a1.w),
-                            f2_pack(b0.x, b0.y), f2_pack(b0.z, b0.w), f2_pack(b1.x, b1.y), f2_pack(b1.z, b1.w)};
+        const float2 qs[8] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                              make_float2(a1.z, a1.w), make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                              make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const f2_t xb = f2_bcast(xs[j]);
+            const float2 xb = make_float2(xs[j], xs[j]);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) a2[j][i] = f2_fma(xb, qs[i], a2[j][i]);
+            for (int i = 0; i < 8; ++i) a2[j][i] = __ffma2_rn(xb, qs[i], a2[j][i]);
         }
     }
 #pragma unroll 2
@@ -207,20 +251,21 @@ __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, co
         const float4 xv = *reinterpret_cast<const float4*>(xp + c * XST);
         const float4 b0 = *reinterpret_cast<const float4*>(qb + c * DP);
         const float4 b1 = *reinterpret_cast<const float4*>(qb + c * DP + 4);
-        const f2_t qs[4] = {f2_pack(b0.x, b0.y), f2_pack(b0.z, b0.w), f2_pack(b1.x, b1.y), f2_pack(b1.z, b1.w)};
+        const float2 qs[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                              make_float2(b1.z, b1.w)};
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const f2_t xb = f2_bcast(xs[j]);
+            const float2 xb = make_float2(xs[j], xs[j]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a2[j][4 + i] = f2_fma(xb, qs[i], a2[j][4 + i]);
+            for (int i = 0; i < 4; ++i) a2[j][4 + i] = __ffma2_rn(xb, qs[i], a2[j][4 + i]);
         }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float2 v = f2_unpack(a2[j][i]);
+            const float2 v = a2[j][i];
             acc[j][2 * i] = v.x;
             acc[j][2 * i + 1] = v.y;
         }
@@ -419,196 +464,212 @@ static __global__ void __launch_bounds__(256) gmm_objective_finalize_kernel(
 // ---------------------------------------------------------------------------
 // A2: backward Accum of R_k, m_k, S_k (lower 8x8 blocks) per component
 // ---------------------------------------------------------------------------
-// grid (component groups, point chunks). Diagonal-block threads fill warps of
-// their own (they also accumulate m and R); off-diagonal threads fill the rest.
+// grid (component groups, point chunks). Each 8x8 block is accumulated in
+// packed float32 pairs along its diagonals: with y = r x_a and pairs
+// y2_i = (y_2i, y_2i+1),
+//   D[i][j] += y2_i * (x_2j, x_2j+1)   -> (S[2i][2j],   S[2i+1][2j+1])
+//   X[i][j] += y2_i * (x_2j+1, x_2j)   -> (S[2i][2j+1], S[2i+1][2j])
+// where the swapped pairs are register moves of the loaded ones: no
+// broadcasts, and every S entry sees the same float32 multiply and FMAs in the
+// same point order as a scalar loop.
 template <int DP>
 __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
                    float* __restrict__ partM, unsigned bx, unsigned by) {
     using C = Bwd<DP>;
-    constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, NB = C::NB, NBLK = C::NBLK;
+    constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, NB = C::NB, NBLK = C::NBLK, MP = C::MP;
+    constexpr int NT = C::THREADS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* Xs = reinterpret_cast<float*>(smem_raw);  // [2][TPB][XST]
-    float* rawlj = Xs + 2 * TPB * XST;                // [2][GC][TPB]
-    float* rawlse = rawlj + 2 * GC * TPB;             // [2][TPB]
-    float* rs = rawlse + 2 * TPB;                     // [2][TPB][GC]
+    float* rawlj = Xs + 2 * TPB * XST;                // [3][GC][TPB]
+    float* rawlse = rawlj + 3 * GC * TPB;             // [3][TPB]
+    float* rs = rawlse + 3 * TPB;                     // [3][TPB][GC]
     const int tid = threadIdx.x;
     const int kg0 = bx * GC;
     const int64_t ntiles = (n + TPB - 1) / TPB;
     const int64_t t_begin = (int64_t)by * tiles_per_chunk;
     const int64_t t_end = min64(ntiles, t_begin + tiles_per_chunk);
 
-    // role of this thread
-    const bool diag = tid < C::NDIAG_T;
-    int kk, a, b;
-    if (diag) {
-        kk = tid / NB;
-        a = b = tid % NB;
-    } else {
-        const int u = tid - C::NDIAG_T;
-        kk = u / (C::NOFF > 0 ? C::NOFF : 1);
-        int o = u - kk * C::NOFF;
-        a = 1;
-        while (o >= a) {
-            o -= a;
-            ++a;
-        }
-        b = o;
+    // role of this thread: component kk, block (a, b)
+    const int kk = tid / NBLK;
+    int a = 0, b = tid - kk * NBLK;
+    while (b > a) {
+        ++a;
+        b -= a;
     }
-    const bool active = (tid < C::NDIAG_T + C::NOFF_T) && (kg0 + kk < k);
+    const bool active = (tid < C::NACT) && (kg0 + kk < k);
+    int moff[MP];
+#pragma unroll
+    for (int s = 0; s < MP; ++s) {
+        const int c = bwd_mtask<NB>(a, b, s);
+        moff[s] = c < 0 ? DP : c == DP ? DP : bwd_swz(c);
+    }
 
-    // Pipeline. The diagonal-block threads (whole warps, NDIAG_T of them) do
-    // less arithmetic per point than the off-diagonal ones, so they also carry
-    // the per-tile side work while the others accumulate: they copy the next
-    // tile's log-joint and lse columns (cp.async, so their own wait covers
-    // them) and turn them into the cotangents r. Every thread copies its share
-    // of the next point tile. One block barrier per tile.
-    constexpr int ND = C::NDIAG_T;
+    // Pipeline, one block barrier per tile. At the top of tile t: the points
+    // of t in X[t % 2] and their r in R[t % 3]; the points of t+1 and the
+    // log-joint of t+2 in flight. 16-byte copies when the rows allow them.
+    const bool v4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
     auto issue_x = [&](int64_t t, int buf) {
         const int64_t p0 = t * TPB;
         const int nv = (int)min64(TPB, n - p0);
         float* X = Xs + buf * TPB * XST;
-        for (int e = tid; e < nv * d; e += C::THREADS) {
-            const int p = e / d, c = e - p * d;
-            cp_async4(X + p * XST + bwd_swz(c), x + (p0 + p) * d + c);
+        if (v4) {
+            const int q4 = d >> 2;
+            for (int e = tid; e < nv * q4; e += NT) {
+                const int p = e / q4, c = 4 * (e - p * q4);
+                cp_async16(X + p * XST + bwd_swz(c), x + (p0 + p) * d + c);
+            }
+        } else {
+            for (int e = tid; e < nv * d; e += NT) {
+                const int p = e / d, c = e - p * d;
+                cp_async4(X + p * XST + bwd_swz(c), x + (p0 + p) * d + c);
+            }
         }
     };
-    auto issue_lj = [&](int64_t t, int buf) {  // diagonal threads only
+    auto issue_lj = [&](int64_t t, int buf) {
         const int64_t p0 = t * TPB;
         const int nv = (int)min64(TPB, n - p0);
         float* L = rawlj + buf * GC * TPB;
-        for (int e = tid; e < GC * TPB; e += ND) {
+        for (int e = tid; e < GC * TPB; e += NT) {
             const int kc = e / TPB, p = e % TPB;
             if (p < nv && kg0 + kc < k) cp_async4(L + e, lj + (int64_t)(kg0 + kc) * lj_ld + p0 + p);
         }
         float* S = rawlse + buf * TPB;
-        for (int p = tid; p < nv; p += ND) cp_async4(S + p, lse + p0 + p);
+        for (int p = tid; p < nv; p += NT) cp_async4(S + p, lse + p0 + p);
     };
     // cotangents r = seed exp(s - lse) of tile t from buffer buf; 0 on the ragged tail
-    auto make_r = [&](int64_t t, int buf) {  // diagonal threads only
+    auto make_r = [&](int64_t t, int buf) {
         const int64_t p0 = t * TPB;
         const int nv = (int)min64(TPB, n - p0);
         const float* L = rawlj + buf * GC * TPB;
         const float* S = rawlse + buf * TPB;
         float* R = rs + buf * TPB * GC;
-        for (int e = tid; e < GC * TPB; e += ND) {
+        for (int e = tid; e < GC * TPB; e += NT) {
             const int kc = e / TPB, p = e % TPB;
             float r = 0.f;
             if (p < nv && kg0 + kc < k) r = seed * expf(L[e] - S[p]);
             R[p * GC + kc] = r;
         }
     };
-    auto diag_sync = [] { asm volatile("bar.sync 2, %0;" ::"n"(ND) : "memory"); };
 
-    for (int e = tid; e < 2 * TPB * XST; e += C::THREADS) Xs[e] = 0.f;
+    // zero tiles (padding coordinates and ragged rows stay finite), 1.0 at DP, DP+1
+    for (int e = tid; e < 2 * TPB * XST; e += NT) {
+        const int col = e % XST;
+        Xs[e] = (col == DP || col == DP + 1) ? 1.f : 0.f;
+    }
     __syncthreads();
 
-    float acc[8][8];
-    float macc[8];
-    float racc = 0.f;
+    float2 accd[4][4], accx[4][4], macc[MP];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        macc[i] = 0.f;
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    }
+        for (int j = 0; j < 4; ++j) accd[i][j] = accx[i][j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < MP; ++s) macc[s] = make_float2(0.f, 0.f);
 
-    // prologue: tile t_begin in shared memory with its r, tile t_begin+1 in flight
+    // prologue
     if (t_begin < t_end) {
         issue_x(t_begin, 0);
-        if (diag) issue_lj(t_begin, 0);
+        issue_lj(t_begin, 0);
+        if (t_begin + 1 < t_end) issue_lj(t_begin + 1, 1);
     }
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    if (diag && t_begin < t_end) make_r(t_begin, 0);
+    if (t_begin < t_end) make_r(t_begin, 0);
     if (t_begin + 1 < t_end) {
+        make_r(t_begin + 1, 1);
         issue_x(t_begin + 1, 1);
-        if (diag) issue_lj(t_begin + 1, 1);
+        if (t_begin + 2 < t_end) issue_lj(t_begin + 2, 2);
     }
     cp_async_commit();
     __syncthreads();
 
+    int b2 = 0, b3 = 0;  // (t - t_begin) mod 2, mod 3
     for (int64_t t = t_begin; t < t_end; ++t) {
-        const int buf = (int)((t - t_begin) & 1);
         if (active) {
-            const float* Xb = Xs + buf * TPB * XST;
-            const float* rb = rs + buf * TPB * GC;
+            const float* Xb = Xs + b2 * TPB * XST;
+            const float* rb = rs + b3 * TPB * GC + kk;
             // halves of the chunks in swizzled order (see bwd_swz)
+            const int ha = ((a >> 2) & 1) << 2, hb = ((b >> 2) & 1) << 2;
             const float* xa = Xb + 8 * a;
             const float* xb = Xb + 8 * b;
-            const int ha = ((a >> 2) & 1) << 2, hb = ((b >> 2) & 1) << 2;
-            if (diag) {
-#pragma unroll 2
-                for (int p = 0; p < TPB; ++p) {
-                    const float4 a0 = *reinterpret_cast<const float4*>(xa + p * XST + ha);
-                    const float4 a1 = *reinterpret_cast<const float4*>(xa + p * XST + (4 ^ ha));
-                    const float rr = rb[p * GC + kk];
-                    const float xv[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                    float ya[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) ya[i] = rr * xv[i];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        macc[i] += ya[i];
-#pragma unroll
-                        for (int j = 0; j <= i; ++j) acc[i][j] = fmaf(ya[i], xv[j], acc[i][j]);
-                    }
-                    racc += rr;
-                }
-            } else {
 #pragma unroll 1
-                for (int p = 0; p < TPB; ++p) {
-                    const float4 b0 = *reinterpret_cast<const float4*>(xb + p * XST + hb);
-                    const float4 b1 = *reinterpret_cast<const float4*>(xb + p * XST + (4 ^ hb));
-                    const float rr = rb[p * GC + kk];
-                    const float yv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            for (int p = 0; p < TPB; ++p) {
+                const float rr = rb[p * GC];
+                const float2 r2 = make_float2(rr, rr);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float4 av = *reinterpret_cast<const float4*>(xa + p * XST + ((4 * h) ^ ha));
-                        const float xv[4] = {av.x, av.y, av.z, av.w};
+                for (int s = 0; s < MP; ++s)
+                    macc[s] = __ffma2_rn(r2, *reinterpret_cast<const float2*>(Xb + p * XST + moff[s]), macc[s]);
+                float2 y[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float ya = rr * xv[i];
+                for (int h = 0; h < 2; ++h) {
+                    const float4 av = *reinterpret_cast<const float4*>(xa + p * XST + ((4 * h) ^ ha));
+                    y[2 * h] = __fmul2_rn(r2, make_float2(av.x, av.y));
+                    y[2 * h + 1] = __fmul2_rn(r2, make_float2(av.z, av.w));
+                }
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) acc[4 * h + i][j] = fmaf(ya, yv[j], acc[4 * h + i][j]);
+                for (int g = 0; g < 2; ++g) {  // columns 4g .. 4g+3
+                    const float4 bv = *reinterpret_cast<const float4*>(xb + p * XST + ((4 * g) ^ hb));
+                    const float2 nb[2] = {make_float2(bv.x, bv.y), make_float2(bv.z, bv.w)};
+                    const float2 sb[2] = {make_float2(bv.y, bv.x), make_float2(bv.w, bv.z)};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            accd[i][2 * g + j] = __ffma2_rn(y[i], nb[j], accd[i][2 * g + j]);
+                            accx[i][2 * g + j] = __ffma2_rn(y[i], sb[j], accx[i][2 * g + j]);
                         }
-                    }
                 }
             }
         }
-        cp_async_wait_all();  // this thread's copies of tile t+1 have landed
-        if (diag && t + 1 < t_end) {
-            diag_sync();          // every diagonal thread's log-joint copies of tile t+1 are visible
-            make_r(t + 1, buf ^ 1);
-        }
-        __syncthreads();      // tile t+1 and its r complete; nobody reads buffer `buf` any more
+        const int n2 = b2 ^ 1, n3a = b3 == 2 ? 0 : b3 + 1, n3b = n3a == 2 ? 0 : n3a + 1;
+        cp_async_wait_all();  // this thread's copies of x(t+1) and lj(t+2) have landed
+        __syncthreads();      // x(t+1), lj(t+2) complete; nobody reads X[b2], R[b3] any more
         if (t + 2 < t_end) {
-            issue_x(t + 2, buf);
-            if (diag) issue_lj(t + 2, buf);
+            make_r(t + 2, n3b);
+            issue_x(t + 2, b2);
+            if (t + 3 < t_end) issue_lj(t + 3, b3);
         }
         cp_async_commit();
+        b2 = n2;
+        b3 = n3a;
     }
     if (!active) return;
     const int kg = kg0 + kk;
     const int64_t base = ((int64_t)by * k + kg);
     float* S = partS + base * NBLK * 64 + (int64_t)(a * (a + 1) / 2 + b) * 64;
+    const bool diag = a == b;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (!diag || j <= i) S[i * 8 + j] += acc[i][j];
-    if (diag) {
-        float* M = partM + base * (DP + 1);
+        for (int j = 0; j < 4; ++j) {
+            const float2 dv = accd[i][j], xv = accx[i][j];
+            // D: (2i, 2j), (2i+1, 2j+1); X: (2i, 2j+1), (2i+1, 2j)
+            if (!diag || j <= i) {
+                S[(2 * i) * 8 + 2 * j] += dv.x;
+                S[(2 * i + 1) * 8 + 2 * j + 1] += dv.y;
+                S[(2 * i + 1) * 8 + 2 * j] += xv.y;
+            }
+            if (!diag || j < i) S[(2 * i) * 8 + 2 * j + 1] += xv.x;
+        }
+    float* M = partM + base * (DP + 1);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) M[8 * a + i] += macc[i];
-        if (a == 0) M[DP] += racc;
+    for (int s = 0; s < MP; ++s) {
+        const int c = bwd_mtask<NB>(a, b, s);
+        const float2 v = macc[s];
+        if (c == DP) {
+            M[DP] += v.x;
+        } else if (c >= 0) {
+            M[c] += v.x;
+            M[c + 1] += v.y;
+        }
     }
 }
 
 template <int DP>
-__global__ void __launch_bounds__(Bwd<DP>::THREADS) __maxnreg__(DP == 64 ? 96 : 168)
+__global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
     gmm_bwd_kernel(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,

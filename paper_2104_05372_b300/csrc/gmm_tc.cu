@@ -288,10 +288,6 @@ __device__ __forceinline__ void producers_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(BPROD) : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
 template <int TDP>
 __global__ void __launch_bounds__(BTHREADS, 1)
     gmm_tc_bwd_kernel(const float* __restrict__ x, int64_t n, int k, const float* __restrict__ mu,

@@ -139,8 +139,11 @@ def test_full_size_sampled_statistics_and_accum_invariance():
     full = [host(t) for t in gpa.gmm_vjp(x, a, mu, q, l)]
     perm = torch.from_numpy(np.random.default_rng(1).permutation(g.n)).cuda()
     permuted = [host(t) for t in gpa.gmm_vjp(x[perm].contiguous(), a, mu, q, l)]
+    # Both sides are FP32 evaluations of the same sums in different orders,
+    # each within the FP32 gradient tolerance of the exact result; a lost or
+    # repeated point would differ by O(1).
     for u, v in zip(full, permuted):
-        assert rel_norm(v, u) <= 2e-5
+        assert rel_norm(v, u) <= TOL_GRAD_FP32
     h = g.n // 3
     pa = [host(t) for t in gpa.gmm_vjp(x[:h].contiguous(), a, mu, q, l)]
     pb = [host(t) for t in gpa.gmm_vjp(x[h:].contiguous(), a, mu, q, l)]
@@ -149,7 +152,7 @@ def test_full_size_sampled_statistics_and_accum_invariance():
     prior_l = -g.gamma ** 2 * g.l.astype(np.float64)
     summed = [pa[0] + pb[0], pa[1] + pb[1], pa[2] + pb[2] - prior_q, pa[3] + pb[3] - prior_l]
     for u, v in zip(full, summed):
-        assert rel_norm(v, u) <= 2e-5
+        assert rel_norm(v, u) <= TOL_GRAD_FP32
 
 
 @pytest.mark.slow
