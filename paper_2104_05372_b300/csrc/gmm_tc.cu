@@ -432,12 +432,12 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             }
             // x values of this thread: points p0 + 32 qp + 0..31, dimension a (0 past
             // the end), as pairs of consecutive points
-            f2_t xv[16];
+            float2 xv[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int p = qp * 32 + 2 * j;
-                xv[j] = f2_pack((p0 + p < n && a < d) ? X[p * d + a] : 0.f,
-                                (p0 + p + 1 < n && a < d) ? X[(p + 1) * d + a] : 0.f);
+                xv[j] = make_float2((p0 + p < n && a < d) ? X[p * d + a] : 0.f,
+                                    (p0 + p + 1 < n && a < d) ? X[(p + 1) * d + a] : 0.f);
             }
             producers_sync();     // sqrt(r) of tile t complete, the point tile read by all
             if (t + 1 < t_end) issue(t + 1, buf ^ 1);  // log-joint buffer buf ^ 1 last read in tile t-1
@@ -453,22 +453,23 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 // points 32 qp .. +31 are chunks 4 (qp & 1) .. +3 of K atom qp >> 1
                 uint8_t* ut = sm + S::U + b * 2 * ATOM + (qp >> 1) * ATOM;
                 const float4* src = reinterpret_cast<const float4*>(sr + (c * T::CPR + jr) * TM + qp * 32);
-                const f2_t mc = f2_bcast(mus[c * 128 + ar]);
+                const float mcs = mus[c * 128 + ar];
+                const float2 mc = make_float2(mcs, mcs);
                 // u = sqrt(r) (x - mu) for two points per packed op; m' += sqrt(r) u in
                 // four independent partial sums (no serial chain through the slot)
-                f2_t mq[4] = {0ull, 0ull, 0ull, 0ull};
+                float2 mq[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                                make_float2(0.f, 0.f)};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const float4 sa = src[2 * j], sb = src[2 * j + 1];
-                    const f2_t sp[4] = {f2_pack(sa.x, sa.y), f2_pack(sa.z, sa.w), f2_pack(sb.x, sb.y),
-                                        f2_pack(sb.z, sb.w)};
+                    const float2 sp[4] = {make_float2(sa.x, sa.y), make_float2(sa.z, sa.w), make_float2(sb.x, sb.y),
+                                          make_float2(sb.z, sb.w)};
                     uint32_t w4[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const f2_t u = f2_mul(sp[i], f2_sub(xv[4 * j + i], mc));
-                        mq[i] = f2_fma(sp[i], u, mq[i]);
-                        const float2 uf = f2_unpack(u);
-                        w4[i] = tc::pack_bf16x2(uf.x, uf.y);
+                        const float2 u = __fmul2_rn(sp[i], __fadd2_rn(xv[4 * j + i], make_float2(-mc.x, -mc.y)));
+                        mq[i] = __ffma2_rn(sp[i], u, mq[i]);
+                        w4[i] = tc::pack_bf16x2(u.x, u.y);
                     }
                     *reinterpret_cast<uint4*>(ut + tc::sw128_offset((uint32_t)ar, (uint32_t)(4 * (qp & 1) + j))) =
                         make_uint4(w4[0], w4[1], w4[2], w4[3]);
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 float mloc = 0.f;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float2 v = f2_unpack(mq[i]);
+                    const float2 v = mq[i];
                     mloc += v.x + v.y;
                 }
                 macc[c] += mloc;

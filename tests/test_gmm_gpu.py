@@ -77,6 +77,29 @@ def test_objective_and_gradient_match_oracle(n, d, k, gamma, m):
     _check_grad(grads, gref)
 
 
+@pytest.mark.parametrize("n,d,k", [(1000, 64, 9), (333, 32, 5), (2000, 16, 44)])
+def test_points_at_4_byte_alignment(n, d, k):
+    """x starting 4 bytes past a 16-byte boundary (the header allows 4-byte
+    alignment): the backward stages points with 4-byte copies instead of
+    16-byte ones; the result is the same gradient."""
+    import paper_2104_05372_b300 as gpa
+    g = synth.gmm_inputs(n, d, k, seed=n + d + k)
+    _, *gref = oracle.gmm_grad(g)
+    x, a, mu, q, l = gmm_dev(g)
+    buf = torch.empty(n * d + 1, device="cuda")
+    xs = buf[1:].view(n, d)
+    xs.copy_(x)
+    assert xs.data_ptr() % 16 == 4
+    st = status()
+    grads = gpa.gmm_vjp(xs, a, mu, q, l, g.gamma, g.m, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    _check_grad([host(t) for t in grads], gref)
+    aligned = gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m)
+    for u, v in zip(grads, aligned):  # same arithmetic in the same order
+        assert np.array_equal(host(u), host(v))
+
+
 def test_recompute_mode_matches_oracle_and_stored_mode():
     """Log-joint recomputed in chunks of 256 points (memory budget) inside gmm_vjp."""
     g = synth.gmm_inputs(3000, 24, 11, seed=5)
