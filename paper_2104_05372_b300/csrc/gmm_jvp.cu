@@ -32,7 +32,7 @@ namespace {
 template <int DP>
 struct Jvp {
     using F = Fwd<DP>;
-    static constexpr int NB = F::NB, NWC = F::NWC, NS = F::NS, TP = F::TP, XST = F::XST, REC = F::REC;
+    static constexpr int NWC = F::NWC, NS = F::NS, TP = F::TP, XST = F::XST, REC = F::REC;
     static constexpr int NBUF = DP == 128 ? 1 : 2;  // record buffers (one at DP = 128: shared memory)
     static constexpr int THREADS = 256;
     static constexpr size_t SMEM =
@@ -222,31 +222,19 @@ __global__ void __launch_bounds__(256) gmm_jvp_kernel(const float* __restrict__ 
         if (kk < k) {
             const float* Q = Qb + (buf * NS + slot) * 2 * REC;
             const float* Qd = Q + REC;
-            const int rb0 = wl, rb1 = C::NB - 1 - wl;
-            float zb[4][16];
-            fwd_gemm_packed<DP>(Xs, Q, lane, wl, zb);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float b0 = Q[DP * DP + rb0 * 8 + i], b1 = Q[DP * DP + rb1 * 8 + i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    zb[j][i] -= b0;
-                    zb[j][8 + i] -= b1;
-                }
-            }
-            float zd[4][16];
-            fwd_gemm_packed<DP>(Xs, Qd, lane, wl, zd);
+            float2 zb[4][8], zd[4][8];
+            fwd_gemm_packed<DP>(Xs, Q, lane, wl, zb);   // Q x - b
+            fwd_gemm_packed<DP>(Xs, Qd, lane, wl, zd);  // Q' x - b'
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float s2 = 0.f, sd = 0.f;
+                float2 s2 = make_float2(0.f, 0.f), sd = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float bd = Qd[DP * DP + (i < 8 ? rb0 * 8 + i : rb1 * 8 + i - 8)];
-                    s2 = fmaf(zb[j][i], zb[j][i], s2);
-                    sd = fmaf(zb[j][i], zd[j][i] - bd, sd);
+                for (int i = 0; i < 8; ++i) {
+                    s2 = __ffma2_rn(zb[j][i], zb[j][i], s2);
+                    sd = __ffma2_rn(zb[j][i], zd[j][i], sd);
                 }
-                redb[(slot * NWC + wl) * TP + lane * 4 + j] = s2;
-                redb[NS * NWC * TP + (slot * NWC + wl) * TP + lane * 4 + j] = sd;
+                redb[(slot * NWC + wl) * TP + lane * 4 + j] = s2.x + s2.y;
+                redb[NS * NWC * TP + (slot * NWC + wl) * TP + lane * 4 + j] = sd.x + sd.y;
             }
         }
         __syncthreads();  // partial sums complete; the records of this round are no longer read

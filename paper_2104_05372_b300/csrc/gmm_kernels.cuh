@@ -212,18 +212,29 @@ __global__ void __launch_bounds__(128) gmm_prep_kernel(const float* __restrict__
 // are packed float32 pairs along Q's rows: the operand pairs of Q come straight
 // from the 16-byte loads and only the four point values need a broadcast per
 // step, so 32 packed FMAs (each two float32 FMAs, rounded as the scalar
-// instruction would) do the work of 64 scalar ones.
+// instruction would) do the work of 64 scalar ones. The accumulators start at
+// -b (the record's b = Q mu), so z = Q x - b comes out directly:
+// z2[j][i] = (z_{r0}, z_{r0+1}) of point j for rows r0 = 8 rb0 + 2i (i < 4) and
+// 8 rb1 + 2(i - 4) (i >= 4).
 template <int DP>
 __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, const float* __restrict__ Q,
-                                                int lane, int wl, float (&acc)[4][16]) {
+                                                int lane, int wl, float2 (&a2)[4][8]) {
     constexpr int NB = Fwd<DP>::NB, XST = Fwd<DP>::XST;
     const int rb0 = wl, rb1 = NB - 1 - wl;
     const int ce0 = 8 * (rb0 + 1), ce1 = 8 * (rb1 + 1);
-    float2 a2[4][8];
+    {
+        const float4 b00 = *reinterpret_cast<const float4*>(Q + DP * DP + rb0 * 8);
+        const float4 b01 = *reinterpret_cast<const float4*>(Q + DP * DP + rb0 * 8 + 4);
+        const float4 b10 = *reinterpret_cast<const float4*>(Q + DP * DP + rb1 * 8);
+        const float4 b11 = *reinterpret_cast<const float4*>(Q + DP * DP + rb1 * 8 + 4);
+        const float2 nb[8] = {make_float2(-b00.x, -b00.y), make_float2(-b00.z, -b00.w), make_float2(-b01.x, -b01.y),
+                              make_float2(-b01.z, -b01.w), make_float2(-b10.x, -b10.y), make_float2(-b10.z, -b10.w),
+                              make_float2(-b11.x, -b11.y), make_float2(-b11.z, -b11.w)};
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a2[j][i] = make_float2(0.f, 0.f);
+            for (int i = 0; i < 8; ++i) a2[j][i] = nb[i];
+    }
     const float* xp = Xs + lane * 4;
     const float* qa = Q + rb0 * 8;
     const float* qb = Q + rb1 * 8;
@@ -261,14 +272,6 @@ __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, co
             for (int i = 0; i < 4; ++i) a2[j][4 + i] = __ffma2_rn(xb, qs[i], a2[j][4 + i]);
         }
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float2 v = a2[j][i];
-            acc[j][2 * i] = v.x;
-            acc[j][2 * i + 1] = v.y;
-        }
 }
 
 // One CTA per tile of 128 points. x, lj, lse are chunk-local; the objective
@@ -339,24 +342,14 @@ __device__ __forceinline__ void gmm_fwd_kernel_body(const float* __restrict__ x,
         float* redb = red + buf * NS * NWC * TP;
         if (kk < k) {
             const float* Q = Qb + (buf * NS + slot) * REC;
-            float acc[4][16];
-            fwd_gemm_packed<DP>(Xs, Q, lane, wl, acc);
-            const int rb0 = wl, rb1 = C::NB - 1 - wl;
-            float bv[16];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                bv[i] = Q[DP * DP + rb0 * 8 + i];
-                bv[8 + i] = Q[DP * DP + rb1 * 8 + i];
-            }
+            float2 z2[4][8];
+            fwd_gemm_packed<DP>(Xs, Q, lane, wl, z2);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float s2 = 0.f;
+                float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float z = acc[j][i] - bv[i];
-                    s2 = fmaf(z, z, s2);
-                }
-                redb[(slot * NWC + wl) * TP + lane * 4 + j] = s2;
+                for (int i = 0; i < 8; ++i) s2 = __ffma2_rn(z2[j][i], z2[j][i], s2);
+                redb[(slot * NWC + wl) * TP + lane * 4 + j] = s2.x + s2.y;
             }
         }
         __syncthreads();
@@ -472,7 +465,9 @@ static __global__ void __launch_bounds__(256) gmm_objective_finalize_kernel(
 // where the swapped pairs are register moves of the loaded ones: no
 // broadcasts, and every S entry sees the same float32 multiply and FMAs in the
 // same point order as a scalar loop.
-template <int DP>
+// UNROLL: point-loop unroll (registers permitting; the plain D=64 kernel
+// takes 4, which lets the next points' shared loads overlap the FMAs).
+template <int DP, int UNROLL = 1>
 __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
@@ -595,7 +590,7 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
             const int ha = ((a >> 2) & 1) << 2, hb = ((b >> 2) & 1) << 2;
             const float* xa = Xb + 8 * a;
             const float* xb = Xb + 8 * b;
-#pragma unroll 1
+#pragma unroll UNROLL
             for (int p = 0; p < TPB; ++p) {
                 const float rr = rb[p * GC];
                 const float2 r2 = make_float2(rr, rr);
@@ -674,7 +669,8 @@ __global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
                    float* __restrict__ partM) {
-    gmm_bwd_kernel_body<DP>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM, blockIdx.x, blockIdx.y);
+    gmm_bwd_kernel_body<DP, DP == 64 ? 4 : 1>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM,
+                                                blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
