@@ -257,7 +257,7 @@ __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, co
             for (int i = 0; i < 8; ++i) a2[j][i] = __ffma2_rn(xb, qs[i], a2[j][i]);
         }
     }
-#pragma unroll 2
+#pragma unroll 4
     for (; c < ce1; ++c) {
         const float4 xv = *reinterpret_cast<const float4*>(xp + c * XST);
         const float4 b0 = *reinterpret_cast<const float4*>(qb + c * DP);
