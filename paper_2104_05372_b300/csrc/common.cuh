@@ -77,6 +77,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_
 // see the phase complete, or all give up after kWaitLimitNs by lane 0's clock).
 // Use it wherever the warp runs .sync.aligned instructions or __syncwarp next.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int32_t* status) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;  // already complete: no clock read
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
         for (int i = 0; i < 64; ++i)

@@ -399,9 +399,9 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             }
             for (int p = tid; p < nv; p += BPROD) cp_async4(lss + buf * TM + p, lse + p0 + p);
         };
-        float macc[BSLOT];
+        float2 macc[BSLOT];  // m' of this thread's row per block, two partial sums
 #pragma unroll
-        for (int c = 0; c < BSLOT; ++c) macc[c] = 0.f;
+        for (int c = 0; c < BSLOT; ++c) macc[c] = make_float2(0.f, 0.f);
         float racc[BGC * TM / BPROD];
 #pragma unroll
         for (int u = 0; u < BGC * TM / BPROD; ++u) racc[u] = 0.f;
@@ -433,11 +433,17 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             // x values of this thread: points p0 + 32 qp + 0..31, dimension a (0 past
             // the end), as pairs of consecutive points
             float2 xv[16];
+            if (a < d && p0 + TM <= n) {  // a full tile: no per-point tests
+                const float* xa = X + qp * 32 * d + a;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int p = qp * 32 + 2 * j;
-                xv[j] = make_float2((p0 + p < n && a < d) ? X[p * d + a] : 0.f,
-                                    (p0 + p + 1 < n && a < d) ? X[(p + 1) * d + a] : 0.f);
+                for (int j = 0; j < 16; ++j) xv[j] = make_float2(xa[(2 * j) * d], xa[(2 * j + 1) * d]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int p = qp * 32 + 2 * j;
+                    xv[j] = make_float2((p0 + p < n && a < d) ? X[p * d + a] : 0.f,
+                                        (p0 + p + 1 < n && a < d) ? X[(p + 1) * d + a] : 0.f);
+                }
             }
             producers_sync();     // sqrt(r) of tile t complete, the point tile read by all
             if (t + 1 < t_end) issue(t + 1, buf ^ 1);  // log-joint buffer buf ^ 1 last read in tile t-1
@@ -474,13 +480,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                     *reinterpret_cast<uint4*>(ut + tc::sw128_offset((uint32_t)ar, (uint32_t)(4 * (qp & 1) + j))) =
                         make_uint4(w4[0], w4[1], w4[2], w4[3]);
                 }
-                float mloc = 0.f;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 v = mq[i];
-                    mloc += v.x + v.y;
-                }
-                macc[c] += mloc;
+                macc[c] = __fadd2_rn(macc[c], __fadd2_rn(__fadd2_rn(mq[0], mq[1]), __fadd2_rn(mq[2], mq[3])));
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&u_full[b]);
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         cp_async_wait_all();  // no copy may land after the block exits
         // m' of quarters 1..3 for quarter 0 to add
         if (qp > 0)
-            for (int c = 0; c < BSLOT; ++c) mred[(qp - 1) * BSLOT * 128 + c * 128 + ar] = macc[c];
+            for (int c = 0; c < BSLOT; ++c) mred[(qp - 1) * BSLOT * 128 + c * 128 + ar] = macc[c].x + macc[c].y;
         // R per component
 #pragma unroll
         for (int u = 0; u < BGC * TM / BPROD; ++u) {
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 if (kg >= k) continue;
                 float* M = partM + (cbase + kg) * (TDP + 1);
                 const float* mr = mred + c * 128 + ar;
-                M[a] += seed * (macc[c] + mr[0] + mr[BSLOT * 128] + mr[2 * BSLOT * 128]);
+                M[a] += seed * ((macc[c].x + macc[c].y) + mr[0] + mr[BSLOT * 128] + mr[2 * BSLOT * 128]);
                 if (a == 0) M[TDP] += seed * rsum[c * T::CPR + jr];
             }
         }
