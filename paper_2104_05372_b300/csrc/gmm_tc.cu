@@ -203,29 +203,35 @@ __global__ void __launch_bounds__(192, 1)
             }
             tc::fence_after_sync();
             float sv[Tc<TDP>::CPR], cst[Tc<TDP>::CPR];
+            // |z - b|^2 per component: z - b and the squares as packed pairs into
+            // four independent partial sums (no serial chain through one register)
+            const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
             for (int j = 0; j < T::CPR; ++j) {
                 const float* bb = reinterpret_cast<const float*>(sm + S::B + (s * T::CPR + j) * T::TAIL);
-                float s2 = 0.f;
+                float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                                 make_float2(0.f, 0.f)};
 #pragma unroll
                 for (int ch = 0; ch < TDP / 32; ++ch) {
                     float v[32];
-                    tc::tmem_ld32(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(as * TM + j * TDP + ch * 32), v);
-                    tc::tmem_wait_ld();
+                    tc::tmem_ld32_wait(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(as * TM + j * TDP + ch * 32), v);
 #pragma unroll
                     for (int i = 0; i < 32; i += 4) {
                         const float4 b4 = *reinterpret_cast<const float4*>(bb + ch * 32 + i);
-                        const float z0 = v[i] - b4.x, z1 = v[i + 1] - b4.y, z2 = v[i + 2] - b4.z,
-                                    z3 = v[i + 3] - b4.w;
-                        s2 = fmaf(z0, z0, s2);
-                        s2 = fmaf(z1, z1, s2);
-                        s2 = fmaf(z2, z2, s2);
-                        s2 = fmaf(z3, z3, s2);
+                        const float2 z0 = __ffma2_rn(make_float2(b4.x, b4.y), neg1, make_float2(v[i], v[i + 1]));
+                        const float2 z1 = __ffma2_rn(make_float2(b4.z, b4.w), neg1, make_float2(v[i + 2], v[i + 3]));
+                        acc[(i >> 2) & 1] = __ffma2_rn(z0, z0, acc[(i >> 2) & 1]);
+                        acc[2 + ((i >> 2) & 1)] = __ffma2_rn(z1, z1, acc[2 + ((i >> 2) & 1)]);
                     }
                 }
-                sv[j] = s2;
+                const float2 t = __fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3]));
+                sv[j] = t.x + t.y;
                 cst[j] = bb[TDP];
             }
+            // The stage's b_k tail was read through the generic proxy and the
+            // producer refills it with a bulk copy (async proxy) once q_empty
+            // completes: order the reads before that write.
+            fence_proxy_async_smem();
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) {
@@ -526,8 +532,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
 #pragma unroll 1
                 for (int ch = 0; ch < TDP / 32; ++ch) {
                     float v[32];
-                    tc::tmem_ld32(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(c * 128 + jw * TDP + ch * 32), v);
-                    tc::tmem_wait_ld();
+                    tc::tmem_ld32_wait(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(c * 128 + jw * TDP + ch * 32), v);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int b = ch * 32 + i;
