@@ -212,17 +212,22 @@ __global__ void __launch_bounds__(192, 1)
                 float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
                                  make_float2(0.f, 0.f)};
 #pragma unroll
-                for (int ch = 0; ch < TDP / 32; ++ch) {
-                    float v[32];
-                    tc::tmem_ld32_wait(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(as * TM + j * TDP + ch * 32), v);
+                for (int h = 0; h < TDP / 64; ++h) {  // 64 columns: two loads in flight, one wait
+                    float v[2][32];
+                    tc::tmem_ld64_wait(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(as * TM + j * TDP + h * 64),
+                                       v[0], v[1]);
 #pragma unroll
-                    for (int i = 0; i < 32; i += 4) {
-                        const float4 b4 = *reinterpret_cast<const float4*>(bb + ch * 32 + i);
-                        const float2 z0 = __ffma2_rn(make_float2(b4.x, b4.y), neg1, make_float2(v[i], v[i + 1]));
-                        const float2 z1 = __ffma2_rn(make_float2(b4.z, b4.w), neg1, make_float2(v[i + 2], v[i + 3]));
-                        acc[(i >> 2) & 1] = __ffma2_rn(z0, z0, acc[(i >> 2) & 1]);
-                        acc[2 + ((i >> 2) & 1)] = __ffma2_rn(z1, z1, acc[2 + ((i >> 2) & 1)]);
-                    }
+                    for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+                        for (int i = 0; i < 32; i += 4) {
+                            const float4 b4 = *reinterpret_cast<const float4*>(bb + h * 64 + ch * 32 + i);
+                            const float2 z0 =
+                                __ffma2_rn(make_float2(b4.x, b4.y), neg1, make_float2(v[ch][i], v[ch][i + 1]));
+                            const float2 z1 =
+                                __ffma2_rn(make_float2(b4.z, b4.w), neg1, make_float2(v[ch][i + 2], v[ch][i + 3]));
+                            acc[(i >> 2) & 1] = __ffma2_rn(z0, z0, acc[(i >> 2) & 1]);
+                            acc[2 + ((i >> 2) & 1)] = __ffma2_rn(z1, z1, acc[2 + ((i >> 2) & 1)]);
+                        }
                 }
                 const float2 t = __fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3]));
                 sv[j] = t.x + t.y;
