@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(256) gmm_jvp_kernel(const float* __restrict__ 
                 redb[NS * NWC * TP + (slot * NWC + wl) * TP + lane * 4 + j] = sd.x + sd.y;
             }
         }
-        __syncthreads();  // partial sums complete; the records of this round are no longer read
+        fence_proxy_async_smem();  // reads of the records before the bulk copy that refills them
+        __syncthreads();           // partial sums complete; the records of this round are no longer read
         if (NBUF == 1 && tid == 0 && round + 1 < rounds) {
             issue(round + 1);
             last_issued = round + 1;

@@ -352,6 +352,10 @@ __device__ __forceinline__ void gmm_fwd_kernel_body(const float* __restrict__ x,
                 redb[(slot * NWC + wl) * TP + lane * 4 + j] = s2.x + s2.y;
             }
         }
+        // this thread's reads of the records in Qb[buf] (ordinary shared loads)
+        // come before the bulk copy (async proxy) that refills the buffer after
+        // the barriers that follow
+        fence_proxy_async_smem();
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < NPAIR; ++u) {
