@@ -327,42 +327,16 @@ __device__ __forceinline__ void gmm_fwd_kernel_body(const float* __restrict__ x,
 #pragma unroll
     for (int u = 0; u < NPAIR; ++u) ls[u].init();
 
-    bool ok = true;
-    int last_issued = 0;  // highest round whose copies were issued (thread 0)
-    for (int round = 0; round < rounds; ++round) {
-        const int buf = round & 1;
-        if (tid == 0 && round + 1 < rounds) {
-            issue(round + 1);
-            last_issued = round + 1;
-        }
-        ok = mbar_wait(&bar[buf], (round >> 1) & 1, status) && ok;
-        ok = __syncthreads_and(ok);  // Xs ready (round 0); all threads agree on ok
-        if (!ok) break;
-        const int kk = round * NS + slot;
-        float* redb = red + buf * NS * NWC * TP;
-        if (kk < k) {
-            const float* Q = Qb + (buf * NS + slot) * REC;
-            float2 z2[4][8];
-            fwd_gemm_packed<DP>(Xs, Q, lane, wl, z2);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) s2 = __ffma2_rn(z2[j][i], z2[j][i], s2);
-                redb[(slot * NWC + wl) * TP + lane * 4 + j] = s2.x + s2.y;
-            }
-        }
-        // this thread's reads of the records in Qb[buf] (ordinary shared loads)
-        // come before the bulk copy (async proxy) that refills the buffer after
-        // the barriers that follow
-        fence_proxy_async_smem();
-        __syncthreads();
+    // per point: the slots' partial squared norms of round `rd` (in red buffer
+    // rd & 1) into the log-joint and the online logsumexp
+    auto finish_round = [&](int rd) {
+        const float* redb = red + (rd & 1) * NS * NWC * TP;
 #pragma unroll
         for (int u = 0; u < NPAIR; ++u) {
             const int e = tid + u * C::THREADS;
             if (e < NS * TP) {
                 const int s = e / TP, p = e % TP;
-                const int kc = round * NS + s;
+                const int kc = rd * NS + s;
                 if (kc < k) {
                     float tot = 0.f;
 #pragma unroll
@@ -375,7 +349,48 @@ __device__ __forceinline__ void gmm_fwd_kernel_body(const float* __restrict__ x,
                 }
             }
         }
+    };
+
+    // One block barrier per round. Round r's contraction writes red buffer
+    // r & 1 and reads records buffer r & 1; the log-joint of round r - 1 is
+    // finished from red buffer (r - 1) & 1 in the same interval. The barrier
+    // at the end of round r orders both before round r + 1 (which finishes
+    // round r, and whose thread 0 refills records buffer r & 1 for round r + 2).
+    __syncthreads();  // the point tile is complete
+    bool ok = true;
+    int last_issued = 0;  // highest round whose copies were issued (thread 0)
+    int done = 0;         // rounds whose contraction completed on every thread
+    for (int round = 0; round < rounds; ++round) {
+        const int buf = round & 1;
+        if (tid == 0 && round + 1 < rounds) {
+            issue(round + 1);
+            last_issued = round + 1;
+        }
+        ok = mbar_wait(&bar[buf], (round >> 1) & 1, status) && ok;
+        const int kk = round * NS + slot;
+        if (ok && kk < k) {
+            float* redb = red + buf * NS * NWC * TP;
+            const float* Q = Qb + (buf * NS + slot) * REC;
+            float2 z2[4][8];
+            fwd_gemm_packed<DP>(Xs, Q, lane, wl, z2);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) s2 = __ffma2_rn(z2[j][i], z2[j][i], s2);
+                redb[(slot * NWC + wl) * TP + lane * 4 + j] = s2.x + s2.y;
+            }
+        }
+        if (round > 0) finish_round(round - 1);
+        // this thread's reads of the records in Qb[buf] (ordinary shared loads)
+        // come before the bulk copy (async proxy) that refills the buffer after
+        // the barrier
+        fence_proxy_async_smem();
+        ok = __syncthreads_and(ok);  // all threads agree on ok
+        if (!ok) break;
+        done = round + 1;
     }
+    if (ok && done > 0) finish_round(done - 1);
     if (!ok && tid == 0) {
         // a wait gave up: let this CTA's copies in flight land (bounded) before exiting
         (void)mbar_wait(&bar[last_issued & 1], (last_issued >> 1) & 1, status);
