@@ -410,11 +410,11 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
     # Gauss-Newton blocks (NEXT-2): U, V, g accumulated, W and res written per observation
     U = torch.zeros(RP_C, 66, device=dev)
     V = torch.zeros(RP_P, 6, device=dev)
-    W = torch.empty(RP_M, 33, device=dev)
+    W = torch.empty(RP_M, 40, device=dev)  # rows padded to whole 32-byte sectors
     gws = _lib.workspace(_lib.load().gpa_reproj_gn_workspace_bytes(RP_C, RP_P, RP_M), dev)
     ms = timed(lambda: gpa.reproj_normal_eqs(cams, pts, obs, tgt, U=U, V=V, W=W, g_cams=dcm, g_pts=dpt, res=res,
                                              strat="sort", plan=plan, ws=gws))
-    gn_bytes = 8 + 8 + 8 + 33 * 4  # indices, target, residual, W block
+    gn_bytes = 8 + 8 + 8 + 33 * 4  # indices, target, residual, W block (the 7 padding floats not counted)
     out["normal_eqs_sort"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
                               "hbm_gbs_algorithmic": gn_bytes * RP_M / (ms / 1e3) / 1e9,
                               "bytes_per_obs": gn_bytes}

@@ -55,7 +55,8 @@ _SIGS = {
     "reproj_residual_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _F, _P, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "reproj_jvp": ([_P, _P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
     "gpa_reproj_gn_workspace_bytes": ([_I32, _I32, _I64], _SZ),
-    "reproj_normal_eqs": ([_P] * 4 + [_I32, _I32, _I64] + [_P] * 6 + [_I32, _P, _P, _SZ, _P, _P], _I32),
+    "reproj_normal_eqs": ([_P] * 4 + [_I32, _I32, _I64] + [_P] * 3 + [_I32] + [_P] * 3 + [_I32, _P, _P, _SZ, _P, _P],
+                          _I32),
     "reproj_vjp_noalloc": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _P], _I32),
     "gpa_plan_bytes": ([_I64, _I32], _SZ),
     "gpa_plan_workspace_bytes": ([_I64, _I32], _SZ),
@@ -437,7 +438,9 @@ def reproj_normal_eqs(cams, pts, obs, tgt, U=None, V=None, W=None, g_cams=None, 
                       want_w=False, want_res=False, strat="auto", plan=None, ws=None, status=None, stream=None):
     """Gauss-Newton blocks (U, V, W, g_cams, g_pts, res): U, V, g_cams, g_pts
     accumulate (+=, zeros if not given); W and res are written when given (or
-    asked for with want_w / want_res), else None."""
+    asked for with want_w / want_res), else None. W is [M][w_ld] with
+    33 <= w_ld <= 64: J_c^T J_p in columns 0..32, zeros after (allocated with
+    w_ld = 40, whole 32-byte sectors per row; take W[:, :33] for the blocks)."""
     nc, npt, no = _reproj_params(cams, pts, obs)
     _check(tgt, torch.float32, "tgt", (no, 2))
     dv = cams.device
@@ -446,9 +449,13 @@ def reproj_normal_eqs(cams, pts, obs, tgt, U=None, V=None, W=None, g_cams=None, 
     g_cams = torch.zeros(nc, 11, device=dv) if g_cams is None else _check(g_cams, torch.float32, "g_cams", (nc, 11))
     g_pts = torch.zeros(npt, 3, device=dv) if g_pts is None else _check(g_pts, torch.float32, "g_pts", (npt, 3))
     if W is None and want_w:
-        W = torch.empty(no, 33, device=dv)
+        W = torch.empty(no, 40, device=dv)
+    w_ld = 0
     if W is not None:
-        _check(W, torch.float32, "W", (no, 33))
+        _check(W, torch.float32, "W")
+        if W.dim() != 2 or W.shape[0] != no or not 33 <= W.shape[1] <= 64:
+            raise ValueError(f"W must have shape ({no}, w_ld) with 33 <= w_ld <= 64, got {tuple(W.shape)}")
+        w_ld = int(W.shape[1])
     if res is None and want_res:
         res = torch.empty(no, 2, device=dv)
     if res is not None:
@@ -456,7 +463,7 @@ def reproj_normal_eqs(cams, pts, obs, tgt, U=None, V=None, W=None, g_cams=None, 
     ws = workspace(int(load().gpa_reproj_gn_workspace_bytes(nc, npt, no)), dv) if ws is None else ws
     st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
     rc = load().reproj_normal_eqs(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, _ptr(U), _ptr(V),
-                                  _ptr(W), _ptr(g_cams), _ptr(g_pts), _ptr(res), st, _ptr(plan), _ptr(ws),
+                                  _ptr(W), w_ld, _ptr(g_cams), _ptr(g_pts), _ptr(res), st, _ptr(plan), _ptr(ws),
                                   ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "reproj_normal_eqs")
     return U, V, W, g_cams, g_pts, res

@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(128) reproj_gn_kernel(
     const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
     const float2* __restrict__ tgt, int n_cams, int n_pts, int64_t n_obs, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ key_s, const int32_t* __restrict__ aux_s, float* __restrict__ U,
-    float* __restrict__ W, float* __restrict__ g_cams, float4* __restrict__ pacc, float2* __restrict__ res,
-    int32_t* __restrict__ status, int pts8) {
+    float* __restrict__ W, int w_ld, float* __restrict__ g_cams, float4* __restrict__ pacc,
+    float2* __restrict__ res, int32_t* __restrict__ status, int pts8) {
     const int lane = threadIdx.x & 31;
     __shared__ float wstage[4 * 32 * 33];  // per warp: 32 rows of W, one per lane
     const int64_t chunk = (int64_t)blockDim.x * kGnOpt;
@@ -641,16 +641,22 @@ __global__ void __launch_bounds__(128) reproj_gn_kernel(
                 atomicAdd(pa + 1, make_float4(v[4], v[5], v[6], v[7]));
                 atomicAdd(pa + 2, make_float4(v[8], 0.f, 0.f, 0.f));
             }
-            if (W) {  // the warp writes its 32 rows, each as contiguous stores (NaN rows for bad indices)
+            if (W) {
+                // the warp writes its 32 rows, each as contiguous stores (NaN rows
+                // for bad indices), padding columns 33 .. w_ld-1 as zeros: with
+                // w_ld a multiple of 8 on a 32-byte aligned W every row is whole
+                // 32-byte sectors, so rows landing in random order (camera-sorted
+                // runs) never leave a sector partly written
                 const int mode = valid ? 1 : (e_ok ? 2 : 0);
                 __syncwarp();
                 for (int rr = 0; rr < 32; ++rr) {
                     const int mr = __shfl_sync(0xffffffffu, mode, rr);
                     const int er = __shfl_sync(0xffffffffu, e, rr);
                     if (mr) {
-                        float* Wr = W + (size_t)er * 33;
+                        float* Wr = W + (size_t)er * w_ld;
                         Wr[lane] = mr == 1 ? stage[rr * 33 + lane] : NAN;
-                        if (lane == 0) Wr[32] = mr == 1 ? stage[rr * 33 + 32] : NAN;
+                        const int c2 = 32 + lane;
+                        if (c2 < w_ld) Wr[c2] = c2 == 32 ? (mr == 1 ? stage[rr * 33 + 32] : NAN) : 0.f;
                     }
                 }
                 __syncwarp();
@@ -897,9 +903,11 @@ extern "C" size_t gpa_reproj_gn_workspace_bytes(int32_t n_cams, int32_t n_pts, i
 
 extern "C" int reproj_normal_eqs(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
                                  int32_t n_cams, int32_t n_pts, int64_t n_obs, float* U, float* V, float* W,
-                                 float* g_cams, float* g_pts, float* res, int32_t strat, const void* plan,
-                                 void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
+                                 int32_t w_ld, float* g_cams, float* g_pts, float* res, int32_t strat,
+                                 const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
+                                 gpa_stream_t stream) {
     if (!cams || !pts || !obs || !tgt || !U || !V || !g_cams || !g_pts || !ws) return GPA_ERR_ARG;
+    if (W && (w_ld < 33 || w_ld > 64)) return GPA_ERR_ARG;
     if (n_cams < 1 || n_pts < 1 || n_obs < 1 || n_obs > INT32_MAX) return GPA_ERR_ARG;
     if (!al(obs, 8) || !al(tgt, 8) || (res && !al(res, 8)) || !al(ws, 256)) return GPA_ERR_ALIGN;
     if (!al(cams, 4) || !al(pts, 4) || !al(U, 4) || !al(V, 4) || (W && !al(W, 4)) || !al(g_cams, 4) ||
@@ -926,13 +934,14 @@ extern "C" int reproj_normal_eqs(const float* cams, const float* pts, const int3
         GPA_LAUNCH("reproj_normal_eqs", s,
                    reproj_gn_kernel<true><<<grid, 128, 0, s>>>(rec, pts, (const int2*)obs, (const float2*)tgt,
                                                                n_cams, n_pts, n_obs, pv.perm, pv.key_sorted,
-                                                               pv.aux_sorted, U, W, g_cams, pacc, (float2*)res,
-                                                               dev_status, p8));
+                                                               pv.aux_sorted, U, W, w_ld, g_cams, pacc,
+                                                               (float2*)res, dev_status, p8));
     else
         GPA_LAUNCH("reproj_normal_eqs", s,
                    reproj_gn_kernel<false><<<grid, 128, 0, s>>>(rec, pts, (const int2*)obs, (const float2*)tgt,
                                                                 n_cams, n_pts, n_obs, nullptr, nullptr, nullptr, U,
-                                                                W, g_cams, pacc, (float2*)res, dev_status, p8));
+                                                                W, w_ld, g_cams, pacc, (float2*)res, dev_status,
+                                                                p8));
     const int64_t pw = (n_pts + 255) / 256, pc = (int64_t)sm_count() * 8;
     GPA_LAUNCH("reproj_gn_points", s,
                gn_points_add_kernel<<<(unsigned)(pw < pc ? pw : pc), 256, 0, s>>>(pacc, n_pts, V, g_pts));

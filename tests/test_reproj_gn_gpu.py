@@ -62,9 +62,31 @@ def test_normal_equations_match_oracle(strat, n_cams, n_pts, n_obs):
     U, V, W, gc, gp, res, bad = oracle.reproj_normal_eqs(r)
     (Ug, Vg, Wg, gcg, gpg, resg), st = _gpu(r, strat)
     assert bad == 0 and st == 0
-    for got, ref in ((Ug, U), (Vg, V), (Wg, W), (gcg, gc), (gpg, gp)):
+    assert Wg.shape == (n_obs, 40) and np.all(Wg[:, 33:] == 0)  # padded rows: whole 32-byte sectors
+    for got, ref in ((Ug, U), (Vg, V), (Wg[:, :33], W), (gcg, gc), (gpg, gp)):
         _compare_rows(got, ref)
     assert rel_norm(resg, res) <= 1e-5
+
+
+@pytest.mark.parametrize("w_ld", [33, 48, 64])
+def test_w_leading_dimension(w_ld):
+    """W [M][w_ld]: the same blocks in columns 0..32 for any 33 <= w_ld <= 64,
+    zeros after; other leading dimensions are rejected before any work."""
+    import paper_2104_05372_b300 as gpa
+    r = synth.reproj_inputs(40, 500, 7001, seed=8)
+    cams, pts, obs, tgt = dev(r.cams), dev(r.pts), dev(r.obs), dev(r.tgt)
+    plan = gpa.gpa_obs_plan_build(obs, r.n_cams, r.n_pts)
+    W = torch.full((r.n_obs, w_ld), 7.0, device="cuda")
+    gpa.reproj_normal_eqs(cams, pts, obs, tgt, W=W, strat="sort", plan=plan)
+    W40 = gpa.reproj_normal_eqs(cams, pts, obs, tgt, want_w=True, strat="sort", plan=plan)[2]
+    torch.cuda.synchronize()
+    Wh, W40h = host(W), host(W40)
+    assert np.array_equal(Wh[:, :33], W40h[:, :33])  # same arithmetic, same order
+    assert np.all(Wh[:, 33:] == 0)
+    for bad_ld in (32, 65):
+        with pytest.raises(ValueError):
+            gpa.reproj_normal_eqs(cams, pts, obs, tgt, W=torch.empty(r.n_obs, bad_ld, device="cuda"),
+                                  strat="sort", plan=plan)
 
 
 def test_blocks_accumulate_and_invalid_observations_are_marked():
@@ -82,7 +104,7 @@ def test_blocks_accumulate_and_invalid_observations_are_marked():
     assert int(st.item()) == 2  # GPA_ERR_INDEX
     assert rel_norm(host(U), 2 * host(U1)) <= 1e-6
     Wh, rh = host(W), host(res)
-    assert np.all(np.isnan(Wh[[7, 11]])) and np.all(np.isnan(rh[[7, 11]]))
+    assert np.all(np.isnan(Wh[[7, 11], :33])) and np.all(np.isnan(rh[[7, 11]]))
     keep = np.ones(r.n_obs, bool)
     keep[[7, 11]] = False
     assert np.all(np.isfinite(Wh[keep])) and np.all(np.isfinite(rh[keep]))
@@ -109,7 +131,7 @@ def test_full_size_normal_action_equals_vjp_of_jvp():
     Vf = torch.zeros(r.n_pts, 3, 3, device="cuda", dtype=torch.float64)
     Vf[:, iv[0], iv[1]] = V.double()
     Vf[:, iv[1], iv[0]] = V.double()
-    Wm = W.double().view(-1, 11, 3)
+    Wm = W[:, :33].double().reshape(-1, 11, 3)
     ci, pi = obs[:, 0].long(), obs[:, 1].long()
     ac = torch.einsum("cab,cb->ca", Uf, vc.double())
     ac.index_add_(0, ci, torch.einsum("jab,jb->ja", Wm, vp.double()[pi]))
