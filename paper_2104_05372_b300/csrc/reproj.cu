@@ -652,11 +652,12 @@ __global__ void __launch_bounds__(128) reproj_gn_kernel(
                 for (int rr = 0; rr < 32; ++rr) {
                     const int mr = __shfl_sync(0xffffffffu, mode, rr);
                     const int er = __shfl_sync(0xffffffffu, e, rr);
-                    if (mr) {
+                    if (mr) {  // streaming stores: W passes through L2 once and should not evict
+                               // the sectors of tgt and res that neighbouring observations reuse
                         float* Wr = W + (size_t)er * w_ld;
-                        Wr[lane] = mr == 1 ? stage[rr * 33 + lane] : NAN;
+                        __stcs(Wr + lane, mr == 1 ? stage[rr * 33 + lane] : NAN);
                         const int c2 = 32 + lane;
-                        if (c2 < w_ld) Wr[c2] = c2 == 32 ? (mr == 1 ? stage[rr * 33 + 32] : NAN) : 0.f;
+                        if (c2 < w_ld) __stcs(Wr + c2, c2 == 32 ? (mr == 1 ? stage[rr * 33 + 32] : NAN) : 0.f);
                     }
                 }
                 __syncwarp();
