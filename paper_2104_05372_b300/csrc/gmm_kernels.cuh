@@ -238,9 +238,9 @@ __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, co
     const float* xp = Xs + lane * 4;
     const float* qa = Q + rb0 * 8;
     const float* qb = Q + rb1 * 8;
-    int c = 0;
-#pragma unroll 2
-    for (; c < ce0; ++c) {
+    // one column c of both row blocks; row pairs of block 0 below i0 are skipped
+    // (their Q entries in column c are zero: above the diagonal)
+    auto step2 = [&](int c, int i0) {
         const float4 xv = *reinterpret_cast<const float4*>(xp + c * XST);
         const float4 a0 = *reinterpret_cast<const float4*>(qa + c * DP);
         const float4 a1 = *reinterpret_cast<const float4*>(qa + c * DP + 4);
@@ -254,11 +254,12 @@ __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, co
         for (int j = 0; j < 4; ++j) {
             const float2 xb = make_float2(xs[j], xs[j]);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) a2[j][i] = __ffma2_rn(xb, qs[i], a2[j][i]);
+            for (int i = 0; i < 8; ++i)
+                if (i >= 4 || i >= i0) a2[j][i] = __ffma2_rn(xb, qs[i], a2[j][i]);
         }
-    }
-#pragma unroll 4
-    for (; c < ce1; ++c) {
+    };
+    // one column c of row block 1 only, row pairs below i0 skipped
+    auto step1 = [&](int c, int i0) {
         const float4 xv = *reinterpret_cast<const float4*>(xp + c * XST);
         const float4 b0 = *reinterpret_cast<const float4*>(qb + c * DP);
         const float4 b1 = *reinterpret_cast<const float4*>(qb + c * DP + 4);
@@ -269,9 +270,22 @@ __device__ __forceinline__ void fwd_gemm_packed(const float* __restrict__ Xs, co
         for (int j = 0; j < 4; ++j) {
             const float2 xb = make_float2(xs[j], xs[j]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a2[j][4 + i] = __ffma2_rn(xb, qs[i], a2[j][4 + i]);
+            for (int i = 0; i < 4; ++i)
+                if (i >= i0) a2[j][4 + i] = __ffma2_rn(xb, qs[i], a2[j][4 + i]);
         }
-    }
+    };
+    // columns left of block 0's diagonal: both blocks in full
+#pragma unroll 2
+    for (int c = 0; c < 8 * rb0; ++c) step2(c, 0);
+    // block 0's diagonal columns 8 rb0 + t: row pairs i >= t / 2 only (row 8 rb0 + 2i + 1 >= c)
+#pragma unroll
+    for (int t = 0; t < 8; ++t) step2(8 * rb0 + t, t / 2);
+    // columns between the diagonals: block 1 only
+#pragma unroll 4
+    for (int c = ce0; c < 8 * rb1; ++c) step1(c, 0);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) step1(8 * rb1 + t, t / 2);
+    (void)ce1;
 }
 
 // One CTA per tile of 128 points. x, lj, lse are chunk-local; the objective
