@@ -463,14 +463,19 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             for (int c = 0; c < BSLOT; ++c) {
                 const int b = c % NUB;
                 const uint32_t use = (uint32_t)(it * (BSLOT / NUB) + c / NUB);
+                // sqrt(r) of this block's 32 points and the mean, loaded before the
+                // wait for the U buffer so that the wait covers their latency
+                const float4* src = reinterpret_cast<const float4*>(sr + (c * T::CPR + jr) * TM + qp * 32);
+                float4 sv4[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sv4[q] = src[q];
+                const float mcs = mus[c * 128 + ar];
                 if (!mbar_wait_warp(&u_empty[b], (use & 1u) ^ 1u, status)) {
                     *abort_flag = 1;  // skip the work; the next decision point stops every warp
                     continue;
                 }
                 // points 32 qp .. +31 are chunks 4 (qp & 1) .. +3 of K atom qp >> 1
                 uint8_t* ut = sm + S::U + b * 2 * ATOM + (qp >> 1) * ATOM;
-                const float4* src = reinterpret_cast<const float4*>(sr + (c * T::CPR + jr) * TM + qp * 32);
-                const float mcs = mus[c * 128 + ar];
                 const float2 mc = make_float2(mcs, mcs);
                 // u = sqrt(r) (x - mu) for two points per packed op; m' += sqrt(r) u in
                 // four independent partial sums (no serial chain through the slot)
@@ -478,7 +483,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                                 make_float2(0.f, 0.f)};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float4 sa = src[2 * j], sb = src[2 * j + 1];
+                    const float4 sa = sv4[2 * j], sb = sv4[2 * j + 1];
                     const float2 sp[4] = {make_float2(sa.x, sa.y), make_float2(sa.z, sa.w), make_float2(sb.x, sb.y),
                                           make_float2(sb.z, sb.w)};
                     uint32_t w4[4];
