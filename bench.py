@@ -298,13 +298,15 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (x is 256 MiB, log-joint 800 MiB)"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches * world, "clocks": clocks,
     }
-    if not args.no_secondary:
+    # the other workloads and the CPU baseline belong to the single-GPU line; a
+    # scaling run (world > 1) reports the data-parallel step only
+    if not args.no_secondary and world == 1:
         result["secondary"] = run_reproj(args, gpa, _lib, dev, stream, rank)
         result["precision_form"] = [run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=GMM_D, k=GMM_K),
                                     run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256)]
         result["batched"] = run_batched(args, gpa, _lib, dev, stream, rank)
         result["scatter"] = run_scatter(args, gpa, _lib, dev, stream, rank)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -357,10 +359,19 @@ def run_e2e(args, gpa, _lib, g, dev, ws, stream, exch, n_total):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
-    h2d = xh.numel() * xh.element_size() + sum(h.numel() * h.element_size() for h in host)
-    d2h = sum(h.numel() * h.element_size() for h in hgrads) + 8
+    world = 1
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        world = dist.get_world_size()
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)  # whole job: the slowest rank's time
+        ms = float(tt.item())
+    # bytes per step over the whole job (every rank copies its points and the
+    # parameters in and its gradient and objective out)
+    h2d = world * (xh.numel() * xh.element_size() + sum(h.numel() * h.element_size() for h in host))
+    d2h = world * (sum(h.numel() * h.element_size() for h in hgrads) + 8)
     del staging, wsc
-    return {"value": GMM_N * GMM_K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+    return {"value": GMM_N * GMM_K * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "note": f"points streamed from pinned host memory in chunks of {chunk} points, "
                                                "copies overlapping the computation (gmm_vjp_from_host)"}
 
