@@ -243,11 +243,12 @@ __global__ void __launch_bounds__(256) scatter_smem_kernel(const int32_t* __rest
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t e0 = 0;
     if (w == 1 && ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(vals)) & 15) == 0) {
-        // four elements per thread and step, 16-byte loads
+        // four elements per thread and step, 16-byte loads; four steps' loads
+        // issued together so that eight are in flight per thread
         const int64_t m4 = m / 4;
-        for (int64_t q = t0; q < m4; q += stride) {
-            const int4 b4 = __ldg(reinterpret_cast<const int4*>(idx) + q);
-            const float4 raw = __ldg(reinterpret_cast<const float4*>(vals) + q);
+        const int4* idx4 = reinterpret_cast<const int4*>(idx);
+        const float4* val4 = reinterpret_cast<const float4*>(vals);
+        auto add4 = [&](const int4 b4, const float4 raw) {
             const int bs[4] = {b4.x, b4.y, b4.z, b4.w};
             const float vf[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
@@ -260,7 +261,20 @@ __global__ void __launch_bounds__(256) scatter_smem_kernel(const int32_t* __rest
                 memcpy(&v, &vf[u], sizeof(T));  // T is float or int32: the same 4 bytes
                 atomicAdd(priv + bs[u], v);
             }
+        };
+        int64_t q = t0;
+        for (; q + 3 * stride < m4; q += 4 * stride) {
+            int4 b4[4];
+            float4 raw[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                b4[h] = __ldg(idx4 + q + h * stride);
+                raw[h] = __ldg(val4 + q + h * stride);
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) add4(b4[h], raw[h]);
         }
+        for (; q < m4; q += stride) add4(__ldg(idx4 + q), __ldg(val4 + q));
         e0 = m4 * 4;
     }
     for (int64_t e = e0 + t0; e < total; e += stride) {
@@ -291,10 +305,12 @@ __global__ void __launch_bounds__(256) scatter_complete_kernel(const int32_t* __
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t j0 = 0;
     if (((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(vals)) & 15) == 0) {
-        const int64_t m4 = m / 4;  // four elements per thread and step, 16-byte loads
-        for (int64_t q = t0; q < m4; q += stride) {
-            const int4 b4 = __ldg(reinterpret_cast<const int4*>(idx) + q);
-            const float4 raw = __ldg(reinterpret_cast<const float4*>(vals) + q);
+        // four elements per thread and step, 16-byte loads; four steps' loads
+        // issued together (eight in flight per thread), summed in step order
+        const int64_t m4 = m / 4;
+        const int4* idx4 = reinterpret_cast<const int4*>(idx);
+        const float4* val4 = reinterpret_cast<const float4*>(vals);
+        auto add4 = [&](const int4 b4, const float4 raw) {
             const int bs[4] = {b4.x, b4.y, b4.z, b4.w};
             const float vf[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
@@ -307,7 +323,20 @@ __global__ void __launch_bounds__(256) scatter_complete_kernel(const int32_t* __
                 memcpy(&v, &vf[u], sizeof(T));
                 sum += v;
             }
+        };
+        int64_t q = t0;
+        for (; q + 3 * stride < m4; q += 4 * stride) {
+            int4 b4[4];
+            float4 raw[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                b4[h] = __ldg(idx4 + q + h * stride);
+                raw[h] = __ldg(val4 + q + h * stride);
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) add4(b4[h], raw[h]);
         }
+        for (; q < m4; q += stride) add4(__ldg(idx4 + q), __ldg(val4 + q));
         j0 = m4 * 4;
     }
     for (int64_t j = j0 + t0; j < m; j += stride) {
