@@ -376,6 +376,41 @@ def run_e2e(args, gpa, _lib, g, dev, ws, stream, exch, n_total):
                                                "copies overlapping the computation (gmm_vjp_from_host)"}
 
 
+def graph_timed(fn, dev, steps, warmup, flush, modes):
+    """Device time of one call of fn, in ms: the call captured once in a CUDA
+    graph and replayed (no host launch gaps inside the timed region; eager
+    calls if the capture fails), `flush` (a buffer larger than L2) written
+    before every timed replay. Adds the mode used to `modes`."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    run = fn
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            fn()
+        torch.cuda.synchronize(dev)
+        run = graph.replay
+        run()
+        modes.add("graph replay")
+    except Exception:  # not capturable: time the eager calls
+        torch.cuda.synchronize(dev)
+        modes.add("eager calls")
+    torch.cuda.synchronize(dev)
+    cs = torch.cuda.current_stream(dev)
+    tot = 0.0
+    for _ in range(steps):
+        flush.fill_(1)  # evict inputs from L2 between timed iterations
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cs)
+        run()
+        e1.record(cs)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
 def run_reproj(args, gpa, _lib, dev, stream, rank):
     import torch
     import synth
@@ -392,36 +427,7 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
     modes = set()
 
     def timed(fn):
-        """Device time of one call: the call captured once in a CUDA graph and
-        replayed (no host launch gaps inside the timed region; eager calls if
-        the capture fails), L2 flushed before every timed replay."""
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize(dev)
-        run = fn
-        try:
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph):
-                fn()
-            torch.cuda.synchronize(dev)
-            run = graph.replay
-            run()
-            modes.add("graph replay")
-        except Exception:  # not capturable: time the eager calls
-            torch.cuda.synchronize(dev)
-            modes.add("eager calls")
-        torch.cuda.synchronize(dev)
-        cs = torch.cuda.current_stream(dev)
-        tot = 0.0
-        for _ in range(args.steps):
-            flush.fill_(1)  # evict inputs from L2 between timed iterations
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(cs)
-            run()
-            e1.record(cs)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        return tot / args.steps
+        return graph_timed(fn, dev, args.steps, args.warmup, flush, modes)
 
     out = {"workload": "reprojection, 8192 cameras x 11, 500000 points, 4000000 observations, FP32",
            "l2": "flushed between timed iterations", "unit": "obs/s"}
@@ -473,20 +479,10 @@ def run_scatter(args, gpa, _lib, dev, stream, rank):
     peaks, src = measured_peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    modes = set()
+
     def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize(dev)
-        tot = 0.0
-        for _ in range(args.steps):
-            flush.fill_(1)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        return tot / args.steps
+        return graph_timed(fn, dev, args.steps, args.warmup, flush, modes)
 
     cases = [("complete", 1 << 24, 1, 1, "f32", None, ("smem", "atomic", "warpagg")),
              ("histogram_256", 1 << 24, 1, 256, "i32", None, ("smem", "warpagg", "atomic")),
@@ -509,6 +505,7 @@ def run_scatter(args, gpa, _lib, dev, stream, rank):
             row[st] = {"ms": round(ms, 4), "elements_per_s": m / (ms / 1e3), "gbs": round(gbs, 1),
                        "frac": round(gbs / peaks["hbm_gbs"], 4)}
         out[name] = row
+    out["timing"] = ", ".join(sorted(modes)) + " (one call per timed iteration)"
     return out
 
 
