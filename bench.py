@@ -379,8 +379,8 @@ def run_e2e(args, gpa, _lib, g, dev, ws, stream, exch, n_total):
 def graph_timed(fn, dev, steps, warmup, flush, modes):
     """Device time of one call of fn, in ms: the call captured once in a CUDA
     graph and replayed (no host launch gaps inside the timed region; eager
-    calls if the capture fails), `flush` (a buffer larger than L2) written
-    before every timed replay. Adds the mode used to `modes`."""
+    calls if the capture fails), `flush` (a buffer larger than L2) written and
+    read back before every timed replay. Adds the mode used to `modes`."""
     import torch
     for _ in range(warmup):
         fn()
@@ -401,7 +401,11 @@ def graph_timed(fn, dev, steps, warmup, flush, modes):
     cs = torch.cuda.current_stream(dev)
     tot = 0.0
     for _ in range(steps):
-        flush.fill_(1)  # evict inputs from L2 between timed iterations
+        # evict inputs from L2 between timed iterations: write a buffer larger
+        # than L2, then read it back, so that the write-back of the dirty flush
+        # lines happens here and not inside the timed call
+        flush.fill_(1)
+        flush.view(torch.int32).max()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(cs)
         run()
