@@ -460,6 +460,14 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
                               "hbm_gbs_algorithmic": gn_bytes * RP_M / (ms / 1e3) / 1e9,
                               "bytes_per_obs": gn_bytes}
     del U, V, W, gws
+    # the SORT plan (stable radix sort of the observations by camera): built
+    # once per observation structure and reused by every SORT call
+    pws = _lib.workspace(_lib.gpa_plan_workspace_bytes(RP_M, RP_C), dev)
+    pbuf = _lib.workspace(_lib.gpa_plan_bytes(RP_M, RP_C), dev)
+    ms = timed(lambda: gpa.gpa_obs_plan_build(obs, RP_C, RP_P, plan=pbuf, ws=pws))
+    out["plan_build"] = {"ms": ms, "note": "stable radix sort by camera, 4M observations; a SORT VJP "
+                                           "repays it after about ms / (ms_atomic - ms_sort) calls"}
+    del pws, pbuf
     out["timing"] = ", ".join(sorted(modes)) + " (one call per timed iteration)"
     best = max(("sort", "atomic", "warpagg"), key=lambda s_: out[f"vjp_{s_}"]["obs_per_s"])
     out["metric"] = "reproj VJP obs/s"

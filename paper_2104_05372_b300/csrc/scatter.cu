@@ -67,32 +67,78 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const int32_t* __restri
     cnt[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of v[0..n) in place, one CTA of 1024 threads, int64 running sum
-__global__ void __launch_bounds__(1024) exclusive_scan_kernel(int32_t* __restrict__ v, int64_t n,
-                                                              int32_t* __restrict__ total) {
-    __shared__ int64_t part[1024];
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t b = (int64_t)threadIdx.x * per, e = min64(n, b + per);
-    int64_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += v[i];
-    part[threadIdx.x] = s;
+
+// Offsets of the radix scatter: cnt [256][ntiles] (digit-major) becomes, in
+// place, the exclusive prefix sum of the flattened array, computed in two
+// parallel steps: digit totals, then one CTA per digit scanning its tiles
+// with the totals of the smaller digits as base.
+__global__ void __launch_bounds__(1024) digit_total_kernel(const int32_t* __restrict__ cnt, int64_t ntiles,
+                                                           int32_t* __restrict__ tot) {
+    __shared__ int32_t part[32];
+    const int d = blockIdx.x;
+    int32_t s = 0;
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) s += cnt[(int64_t)d * ntiles + t];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
     __syncthreads();
+    if (threadIdx.x < 32) {
+        int32_t v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) tot[d] = v;
+    }
+}
+
+__global__ void __launch_bounds__(1024) digit_scan_kernel(int32_t* __restrict__ cnt, int64_t ntiles,
+                                                          const int32_t* __restrict__ tot) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry;
+    const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        int64_t run = 0;
-        for (int i = 0; i < 1024; ++i) {
-            const int64_t t = part[i];
-            part[i] = run;
-            run += t;
-        }
-        if (total) *total = (int32_t)run;
+        int32_t b = 0;
+        for (int e = 0; e < d; ++e) b += tot[e];
+        carry = b;
     }
     __syncthreads();
-    int64_t run = part[threadIdx.x];
-    for (int64_t i = b; i < e; ++i) {
-        const int64_t t = v[i];
-        v[i] = (int32_t)run;
-        run += t;
+    int32_t* row = cnt + (int64_t)d * ntiles;
+    for (int64_t t0 = 0; t0 < ntiles; t0 += blockDim.x) {  // uniform trip count
+        const int64_t t = t0 + threadIdx.x;
+        const int32_t v = t < ntiles ? row[t] : 0;
+        int32_t x = v;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {  // scan of the warp sums
+            int32_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;  // inclusive
+        }
+        __syncthreads();
+        const int32_t before = carry + (warp > 0 ? wsum[warp - 1] : 0);
+        if (t < ntiles) row[t] = before + x - v;  // exclusive
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[(blockDim.x >> 5) - 1];
+        __syncthreads();
     }
+}
+
+// seg_off[k] = first position of key k in the sorted keys (n_keys + 1 entries;
+// seg_off[n_keys] = number of valid elements, invalid keys being n_keys and
+// sorted last): from the boundaries of the sorted runs, no atomics.
+__global__ void __launch_bounds__(256) seg_offsets_kernel(const int32_t* __restrict__ key_s, int64_t n,
+                                                          int n_keys, int32_t* __restrict__ seg_off) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > n) return;
+    const int prev = j == 0 ? -1 : key_s[j - 1];
+    const int cur = j == n ? n_keys : key_s[j];
+    for (int k = prev + 1; k <= cur; ++k) seg_off[k] = (int32_t)j;
 }
 
 // stable scatter of one tile by one warp
@@ -107,22 +153,32 @@ __global__ void __launch_bounds__(32) radix_scatter_kernel(const int32_t* __rest
     const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
     const int64_t t1 = min64(n, t0 + kSortTile);
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t j0 = t0; j0 < t1; j0 += 32) {
-        const int64_t j = j0 + lane;
-        const bool v = j < t1;
-        const int k = v ? kin[j] : 0;
-        const int dgt = v ? ((k >> shift) & 255) : 256 + lane;  // unique dummy digit
-        const unsigned grp = __match_any_sync(0xffffffffu, dgt);
-        const int rank = __popc(grp & lt);
-        int pos = 0;
-        if (v) pos = base[dgt] + rank;
-        __syncwarp();
-        if (v) {
-            kout[pos] = k;
-            iout[pos] = iin[j];
-            if (rank == 0) base[dgt] += __popc(grp);
+    constexpr int U = 4;  // iterations whose keys and ids are loaded together
+    for (int64_t j0 = t0; j0 < t1; j0 += 32 * U) {
+        int kk[U], ii[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + 32 * u + lane;
+            kk[u] = j < t1 ? kin[j] : 0;
+            ii[u] = j < t1 ? iin[j] : 0;
         }
-        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + 32 * u + lane;
+            const bool v = j < t1;
+            const int dgt = v ? ((kk[u] >> shift) & 255) : 256 + lane;  // unique dummy digit
+            const unsigned grp = __match_any_sync(0xffffffffu, dgt);
+            const int rank = __popc(grp & lt);
+            int pos = 0;
+            if (v) pos = base[dgt] + rank;
+            __syncwarp();
+            if (v) {
+                kout[pos] = kk[u];
+                iout[pos] = ii[u];
+                if (rank == 0) base[dgt] += __popc(grp);
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -137,14 +193,6 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(const int32_t* __restr
     perm[j] = e;
     key_sorted[j] = ks[j];
     aux_sorted[j] = aux[e];
-}
-
-__global__ void __launch_bounds__(256) key_count_kernel(const int32_t* __restrict__ key, int64_t n, int n_keys,
-                                                        int32_t* __restrict__ cnt) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int k = key[j];
-    if (k < n_keys) atomicAdd(cnt + k, 1);
 }
 
 __global__ void plan_header_kernel(int64_t* __restrict__ hdr, int64_t n, int n_keys,
@@ -394,10 +442,11 @@ static unsigned grid_for(int64_t n) {
     return (unsigned)(want < cap ? want : cap);
 }
 
-// workspace: key_a, id_a, key_b, id_b, aux (n each), cnt (256 * ntiles)
+// workspace: key_a, id_a, key_b, id_b, aux (n each), cnt (256 * ntiles), digit totals (256)
 static size_t plan_ws_bytes(int64_t n) {
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    return 5 * plan_a256(sizeof(int32_t) * (size_t)n) + plan_a256(sizeof(int32_t) * 256 * (size_t)ntiles) + 256;
+    return 5 * plan_a256(sizeof(int32_t) * (size_t)n) + plan_a256(sizeof(int32_t) * 256 * (size_t)ntiles) +
+           plan_a256(sizeof(int32_t) * 256) + 256;
 }
 
 static int build_plan(const int2* obs, const int32_t* idx, int64_t n, int n_keys, int n_aux, void* plan,
@@ -410,6 +459,7 @@ static int build_plan(const int2* obs, const int32_t* idx, int64_t n, int n_keys
     int32_t* ib = (int32_t*)(w + 3 * vb);
     int32_t* aux = (int32_t*)(w + 4 * vb);
     int32_t* cnt = (int32_t*)(w + 5 * vb);
+    int32_t* tot = (int32_t*)(w + 5 * vb + plan_a256(sizeof(int32_t) * 256 * (size_t)((n + kSortTile - 1) / kSortTile)));
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     const unsigned g = (unsigned)((n + 255) / 256);
     if (obs)
@@ -423,7 +473,8 @@ static int build_plan(const int2* obs, const int32_t* idx, int64_t n, int n_keys
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         GPA_LAUNCH("radix_hist", s, radix_hist_kernel<<<(unsigned)ntiles, 256, 0, s>>>(ka, n, shift, ntiles, cnt));
-        GPA_LAUNCH("exclusive_scan", s, exclusive_scan_kernel<<<1, 1024, 0, s>>>(cnt, 256 * ntiles, nullptr));
+        GPA_LAUNCH("digit_total", s, digit_total_kernel<<<256, 1024, 0, s>>>(cnt, ntiles, tot));
+        GPA_LAUNCH("digit_scan", s, digit_scan_kernel<<<256, 1024, 0, s>>>(cnt, ntiles, tot));
         GPA_LAUNCH("radix_scatter", s, radix_scatter_kernel<<<(unsigned)ntiles, 32, 0, s>>>(ka, ia, n, shift, ntiles, cnt, kb, ib));
         GPA_LAUNCH_CHECK();
         int32_t* t = ka; ka = kb; kb = t;
@@ -431,9 +482,8 @@ static int build_plan(const int2* obs, const int32_t* idx, int64_t n, int n_keys
     }
     PlanView pv = plan_view(plan, n, n_keys);
     GPA_LAUNCH("plan_finish", s, plan_finish_kernel<<<g, 256, 0, s>>>(ka, ia, aux, n, pv.perm, pv.key_sorted, pv.aux_sorted));
-    if (cudaMemsetAsync(pv.seg_off, 0, sizeof(int32_t) * ((size_t)n_keys + 1), s) != cudaSuccess) return GPA_ERR_CUDA;
-    GPA_LAUNCH("key_count", s, key_count_kernel<<<g, 256, 0, s>>>(pv.key_sorted, n, n_keys, pv.seg_off));
-    GPA_LAUNCH("exclusive_scan", s, exclusive_scan_kernel<<<1, 1024, 0, s>>>(pv.seg_off, (int64_t)n_keys + 1, nullptr));
+    GPA_LAUNCH("seg_offsets", s,
+               seg_offsets_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(pv.key_sorted, n, n_keys, pv.seg_off));
     GPA_LAUNCH("plan_header", s, plan_header_kernel<<<1, 1, 0, s>>>(pv.header, n, n_keys, pv.seg_off));
     GPA_LAUNCH_CHECK();
     return GPA_OK;
