@@ -498,8 +498,9 @@ static __global__ void __launch_bounds__(256) gmm_objective_finalize_kernel(
 // where the swapped pairs are register moves of the loaded ones: no
 // broadcasts, and every S entry sees the same float32 multiply and FMAs in the
 // same point order as a scalar loop.
-// UNROLL: point-loop unroll (registers permitting; the plain D=64 kernel
-// takes 4, which lets the next points' shared loads overlap the FMAs).
+// UNROLL: point-loop unroll, registers permitting (the plain kernel takes 4
+// for padded dimensions up to 64, the persistent batched kernel 2): the next
+// points' shared loads overlap the FMAs.
 template <int DP, int UNROLL = 1>
 __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
@@ -702,7 +703,7 @@ __global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
                    float* __restrict__ partM) {
-    gmm_bwd_kernel_body<DP, DP == 64 ? 4 : 1>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM,
+    gmm_bwd_kernel_body<DP, DP <= 64 ? 4 : 1>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM,
                                                 blockIdx.x, blockIdx.y);
 }
 
