@@ -84,6 +84,44 @@ def test_index_plan_bit_exact():
         assert np.array_equal(seg, seg_ref.astype(np.int32))
 
 
+def test_index_plan_segments_empty_and_invalid_keys():
+    """Segment offsets of the sorted plan: keys with no updates (leading,
+    interior and trailing) get empty segments, invalid indices sort after
+    every valid key and are counted, not placed in a segment."""
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300._lib import plan_arrays
+    rng = np.random.default_rng(21)
+    nk = 50000
+    cases = []
+    # 3.5 sort tiles of keys drawn from [1000, 20000): keys 0..999 and
+    # 20000..nk-1 are empty; every 97th index is out of range.
+    idx = rng.integers(1000, 20000, 14336).astype(np.int32)
+    idx[::97] = nk + 5
+    idx[1::211] = -7
+    cases.append((idx, nk))
+    cases.append((np.full(5000, -1, np.int32), nk))      # every index invalid
+    cases.append((np.full(9000, nk - 1, np.int32), nk))  # one key, the last
+    # 2^16 keys: the invalid key 2^16 needs a third 8-bit radix pass.
+    idx = rng.integers(0, 1 << 16, 20000).astype(np.int32)
+    idx[::13] = 1 << 16
+    cases.append((idx, 1 << 16))
+    for idx, nk in cases:
+        m = idx.shape[0]
+        st = status()
+        plan = gpa.gpa_index_plan_build(dev(idx), nk, status=st)
+        hdr, perm, keys, _, seg = (host(t) for t in plan_arrays(plan, m, nk))
+        keys_in = np.where((idx >= 0) & (idx < nk), idx, nk).astype(np.int32)
+        perm_ref, seg_ref, bad = oracle.stable_sort_by_key(keys_in, nk)
+        n_valid = m - int(np.sum(keys_in == nk))
+        assert bad == m - n_valid and hdr[2] == n_valid
+        assert int(st.item()) == (2 if n_valid < m else 0)
+        assert np.array_equal(seg, seg_ref.astype(np.int32))
+        assert seg[0] == 0 and seg[-1] == n_valid
+        assert np.array_equal(perm[:n_valid], perm_ref)
+        assert np.array_equal(keys[:n_valid], keys_in[perm_ref])
+        assert np.array_equal(np.sort(perm[n_valid:]), np.flatnonzero(keys_in == nk))
+
+
 def test_partition_invariance_bit_exact_int32():
     """Accum: splitting the updates into shards and adding the shard sums
     gives the same histogram (Sec. 2.3.2)."""
