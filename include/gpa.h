@@ -283,7 +283,9 @@ GPA_API int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_
  * tgt / res / w 8-byte, others 4-byte.
  */
 
-/* Workspace for reproj_residual / reproj_vjp (the expanded cameras). */
+/* Workspace for reproj_residual / reproj_vjp / reproj_residual_vjp / reproj_jvp:
+ * the expanded cameras, and for the VJPs the points copied into 16-byte rows
+ * and the padded point accumulators. */
 GPA_API size_t gpa_reproj_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs);
 
 /* res [M][2] = projection - target. Observations whose indices fall outside

@@ -37,10 +37,7 @@ constexpr int kCamRec = 32;  // floats per expanded camera: one 128-byte line
 // The residual reads the first 20 floats only.
 constexpr int kCamResid = 20;
 
-__global__ void __launch_bounds__(128) cam_expand_kernel(const float* __restrict__ cams, int n_cams,
-                                                         float* __restrict__ rec) {
-    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci >= n_cams) return;
+__device__ void cam_expand_one(const float* __restrict__ cams, int ci, float* __restrict__ rec) {
     const float* c = cams + (size_t)ci * 11;
     const double w0 = c[0], w1 = c[1], w2 = c[2];
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
@@ -90,6 +87,32 @@ __global__ void __launch_bounds__(128) cam_expand_kernel(const float* __restrict
     o[29] = 0.f; o[30] = 0.f; o[31] = 0.f;
 }
 
+__global__ void __launch_bounds__(128) cam_expand_kernel(const float* __restrict__ cams, int n_cams,
+                                                         float* __restrict__ rec) {
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci < n_cams) cam_expand_one(cams, ci, rec);
+}
+
+// Per-call preparation of the VJP: the first ncb blocks expand the cameras,
+// the others copy the points into 16-byte rows (x, y, z, 0), so that a
+// gathered point is one 16-byte load, and zero the padded point accumulators.
+__global__ void __launch_bounds__(128) vjp_prep_kernel(const float* __restrict__ cams, int n_cams,
+                                                       float* __restrict__ rec, int ncb,
+                                                       const float* __restrict__ pts, int n_pts,
+                                                       float4* __restrict__ pts4, float4* __restrict__ acc) {
+    if ((int)blockIdx.x < ncb) {
+        const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+        if (ci < n_cams) cam_expand_one(cams, ci, rec);
+        return;
+    }
+    const int64_t stride = (int64_t)(gridDim.x - ncb) * blockDim.x;
+    for (int64_t p = (int64_t)(blockIdx.x - ncb) * blockDim.x + threadIdx.x; p < n_pts; p += stride) {
+        const float* X = pts + p * 3;
+        pts4[p] = make_float4(__ldg(X), __ldg(X + 1), __ldg(X + 2), 0.f);
+        acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 // ---- error-free transformations ---------------------------------------------
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
@@ -97,8 +120,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// The first NF floats of the record of camera ci, with 16-byte loads (records
-// are 128 B apart and the workspace is 256-byte aligned).
 // The first NF floats of camera ci's record (128-byte aligned) in 32-byte loads:
 // one sector per lane per load instruction (16-byte loads would fetch every
 // sector of a gathered record twice).
@@ -113,9 +134,6 @@ __device__ __forceinline__ void load_cam(const float* __restrict__ rec, int ci, 
             : "l"(p + 8 * i));
 }
 
-// d_pts[pi][0..2] += g with one 8-byte vector reduction and one scalar one: row
-// pi starts 12*pi bytes in, 8-byte aligned for even pi (pair first) and 4 bytes
-// off for odd pi (scalar first).
 // Point pi of a [P][3] array: one float2 and one float load when the array is
 // 8-byte aligned (which half is 8-byte aligned follows the parity of pi),
 // three float loads otherwise.
@@ -136,6 +154,19 @@ __device__ __forceinline__ void load_point(const float* __restrict__ pts, int pi
         const float2 v = __ldg(reinterpret_cast<const float2*>(X + 1));
         X1 = v.x;
         X2 = v.y;
+    }
+}
+
+// Point pi from the padded copy (one 16-byte load) when there is one.
+__device__ __forceinline__ void load_point_any(const float4* __restrict__ pts4, const float* __restrict__ pts, int pi,
+                                               bool al8, float& X0, float& X1, float& X2) {
+    if (pts4) {
+        const float4 v = __ldg(pts4 + pi);
+        X0 = v.x;
+        X1 = v.y;
+        X2 = v.z;
+    } else {
+        load_point(pts, pi, al8, X0, X1, X2);
     }
 }
 
@@ -313,7 +344,8 @@ __global__ void __launch_bounds__(256) reproj_residual_kernel(
 // VJP over observations; FUSED also writes res and uses w = wscale * res.
 template <int STRAT, bool FUSED>
 __global__ void __launch_bounds__(256) reproj_vjp_kernel(
-    const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
+    const float* __restrict__ rec, const float* __restrict__ pts, const float4* __restrict__ pts4,
+    const int2* __restrict__ obs,
     const float2* __restrict__ wv, const float2* __restrict__ tgt, float wscale, int n_cams, int n_pts,
     int64_t n_obs, float* __restrict__ d_cams, float* __restrict__ d_pts,
     float4* __restrict__ d_pts4, float2* __restrict__ res, int32_t* __restrict__ status, int pts8, int dpts8) {
@@ -346,7 +378,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_kernel(
             float rc[kCamRec];
             load_cam<kCamRec>(rec, ci, rc);
             float X0, X1, X2;
-            load_point(pts, pi, pts8, X0, X1, X2);
+            load_point_any(pts4, pts, pi, pts8, X0, X1, X2);
             const Proj P = project(rc, X0, X1, X2);
             float w0, w1;
             if (FUSED) {
@@ -420,7 +452,8 @@ __device__ __forceinline__ void seg_scan11(float (&v)[11], int key) {
 
 template <bool FUSED>
 __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
-    const float* __restrict__ rec, const float* __restrict__ pts, const float2* __restrict__ wv,
+    const float* __restrict__ rec, const float* __restrict__ pts, const float4* __restrict__ pts4,
+    const float2* __restrict__ wv,
     const float2* __restrict__ tgt, float wscale, int n_cams, int n_pts, int64_t n_obs,
     const int32_t* __restrict__ perm, const int32_t* __restrict__ key_s, const int32_t* __restrict__ aux_s,
     float* __restrict__ d_cams, float* __restrict__ d_pts, float4* __restrict__ d_pts4, float2* __restrict__ res,
@@ -460,7 +493,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
             xq[i][0] = xq[i][1] = xq[i][2] = 0.f;
             wq[i] = make_float2(0.f, 0.f);
             if (ok) {
-                load_point(pts, pv[i], pts8, xq[i][0], xq[i][1], xq[i][2]);
+                load_point_any(pts4, pts, pv[i], pts8, xq[i][0], xq[i][1], xq[i][2]);
                 wq[i] = __ldg((FUSED ? tgt : wv) + ev[i]);
             }
         }
@@ -729,50 +762,51 @@ static int expand_cams(const float* cams, int n_cams, float* rec, cudaStream_t s
 static bool al_dev(const void* p, uintptr_t a) { return (((uintptr_t)p) & (a - 1)) == 0; }
 
 template <int STRAT, bool FUSED>
-static int launch_vjp(const float* rec, const float* pts, const int32_t* obs, const float* w, const float* tgt,
+static int launch_vjp(const float* rec, const float* pts, const float4* pts4, const int32_t* obs, const float* w, const float* tgt,
                       float wscale, int n_cams, int n_pts, int64_t n_obs, const PlanView& pv, float* d_cams,
                       float* d_pts, float4* d_pts4, float* res, int32_t* status, cudaStream_t s) {
     GPA_LAUNCH(FUSED ? "reproj_residual_vjp" : "reproj_vjp", s,
                reproj_vjp_kernel<STRAT, FUSED><<<obs_grid(n_obs), 256, 0, s>>>(
-                   rec, pts, (const int2*)obs, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts,
+                   rec, pts, pts4, (const int2*)obs, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts,
                    n_obs, d_cams, d_pts, d_pts4, (float2*)res, status, al_dev(pts, 8) ? 1 : 0,
                    al_dev(d_pts, 8) ? 1 : 0));
     return GPA_OK;
 }
 
 template <bool FUSED>
-static int launch_vjp_sorted(const float* rec, const float* pts, const float* w, const float* tgt, float wscale,
+static int launch_vjp_sorted(const float* rec, const float* pts, const float4* pts4, const float* w, const float* tgt, float wscale,
                              int n_cams, int n_pts, int64_t n_obs, const PlanView& pv, float* d_cams, float* d_pts,
                              float4* d_pts4, float* res, int32_t* status, cudaStream_t s) {
     const int64_t want = (n_obs + 256 * kOpt - 1) / (256 * kOpt), cap = (int64_t)sm_count() * 8;
     GPA_LAUNCH(FUSED ? "reproj_residual_vjp" : "reproj_vjp", s,
                reproj_vjp_sorted_kernel<FUSED><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
-                   rec, pts, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts, n_obs, pv.perm,
+                   rec, pts, pts4, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts, n_obs, pv.perm,
                    pv.key_sorted, pv.aux_sorted, d_cams, d_pts, d_pts4, (float2*)res, status, al_dev(pts, 8) ? 1 : 0,
                    al_dev(d_pts, 8) ? 1 : 0));
     return GPA_OK;
 }
 
-// d_pts4: padded point accumulators in the workspace (zeroed here, added into
-// d_pts after the scatter), or null to scatter into d_pts directly.
+// pts4: the points in 16-byte rows; d_pts4: padded point accumulators, added
+// into d_pts after the scatter. Both in the workspace, written by
+// vjp_prep_kernel before this call.
 template <bool FUSED>
-static int dispatch_vjp(int strat, const float* rec, const float* pts, const int32_t* obs, const float* w,
+static int dispatch_vjp(int strat, const float* rec, const float* pts, const float4* pts4, const int32_t* obs,
+                        const float* w,
                         const float* tgt, float wscale, int n_cams, int n_pts, int64_t n_obs,
                         const PlanView& pv, float* d_cams, float* d_pts, float4* d_pts4, float* res,
                         int32_t* status, cudaStream_t s) {
-    if (d_pts4 && cudaMemsetAsync(d_pts4, 0, sizeof(float4) * (size_t)n_pts, s) != cudaSuccess) return GPA_ERR_CUDA;
     int rc = GPA_ERR_ARG;
     switch (strat) {
         case GPA_SCATTER_ATOMIC:
-            rc = launch_vjp<GPA_SCATTER_ATOMIC, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs, pv,
+            rc = launch_vjp<GPA_SCATTER_ATOMIC, FUSED>(rec, pts, pts4, obs, w, tgt, wscale, n_cams, n_pts, n_obs, pv,
                                                       d_cams, d_pts, d_pts4, res, status, s);
             break;
         case GPA_SCATTER_WARPAGG:
-            rc = launch_vjp<GPA_SCATTER_WARPAGG, FUSED>(rec, pts, obs, w, tgt, wscale, n_cams, n_pts, n_obs, pv,
+            rc = launch_vjp<GPA_SCATTER_WARPAGG, FUSED>(rec, pts, pts4, obs, w, tgt, wscale, n_cams, n_pts, n_obs, pv,
                                                        d_cams, d_pts, d_pts4, res, status, s);
             break;
         case GPA_SCATTER_SORT:
-            rc = launch_vjp_sorted<FUSED>(rec, pts, w, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams, d_pts, d_pts4,
+            rc = launch_vjp_sorted<FUSED>(rec, pts, pts4, w, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams, d_pts, d_pts4,
                                           res, status, s);
             break;
     }
@@ -789,16 +823,32 @@ using namespace gpa;
 
 static bool al(const void* p, uintptr_t a) { return (((uintptr_t)p) & (a - 1)) == 0; }
 
-// Workspace: expanded cameras, then the padded point accumulators of the VJP.
+// Workspace: expanded cameras, then the padded point accumulators of the VJP,
+// then the points in 16-byte rows.
 static size_t cam_area(int32_t n_cams) { return (sizeof(float) * (size_t)n_cams * kCamRec + 255) & ~(size_t)255; }
+static size_t pt4_area(int32_t n_pts) { return (sizeof(float4) * (size_t)n_pts + 255) & ~(size_t)255; }
 
 extern "C" size_t gpa_reproj_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs) {
     (void)n_obs;
     if (n_cams < 1 || n_pts < 1) return 0;
-    return cam_area(n_cams) + ((sizeof(float4) * (size_t)n_pts + 255) & ~(size_t)255);
+    return cam_area(n_cams) + 2 * pt4_area(n_pts);
 }
 
 static float4* pts_acc(void* ws, int32_t n_cams) { return (float4*)((char*)ws + cam_area(n_cams)); }
+static float4* pts_pad(void* ws, int32_t n_cams, int32_t n_pts) {
+    return (float4*)((char*)ws + cam_area(n_cams) + pt4_area(n_pts));
+}
+
+// Camera expansion, padded point copy and zeroed point accumulators in one launch.
+static int vjp_prep(const float* cams, int n_cams, float* rec, const float* pts, int n_pts, float4* pts4,
+                    float4* acc, cudaStream_t s) {
+    const int ncb = (n_cams + 127) / 128;
+    const int64_t want = ((int64_t)n_pts + 127) / 128, cap = (int64_t)sm_count() * 16;
+    const int npb = (int)(want < cap ? want : cap);
+    GPA_LAUNCH("reproj_vjp_prep", s,
+               vjp_prep_kernel<<<(unsigned)(ncb + npb), 128, 0, s>>>(cams, n_cams, rec, ncb, pts, n_pts, pts4, acc));
+    return GPA_OK;
+}
 
 static int reproj_check(const float* cams, const float* pts, const int32_t* obs, int32_t n_cams,
                         int32_t n_pts, int64_t n_obs, void* ws, size_t ws_bytes) {
@@ -849,10 +899,12 @@ extern "C" int reproj_vjp(const float* cams, const float* pts, const int32_t* ob
     }
     cudaStream_t s = (cudaStream_t)stream;
     float* rec = (float*)ws;
-    rc = expand_cams(cams, n_cams, rec, s);
+    float4* acc = pts_acc(ws, n_cams);
+    float4* pts4 = pts_pad(ws, n_cams, n_pts);
+    rc = vjp_prep(cams, n_cams, rec, pts, n_pts, pts4, acc, s);
     if (rc) return rc;
-    return dispatch_vjp<false>(strat, rec, pts, obs, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
-                               pts_acc(ws, n_cams), nullptr, dev_status, s);
+    return dispatch_vjp<false>(strat, rec, pts, pts4, obs, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
+                               acc, nullptr, dev_status, s);
 }
 
 extern "C" int reproj_jvp(const float* cams, const float* pts, const int32_t* obs, const float* v_cams,
@@ -890,10 +942,12 @@ extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const in
     }
     cudaStream_t s = (cudaStream_t)stream;
     float* rec = (float*)ws;
-    rc = expand_cams(cams, n_cams, rec, s);
+    float4* acc = pts_acc(ws, n_cams);
+    float4* pts4 = pts_pad(ws, n_cams, n_pts);
+    rc = vjp_prep(cams, n_cams, rec, pts, n_pts, pts4, acc, s);
     if (rc) return rc;
-    return dispatch_vjp<true>(strat, rec, pts, obs, nullptr, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams,
-                              d_pts, pts_acc(ws, n_cams), res, dev_status, s);
+    return dispatch_vjp<true>(strat, rec, pts, pts4, obs, nullptr, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams,
+                              d_pts, acc, res, dev_status, s);
 }
 
 extern "C" size_t gpa_reproj_gn_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs) {
@@ -1016,16 +1070,16 @@ extern "C" int reproj_vjp_noalloc(const float* cams, const float* pts, const int
     switch (strat) {
         case GPA_SCATTER_ATOMIC:
             reproj_vjp_kernel<GPA_SCATTER_ATOMIC, false><<<grid, 256, 0, s>>>(
-                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, d_cams, d_pts,
+                rec, pts, nullptr, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, d_cams, d_pts,
                 nullptr, nullptr, dev_status, p8, dp8);
             break;
         case GPA_SCATTER_WARPAGG:
             reproj_vjp_kernel<GPA_SCATTER_WARPAGG, false><<<grid, 256, 0, s>>>(
-                rec, pts, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, d_cams, d_pts,
+                rec, pts, nullptr, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, d_cams, d_pts,
                 nullptr, nullptr, dev_status, p8, dp8);
             break;
         default:
-            return launch_vjp_sorted<false>(rec, pts, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
+            return launch_vjp_sorted<false>(rec, pts, nullptr, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
                                             nullptr, nullptr, dev_status, s);
     }
     GPA_LAUNCH_CHECK();
