@@ -277,8 +277,9 @@ GPA_API int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_
  * Per observation: u = X - c, Y = R(w) u, p = (Y_0, Y_1) / Y_2, rho = |p|^2,
  * L = 1 + kappa_0 rho + kappa_1 rho^2, res = f L p + pp - tgt.
  * R(w) = exp([w]x) (rotation by |w| about w/|w|); the rotation of each camera
- * is expanded once per call in float64 and carried as a float32 hi/lo pair so
- * that Y_2 keeps its relative accuracy for points close to the image plane.
+ * is expanded once per call in float64 and its last row carried as a float32
+ * hi/lo pair so that Y_2 keeps its relative accuracy for points close to the
+ * image plane.
  * Supported: 1 <= C, P <= 2^31 - 1, 1 <= M <= 2^31 - 1. Alignment: obs 8-byte,
  * tgt / res / w 8-byte, others 4-byte.
  */

@@ -37,12 +37,51 @@ constexpr int kCamRec = 32;  // floats per expanded camera: one 128-byte line
 // The residual reads the first 20 floats only.
 constexpr int kCamResid = 20;
 
-__device__ void cam_expand_one(const float* __restrict__ cams, int ci, float* __restrict__ rec) {
-    const float* c = cams + (size_t)ci * 11;
+// Rodrigues coefficients as power series in x = theta^2 (the Taylor series of
+// sin and cos), summed by Horner's rule with constant coefficients:
+//   f1 = sin t / t         = sum_n (-1)^n x^n / (2n+1)!
+//   f2 = (1 - cos t) / t^2 = sum_n (-1)^n x^n / (2n+2)!
+//   g  = (t - sin t) / t^3 = sum_n (-1)^n x^n / (2n+3)!
+// Terms n = 0 .. kSeriesTerms; for x <= kSeriesMaxTh2 the first omitted term
+// is below 1e-17, and the float64 sums are within 4e-16 of the exact values
+// (checked against 120-digit arithmetic over [0, 16]).
+constexpr int kSeriesTerms = 16;
+constexpr double kSeriesMaxTh2 = 16.0;
+
+__host__ __device__ constexpr double inv_factorial(int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= (double)i;
+    return 1.0 / f;
+}
+
+// sum_{n=0}^{kSeriesTerms} (-1)^n x^n / (2n + off)!
+template <int OFF, typename T>
+__device__ __forceinline__ T rodrigues_series(T x) {
+    constexpr int N = kSeriesTerms;
+    T t = (T)((N & 1 ? -1.0 : 1.0) * inv_factorial(2 * N + OFF));
+#pragma unroll
+    for (int n = N - 1; n >= 0; --n) t = fma(t, x, (T)((n & 1 ? -1.0 : 1.0) * inv_factorial(2 * n + OFF)));
+    return t;
+}
+
+// The record o of the camera with parameters c. The rotation is formed in
+// float64 (its last row is stored as a float32 hi/lo pair); the right
+// Jacobian J_r = I - A [w]x + B [w]x^2, stored in float32, is formed in float32.
+__device__ __forceinline__ void cam_expand_one(const float (&c)[11], float (&o)[kCamRec]) {
     const double w0 = c[0], w1 = c[1], w2 = c[2];
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-    double R[9], A, B;
-    if (th2 > 1e-16) {
+    double R[9];
+    float A, B;
+    if (th2 <= kSeriesMaxTh2) {
+        // R = I + f1 [w]x + f2 [w]x^2 with [w]x^2 = w w^T - theta^2 I
+        const double f1 = rodrigues_series<1>(th2), f2 = rodrigues_series<2>(th2);
+        const double d = 1.0 - f2 * th2;  // cos theta
+        R[0] = fma(f2, w0 * w0, d);          R[1] = fma(f2, w0 * w1, -f1 * w2); R[2] = fma(f2, w0 * w2, f1 * w1);
+        R[3] = fma(f2, w1 * w0, f1 * w2);    R[4] = fma(f2, w1 * w1, d);        R[5] = fma(f2, w1 * w2, -f1 * w0);
+        R[6] = fma(f2, w2 * w0, -f1 * w1);   R[7] = fma(f2, w2 * w1, f1 * w0);  R[8] = fma(f2, w2 * w2, d);
+        A = (float)f2;
+        B = rodrigues_series<3>((float)th2);
+    } else {  // theta > 4: unit axis k, sin and cos of theta
         const double th = sqrt(th2);
         const double k0 = w0 / th, k1 = w1 / th, k2 = w2 / th;
         double st, ct;
@@ -51,35 +90,21 @@ __device__ void cam_expand_one(const float* __restrict__ cams, int ci, float* __
         R[0] = ct + omc * k0 * k0;      R[1] = -st * k2 + omc * k0 * k1; R[2] = st * k1 + omc * k0 * k2;
         R[3] = st * k2 + omc * k1 * k0; R[4] = ct + omc * k1 * k1;      R[5] = -st * k0 + omc * k1 * k2;
         R[6] = -st * k1 + omc * k2 * k0; R[7] = st * k0 + omc * k2 * k1; R[8] = ct + omc * k2 * k2;
-        if (th < 1e-3) {  // series of (1-cos t)/t^2 and (t-sin t)/t^3
-            A = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-            B = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
-        } else {
-            A = omc / th2;
-            B = (th - st) / (th2 * th);
-        }
-    } else {  // first order: R = I + [w]x
-        R[0] = 1.0; R[1] = -w2; R[2] = w1;
-        R[3] = w2;  R[4] = 1.0; R[5] = -w0;
-        R[6] = -w1; R[7] = w0;  R[8] = 1.0;
-        A = 0.5;
-        B = 1.0 / 6.0;
+        A = (float)(omc / th2);
+        B = (float)((th - st) / (th2 * th));
     }
-    // [w]x and [w]x^2
-    const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
-    double W2[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int t = 0; t < 3; ++t) s += W[i * 3 + t] * W[t * 3 + j];
-            W2[i * 3 + j] = s;
-        }
-    float* o = rec + (size_t)ci * kCamRec;
+    // [w]x and [w]x^2 = w w^T - theta^2 I in float32
+    const float v[3] = {c[0], c[1], c[2]};
+    const float x2 = (float)th2;
+    const float W[9] = {0.f, -v[2], v[1], v[2], 0.f, -v[0], -v[1], v[0], 0.f};
+#pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float hi = (float)R[i];
         o[i] = hi;
         if (i >= 6) o[9 + (i - 6)] = (float)(R[i] - (double)hi);
-        o[20 + i] = (float)(((i % 4) == 0 ? 1.0 : 0.0) - A * W[i] + B * W2[i]);
+        const int r = i / 3, q = i % 3;
+        const float W2 = v[r] * v[q] - (r == q ? x2 : 0.f);
+        o[20 + i] = fmaf(B, W2, fmaf(-A, W[i], r == q ? 1.f : 0.f));
     }
     o[12] = c[3]; o[13] = c[4]; o[14] = c[5];
     o[15] = c[6]; o[16] = c[7]; o[17] = c[8];
@@ -87,22 +112,49 @@ __device__ void cam_expand_one(const float* __restrict__ cams, int ci, float* __
     o[29] = 0.f; o[30] = 0.f; o[31] = 0.f;
 }
 
-__global__ void __launch_bounds__(128) cam_expand_kernel(const float* __restrict__ cams, int n_cams,
-                                                         float* __restrict__ rec) {
-    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci < n_cams) cam_expand_one(cams, ci, rec);
+// One warp per block: a camera's expansion is a chain of dependent float64
+// operations, which this GPU issues at a low rate, so the cameras are spread
+// over as many SMs as possible.
+constexpr int kCamPerBlock = 32;
+
+// Cameras cam0 .. cam0 + 31 by one warp, lane = camera. Parameters and
+// records pass through shared memory (sm: 32 x 33 floats) so that both move
+// as contiguous rows: a thread storing its own 128-byte record would touch 32
+// lines per store instruction.
+__device__ __forceinline__ void cam_expand_warp(const float* __restrict__ cams, int n_cams, int cam0,
+                                                float* __restrict__ rec, float* sm) {
+    const int lane = threadIdx.x & 31;
+    const int nv = min(32, n_cams - cam0);
+    for (int i = lane; i < nv * 11; i += 32) sm[i] = __ldg(cams + (size_t)cam0 * 11 + i);
+    __syncwarp();
+    float c[11], o[kCamRec];
+#pragma unroll
+    for (int j = 0; j < 11; ++j) c[j] = lane < nv ? sm[lane * 11 + j] : 0.f;
+    __syncwarp();
+    cam_expand_one(c, o);
+#pragma unroll
+    for (int j = 0; j < kCamRec; ++j) sm[lane * (kCamRec + 1) + j] = o[j];
+    __syncwarp();
+    for (int i = 0; i < nv; ++i) rec[(size_t)(cam0 + i) * kCamRec + lane] = sm[i * (kCamRec + 1) + lane];
 }
 
-// Per-call preparation of the VJP: the first ncb blocks expand the cameras,
-// the others copy the points into 16-byte rows (x, y, z, 0), so that a
-// gathered point is one 16-byte load, and zero the padded point accumulators.
+__global__ void __launch_bounds__(32) cam_expand_kernel(const float* __restrict__ cams, int n_cams,
+                                                        float* __restrict__ rec) {
+    __shared__ float sm[32 * (kCamRec + 1)];
+    cam_expand_warp(cams, n_cams, blockIdx.x * kCamPerBlock, rec, sm);
+}
+
+// Per-call preparation of the VJP: the first ncb blocks expand the cameras
+// (kCamPerBlock each, by their first warp), the others copy the points into
+// 16-byte rows (x, y, z, 0), so that a gathered point is one 16-byte load, and
+// zero the padded point accumulators.
 __global__ void __launch_bounds__(128) vjp_prep_kernel(const float* __restrict__ cams, int n_cams,
                                                        float* __restrict__ rec, int ncb,
                                                        const float* __restrict__ pts, int n_pts,
                                                        float4* __restrict__ pts4, float4* __restrict__ acc) {
+    __shared__ float sm[32 * (kCamRec + 1)];
     if ((int)blockIdx.x < ncb) {
-        const int ci = blockIdx.x * blockDim.x + threadIdx.x;
-        if (ci < n_cams) cam_expand_one(cams, ci, rec);
+        if (threadIdx.x < kCamPerBlock) cam_expand_warp(cams, n_cams, blockIdx.x * kCamPerBlock, rec, sm);
         return;
     }
     const int64_t stride = (int64_t)(gridDim.x - ncb) * blockDim.x;
@@ -755,7 +807,9 @@ static unsigned obs_grid(int64_t n_obs) {
 }
 
 static int expand_cams(const float* cams, int n_cams, float* rec, cudaStream_t s) {
-    GPA_LAUNCH("cam_expand", s, cam_expand_kernel<<<(n_cams + 127) / 128, 128, 0, s>>>(cams, n_cams, rec));
+    GPA_LAUNCH("cam_expand", s,
+               cam_expand_kernel<<<(n_cams + kCamPerBlock - 1) / kCamPerBlock, kCamPerBlock, 0, s>>>(cams, n_cams,
+                                                                                                       rec));
     return GPA_OK;
 }
 
@@ -842,7 +896,7 @@ static float4* pts_pad(void* ws, int32_t n_cams, int32_t n_pts) {
 // Camera expansion, padded point copy and zeroed point accumulators in one launch.
 static int vjp_prep(const float* cams, int n_cams, float* rec, const float* pts, int n_pts, float4* pts4,
                     float4* acc, cudaStream_t s) {
-    const int ncb = (n_cams + 127) / 128;
+    const int ncb = (n_cams + kCamPerBlock - 1) / kCamPerBlock;
     const int64_t want = ((int64_t)n_pts + 127) / 128, cap = (int64_t)sm_count() * 16;
     const int npb = (int)(want < cap ? want : cap);
     GPA_LAUNCH("reproj_vjp_prep", s,
@@ -1063,7 +1117,7 @@ extern "C" int reproj_vjp_noalloc(const float* cams, const float* pts, const int
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     // every record the VJP reads is rewritten here first: nothing needs clearing
-    cam_expand_kernel<<<(n_cams + 127) / 128, 128, 0, s>>>(cams, n_cams, rec);
+    cam_expand_kernel<<<(n_cams + kCamPerBlock - 1) / kCamPerBlock, kCamPerBlock, 0, s>>>(cams, n_cams, rec);
     GPA_LAUNCH_CHECK();
     const unsigned grid = obs_grid(n_obs);
     const int p8 = al(pts, 8) ? 1 : 0, dp8 = al(d_pts, 8) ? 1 : 0;  // no padded accumulators: direct atomics

@@ -83,6 +83,51 @@ def test_vjp_matches_oracle(strat, n_cams, n_pts, n_obs):
     assert rel_norm(host(dpt), dpt_ref) <= TOL_GRAD_FP32
 
 
+def _rotation_sweep():
+    """Cameras whose rotation angles span 0 .. 6.2 rad (both sides of theta = 4,
+    where the camera expansion switches from the power series of the Rodrigues
+    coefficients to sin / cos of theta), each observing its own points placed
+    3 .. 8 units in front of it."""
+    from scipy.spatial.transform import Rotation
+    angles = np.array([0.0, 1e-12, 1e-7, 1e-4, 0.03, 0.5, 1.0, 2.0, 3.0, 3.1416, 3.5, 3.99, 3.9999,
+                       4.0, 4.0001, 4.01, 4.5, 5.0, 5.9, 6.2])
+    nc, per = angles.size, 40
+    r = synth.reproj_inputs(nc, nc * per, nc * per, seed=77)
+    rng = np.random.default_rng(77)
+    axes = rng.standard_normal((nc, 3))
+    axes /= np.linalg.norm(axes, axis=1, keepdims=True)
+    r.cams[:, 0:3] = (axes * angles[:, None]).astype(np.float32)
+    for ci in range(nc):
+        rot = Rotation.from_rotvec(r.cams[ci, 0:3].astype(np.float64))
+        y = np.column_stack([rng.uniform(-1, 1, per), rng.uniform(-1, 1, per), rng.uniform(3, 8, per)])
+        js = np.arange(ci * per, (ci + 1) * per)
+        r.pts[js] = (r.cams[ci, 3:6].astype(np.float64) + rot.inv().apply(y)).astype(np.float32)
+        r.obs[js, 0] = ci
+        r.obs[js, 1] = js
+    return r
+
+
+def test_rotation_angles_across_expansion_branches():
+    import paper_2104_05372_b300 as gpa
+    r = _rotation_sweep()
+    cams, pts, obs, tgt, w = _dev_inputs(r)
+    res_ref, bad = oracle.reproj_residual(r)
+    assert bad == 0
+    res = host(gpa.reproj_residual(cams, pts, obs, tgt))
+    assert rel_norm(res, res_ref) <= 1e-5
+    dcm_ref, dpt_ref, _ = oracle.reproj_vjp(r)
+    for strat in STRATS:
+        plan = gpa.gpa_obs_plan_build(obs, r.n_cams, r.n_pts) if strat == "sort" else None
+        dcm, dpt = gpa.reproj_vjp(cams, pts, obs, w, strat=strat, plan=plan)
+        assert rel_norm(host(dcm), dcm_ref) <= TOL_GRAD_FP32, strat
+        assert rel_norm(host(dpt), dpt_ref) <= TOL_GRAD_FP32, strat
+    vc, vp = synth.reproj_tangents(r.n_cams, r.n_pts, seed=5)
+    vc32, vp32 = vc.astype(np.float32), vp.astype(np.float32)
+    jv_ref, _ = oracle.reproj_jvp(r, vc32.astype(np.float64), vp32.astype(np.float64))
+    jv = host(gpa.reproj_jvp(cams, pts, obs, dev(vc32), dev(vp32)))
+    assert rel_norm(jv, jv_ref) <= 1e-5
+
+
 def test_dot_product_adjoint_against_oracle_jvp():
     """<J v, w> (oracle, forward mode) = <v, J^T w> (GPU, Accum scatter)."""
     import paper_2104_05372_b300 as gpa
