@@ -444,6 +444,9 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
     ms = timed(lambda: gpa.reproj_residual(cams, pts, obs, tgt, res=res, ws=ws))
     out["residual"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
                        "hbm_gbs_algorithmic": 25.6 * RP_M / (ms / 1e3) / 1e9}
+    ms = timed(lambda: gpa.reproj_residual(cams, pts, obs, tgt, res=res, plan=plan, ws=ws))
+    out["residual_sort"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
+                            "hbm_gbs_algorithmic": 25.6 * RP_M / (ms / 1e3) / 1e9}
     ms = timed(lambda: gpa.reproj_residual_vjp(cams, pts, obs, tgt, 1.0, res=res, d_cams=dcm, d_pts=dpt,
                                                strat="sort", plan=plan, ws=ws))
     out["fused_residual_vjp_sort"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,

@@ -295,6 +295,16 @@ GPA_API int reproj_residual(const float* cams, const float* pts, const int32_t* 
                     int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, void* ws,
                     size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
 
+/* reproj_residual computed in the camera-sorted order of a plan built from obs
+ * by gpa_obs_plan_build (each camera's record is read once per run of its
+ * observations instead of once per observation); res is still written in
+ * input order, and every entry equals reproj_residual's bit for bit. obs is
+ * checked (non-null, 8-byte aligned) but not read: the plan carries the
+ * indices. Invalid indices: NaN rows and GPA_ERR_INDEX, as above. */
+GPA_API int reproj_residual_sorted(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
+                    int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, const void* plan, void* ws,
+                    size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
+
 /*
  * VJP of the residual with cotangent w [M][2]: d_cams[c] += J_cam^T w_j and
  * d_pts[p] += J_pt^T w_j over all observations j with obs[j] = (c, p): the

@@ -54,6 +54,7 @@ _SIGS = {
     "reproj_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "reproj_residual_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _F, _P, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "reproj_jvp": ([_P, _P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
+    "reproj_residual_sorted": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _P, _SZ, _P, _P], _I32),
     "gpa_reproj_gn_workspace_bytes": ([_I32, _I32, _I64], _SZ),
     "reproj_normal_eqs": ([_P] * 4 + [_I32, _I32, _I64] + [_P] * 3 + [_I32] + [_P] * 3 + [_I32, _P, _P, _SZ, _P, _P],
                           _I32),
@@ -392,15 +393,22 @@ def _reproj_params(cams, pts, obs):
     return cams.shape[0], pts.shape[0], obs.shape[0]
 
 
-def reproj_residual(cams, pts, obs, tgt, res=None, ws=None, status=None, stream=None):
+def reproj_residual(cams, pts, obs, tgt, res=None, plan=None, ws=None, status=None, stream=None):
+    """res [M, 2] = projection - target; with a plan (gpa_obs_plan_build) the
+    observations are visited in camera-sorted order (reproj_residual_sorted)."""
     nc, npt, no = _reproj_params(cams, pts, obs)
     _check(tgt, torch.float32, "tgt", (no, 2))
     res = torch.empty(no, 2, dtype=torch.float32, device=cams.device) if res is None else res
     _check(res, torch.float32, "res", (no, 2))
     ws = workspace(gpa_reproj_workspace_bytes(nc, npt, no), cams.device) if ws is None else ws
-    rc = load().reproj_residual(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, _ptr(res), _ptr(ws),
-                                ws.numel(), _ptr(status), _stream(stream))
-    _ok(rc, "reproj_residual")
+    if plan is None:
+        rc = load().reproj_residual(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, _ptr(res), _ptr(ws),
+                                    ws.numel(), _ptr(status), _stream(stream))
+        _ok(rc, "reproj_residual")
+    else:
+        rc = load().reproj_residual_sorted(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, _ptr(res),
+                                           _ptr(plan), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+        _ok(rc, "reproj_residual_sorted")
     return res
 
 

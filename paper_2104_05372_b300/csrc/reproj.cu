@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(32) cam_expand_kernel(const float* __restrict_
 // Per-call preparation of the VJP: the first ncb blocks expand the cameras
 // (kCamPerBlock each, by their first warp), the others copy the points into
 // 16-byte rows (x, y, z, 0), so that a gathered point is one 16-byte load, and
-// zero the padded point accumulators.
+// zero the padded point accumulators (when acc is given).
 __global__ void __launch_bounds__(128) vjp_prep_kernel(const float* __restrict__ cams, int n_cams,
                                                        float* __restrict__ rec, int ncb,
                                                        const float* __restrict__ pts, int n_pts,
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(128) vjp_prep_kernel(const float* __restrict__
     for (int64_t p = (int64_t)(blockIdx.x - ncb) * blockDim.x + threadIdx.x; p < n_pts; p += stride) {
         const float* X = pts + p * 3;
         pts4[p] = make_float4(__ldg(X), __ldg(X + 1), __ldg(X + 2), 0.f);
-        acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (acc) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -502,7 +502,8 @@ __device__ __forceinline__ void seg_scan11(float (&v)[11], int key) {
     for (int i = 0; i < 11; ++i) v[i] = run_scan_head(v[i], head);
 }
 
-template <bool FUSED>
+// VJP = false (with FUSED): the residual alone, in camera-sorted order.
+template <bool FUSED, bool VJP = true>
 __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
     const float* __restrict__ rec, const float* __restrict__ pts, const float4* __restrict__ pts4,
     const float2* __restrict__ wv,
@@ -564,7 +565,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
                 report(status, GPA_ERR_INDEX);
                 continue;
             }
-            if (ci != cur) {
+            if (VJP && ci != cur) {
                 if (cur >= 0) {
                     float* dc = d_cams + (size_t)cur * 11;
 #pragma unroll
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
                 cur = ci;
             }
             if (ci != rcam) {
-                load_cam<kCamRec>(rec, ci, rc);
+                load_cam<VJP ? kCamRec : kCamResid>(rec, ci, rc);
                 rcam = ci;
             }
             const Proj P = project(rc, xq[i][0], xq[i][1], xq[i][2]);
@@ -591,22 +592,26 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
                 w0 = wq[i].x;
                 w1 = wq[i].y;
             }
-            float gl[11], gp[3];
-            project_vjp(rc, P, w0, w1, gl, gp);
+            if constexpr (VJP) {
+                float gl[11], gp[3];
+                project_vjp(rc, P, w0, w1, gl, gp);
 #pragma unroll
-            for (int j = 0; j < 11; ++j) gc[j] += gl[j];
-            if (d_pts4)
-                atomicAdd(d_pts4 + pi, make_float4(gp[0], gp[1], gp[2], 0.f));
-            else
-                red_add_point(d_pts, pi, gp, dpts8);
+                for (int j = 0; j < 11; ++j) gc[j] += gl[j];
+                if (d_pts4)
+                    atomicAdd(d_pts4 + pi, make_float4(gp[0], gp[1], gp[2], 0.f));
+                else
+                    red_add_point(d_pts, pi, gp, dpts8);
+            }
         }
-        const int ck = cur >= 0 ? cur : -1 - lane;
-        seg_scan11(gc, ck);
-        const bool last = run_end(ck);  // a shuffle: every lane evaluates it
-        if (cur >= 0 && last) {
-            float* dc = d_cams + (size_t)cur * 11;
+        if constexpr (VJP) {
+            const int ck = cur >= 0 ? cur : -1 - lane;
+            seg_scan11(gc, ck);
+            const bool last = run_end(ck);  // a shuffle: every lane evaluates it
+            if (cur >= 0 && last) {
+                float* dc = d_cams + (size_t)cur * 11;
 #pragma unroll
-            for (int j = 0; j < 11; ++j) red_add(dc + j, gc[j]);
+                for (int j = 0; j < 11; ++j) red_add(dc + j, gc[j]);
+            }
         }
     }
 }
@@ -928,6 +933,27 @@ extern "C" int reproj_residual(const float* cams, const float* pts, const int32_
                reproj_residual_kernel<<<obs_grid(n_obs), 256, 0, s>>>(rec, pts, (const int2*)obs,
                                                                       (const float2*)tgt, n_cams, n_pts, n_obs,
                                                                       (float2*)res, dev_status, al(pts, 8) ? 1 : 0));
+    return GPA_OK;
+}
+
+extern "C" int reproj_residual_sorted(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
+                                      int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, const void* plan,
+                                      void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
+    int rc = reproj_check(cams, pts, obs, n_cams, n_pts, n_obs, ws, ws_bytes);
+    if (rc) return rc;
+    if (!tgt || !res || !plan) return GPA_ERR_ARG;
+    if (!al(tgt, 8) || !al(res, 8)) return GPA_ERR_ALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rec = (float*)ws;
+    float4* pts4 = pts_pad(ws, n_cams, n_pts);
+    rc = vjp_prep(cams, n_cams, rec, pts, n_pts, pts4, nullptr, s);
+    if (rc) return rc;
+    const PlanView pv = plan_view(plan, n_obs, n_cams);
+    const int64_t want = (n_obs + 256 * kOpt - 1) / (256 * kOpt), cap = (int64_t)sm_count() * 8;
+    GPA_LAUNCH("reproj_residual_sorted", s,
+               (reproj_vjp_sorted_kernel<true, false><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
+                   rec, pts, pts4, nullptr, (const float2*)tgt, 1.f, n_cams, n_pts, n_obs, pv.perm, pv.key_sorted,
+                   pv.aux_sorted, nullptr, nullptr, nullptr, (float2*)res, dev_status, al_dev(pts, 8) ? 1 : 0, 0)));
     return GPA_OK;
 }
 

@@ -65,6 +65,44 @@ def test_residual_matches_oracle(n_cams, n_pts, n_obs):
     assert np.allclose(res, ref, rtol=2e-5, atol=1e-3)
 
 
+@pytest.mark.parametrize("n_cams,n_pts,n_obs", [(1, 1, 1), (3, 7, 33), (50, 300, 20000), (200, 5000, 100003)])
+def test_sorted_residual_is_bit_identical(n_cams, n_pts, n_obs):
+    """The camera-sorted residual visits observations in plan order and writes
+    them back in input order with the same per-observation arithmetic."""
+    import paper_2104_05372_b300 as gpa
+    r = synth.reproj_inputs(n_cams, n_pts, n_obs, seed=n_obs + 3)
+    if n_obs > 1000:
+        _near_plane(r)
+    ref, _ = oracle.reproj_residual(r)
+    cams, pts, obs, tgt, _ = _dev_inputs(r)
+    plan = gpa.gpa_obs_plan_build(obs, n_cams, n_pts)
+    st = status()
+    res_s = host(gpa.reproj_residual(cams, pts, obs, tgt, plan=plan, status=st))
+    res_n = host(gpa.reproj_residual(cams, pts, obs, tgt))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert np.array_equal(res_s, res_n)
+    assert rel_norm(res_s, ref) <= 1e-5
+
+
+def test_sorted_residual_invalid_indices():
+    import paper_2104_05372_b300 as gpa
+    r = synth.reproj_inputs(10, 20, 500, seed=16)
+    r.obs[3, 0] = 10
+    r.obs[9, 1] = -1
+    cams, pts, obs, tgt, _ = _dev_inputs(r)
+    st = status()
+    plan = gpa.gpa_obs_plan_build(obs, 10, 20)
+    st.zero_()
+    res = host(gpa.reproj_residual(cams, pts, obs, tgt, plan=plan, status=st))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 2
+    assert np.isnan(res[[3, 9]]).all() and np.isfinite(np.delete(res, [3, 9], axis=0)).all()
+    ref, _ = oracle.reproj_residual(r)
+    ok = np.delete(np.arange(500), [3, 9])
+    assert rel_norm(res[ok], ref[ok]) <= 1e-5
+
+
 @pytest.mark.parametrize("strat", STRATS)
 @pytest.mark.parametrize("n_cams,n_pts,n_obs", [(1, 1, 1), (3, 7, 33), (50, 300, 20000), (200, 5000, 100003)])
 def test_vjp_matches_oracle(strat, n_cams, n_pts, n_obs):
