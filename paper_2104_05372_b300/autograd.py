@@ -60,7 +60,10 @@ class ReprojResidual(torch.autograd.Function):
     @staticmethod
     def forward(ctx, cams, pts, obs, tgt, strat="auto", plan=None):
         cams, pts, obs, tgt = (t.contiguous() for t in (cams, pts, obs, tgt))
-        res = _lib.reproj_residual(cams, pts, obs, tgt)
+        # with a plan the residual is computed in its camera-sorted order too
+        # (bit-identical to the input-order kernel)
+        sorted_plan = plan if plan is not None and strat in ("auto", "sort") else None
+        res = _lib.reproj_residual(cams, pts, obs, tgt, plan=sorted_plan)
         ctx.save_for_backward(cams, pts, obs)
         ctx.strat, ctx.plan = strat, plan
         return res
