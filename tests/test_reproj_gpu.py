@@ -271,6 +271,15 @@ def test_autograd_reprojection():
     dcm_ref, dpt_ref, _ = oracle.reproj_vjp(r)
     assert rel_norm(host(cams.grad), dcm_ref) <= TOL_GRAD_FP32
     assert rel_norm(host(pts.grad), dpt_ref) <= TOL_GRAD_FP32
+    # with a plan: camera-sorted forward (bit-identical residual) and SORT backward
+    import paper_2104_05372_b300 as gpa
+    plan = gpa.gpa_obs_plan_build(obs, r.n_cams, r.n_pts)
+    cams.grad = pts.grad = None
+    res_p = reproj_residual(cams, pts, obs, tgt, plan=plan)
+    assert torch.equal(res_p.detach(), res.detach())
+    res_p.backward(w)
+    assert rel_norm(host(cams.grad), dcm_ref) <= TOL_GRAD_FP32
+    assert rel_norm(host(pts.grad), dpt_ref) <= TOL_GRAD_FP32
 
 
 @pytest.mark.parametrize("n_cams,n_pts,n_obs", [(1, 1, 1), (50, 300, 20000), (200, 5000, 100003)])
