@@ -107,6 +107,7 @@ template <int DP>
 static int launch_prep(const GmmArgs& A, const GmmLayout& L, char* ws, cudaStream_t s) {
     GPA_LAUNCH("gmm_prep", s,
                gmm_prep_kernel<DP><<<A.k, 128, 0, s>>>(A.alpha, A.mu, A.q, A.l, A.d, A.k, A.gamma, A.m,
+                                                       gmm_prior_const(A.d, A.m, A.gamma),
                                                        (float*)(ws + L.off_rec), (double*)(ws + L.off_lpk),
                                                        (double*)(ws + L.off_scal)));
     return GPA_OK;

@@ -39,7 +39,7 @@ struct BInst {
     float *rec, *bS, *bM, *lj, *lse;
     double *scal, *lpk, *fwd;
     int64_t n, tiles_per_chunk;
-    double gamma, seed;
+    double gamma, seed, cw;  // cw: gmm_prior_const(d, m, gamma)
     int d, k, m, dp, nchunks, ntiles128;
 };
 
@@ -129,6 +129,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
         B.m = I.m;
         B.dp = dp;
         B.gamma = I.gamma;
+        B.cw = gmm_prior_const(I.d, I.m, I.gamma);
         B.seed = I.seed;
         B.ntiles128 = (int)((I.n + 127) / 128);
         const int64_t ntiles64 = (I.n + bwd_tpb(dp) - 1) / bwd_tpb(dp);  // backward tiles
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(128) batched_prep_kernel(const BInst* __restri
         if (it >= n_items) break;
         const BItem w = items[it];
         const BInst& B = inst[w.inst];
-        gmm_prep_kernel_body<DP>(B.alpha, B.mu, B.q, B.l, B.d, B.k, B.gamma, B.m, B.rec, B.lpk, B.scal,
+        gmm_prep_kernel_body<DP>(B.alpha, B.mu, B.q, B.l, B.d, B.k, B.gamma, B.m, B.cw, B.rec, B.lpk, B.scal,
                                  (unsigned)w.a);
         __syncthreads();
     }

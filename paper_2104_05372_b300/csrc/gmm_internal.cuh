@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -66,5 +67,17 @@ bool gmm_tc_supported(int d);
 size_t gmm_tc_extra_bytes(int64_t n, int d, int k);
 int gmm_tc_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s);
 int gmm_tc_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s);
+
+// The data-independent part of each component's Wishart log-prior, for
+// n = d + m + 1 degrees of freedom: n d log(gamma) - (n d / 2) log 2 - log
+// Gamma_d(n/2), with log Gamma_d(a) = d (d - 1) / 4 log(pi) + sum_{j<d}
+// lgamma(a - j / 2). Computed once per call on the host in float64.
+inline double gmm_prior_const(int d, int m, double gamma) {
+    const double nn = (double)(d + m + 1);
+    double lg = 0.0;
+    for (int j = 0; j < d; ++j) lg += lgamma(0.5 * nn - 0.5 * (double)j);
+    const double log_mvg = 0.25 * d * (d - 1) * log(3.14159265358979323846) + lg;
+    return nn * d * log(gamma) - 0.5 * nn * d * log(2.0) - log_mvg;
+}
 
 }  // namespace gpa

@@ -103,7 +103,7 @@ __device__ __forceinline__ void gmm_prep_kernel_body(const float* __restrict__ a
                                                        const float* __restrict__ mu,
                                                        const float* __restrict__ q,
                                                        const float* __restrict__ l, int d, int k,
-                                                       double gamma, int m, float* __restrict__ rec,
+                                                       double gamma, int m, double cw, float* __restrict__ rec,
                                                        double* __restrict__ lpk,
                                                        double* __restrict__ scal, unsigned bx) {
     constexpr int REC = Fwd<DP>::REC;
@@ -122,23 +122,41 @@ __device__ __forceinline__ void gmm_prep_kernel_body(const float* __restrict__ a
         const int c = e / DP, r = e % DP;
         R[e] = Qrc(r, c);  // transposed: Qt[c][r]
     }
-    // b = Q mu: one warp per row, lanes over the row's columns (coalesced reads of l)
+    // b = Q mu: one warp per row, lanes over the row's columns (coalesced reads
+    // of l). Compensated float32 dot product (Dot2 of Ogita, Rump and Oishi:
+    // exact products by FMA, TwoSum accumulation, pairs merged across lanes by
+    // TwoSum), as accurate as a float64 sum before the final rounding to float.
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    auto two_sum_acc = [](float& hi, float& lo, float x) {
+        const float t = __fadd_rn(hi, x);
+        const float bb = __fsub_rn(t, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+        hi = t;
+    };
     for (int r = threadIdx.x >> 5; r < DP; r += nw) {
-        double s = 0.0;
+        float hi = 0.f, lo = 0.f;
         if (r < d)
-            for (int c = lane; c <= r; c += 32) s += (double)Qrc(r, c) * (double)muk[c];
-        s = warp_sum(s);
-        if (lane == 0) R[DP * DP + r] = (float)s;
+            for (int c = lane; c <= r; c += 32) {
+                const float a = Qrc(r, c), b = muk[c];
+                const float p = __fmul_rn(a, b);
+                two_sum_acc(hi, lo, p);
+                lo = __fadd_rn(lo, fmaf(a, b, -p));
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            two_sum_acc(hi, lo, h2);
+            lo = __fadd_rn(lo, l2);
+        }
+        if (lane == 0) R[DP * DP + r] = __fadd_rn(hi, lo);
     }
     // log-prior of this component and the constant alpha_k + sum_d q_kd
-    const double nn = (double)(d + m + 1);
-    double sq = 0.0, fro = 0.0, lg = 0.0;
+    double sq = 0.0, fro = 0.0;
     for (int r = threadIdx.x; r < d; r += blockDim.x) {
         const double qv = qk[r];
         sq += qv;
         fro += exp(2.0 * qv);
-        lg += lgamma(0.5 * nn + 0.5 * (double)(-r));  // log Gamma_D(n/2) term j = r + 1
     }
     for (int j = threadIdx.x; j < t; j += blockDim.x) {
         const double lv = lk[j];
@@ -151,13 +169,11 @@ __device__ __forceinline__ void gmm_prep_kernel_body(const float* __restrict__ a
     __shared__ double red[4][8];  // up to 256 threads
     sq = warp_sum(sq);
     fro = warp_sum(fro);
-    lg = warp_sum(lg);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if (lane == 0) {
         red[0][threadIdx.x >> 5] = sq;
         red[1][threadIdx.x >> 5] = fro;
-        red[2][threadIdx.x >> 5] = lg;
         red[3][threadIdx.x >> 5] = amax;
     }
     __syncthreads();
@@ -173,21 +189,17 @@ __device__ __forceinline__ void gmm_prep_kernel_body(const float* __restrict__ a
     if (threadIdx.x == 0) {
         sq = 0.0;
         fro = 0.0;
-        lg = 0.0;
         ae = 0.0;
         for (int w = 0; w < nw; ++w) {
             sq += red[0][w];
             fro += red[1][w];
-            lg += red[2][w];
             ae += red[3][w];
         }
         R[DP * DP + DP] = (float)((double)alpha[kk] + sq);
         R[DP * DP + DP + 1] = 0.f;
         R[DP * DP + DP + 2] = 0.f;
         R[DP * DP + DP + 3] = 0.f;
-        const double log_mvg = 0.25 * d * (d - 1) * log(3.14159265358979323846) + lg;
-        const double cw = nn * d * log(gamma) - 0.5 * nn * d * log(2.0) - log_mvg;
-        lpk[kk] = (double)m * sq - 0.5 * gamma * gamma * fro + cw;
+        lpk[kk] = (double)m * sq - 0.5 * gamma * gamma * fro + cw;  // cw: gmm_prior_const
         if (kk == 0) scal[0] = mx + log(ae);
     }
 }
@@ -197,10 +209,10 @@ __global__ void __launch_bounds__(128) gmm_prep_kernel(const float* __restrict__
                                                        const float* __restrict__ mu,
                                                        const float* __restrict__ q,
                                                        const float* __restrict__ l, int d, int k,
-                                                       double gamma, int m, float* __restrict__ rec,
-                                                       double* __restrict__ lpk,
+                                                       double gamma, int m, double cw,
+                                                       float* __restrict__ rec, double* __restrict__ lpk,
                                                        double* __restrict__ scal) {
-    gmm_prep_kernel_body<DP>(alpha, mu, q, l, d, k, gamma, m, rec, lpk, scal, blockIdx.x);
+    gmm_prep_kernel_body<DP>(alpha, mu, q, l, d, k, gamma, m, cw, rec, lpk, scal, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -707,6 +719,31 @@ __global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
                                                 blockIdx.x, blockIdx.y);
 }
 
+// Sum over chunks c = 0 .. n-1 of p[c * stride] (float32 partials), in chunk
+// order, as an unevaluated pair hi + lo of float32 (TwoSum, Knuth): about 48
+// significant bits, as good as a float64 sum of float32 terms, but on the
+// float32 pipe (this GPU issues float64 at a small fraction of that rate).
+__device__ __forceinline__ double chunk_sum(const float* __restrict__ p, int64_t stride, int n) {
+    float hi = 0.f, lo = 0.f;
+    for (int c = 0; c < n; ++c) {
+        const float x = p[(int64_t)c * stride];
+        const float t = __fadd_rn(hi, x);
+        const float bb = __fsub_rn(t, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+        hi = t;
+    }
+    return (double)hi + (double)lo;
+}
+
+// Row r and column c <= r of the e-th entry of a lower triangle stored by rows
+// (e = r (r + 1) / 2 + c): float estimate of r, then exact integer fix-ups.
+__device__ __forceinline__ void tri_index(int e, int& r, int& c) {
+    r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while (r * (r + 1) / 2 > e) --r;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    c = e - r * (r + 1) / 2;
+}
+
 // ---------------------------------------------------------------------------
 // A3: finalize gradients per component (fixed-order sums over chunks)
 // ---------------------------------------------------------------------------
@@ -727,8 +764,8 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double* Sd = reinterpret_cast<double*>(smem_raw);  // [NBLK*64]
     double* md = Sd + NBLK * 64;                         // [DP+1]
-    double* vd = md + DP + 1;                            // [DP]  Q (m - R mu)
-    double* mud = vd + DP;                               // [DP]
+    double* vd = md + DP + 1;                            // [DP]  v = m - R mu
+    double* mud = vd + DP;                               // [DP]  mu, then Q v
     float* Cf = reinterpret_cast<float*>(mud + DP);      // [DP][DP] symmetric
     float* Qf = Cf + DP * DP;                            // [DP][DP] lower
     const int kk = bx, tid = threadIdx.x;
@@ -740,16 +777,10 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
         for (int e = tid; e < NBLK * 64; e += 256) Sd[e] = exch[(size_t)kk * E + e];
         for (int e = tid; e < DP + 1; e += 256) md[e] = exch[(size_t)kk * E + NBLK * 64 + e];
     } else {
-        for (int e = tid; e < NBLK * 64; e += 256) {
-            double s = 0.0;
-            for (int c = 0; c < nchunks; ++c) s += partS[((int64_t)c * k + kk) * NBLK * 64 + e];
-            Sd[e] = s;
-        }
-        for (int e = tid; e < DP + 1; e += 256) {
-            double s = 0.0;
-            for (int c = 0; c < nchunks; ++c) s += partM[((int64_t)c * k + kk) * (DP + 1) + e];
-            md[e] = s;
-        }
+        for (int e = tid; e < NBLK * 64; e += 256)
+            Sd[e] = chunk_sum(partS + (int64_t)kk * NBLK * 64 + e, (int64_t)k * NBLK * 64, nchunks);
+        for (int e = tid; e < DP + 1; e += 256)
+            md[e] = chunk_sum(partM + (int64_t)kk * (DP + 1) + e, (int64_t)k * (DP + 1), nchunks);
     }
     for (int e = tid; e < DP * DP; e += 256) {
         const int r = e / DP, c = e % DP;
@@ -760,32 +791,36 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
     for (int e = tid; e < DP; e += 256) mud[e] = e < d ? (double)mu[(size_t)kk * d + e] : 0.0;
     __syncthreads();
     const double R = md[DP];
-    for (int e = tid; e < DP * DP; e += 256) {
-        const int a = e / DP, b = e % DP;
-        if (b > a) continue;
+    // v = m - R mu (raw moments) or m (centred sums)
+    for (int j = tid; j < DP; j += 256) vd[j] = centered ? md[j] : md[j] - R * mud[j];
+    __syncthreads();
+    // C = S - mu v^T - m mu^T (= S - mu m^T - m mu^T + R mu mu^T), mirrored
+    for (int e = tid; e < DP * (DP + 1) / 2; e += 256) {
+        int a, b;
+        tri_index(e, a, b);
         double c = 0.0;
         if (a < d) {
             const int A = a >> 3, B = b >> 3;
             const double S = Sd[(A * (A + 1) / 2 + B) * 64 + (a & 7) * 8 + (b & 7)];
-            c = centered ? S : S - mud[a] * md[b] - md[a] * mud[b] + R * mud[a] * mud[b];
+            c = centered ? S : S - mud[a] * vd[b] - md[a] * mud[b];
         }
         Cf[a * DP + b] = (float)c;
         Cf[b * DP + a] = (float)c;
     }
+    __syncthreads();  // last read of mu
+    // w = Q v, stored over mu
     for (int r = tid; r < DP; r += 256) {
-        double v = 0.0;
+        double w = 0.0;
         if (r < d)
-            for (int j = 0; j <= r; ++j) v += (double)Qf[r * DP + j] * (centered ? md[j] : md[j] - R * mud[j]);
-        vd[r] = v;
+            for (int j = 0; j <= r; ++j) w += (double)Qf[r * DP + j] * vd[j];
+        mud[r] = w;
     }
     __syncthreads();
     // H = Q C on the lower triangle; dq from its diagonal, dl from the rest
     const int ne = d * (d + 1) / 2;
     for (int e = tid; e < ne; e += 256) {
-        int r = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-        while (r * (r + 1) / 2 > e) --r;
-        while ((r + 1) * (r + 2) / 2 <= e) ++r;
-        const int c = e - r * (r + 1) / 2;
+        int r, c;
+        tri_index(e, r, c);
         float h = 0.f;
         for (int j = 0; j <= r; ++j) h = fmaf(Qf[r * DP + j], Cf[j * DP + c], h);
         if (c == r) {
@@ -796,9 +831,10 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
             d_l[(size_t)kk * t + li] += (float)(-(double)h - seed * gamma * gamma * (double)lk[li]);
         }
     }
+    // d mu = Q^T w
     for (int c = tid; c < d; c += 256) {
         double s = 0.0;
-        for (int r = c; r < d; ++r) s += (double)Qf[r * DP + c] * vd[r];
+        for (int r = c; r < d; ++r) s += (double)Qf[r * DP + c] * mud[r];
         d_mu[(size_t)kk * d + c] += (float)s;
     }
     if (tid == 0) d_alpha[kk] += (float)(R - seed * (double)n * exp((double)alpha[kk] - scal[0]));
@@ -816,7 +852,7 @@ __global__ void __launch_bounds__(256) gmm_finalize_kernel(
 }
 
 // Exchange vector of one shard of points: per component the chunk partial sums
-// [S blocks | m | R] combined in chunk order in float64, then the sum of the
+// [S blocks | m | R] combined in chunk order (chunk_sum), then the sum of the
 // shard's per-point logsumexp (tile partials in tile order), added (+=) into
 // exch. Sums of these vectors over shards are the Accum sums of all points
 // (Sec. 2.3.2).
@@ -830,15 +866,11 @@ __global__ void __launch_bounds__(256) gmm_exchange_kernel(const float* __restri
     const int kk = blockIdx.x;
     if (kk < k) {
         const int e = blockIdx.y * 256 + threadIdx.x;
-        if (e < NS) {
-            double s = 0.0;
-            for (int c = 0; c < nchunks; ++c) s += partS[((int64_t)c * k + kk) * NS + e];
-            exch[(size_t)kk * E + e] += s;
-        } else if (e < E) {
-            double s = 0.0;
-            for (int c = 0; c < nchunks; ++c) s += partM[((int64_t)c * k + kk) * (DP + 1) + (e - NS)];
-            exch[(size_t)kk * E + e] += s;
-        }
+        if (e < NS)
+            exch[(size_t)kk * E + e] += chunk_sum(partS + (int64_t)kk * NS + e, (int64_t)k * NS, nchunks);
+        else if (e < E)
+            exch[(size_t)kk * E + e] +=
+                chunk_sum(partM + (int64_t)kk * (DP + 1) + (e - NS), (int64_t)k * (DP + 1), nchunks);
         return;
     }
     if (blockIdx.y != 0) return;
