@@ -156,6 +156,28 @@ def test_runs_regular_segmented(dtype, seg):
             assert np.all(np.abs(got.reshape(nb, w) - ref) <= bound)
 
 
+@pytest.mark.parametrize("w", [1, 11, 31, 33])
+def test_runs_unaligned_values_bit_exact(w):
+    """RUNS with the value rows at a 4-byte offset and a ragged last block
+    gives the oracle's integer sums."""
+    import paper_2104_05372_b300 as gpa
+    m, seg = 70001, 37
+    nb = (m + seg - 1) // seg
+    idx = (np.arange(m) // seg).astype(np.int32)
+    _, vals = synth.scatter_inputs(m, w, nb, "i32", seed=w)
+    ref, _ = oracle.scatter_add(idx, vals, nb)
+    buf = torch.empty(m * w + 1, dtype=torch.int32, device="cuda")
+    off = buf[1:].view(m, w)
+    off.copy_(dev(vals))
+    assert off.data_ptr() % 16 == 4
+    acc = torch.zeros(nb, w, dtype=torch.int32, device="cuda")
+    st = status()
+    gpa.accum_scatter_add(dev(idx), off, acc, strat="runs", status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert np.array_equal(host(acc).astype(np.int64), ref)
+
+
 def test_complete_reduction_float_within_bound():
     """One bucket, width 1: the complete pattern (tree sums, one atomic per CTA)."""
     m = 3000017
