@@ -462,6 +462,11 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
     out["normal_eqs_sort"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
                               "hbm_gbs_algorithmic": gn_bytes * RP_M / (ms / 1e3) / 1e9,
                               "bytes_per_obs": gn_bytes}
+    ms = timed(lambda: gpa.reproj_normal_eqs(cams, pts, obs, tgt, U=U, V=V, W=W, g_cams=dcm, g_pts=dpt, res=res,
+                                             strat="sort", plan=plan, w_order="plan", ws=gws))
+    out["normal_eqs_sort_w_plan_order"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
+                                           "hbm_gbs_algorithmic": gn_bytes * RP_M / (ms / 1e3) / 1e9,
+                                           "bytes_per_obs": gn_bytes}
     del U, V, W, gws
     # the SORT plan (stable radix sort of the observations by camera): built
     # once per observation structure and reused by every SORT call

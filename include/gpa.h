@@ -328,10 +328,14 @@ GPA_API int reproj_vjp(const float* cams, const float* pts, const int32_t* obs, 
  *   V [P][6]   += sum over the point's observations of J_p^T J_p (3 x 3, same packing)
  *   W [M][w_ld] = J_c^T J_p of each observation in columns 0..32 (11 x 3
  *                 row-major; nullable); columns 33..w_ld-1 are set to 0.
- *                 33 <= w_ld <= 64. With w_ld a multiple of 8 and W 32-byte
- *                 aligned every row is written as whole 32-byte sectors, which
- *                 matters under SORT, where rows land in camera order: a
- *                 partly written sector costs a read-modify-write in DRAM.
+ *                 33 <= w_ld <= 64. w_order 0: row j holds observation j;
+ *                 w_order 1 (SORT only): row i holds the observation at
+ *                 position i of the plan's camera-sorted order (plan perm[i]),
+ *                 so that rows are written in order. With w_ld a multiple of 8
+ *                 and W 32-byte aligned every row is written as whole 32-byte
+ *                 sectors, which matters under SORT with w_order 0, where rows
+ *                 land in camera order: a partly written sector costs a
+ *                 read-modify-write in DRAM.
  *   g_cams [C][11] += J_c^T r,  g_pts [P][3] += J_p^T r,  res [M][2] = r (nullable)
  * The camera and point blocks are Accum reductions like the VJP's, with a
  * 66 + 11 and a 6 + 3 float payload. strat: SORT (camera-sorted runs from
@@ -344,7 +348,7 @@ GPA_API int reproj_vjp(const float* cams, const float* pts, const int32_t* obs, 
 GPA_API size_t gpa_reproj_gn_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs);
 GPA_API int reproj_normal_eqs(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
                               int32_t n_cams, int32_t n_pts, int64_t n_obs, float* U, float* V, float* W,
-                              int32_t w_ld, float* g_cams, float* g_pts, float* res, int32_t strat,
+                              int32_t w_ld, int32_t w_order, float* g_cams, float* g_pts, float* res, int32_t strat,
                               const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
                               gpa_stream_t stream);
 

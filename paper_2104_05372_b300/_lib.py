@@ -56,7 +56,7 @@ _SIGS = {
     "reproj_jvp": ([_P, _P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
     "reproj_residual_sorted": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _P, _SZ, _P, _P], _I32),
     "gpa_reproj_gn_workspace_bytes": ([_I32, _I32, _I64], _SZ),
-    "reproj_normal_eqs": ([_P] * 4 + [_I32, _I32, _I64] + [_P] * 3 + [_I32] + [_P] * 3 + [_I32, _P, _P, _SZ, _P, _P],
+    "reproj_normal_eqs": ([_P] * 4 + [_I32, _I32, _I64] + [_P] * 3 + [_I32, _I32] + [_P] * 3 + [_I32, _P, _P, _SZ, _P, _P],
                           _I32),
     "reproj_vjp_noalloc": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _P], _I32),
     "gpa_plan_bytes": ([_I64, _I32], _SZ),
@@ -443,12 +443,17 @@ def reproj_jvp(cams, pts, obs, v_cams, v_pts, jv=None, ws=None, status=None, str
 
 
 def reproj_normal_eqs(cams, pts, obs, tgt, U=None, V=None, W=None, g_cams=None, g_pts=None, res=None,
-                      want_w=False, want_res=False, strat="auto", plan=None, ws=None, status=None, stream=None):
+                      want_w=False, want_res=False, strat="auto", plan=None, w_order="input", ws=None, status=None,
+                      stream=None):
     """Gauss-Newton blocks (U, V, W, g_cams, g_pts, res): U, V, g_cams, g_pts
     accumulate (+=, zeros if not given); W and res are written when given (or
     asked for with want_w / want_res), else None. W is [M][w_ld] with
     33 <= w_ld <= 64: J_c^T J_p in columns 0..32, zeros after (allocated with
-    w_ld = 40, whole 32-byte sectors per row; take W[:, :33] for the blocks)."""
+    w_ld = 40, whole 32-byte sectors per row; take W[:, :33] for the blocks).
+    w_order "input": row j is observation j; "plan" (with a plan): row i is
+    the observation at position i of the plan's camera-sorted order."""
+    if w_order not in ("input", "plan"):
+        raise ValueError(f"w_order must be 'input' or 'plan', got {w_order!r}")
     nc, npt, no = _reproj_params(cams, pts, obs)
     _check(tgt, torch.float32, "tgt", (no, 2))
     dv = cams.device
@@ -471,7 +476,8 @@ def reproj_normal_eqs(cams, pts, obs, tgt, U=None, V=None, W=None, g_cams=None, 
     ws = workspace(int(load().gpa_reproj_gn_workspace_bytes(nc, npt, no)), dv) if ws is None else ws
     st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
     rc = load().reproj_normal_eqs(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, _ptr(U), _ptr(V),
-                                  _ptr(W), w_ld, _ptr(g_cams), _ptr(g_pts), _ptr(res), st, _ptr(plan), _ptr(ws),
+                                  _ptr(W), w_ld, 1 if w_order == "plan" else 0, _ptr(g_cams), _ptr(g_pts),
+                                  _ptr(res), st, _ptr(plan), _ptr(ws),
                                   ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "reproj_normal_eqs")
     return U, V, W, g_cams, g_pts, res

@@ -632,8 +632,11 @@ __global__ void __launch_bounds__(128) reproj_gn_kernel(
     const float* __restrict__ rec, const float* __restrict__ pts, const int2* __restrict__ obs,
     const float2* __restrict__ tgt, int n_cams, int n_pts, int64_t n_obs, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ key_s, const int32_t* __restrict__ aux_s, float* __restrict__ U,
-    float* __restrict__ W, int w_ld, float* __restrict__ g_cams, float4* __restrict__ pacc,
+    float* __restrict__ W, int w_ld, int w_plan, float* __restrict__ g_cams, float4* __restrict__ pacc,
     float2* __restrict__ res, int32_t* __restrict__ status, int pts8) {
+    // w_plan (SORTED only): W row of the observation at plan position pos is
+    // row pos, so a warp fills one contiguous range of rows over its kGnOpt
+    // iterations; otherwise row e (input order)
     const int lane = threadIdx.x & 31;
     __shared__ float wstage[4 * 32 * 33];  // per warp: 32 rows of W, one per lane
     const int64_t chunk = (int64_t)blockDim.x * kGnOpt;
@@ -737,11 +740,13 @@ __global__ void __launch_bounds__(128) reproj_gn_kernel(
                 // w_ld a multiple of 8 on a 32-byte aligned W every row is whole
                 // 32-byte sectors, so rows landing in random order (camera-sorted
                 // runs) never leave a sector partly written
-                const int mode = valid ? 1 : (e_ok ? 2 : 0);
+                const bool by_pos = SORTED && w_plan;
+                const int mode = valid ? 1 : ((by_pos ? active : e_ok) ? 2 : 0);
+                const int wrow = by_pos ? (int)(pos0 + i) : e;
                 __syncwarp();
                 for (int rr = 0; rr < 32; ++rr) {
                     const int mr = __shfl_sync(0xffffffffu, mode, rr);
-                    const int er = __shfl_sync(0xffffffffu, e, rr);
+                    const int er = __shfl_sync(0xffffffffu, wrow, rr);
                     if (mr) {  // streaming stores: W passes through L2 once and should not evict
                                // the sectors of tgt and res that neighbouring observations reuse
                         float* Wr = W + (size_t)er * w_ld;
@@ -1038,11 +1043,12 @@ extern "C" size_t gpa_reproj_gn_workspace_bytes(int32_t n_cams, int32_t n_pts, i
 
 extern "C" int reproj_normal_eqs(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
                                  int32_t n_cams, int32_t n_pts, int64_t n_obs, float* U, float* V, float* W,
-                                 int32_t w_ld, float* g_cams, float* g_pts, float* res, int32_t strat,
-                                 const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
+                                 int32_t w_ld, int32_t w_order, float* g_cams, float* g_pts, float* res,
+                                 int32_t strat, const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
                                  gpa_stream_t stream) {
     if (!cams || !pts || !obs || !tgt || !U || !V || !g_cams || !g_pts || !ws) return GPA_ERR_ARG;
     if (W && (w_ld < 33 || w_ld > 64)) return GPA_ERR_ARG;
+    if (w_order != 0 && w_order != 1) return GPA_ERR_ARG;
     if (n_cams < 1 || n_pts < 1 || n_obs < 1 || n_obs > INT32_MAX) return GPA_ERR_ARG;
     if (!al(obs, 8) || !al(tgt, 8) || (res && !al(res, 8)) || !al(ws, 256)) return GPA_ERR_ALIGN;
     if (!al(cams, 4) || !al(pts, 4) || !al(U, 4) || !al(V, 4) || (W && !al(W, 4)) || !al(g_cams, 4) ||
@@ -1051,6 +1057,7 @@ extern "C" int reproj_normal_eqs(const float* cams, const float* pts, const int3
     if (ws_bytes < gpa_reproj_gn_workspace_bytes(n_cams, n_pts, n_obs)) return GPA_ERR_WORKSPACE;
     strat = resolve_strat(strat, plan);
     if (strat != GPA_SCATTER_ATOMIC && strat != GPA_SCATTER_SORT) return GPA_ERR_UNSUPPORTED;
+    if (w_order == 1 && strat != GPA_SCATTER_SORT) return GPA_ERR_ARG;  // plan order needs the plan
     PlanView pv{};
     if (strat == GPA_SCATTER_SORT) {
         if (!plan) return GPA_ERR_ARG;
@@ -1069,13 +1076,13 @@ extern "C" int reproj_normal_eqs(const float* cams, const float* pts, const int3
         GPA_LAUNCH("reproj_normal_eqs", s,
                    reproj_gn_kernel<true><<<grid, 128, 0, s>>>(rec, pts, (const int2*)obs, (const float2*)tgt,
                                                                n_cams, n_pts, n_obs, pv.perm, pv.key_sorted,
-                                                               pv.aux_sorted, U, W, w_ld, g_cams, pacc,
+                                                               pv.aux_sorted, U, W, w_ld, w_order, g_cams, pacc,
                                                                (float2*)res, dev_status, p8));
     else
         GPA_LAUNCH("reproj_normal_eqs", s,
                    reproj_gn_kernel<false><<<grid, 128, 0, s>>>(rec, pts, (const int2*)obs, (const float2*)tgt,
                                                                 n_cams, n_pts, n_obs, nullptr, nullptr, nullptr, U,
-                                                                W, w_ld, g_cams, pacc, (float2*)res, dev_status,
+                                                                W, w_ld, 0, g_cams, pacc, (float2*)res, dev_status,
                                                                 p8));
     const int64_t pw = (n_pts + 255) / 256, pc = (int64_t)sm_count() * 8;
     GPA_LAUNCH("reproj_gn_points", s,

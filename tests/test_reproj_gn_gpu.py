@@ -89,6 +89,29 @@ def test_w_leading_dimension(w_ld):
                                   strat="sort", plan=plan)
 
 
+def test_w_in_plan_order():
+    """w_order "plan": row i of W is the block of the observation at position i
+    of the camera-sorted plan, bit for bit the input-order row perm[i]; an
+    invalid observation (sorted last) gets a NaN row; plan order without a plan
+    is rejected."""
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300._lib import plan_arrays
+    r = synth.reproj_inputs(40, 500, 7001, seed=9)
+    r.obs[11] = (40, 3)  # camera out of range
+    cams, pts, obs, tgt = dev(r.cams), dev(r.pts), dev(r.obs), dev(r.tgt)
+    plan = gpa.gpa_obs_plan_build(obs, r.n_cams, r.n_pts)
+    Wi = gpa.reproj_normal_eqs(cams, pts, obs, tgt, want_w=True, strat="sort", plan=plan)[2]
+    Wp = gpa.reproj_normal_eqs(cams, pts, obs, tgt, want_w=True, strat="sort", plan=plan, w_order="plan")[2]
+    torch.cuda.synchronize()
+    _, perm, _, _, _ = (host(t) for t in plan_arrays(plan, r.n_obs, r.n_cams))
+    Wi, Wp = host(Wi), host(Wp)
+    n_valid = r.n_obs - 1
+    assert np.array_equal(Wp[:n_valid], Wi[perm[:n_valid]])
+    assert np.all(np.isnan(Wp[n_valid:, :33])) and np.all(np.isnan(Wi[11, :33]))
+    with pytest.raises(RuntimeError):
+        gpa.reproj_normal_eqs(cams, pts, obs, tgt, want_w=True, strat="atomic", w_order="plan")
+
+
 def test_blocks_accumulate_and_invalid_observations_are_marked():
     import paper_2104_05372_b300 as gpa
     r = synth.reproj_inputs(20, 100, 3000, seed=5)
