@@ -69,19 +69,25 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 }
 
 // ---- forward ------------------------------------------------------------------
-constexpr int FQ = 2;  // Q stages (hi and lo parts each)
 template <int TDP>
 struct FwdSm {
     using T = Tc<TDP>;
+    // Q stages (hi and lo parts and the b_k tails each). A stage is refilled
+    // only after the epilogue has read its tails, so the ring must cover the
+    // epilogue's lag plus a TMA round trip: four stages where shared memory
+    // allows (TDP = 64), two at TDP = 128.
+    static constexpr int FQ = TDP == 64 ? 4 : 2;
     static constexpr uint32_t X = 0;                            // x_hi, x_lo tiles
     static constexpr uint32_t Q = X + 2 * T::TILE;              // [FQ] x (Q_hi, Q_lo)
     static constexpr uint32_t B = Q + FQ * 2 * T::TILE;         // [FQ][CPR] tails
     static constexpr uint32_t RED = B + FQ * T::CPR * T::TAIL;
     static constexpr uint32_t BAR = RED + 8 * 8;  // x_full, q_full[FQ], q_empty[FQ], acc_full[2], acc_empty[2]
+    static_assert(1 + 2 * FQ + 4 <= 16, "barrier slots");
     static constexpr uint32_t TMEMP = BAR + 16 * 8;
     static constexpr uint32_t FLAG = TMEMP + 8;
     static constexpr uint32_t END = FLAG + 8;
     static constexpr size_t SMEM = END + 1024;  // + alignment slack
+    static_assert(SMEM <= 227 * 1024, "forward shared memory");
 };
 
 template <int TDP>
@@ -93,6 +99,7 @@ __global__ void __launch_bounds__(192, 1)
                       int32_t* __restrict__ status) {
     using T = Tc<TDP>;
     using S = FwdSm<TDP>;
+    constexpr int FQ = S::FQ;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::BAR);
