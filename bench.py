@@ -44,8 +44,14 @@ FLOPS_PER_PAIR_BWD = GMM_D * GMM_D + 3 * GMM_D
 # camera and point parameters read once 1.6, gradient read-modify-write 3.2
 BYTES_PER_OBS_VJP = 20.8
 BYTES_PER_OBS_FUSED = 25.6 + 3.2
-# FP32 CUDA-core peak: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# FP32 CUDA-core peak = SMs x 128 FP32 lanes x 2 flop x SM clock; the SM count
+# is read from the device, the clock is the median sampled during the timed
+# region (the maximum SM clock when no sample is available)
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
 def parse():
@@ -201,8 +207,10 @@ def run_ours(args):
         import paper_2104_05372_b300 as gpa
         from paper_2104_05372_b300 import _lib
         dev = torch.device("cuda", 0)
-        print(json.dumps(run_gmm_tc(args, gpa, _lib, dev, torch.cuda.current_stream(dev), 0, d=args.tc_d,
-                                    k=args.tc_k, fp32_steps=args.tc_fp32_steps)))
+        pf = run_gmm_tc(args, gpa, _lib, dev, torch.cuda.current_stream(dev), 0, d=args.tc_d, k=args.tc_k,
+                        fp32_steps=args.tc_fp32_steps)
+        pf.pop("_oracle_sample")
+        print(json.dumps(pf))
         return
     rank, world, local = dist_info()
     if world > 1:
@@ -273,10 +281,18 @@ def run_ours(args):
     fl = {"gmm_fwd": FLOPS_PER_PAIR_FWD, "gmm_bwd": FLOPS_PER_PAIR_BWD}.get(dom_name, 0)
     achieved = fl * pairs / (per_launch_ms / 1e3) / 1e12
     traffic, traffic_note = traffic_record(dom_name)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or measured_peaks()[0].get("sm_max_mhz", 2032.0)
+    run_mhz = clocks.get("sm_mhz") or max_mhz
+    peak = fp32_peak_tflops(sms, run_mhz)
+    peak_max = fp32_peak_tflops(sms, max_mhz)
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": round(achieved, 3),
-                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "frac_at_max_clock": round(achieved / peak_max, 4),
                 "traffic": traffic, "traffic_note": traffic_note,
-                "peak_note": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 flop x 2032 MHz (max SM clock)",
+                "peak_note": f"FP32 CUDA-core peak = {sms} SMs (read from the device) x {FP32_LANES_PER_SM} lanes x "
+                             f"2 flop x {run_mhz:.0f} MHz (median SM clock sampled during the timed region; "
+                             f"maximum {max_mhz:.0f} MHz gives {peak_max:.2f} TFLOP/s)",
                 "kernel_ms_per_launch": round(per_launch_ms, 4),
                 "kernels": {k: {"launches": c, "ms_per_launch": round(v / c, 4),
                                 "share": round(v / sum(vv for _, vv in trace.values()), 4)}
@@ -308,6 +324,10 @@ def run_ours(args):
         result["scatter"] = run_scatter(args, gpa, _lib, dev, stream, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline()
+        for pf in result.get("precision_form", []):
+            pf["errors_vs_oracle_sampled"] = precision_form_oracle_check(*pf.pop("_oracle_sample"))
+    for pf in result.get("precision_form", []):
+        pf.pop("_oracle_sample", None)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -570,6 +590,26 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256, fp32_steps=1):
 
     ms_tc, tr = timed(1, args.steps, args.warmup)
     ms_fp32 = float("nan") if fp32_steps == 0 else timed(0, fp32_steps, 1)[0]
+
+    # outputs of both precisions (outside the timed region): every output of
+    # the tensor-core form against the FP32 CUDA-core path at full size
+    def outputs(prec):
+        lse = torch.empty(n, device=dev)
+        f = gpa.gmm_objective(x, a, mu, q, l, g.gamma, g.m, prec, lse_out=lse)
+        gr = gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m, prec)
+        torch.cuda.synchronize(dev)
+        return float(f.item()), lse.cpu().numpy().astype(np.float64), [t_.cpu().numpy().astype(np.float64)
+                                                                        for t_ in gr]
+    f_tc, lse_tc, g_tc = outputs(1)
+    f_32, lse_32, g_32 = outputs(0)
+
+    def rel(u, v):
+        return float(np.linalg.norm(u - v) / max(np.linalg.norm(v), 1e-300))
+    vs_fp32 = {"objective": abs(f_tc - f_32) / abs(f_32),
+               "lse_max": float(np.max(np.abs(lse_tc - lse_32) / np.maximum(np.abs(lse_32), 1.0)))}
+    for name_, u, v in zip(("alpha", "mu", "q", "l"), g_tc, g_32):
+        vs_fp32["grad_" + name_] = rel(u, v)
+    sample = np.random.default_rng(7).choice(n, 4096, replace=False)
     pairs = n * k
     kern = {kk: {"launches": c, "ms_per_launch": round(v / c, 4)} for kk, (c, v) in tr.items()}
     fwd = tr.get("gmm_tc_fwd", (1, float("nan")))
@@ -596,6 +636,11 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256, fp32_steps=1):
                      "executed_frac": round(dense / peaks["bf16_tflops"], 4), "peak_source": src,
                      "note": "achieved counts D^2 + 3D flops per (point, component); executed counts every "
                              "MMA (128x128 tiles of the padded dimension, 3 passes in the forward)"},
+        "errors_vs_fp32_path": dict(vs_fp32, note="every output at full size against the FP32 CUDA-core path on "
+                                                  "the same inputs (normwise per gradient block; lse per point "
+                                                  "relative to max(|lse|, 1)); the FP32 path's own error against "
+                                                  "the FP64 oracle is within 1e-5 / 1e-4"),
+        "_oracle_sample": (g, sample, lse_tc[sample], lse_32[sample]),
     }
 
 
@@ -704,6 +749,20 @@ def cpu_baseline(target_s: float = 15.0):
             break
     return {"value": n * GMM_K / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"FP64 oracle objective+gradient on {n} of the 2^20 points (D=64, K=200), {dt:.2f} s"}
+
+
+def precision_form_oracle_check(g, idx, lse_tc, lse_fp32):
+    """The tensor-core form's per-point statistics at sampled points against
+    the FP64 oracle (each point's lse computed by the oracle one by one; run on
+    the host after the GPU measurements, outside every timed region)."""
+    import oracle
+    t0 = time.perf_counter()
+    _, lse_ref = oracle.gmm_logjoint_at(g, idx)
+    den = np.maximum(np.abs(lse_ref), 1.0)
+    return {"points": int(len(idx)), "lse_max_tc": float(np.max(np.abs(lse_tc - lse_ref) / den)),
+            "lse_max_fp32": float(np.max(np.abs(lse_fp32 - lse_ref) / den)),
+            "lse_max_plain_relative_tc": float(np.max(np.abs(lse_tc - lse_ref) / np.abs(lse_ref))),
+            "oracle_s": round(time.perf_counter() - t0, 2)}
 
 
 def run_reference(args):

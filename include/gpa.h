@@ -380,12 +380,16 @@ GPA_API int reproj_residual_vjp(const float* cams, const float* pts, const int32
  * memory owned by the library (GPA_NOALLOC_MAX_CAMS cameras, 2 MiB on every
  * GPU that loads the library, held until the process exits); the call itself
  * allocates nothing. More cameras than that return GPA_ERR_WORKSPACE and
- * enqueue nothing. The first call on a device looks up the array's device
- * address for that device (with it current); make that first call before any
- * stream capture. Every call shares the array and it keeps the last call's
- * contents (each call rewrites the records it reads): calls that overlap on the
- * GPU, on any streams, race. Arguments, strategies and Accum (+=) semantics
- * are those of reproj_vjp.
+ * enqueue nothing. Each call looks up the array's address in the calling
+ * thread's current device context (a host-side lookup), so the array is found
+ * again after cudaDeviceReset or in another context; the first call in a
+ * context loads the library's device code there, so make that first call
+ * before any stream capture. Every call shares the array and it keeps the last
+ * call's contents (each call rewrites the records it reads before reading
+ * them): calls that overlap on the GPU, on any streams, race. The points are
+ * gathered in place and d_pts is updated with one atomic per coordinate (no
+ * padded rows). Arguments, strategies and Accum (+=) semantics are those of
+ * reproj_vjp.
  */
 #define GPA_NOALLOC_MAX_CAMS 16384
 GPA_API int reproj_vjp_noalloc(const float* cams, const float* pts, const int32_t* obs, const float* w,
@@ -436,6 +440,24 @@ GPA_API int gpa_index_plan_build(const int32_t* idx, int64_t m, int32_t n_keys, 
 GPA_API int accum_scatter_add(const int32_t* idx, const void* vals, int64_t m, int32_t w, int32_t dtype,
                       void* acc, int32_t n_buckets, int32_t strat, const void* plan,
                       int32_t* dev_status, gpa_stream_t stream);
+
+/* ========================================================================= */
+/* Diagnostics                                                               */
+/* ========================================================================= */
+/*
+ * Check that this device's bounded waits give up as the error convention
+ * above states: launches one CTA whose 64 threads wait, with the library's
+ * per-thread wait and with its warp-uniform wait, on a shared-memory mbarrier
+ * that expects one arrival that never comes. Each wait gives up after limit_ns
+ * nanoseconds of the device's global timer (1 <= limit_ns <= 1e9; the
+ * library's own waits use 1e9), ORs GPA_ERR_TIMEOUT into *dev_status and adds 1
+ * to *gave_up (device int32, zeroed by the caller; 64 after the launch
+ * completes). No copy engine, tensor memory or other kernel is involved, and
+ * the device stays usable afterwards. The paper has no counterpart; it makes
+ * the library's failure path testable without a fault.
+ */
+GPA_API int gpa_check_bounded_wait(int64_t limit_ns, int32_t* dev_status, int32_t* gave_up,
+                                   gpa_stream_t stream);
 
 /* ========================================================================= */
 /* Tracing                                                                   */

@@ -67,6 +67,7 @@ _SIGS = {
     "gpa_gmm_batched_workspace_bytes": ([_P, _I32, _I64], _SZ),
     "gmm_batched_prepare": ([_P, _I32, _I64, _P, _SZ, _P], _I32),
     "gmm_batched_vjp": ([_P, _I32, _I64, _I32, _P, _SZ, _P, _P], _I32),
+    "gpa_check_bounded_wait": ([_I64, _P, _P, _P], _I32),
     "gpa_trace_enable": ([_I32], None),
     "gpa_trace_summary": ([C.c_char_p, _SZ], _I32),
 }
@@ -481,6 +482,16 @@ def reproj_normal_eqs(cams, pts, obs, tgt, U=None, V=None, W=None, g_cams=None, 
                                   ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "reproj_normal_eqs")
     return U, V, W, g_cams, g_pts, res
+
+
+def gpa_check_bounded_wait(limit_ns, status, gave_up, stream=None):
+    """Launch the device-wait check: 64 threads wait on an mbarrier nobody
+    arrives at and give up after limit_ns (status |= GPA_ERR_TIMEOUT, gave_up
+    += 1 per thread). status and gave_up: zeroed int32 device tensors."""
+    _check(status, torch.int32, "status", (1,))
+    _check(gave_up, torch.int32, "gave_up", (1,))
+    rc = load().gpa_check_bounded_wait(int(limit_ns), _ptr(status), _ptr(gave_up), _stream(stream))
+    _ok(rc, "gpa_check_bounded_wait")
 
 
 def reproj_vjp_noalloc(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=None, status=None,

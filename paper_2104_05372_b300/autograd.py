@@ -41,6 +41,10 @@ class GMMObjective(torch.autograd.Function):
         x, alpha, mu, q, l = ctx.saved_tensors
         n, d = x.shape
         k = alpha.shape[0]
+        # The C ABI takes the cotangent seed as a host scalar (every kernel gets
+        # it as a launch argument), so it is read here: one device-to-host copy
+        # of one float64 per backward pass. It waits for the stream up to the
+        # objective, which the gradient kernels depend on anyway.
         seed = float(grad_out.item())
         lp = 0
         if ctx.lj is None:  # chunk size that keeps the log-joint within the budget

@@ -1,5 +1,7 @@
-// Library-wide entry points of the C ABI: status names and version.
+// Library-wide entry points of the C ABI: status names, version, and the
+// check of the device's bounded waits.
 #include "common.cuh"
+#include "trace.cuh"
 
 extern "C" const char* gpa_status_string(int status) {
     switch (status) {
@@ -16,3 +18,32 @@ extern "C" const char* gpa_status_string(int status) {
 }
 
 extern "C" int gpa_version(void) { return 100; }
+
+namespace gpa {
+// One CTA of two warps waits on an mbarrier that expects one arrival which never
+// comes: warp 0 with the per-thread wait, warp 1 with the warp-uniform wait
+// used before .sync.aligned instructions. Both give up after limit_ns and
+// report GPA_ERR_TIMEOUT; nothing else happens (no copies, no tensor memory).
+__global__ void __launch_bounds__(64) wait_timeout_kernel(unsigned long long limit_ns, int32_t* status,
+                                                          int32_t* gave_up) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = threadIdx.x < 32 ? mbar_wait(&bar, 0, status, limit_ns)
+                                     : mbar_wait_warp(&bar, 0, status, limit_ns);
+    if (!ok) atomicAdd(gave_up, 1);
+}
+}  // namespace gpa
+
+extern "C" int gpa_check_bounded_wait(int64_t limit_ns, int32_t* dev_status, int32_t* gave_up,
+                                      gpa_stream_t stream) {
+    if (!dev_status || !gave_up) return GPA_ERR_ARG;
+    if (limit_ns < 1 || limit_ns > (int64_t)gpa::kWaitLimitNs) return GPA_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    GPA_LAUNCH("wait_timeout_check", s,
+               gpa::wait_timeout_kernel<<<1, 64, 0, s>>>((unsigned long long)limit_ns, dev_status, gave_up));
+    return GPA_OK;
+}

@@ -59,14 +59,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase with the given parity to complete. Gives up after
-// kWaitLimitNs, reports GPA_ERR_TIMEOUT and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* status) {
+// limit_ns (kWaitLimitNs unless a caller asks for less), reports
+// GPA_ERR_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* status,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        if (globaltimer_ns() - t0 > limit_ns) {
             report(status, GPA_ERR_TIMEOUT);
             return false;
         }
@@ -74,15 +76,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_
 }
 
 // Warp-uniform variant: every lane polls, the warp leaves together (all lanes
-// see the phase complete, or all give up after kWaitLimitNs by lane 0's clock).
+// see the phase complete, or all give up after limit_ns by lane 0's clock).
 // Use it wherever the warp runs .sync.aligned instructions or __syncwarp next.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int32_t* status) {
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int32_t* status,
+                                               unsigned long long limit_ns = kWaitLimitNs) {
     if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;  // already complete: no clock read
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
         for (int i = 0; i < 64; ++i)
             if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
-        int late = (globaltimer_ns() - t0 > kWaitLimitNs) ? 1 : 0;
+        int late = (globaltimer_ns() - t0 > limit_ns) ? 1 : 0;
         late = __shfl_sync(0xffffffffu, late, 0);
         if (late) {
             if ((threadIdx.x & 31) == 0) report(status, GPA_ERR_TIMEOUT);

@@ -12,7 +12,8 @@
 // a single BF16 pass leaves log-joint errors of ~0.4 at D = 128, i.e. ~40 %
 // errors in the responsibilities exp(s - lse). Warp roles in a 192-thread CTA:
 // warp 0 issues TMA loads (the point tile once, then each round's Q rows and
-// the b_k / constants through a 2-stage ring), warp 1 owns the TMEM allocation
+// the b_k / constants through a ring of FQ stages: four at TDP = 64, two at
+// TDP = 128, where shared memory holds no more), warp 1 owns the TMEM allocation
 // and one of its lanes issues the MMAs (M=128 points, N=128 rows of CPR
 // components, K=TDP in steps of 16, 3 passes each) into a double-buffered
 // accumulator, warps 2-5 read the accumulator back (TMEM lane = point, one
@@ -23,7 +24,7 @@
 //   C_k = sum_i r_ik (x_i - mu_k)(x_i - mu_k)^T,  m'_k = sum_i r_ik (x_i - mu_k),
 //   R_k = sum_i r_ik,
 // with C_k = U_k^T U_k for U_k[p][a] = sqrt(r_pk) (x_p - mu_k)[a] (x read in
-// FP32, U rounded once to BF16; r from the forward's log-joint). Eight
+// FP32, U rounded once to BF16; r from the forward's log-joint). Sixteen
 // producer warps build the 128-row blocks [U_k^T; ...] (CPR components stacked,
 // points contiguous) directly in the 128-byte-swizzled layout the MMA reads; one
 // MMA thread accumulates D += U^T U (A and B the same tile) in TMEM for four

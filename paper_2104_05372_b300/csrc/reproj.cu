@@ -1095,38 +1095,26 @@ extern "C" int reproj_normal_eqs(const float* cams, const float* pts, const int3
 // in a fixed array in device memory that the library owns, for callers that
 // cannot hand the library a workspace.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace gpa {
 // Largest camera count the built-in scratch holds (32 floats per camera,
 // 2 MiB per GPU that loads the library, kept until the process exits).
-constexpr int kNoAllocMaxCams = 16384;
+constexpr int kNoAllocMaxCams = GPA_NOALLOC_MAX_CAMS;
+static_assert(kNoAllocMaxCams * kCamRec * sizeof(float) == (2u << 20), "scratch size stated in gpa.h");
 static __device__ __align__(256) float g_cam_scratch[kNoAllocMaxCams * kCamRec];
 
-constexpr int kNoAllocMaxDevices = 256;
-static float* g_cam_scratch_addr[kNoAllocMaxDevices];  // device address, per device
-static std::mutex g_cam_scratch_mu;
-
-// Device address of g_cam_scratch on the current device. In host code the
-// array's name only stands in for the symbol, so its address is looked up once
-// per device, with that device current.
+// Device address of g_cam_scratch in the current device's context. In host
+// code the array's name only stands in for the symbol, so its address has to be
+// looked up, with the device current. The lookup is repeated on every call (a
+// host-side table lookup once the module is loaded): an address cached per
+// device ordinal would go stale after cudaDeviceReset or in another context of
+// the same device, where the module is loaded again at another address.
 static int cam_scratch_address(float** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_cam_scratch) != cudaSuccess || p == nullptr) {
         (void)cudaGetLastError();
         return GPA_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return GPA_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_cam_scratch_mu);
-    if (!g_cam_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_cam_scratch) != cudaSuccess || p == nullptr) {
-            (void)cudaGetLastError();
-            return GPA_ERR_CUDA;
-        }
-        g_cam_scratch_addr[dev] = static_cast<float*>(p);
-    }
-    *out = g_cam_scratch_addr[dev];
+    *out = static_cast<float*>(p);
     return GPA_OK;
 }
 }  // namespace gpa
@@ -1150,25 +1138,10 @@ extern "C" int reproj_vjp_noalloc(const float* cams, const float* pts, const int
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     // every record the VJP reads is rewritten here first: nothing needs clearing
-    cam_expand_kernel<<<(n_cams + kCamPerBlock - 1) / kCamPerBlock, kCamPerBlock, 0, s>>>(cams, n_cams, rec);
-    GPA_LAUNCH_CHECK();
-    const unsigned grid = obs_grid(n_obs);
-    const int p8 = al(pts, 8) ? 1 : 0, dp8 = al(d_pts, 8) ? 1 : 0;  // no padded accumulators: direct atomics
-    switch (strat) {
-        case GPA_SCATTER_ATOMIC:
-            reproj_vjp_kernel<GPA_SCATTER_ATOMIC, false><<<grid, 256, 0, s>>>(
-                rec, pts, nullptr, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, d_cams, d_pts,
-                nullptr, nullptr, dev_status, p8, dp8);
-            break;
-        case GPA_SCATTER_WARPAGG:
-            reproj_vjp_kernel<GPA_SCATTER_WARPAGG, false><<<grid, 256, 0, s>>>(
-                rec, pts, nullptr, (const int2*)obs, (const float2*)w, nullptr, 1.f, n_cams, n_pts, n_obs, d_cams, d_pts,
-                nullptr, nullptr, dev_status, p8, dp8);
-            break;
-        default:
-            return launch_vjp_sorted<false>(rec, pts, nullptr, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
-                                            nullptr, nullptr, dev_status, s);
-    }
-    GPA_LAUNCH_CHECK();
-    return GPA_OK;
+    rc = expand_cams(cams, n_cams, rec, s);
+    if (rc) return rc;
+    // no 16-byte point rows and no padded accumulators (they would need scratch
+    // per point): the kernels gather the points directly and add into d_pts
+    return dispatch_vjp<false>(strat, rec, pts, nullptr, obs, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
+                               nullptr, nullptr, dev_status, s);
 }

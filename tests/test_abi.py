@@ -85,3 +85,11 @@ def test_host_argument_errors_return_before_any_launch(lib):
     assert lib.accum_scatter_add(fake, fake, 10, 1, 2, fake, 4, 1, None, None, None) == 1
     # plans: workspace too small
     assert lib.gpa_index_plan_build(fake, 100, 10, fake, 16, fake, 1 << 20, None, None) == 4
+
+
+def test_bounded_wait_check_rejects_bad_arguments(lib):
+    fake = C.c_void_p(256)
+    assert lib.gpa_check_bounded_wait(0, fake, fake, None) == 1
+    assert lib.gpa_check_bounded_wait(1_000_000_001, fake, fake, None) == 1
+    assert lib.gpa_check_bounded_wait(1000, None, fake, None) == 1
+    assert lib.gpa_check_bounded_wait(1000, fake, None, None) == 1

@@ -181,63 +181,20 @@ def test_full_size_sampled_statistics_and_accum_invariance():
 @pytest.mark.slow
 def test_full_size_gradient_matches_finite_differences_on_64_coordinates():
     """N=2^20, D=64, K=200: 64 random gradient coordinates (16 per parameter
-    block) against central differences of the FP64 oracle objective. A
-    coordinate of component k moves only column k of the log-joint, so each
-    difference recomputes that column with the oracle and updates the per-point
-    logsumexp exactly: lse' - lse = log1p(p_ik expm1(s'_ik - s_ik)) with
-    p_ik = exp(s_ik - lse_i); -N logsumexp(alpha) and the prior's terms
-    change in closed form. The steps are taken in float32 (the parameters'
-    type) and the difference quotient divides by the steps actually taken."""
-    import dataclasses
-    from scipy.special import logsumexp
+    block) against central differences of the FP64 oracle objective, each
+    difference recomputing only the moved component's column of the log-joint
+    (fd_util)."""
     import paper_2104_05372_b300 as gpa
+    from fd_util import fd_coordinates
     g = synth.gmm_inputs(1 << 20, 64, 200, seed=0)
     x, a, mu, q, l = gmm_dev(g)
     grads = [host(t).astype(np.float64) for t in gpa.gmm_vjp(x, a, mu, q, l, g.gamma, g.m)]
     _, lse = oracle.gmm_objective(g, want_lse=True)
-    every = np.arange(g.n, dtype=np.int64)
-    n, gam2 = float(g.n), g.gamma ** 2
-
-    def column(k, al, m_, q_, l_):
-        g1 = dataclasses.replace(g, alpha=np.array([al], np.float32), mu=m_[None].copy(), q=q_[None].copy(),
-                                 l=l_[None].copy())
-        return oracle.gmm_logjoint_at(g1, every)[0][:, 0]
-
-    rng = np.random.default_rng(64)
-    t = g.d * (g.d - 1) // 2
-    worst = 0.0
-    for block, h in (("alpha", 2.0 ** -10), ("mu", 2.0 ** -10), ("q", 2.0 ** -10), ("l", 2.0 ** -12)):
-        gb = grads[["alpha", "mu", "q", "l"].index(block)]
-        rms = float(np.sqrt(np.mean(gb ** 2)))
-        for _ in range(16):
-            k = int(rng.integers(g.k))
-            j = int(rng.integers({"alpha": 1, "mu": g.d, "q": g.d, "l": t}[block]))
-            base = {"alpha": g.alpha[k:k + 1].copy(), "mu": g.mu[k].copy(), "q": g.q[k].copy(), "l": g.l[k].copy()}
-            s0 = column(k, base["alpha"][0], base["mu"], base["q"], base["l"])
-            p = np.exp(s0 - lse)
-            d = {}
-            for sign in (1, -1):
-                pv = {b: v.copy() for b, v in base.items()}
-                pv[block][j] = np.float32(np.float64(base[block][j]) + sign * h)
-                s1 = column(k, pv["alpha"][0], pv["mu"], pv["q"], pv["l"])
-                dll = float(np.sum(np.log1p(p * np.expm1(s1 - s0))))
-                if block == "alpha":
-                    al1 = g.alpha.astype(np.float64).copy()
-                    al1[k] = pv["alpha"][0]
-                    dll -= n * (logsumexp(al1) - logsumexp(g.alpha.astype(np.float64)))
-                elif block == "q":
-                    q0, q1 = np.float64(base["q"][j]), np.float64(pv["q"][j])
-                    dll += g.m * (q1 - q0) - 0.5 * gam2 * (np.exp(2 * q1) - np.exp(2 * q0))
-                elif block == "l":
-                    l0, l1 = np.float64(base["l"][j]), np.float64(pv["l"][j])
-                    dll -= 0.5 * gam2 * (l1 * l1 - l0 * l0)
-                d[sign] = (dll, np.float64(pv[block][j]))
-            fd = (d[1][0] - d[-1][0]) / (d[1][1] - d[-1][1])
-            got = gb[k] if block == "alpha" else gb[k, j]
-            err = abs(got - fd) / max(abs(fd), rms)
-            worst = max(worst, err)
-            assert err <= TOL_GRAD_FP32, (block, k, j, got, fd)
+    rows = fd_coordinates(g, lse, grads, per_block=16, seed=64)
+    worst = max(r[5] for r in rows)
     print(f"\nfull size: 64 gradient coordinates vs central differences, worst relative error {worst:.2e}")
+    for block, k, j, got, fd, err in rows:
+        assert err <= TOL_GRAD_FP32, (block, k, j, got, fd)
 
 
 def test_host_errors_enqueue_nothing():
