@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
         if (it >= n_items) break;
         const BItem w = items[it];
         const BInst& B = inst[w.inst];
-        gmm_bwd_kernel_body<DP, (DP <= 64 ? 2 : 1)>(B.x, B.n, B.d, B.k, B.lj, B.n, B.lse, (float)B.seed,
+        gmm_bwd_kernel_body<DP, Bwd<DP>::UNROLL_BATCHED>(B.x, B.n, B.d, B.k, B.lj, B.n, B.lse, (float)B.seed,
                                                      B.tiles_per_chunk, B.bS, B.bM,
                                 (unsigned)w.a, (unsigned)w.b);
         __syncthreads();

@@ -36,26 +36,86 @@ __host__ __device__ __forceinline__ int bwd_swz(int c) {
     return (a << 3) + ((h ^ ((a >> 2) & 1)) << 2) + (c & 3);
 }
 
-// Backward layout. Every thread owns one full 8x8 block (a, b), a >= b, of one
-// component's S and runs the same instruction stream: diagonal blocks are
-// accumulated in full (their upper halves are dropped at the write-out), and
-// the m and R sums are spread over the threads as MP extra packed FMAs per
-// point each (see bwd_mtask). GC components per CTA.
+// Backward layouts. Every thread owns one full 8x8 block (a, b), a >= b, of one
+// component's S (or, on the diagonal of the block-per-warp layout, two
+// diagonal blocks); the m and R sums are spread over the threads as MP extra
+// packed FMAs per point and block (see bwd_mtask). GC components per CTA.
+//   D <= 32 (WB false): consecutive threads take consecutive blocks of a
+//     component and run one instruction stream (diagonal blocks accumulated in
+//     full, their upper halves dropped at the write-out).
+//   D > 32 (WB true, blocks per warp): lane l of a warp takes component l % GC
+//     of the CTA on slot l / GC of the warp's BPW = 32 / GC slots, so that the
+//     lanes reading one chunk of a point row form a contiguous group and each
+//     16-byte shared load serves BPW distinct addresses (one wavefront, given
+//     distinct bank groups: see bwd_pos). The first NDW warps hold the diagonal
+//     blocks, two per lane ((q, q) and (NB-1-q, NB-1-q)), and skip their upper
+//     halves; the other NOW warps hold one off-diagonal block per lane. The 16
+//     warps (4 per scheduler) carry equal work except the diagonal warps'
+//     one-third extra, spread over different schedulers.
 template <int DP>
 struct Bwd {
     static constexpr int NB = DP / 8;
     static constexpr int NBLK = NB * (NB + 1) / 2;     // lower blocks incl. diagonal
-    static constexpr int GC = DP == 16 ? 42 : DP == 32 ? 25 : DP == 64 ? 7 : 3;  // components per CTA
-    static constexpr int TPB = DP == 64 ? 128 : DP == 16 ? 32 : 64;  // points per tile
-    static constexpr int MP = NB == 2 ? 3 : NB == 4 ? 2 : 1;  // m / R pairs per thread
-    static constexpr int NACT = GC * NBLK;               // threads with a block
-    static constexpr int THREADS = ((NACT + 31) / 32) * 32;
-    static constexpr int MINB = DP == 16 ? 3 : DP == 128 ? 1 : 2;  // resident CTAs per SM
+    static constexpr bool WB = DP >= 64;
+    static constexpr int GC = DP == 16 ? 42 : DP == 32 ? 25 : DP == 64 ? 16 : 4;  // components per CTA
+    static constexpr int BPW = WB ? 32 / GC : 0;                 // slots per warp (lanes per slot = GC)
+    static constexpr int NDW = WB ? (NB / 2) * GC / 32 : 0;      // warps on pairs of diagonal blocks
+    static constexpr int NOW = WB ? (NBLK - NB) * GC / 32 : 0;   // warps on off-diagonal blocks
+    static_assert(!WB || ((NB / 2) * GC % 32 == 0 && (NBLK - NB) * GC % 32 == 0), "whole warps of blocks");
+    static constexpr int TPB = DP == 16 ? 32 : DP == 32 ? 64 : 128;  // points per tile
+    static constexpr int MP = NB == 2 ? 3 : NB == 4 ? 2 : 1;  // m / R pairs per thread and block
+    static constexpr int NACT = GC * NBLK;               // threads with a block (sequential layout)
+    static constexpr int THREADS = WB ? 32 * (NDW + NOW) : ((NACT + 31) / 32) * 32;
+    static constexpr int MINB = DP == 16 ? 3 : DP == 32 ? 2 : 1;  // resident CTAs per SM
     static constexpr int XST = DP + 4;  // row stride of the point tiles; floats DP, DP+1 hold 1.0
+    // point-loop unroll of the per-call kernel and of the persistent batched
+    // kernel, as far as the register budget of MINB resident CTAs allows
+    static constexpr int UNROLL = DP == 128 ? 2 : 4;
+    static constexpr int UNROLL_BATCHED = DP == 128 ? 1 : 2;
     // point tiles double-buffered; raw log-joint, lse and the cotangents r
     // triple-buffered
     static constexpr size_t SMEM = sizeof(float) * (size_t)(2 * TPB * XST + 3 * GC * TPB + 3 * TPB + 3 * TPB * GC);
 };
+
+// Float offset of coordinate c in a point row of the block-per-warp tile: the
+// 16-byte half h of chunk a (coordinates 8a + 4h .. 8a + 4h + 3) sits in
+// 16-byte slot h * NB + a, i.e. in bank group a mod 8 for both halves. A warp
+// reads half h of its blocks' chunks in one instruction; chunks that differ
+// mod 8 never share a bank.
+template <int NB>
+__host__ __device__ __forceinline__ int bwd_pos(int c) {
+    return (((((c >> 2) & 1) * NB) + (c >> 3)) << 2) + (c & 3);
+}
+
+// Off-diagonal blocks of the 16 x 16 block triangle (D = 128) in warp order,
+// (a << 4) | b: eight per warp, chosen (by a search over groupings) so that the
+// distinct row chunks a of a warp differ mod 8, and so do its column chunks b.
+__device__ __constant__ const unsigned char kOffBlocks16[120] = {
+    0x32, 0x80, 0xa3, 0xa5, 0xa9, 0xe9, 0xf7, 0xfe,  0x81, 0x90, 0xb1, 0xb3, 0xc7, 0xd1, 0xd7, 0xfa,
+    0x76, 0x82, 0x95, 0xb7, 0xc8, 0xc9, 0xd8, 0xeb,  0x20, 0x43, 0x51, 0xe3, 0xea, 0xed, 0xf1, 0xf3,
+    0x61, 0x65, 0x73, 0x86, 0x98, 0xb8, 0xba, 0xda,  0x70, 0x72, 0x85, 0xb2, 0xb4, 0xc6, 0xcb, 0xd2,
+    0x31, 0x52, 0xe5, 0xf2, 0xf5, 0xf8, 0xfb, 0xfc,  0x10, 0x40, 0x53, 0xa0, 0xb6, 0xe0, 0xf0, 0xf9,
+    0x97, 0xa2, 0xb0, 0xc1, 0xd0, 0xd4, 0xd5, 0xdb,  0x21, 0x50, 0x60, 0x63, 0x93, 0xb5, 0xca, 0xf4,
+    0x42, 0x74, 0x75, 0x96, 0xa7, 0xe2, 0xe6, 0xe8,  0x62, 0x64, 0xa6, 0xc2, 0xc4, 0xc5, 0xd3, 0xd9,
+    0x41, 0x83, 0x84, 0x94, 0xa4, 0xe1, 0xe4, 0xfd,  0x54, 0x87, 0x92, 0xa8, 0xb9, 0xc3, 0xe7, 0xf6,
+    0x30, 0x71, 0x91, 0xa1, 0xc0, 0xd6, 0xdc, 0xec};
+
+// Off-diagonal block o (0 <= o < NB(NB-1)/2) of the block-per-warp layout.
+template <int NB>
+__device__ __forceinline__ void bwd_off_block(int o, int& a, int& b) {
+    if constexpr (NB == 16) {
+        const int v = kOffBlocks16[o];
+        a = v >> 4;
+        b = v & 15;
+    } else {  // NB <= 8: every chunk index differs mod 8 anyway
+        a = 1;
+        b = o;
+        while (b >= a) {
+            b -= a;
+            ++a;
+        }
+    }
+}
 
 // The m / R task of slot s of the thread on block (a, b): the natural
 // coordinate index 2j of the pair (m_2j, m_2j+1) it accumulates, DP for R
@@ -514,7 +574,7 @@ static __global__ void __launch_bounds__(256) gmm_objective_finalize_kernel(
 // for padded dimensions up to 64, the persistent batched kernel 2): the next
 // points' shared loads overlap the FMAs.
 template <int DP, int UNROLL = 1>
-__device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x, int64_t n, int d, int k,
+__device__ __forceinline__ void gmm_bwd_seq_body(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
                    float* __restrict__ partM, unsigned bx, unsigned by) {
@@ -709,13 +769,337 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
     }
 }
 
+// Block-per-warp backward (D > 32): the same Accum sums as gmm_bwd_seq_body
+// with every S entry, m pair and R receiving the same float32 operations in
+// the same point order. Per point, a thread loads its row chunk (two 16-byte
+// loads; two more for its second chunk), its component's r and the operands
+// of its m / R tasks, then issues 4 packed multiplies and 32 packed FMAs per
+// off-diagonal block, or 2 x (4 + 20) on its two diagonal blocks (upper
+// halves skipped).
+template <bool DIAG>
+__device__ __forceinline__ void bwd_block_update(float2 r2, float4 a0, float4 a1, float4 b0, float4 b1,
+                                                 float2 (&accd)[4][4], float2 (&accx)[4][4]) {
+    float2 y[4];
+    y[0] = __fmul2_rn(r2, make_float2(a0.x, a0.y));
+    y[1] = __fmul2_rn(r2, make_float2(a0.z, a0.w));
+    y[2] = __fmul2_rn(r2, make_float2(a1.x, a1.y));
+    y[3] = __fmul2_rn(r2, make_float2(a1.z, a1.w));
+    const float4 bq[2] = {b0, b1};
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {  // columns 4g .. 4g+3
+        const float4 bv = bq[g];
+        const float2 nb[2] = {make_float2(bv.x, bv.y), make_float2(bv.z, bv.w)};
+        const float2 sb[2] = {make_float2(bv.y, bv.x), make_float2(bv.w, bv.z)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (DIAG && 2 * g + j > i) continue;  // pair column above the row pair
+                accd[i][2 * g + j] = __ffma2_rn(y[i], nb[j], accd[i][2 * g + j]);
+                accx[i][2 * g + j] = __ffma2_rn(y[i], sb[j], accx[i][2 * g + j]);
+            }
+    }
+}
+
+// Lower triangle (diagonal included) of the diagonal block of chunk v with
+// row-scaled values y = r v (4 pairs) and v itself (a0, a1): the 10 pairs
+// (S[2i][2j], S[2i+1][2j+1]), j <= i, through D(i, j), the 6 pairs
+// (S[2i][2j+1], S[2i+1][2j]), j < i, through X(i, j), and the 4 entries
+// S[2i+1][2i] as scalars h[i].
+template <typename FD, typename FX>
+__device__ __forceinline__ void bwd_tri_update(const float2 (&y)[4], float4 a0, float4 a1, FD&& D, FX&& X,
+                                               float (&h)[4]) {
+    const float v[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            D(i, j) = __ffma2_rn(y[i], make_float2(v[2 * j], v[2 * j + 1]), D(i, j));
+            if (j < i) X(i, j) = __ffma2_rn(y[i], make_float2(v[2 * j + 1], v[2 * j]), X(i, j));
+        }
+        h[i] = fmaf(y[i].y, v[2 * i], h[i]);
+    }
+}
+
+// One pass over a point tile. Off the diagonal (DIAG false): block (a, b)
+// (pa*, pb* locate chunks a and b) into accd / accx, the m / R task through
+// moff. On the diagonal: the lower triangles of blocks (a, a) and (b, b) in one
+// set of 32 pairs -- block a in accd[i][j] (j <= i) and accx[i][j] (j < i),
+// block b transposed into the other slots, accx[j][i] (j <= i) and accd[j][i]
+// (j < i) -- plus the 8 scalars h; each block's m task is its chunk's first
+// pair, i.e. the sum of y[0] (macc[0], macc[1]).
+template <int DP, bool DIAG, int UNROLL>
+__device__ __forceinline__ void bwd_wb_tile(const float* __restrict__ Xb, const float* __restrict__ rb, int pa0,
+                                            int pb0, int moff, float2 (&accd)[4][4], float2 (&accx)[4][4],
+                                            float (&h)[8], float2 (&macc)[2]) {
+    using C = Bwd<DP>;
+    constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, H1 = 4 * C::NB;  // second half of a chunk
+#pragma unroll UNROLL
+    for (int p = 0; p < TPB; ++p) {
+        const float* row = Xb + p * XST;
+        const float rr = rb[p * GC];
+        const float2 r2 = make_float2(rr, rr);
+        const float4 a0 = *reinterpret_cast<const float4*>(row + pa0);
+        const float4 a1 = *reinterpret_cast<const float4*>(row + pa0 + H1);
+        float2 y[4];
+        y[0] = __fmul2_rn(r2, make_float2(a0.x, a0.y));
+        y[1] = __fmul2_rn(r2, make_float2(a0.z, a0.w));
+        y[2] = __fmul2_rn(r2, make_float2(a1.x, a1.y));
+        y[3] = __fmul2_rn(r2, make_float2(a1.z, a1.w));
+        if constexpr (DIAG) {
+            float ha[4] = {h[0], h[1], h[2], h[3]};
+            bwd_tri_update(y, a0, a1, [&](int i, int j) -> float2& { return accd[i][j]; },
+                           [&](int i, int j) -> float2& { return accx[i][j]; }, ha);
+            macc[0] = __fadd2_rn(macc[0], y[0]);
+            const float4 b0 = *reinterpret_cast<const float4*>(row + pb0);
+            const float4 b1 = *reinterpret_cast<const float4*>(row + pb0 + H1);
+            float2 z[4];
+            z[0] = __fmul2_rn(r2, make_float2(b0.x, b0.y));
+            z[1] = __fmul2_rn(r2, make_float2(b0.z, b0.w));
+            z[2] = __fmul2_rn(r2, make_float2(b1.x, b1.y));
+            z[3] = __fmul2_rn(r2, make_float2(b1.z, b1.w));
+            float hb[4] = {h[4], h[5], h[6], h[7]};
+            bwd_tri_update(z, b0, b1, [&](int i, int j) -> float2& { return accx[j][i]; },
+                           [&](int i, int j) -> float2& { return accd[j][i]; }, hb);
+            macc[1] = __fadd2_rn(macc[1], z[0]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                h[i] = ha[i];
+                h[4 + i] = hb[i];
+            }
+        } else {
+            macc[0] = __ffma2_rn(r2, *reinterpret_cast<const float2*>(row + moff), macc[0]);
+            const float4 b0 = *reinterpret_cast<const float4*>(row + pb0);
+            const float4 b1 = *reinterpret_cast<const float4*>(row + pb0 + H1);
+            bwd_block_update<false>(r2, a0, a1, b0, b1, accd, accx);
+        }
+    }
+}
+
+// S block (a, b) of one component from its packed accumulators into the
+// chunk's partial sums (+=); diagonal blocks keep their lower half.
+__device__ __forceinline__ void bwd_store_block(float* __restrict__ S, bool diag, const float2 (&accd)[4][4],
+                                                const float2 (&accx)[4][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 dv = accd[i][j], xv = accx[i][j];
+            // D: (2i, 2j), (2i+1, 2j+1); X: (2i, 2j+1), (2i+1, 2j)
+            if (!diag || j <= i) {
+                S[(2 * i) * 8 + 2 * j] += dv.x;
+                S[(2 * i + 1) * 8 + 2 * j + 1] += dv.y;
+                S[(2 * i + 1) * 8 + 2 * j] += xv.y;
+            }
+            if (!diag || j < i) S[(2 * i) * 8 + 2 * j + 1] += xv.x;
+        }
+}
+
+template <int DP, int UNROLL = 1>
+__device__ __forceinline__ void gmm_bwd_wb_body(const float* __restrict__ x, int64_t n, int d, int k,
+                   const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
+                   float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
+                   float* __restrict__ partM, unsigned bx, unsigned by) {
+    using C = Bwd<DP>;
+    constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, NB = C::NB, NBLK = C::NBLK, MP = C::MP;
+    constexpr int NT = C::THREADS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* Xs = reinterpret_cast<float*>(smem_raw);  // [2][TPB][XST]
+    float* rawlj = Xs + 2 * TPB * XST;                // [3][GC][TPB]
+    float* rawlse = rawlj + 3 * GC * TPB;             // [3][TPB]
+    float* rs = rawlse + 3 * TPB;                     // [3][TPB][GC]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kg0 = bx * GC;
+    const int64_t ntiles = (n + TPB - 1) / TPB;
+    const int64_t t_begin = (int64_t)by * tiles_per_chunk;
+    const int64_t t_end = min64(ntiles, t_begin + tiles_per_chunk);
+
+    // role of this thread: component kk of the CTA; diagonal blocks (a, a) and
+    // (b, b) with b = NB - 1 - a, or off-diagonal block (a, b)
+    const int kk = lane % GC, slot = lane / GC;
+    const bool diag = warp < C::NDW;
+    int a, b;
+    if (diag) {
+        a = warp * C::BPW + slot;
+        b = NB - 1 - a;
+    } else {
+        bwd_off_block<NB>((warp - C::NDW) * C::BPW + slot, a, b);
+    }
+    const bool active = kg0 + kk < k;
+    const int pa0 = bwd_pos<NB>(8 * a), pb0 = bwd_pos<NB>(8 * b);
+    // m / R task of an off-diagonal thread (one per block at D > 32); a
+    // diagonal block's task is its chunk's first pair (bwd_mtask), which the
+    // diagonal threads sum from their scaled row values instead of a load
+    static_assert(MP == 1, "one m / R task per block");
+    const int mt = diag ? -1 : bwd_mtask<NB>(a, b, 0);
+    const int moff = mt < 0 || mt == DP ? DP : bwd_pos<NB>(mt);
+
+    // Pipeline, one block barrier per tile. At the top of tile t: the points
+    // of t in X[t % 2] and their r in R[t % 3]; the points of t+1 and the
+    // log-joint of t+2 in flight. 16-byte copies when the rows allow them.
+    const bool v4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+    auto issue_x = [&](int64_t t, int buf) {
+        const int64_t p0 = t * TPB;
+        const int nv = (int)min64(TPB, n - p0);
+        float* X = Xs + buf * TPB * XST;
+        if (v4) {
+            const int q4 = d >> 2;
+            for (int e = tid; e < nv * q4; e += NT) {
+                const int p = e / q4, c = 4 * (e - p * q4);
+                cp_async16(X + p * XST + bwd_pos<NB>(c), x + (p0 + p) * d + c);
+            }
+        } else {
+            for (int e = tid; e < nv * d; e += NT) {
+                const int p = e / d, c = e - p * d;
+                cp_async4(X + p * XST + bwd_pos<NB>(c), x + (p0 + p) * d + c);
+            }
+        }
+    };
+    auto issue_lj = [&](int64_t t, int buf) {
+        const int64_t p0 = t * TPB;
+        const int nv = (int)min64(TPB, n - p0);
+        float* L = rawlj + buf * GC * TPB;
+        for (int e = tid; e < GC * TPB; e += NT) {
+            const int kc = e / TPB, p = e % TPB;
+            if (p < nv && kg0 + kc < k) cp_async4(L + e, lj + (int64_t)(kg0 + kc) * lj_ld + p0 + p);
+        }
+        float* S = rawlse + buf * TPB;
+        for (int p = tid; p < nv; p += NT) cp_async4(S + p, lse + p0 + p);
+    };
+    // cotangents r = seed exp(s - lse) of tile t from buffer buf; 0 on the ragged tail
+    auto make_r = [&](int64_t t, int buf) {
+        const int64_t p0 = t * TPB;
+        const int nv = (int)min64(TPB, n - p0);
+        const float* L = rawlj + buf * GC * TPB;
+        const float* S = rawlse + buf * TPB;
+        float* R = rs + buf * TPB * GC;
+        for (int e = tid; e < GC * TPB; e += NT) {
+            const int kc = e / TPB, p = e % TPB;
+            float r = 0.f;
+            if (p < nv && kg0 + kc < k) r = seed * expf(L[e] - S[p]);
+            R[p * GC + kc] = r;
+        }
+    };
+
+    // zero tiles (padding coordinates and ragged rows stay finite), 1.0 at DP, DP+1
+    for (int e = tid; e < 2 * TPB * XST; e += NT) {
+        const int col = e % XST;
+        Xs[e] = (col == DP || col == DP + 1) ? 1.f : 0.f;
+    }
+    __syncthreads();
+
+    float2 accd[4][4], accx[4][4], macc[2];
+    float h[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) accd[i][j] = accx[i][j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = 0.f;
+    macc[0] = macc[1] = make_float2(0.f, 0.f);
+
+    // prologue
+    if (t_begin < t_end) {
+        issue_x(t_begin, 0);
+        issue_lj(t_begin, 0);
+        if (t_begin + 1 < t_end) issue_lj(t_begin + 1, 1);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (t_begin < t_end) make_r(t_begin, 0);
+    if (t_begin + 1 < t_end) {
+        make_r(t_begin + 1, 1);
+        issue_x(t_begin + 1, 1);
+        if (t_begin + 2 < t_end) issue_lj(t_begin + 2, 2);
+    }
+    cp_async_commit();
+    __syncthreads();
+
+    int b2 = 0, b3 = 0;  // (t - t_begin) mod 2, mod 3
+    for (int64_t t = t_begin; t < t_end; ++t) {
+        const float* Xb = Xs + b2 * TPB * XST;
+        const float* rb = rs + b3 * TPB * GC + kk;
+        if (diag)  // warp-uniform
+            bwd_wb_tile<DP, true, UNROLL>(Xb, rb, pa0, pb0, moff, accd, accx, h, macc);
+        else
+            bwd_wb_tile<DP, false, UNROLL>(Xb, rb, pa0, pb0, moff, accd, accx, h, macc);
+        const int n2 = b2 ^ 1, n3a = b3 == 2 ? 0 : b3 + 1, n3b = n3a == 2 ? 0 : n3a + 1;
+        cp_async_wait_all();  // this thread's copies of x(t+1) and lj(t+2) have landed
+        __syncthreads();      // x(t+1), lj(t+2) complete; nobody reads X[b2], R[b3] any more
+        if (t + 2 < t_end) {
+            make_r(t + 2, n3b);
+            issue_x(t + 2, b2);
+            if (t + 3 < t_end) issue_lj(t + 3, b3);
+        }
+        cp_async_commit();
+        b2 = n2;
+        b3 = n3a;
+    }
+    if (!active) return;
+    const int kg = kg0 + kk;
+    const int64_t base = ((int64_t)by * k + kg);
+    float* Sk = partS + base * NBLK * 64;
+    float* M = partM + base * (DP + 1);
+    if (diag) {
+        // block (a, a): accd[i][j] (j <= i), accx[i][j] (j < i), h[0..3];
+        // block (b, b): accx[j][i] (j <= i), accd[j][i] (j < i), h[4..7]
+        float* Sa = Sk + (int64_t)(a * (a + 1) / 2 + a) * 64;
+        float* Sb = Sk + (int64_t)(b * (b + 1) / 2 + b) * 64;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                const float2 da = accd[i][j], db = accx[j][i];
+                Sa[(2 * i) * 8 + 2 * j] += da.x;
+                Sa[(2 * i + 1) * 8 + 2 * j + 1] += da.y;
+                Sb[(2 * i) * 8 + 2 * j] += db.x;
+                Sb[(2 * i + 1) * 8 + 2 * j + 1] += db.y;
+                if (j < i) {
+                    const float2 xa = accx[i][j], xb = accd[j][i];
+                    Sa[(2 * i) * 8 + 2 * j + 1] += xa.x;
+                    Sa[(2 * i + 1) * 8 + 2 * j] += xa.y;
+                    Sb[(2 * i) * 8 + 2 * j + 1] += xb.x;
+                    Sb[(2 * i + 1) * 8 + 2 * j] += xb.y;
+                }
+            }
+            Sa[(2 * i + 1) * 8 + 2 * i] += h[i];
+            Sb[(2 * i + 1) * 8 + 2 * i] += h[4 + i];
+        }
+        const int ma = bwd_mtask<NB>(a, a, 0), mb = bwd_mtask<NB>(b, b, 0);  // 8a, 8b
+        M[ma] += macc[0].x;
+        M[ma + 1] += macc[0].y;
+        M[mb] += macc[1].x;
+        M[mb + 1] += macc[1].y;
+    } else {
+        bwd_store_block(Sk + (int64_t)(a * (a + 1) / 2 + b) * 64, false, accd, accx);
+        if (mt == DP) {
+            M[DP] += macc[0].x;
+        } else if (mt >= 0) {
+            M[mt] += macc[0].x;
+            M[mt + 1] += macc[0].y;
+        }
+    }
+}
+
+template <int DP, int UNROLL = 1>
+__device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x, int64_t n, int d, int k,
+                   const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
+                   float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
+                   float* __restrict__ partM, unsigned bx, unsigned by) {
+    if constexpr (Bwd<DP>::WB)
+        gmm_bwd_wb_body<DP, UNROLL>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM, bx, by);
+    else
+        gmm_bwd_seq_body<DP, UNROLL>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM, bx, by);
+}
+
 template <int DP>
 __global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
     gmm_bwd_kernel(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
                    float* __restrict__ partM) {
-    gmm_bwd_kernel_body<DP, DP <= 64 ? 4 : 1>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM,
+    gmm_bwd_kernel_body<DP, Bwd<DP>::UNROLL>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM,
                                                 blockIdx.x, blockIdx.y);
 }
 
