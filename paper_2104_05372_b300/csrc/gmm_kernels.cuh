@@ -62,6 +62,11 @@ struct Bwd {
     static constexpr int NDW = WB ? (NB / 2) * GC / 32 : 0;      // warps on pairs of diagonal blocks
     static constexpr int NOW = WB ? (NBLK - NB) * GC / 32 : 0;   // warps on off-diagonal blocks
     static_assert(!WB || ((NB / 2) * GC % 32 == 0 && (NBLK - NB) * GC % 32 == 0), "whole warps of blocks");
+    // m / R tasks per thread on the off-diagonal warps of the schedulers
+    // without a diagonal warp (3 NB + 1 tasks over their threads)
+    static constexpr int NLIGHT = WB ? ((NDW + NOW) / 4) * (4 - NDW) * BPW : 1;
+    static constexpr int MTL = WB ? (3 * NB + 1 + NLIGHT - 1) / NLIGHT : 0;
+    static_assert(!WB || (MTL <= 2 && NDW < 4 && (NDW + NOW) % 4 == 0), "task split");
     static constexpr int TPB = DP == 16 ? 32 : DP == 32 ? 64 : 128;  // points per tile
     static constexpr int MP = NB == 2 ? 3 : NB == 4 ? 2 : 1;  // m / R pairs per thread and block
     static constexpr int NACT = GC * NBLK;               // threads with a block (sequential layout)
@@ -822,16 +827,16 @@ __device__ __forceinline__ void bwd_tri_update(const float2 (&y)[4], float4 a0, 
 }
 
 // One pass over a point tile. Off the diagonal (DIAG false): block (a, b)
-// (pa*, pb* locate chunks a and b) into accd / accx, the m / R task through
-// moff. On the diagonal: the lower triangles of blocks (a, a) and (b, b) in one
+// (pa*, pb* locate chunks a and b) into accd / accx, and MT m / R tasks, the
+// pairs at moff[t] into macc[t]. On the diagonal: the lower triangles of blocks (a, a) and (b, b) in one
 // set of 32 pairs -- block a in accd[i][j] (j <= i) and accx[i][j] (j < i),
 // block b transposed into the other slots, accx[j][i] (j <= i) and accd[j][i]
 // (j < i) -- plus the 8 scalars h; each block's m task is its chunk's first
 // pair, i.e. the sum of y[0] (macc[0], macc[1]).
-template <int DP, bool DIAG, int UNROLL>
+template <int DP, bool DIAG, int MT, int UNROLL>
 __device__ __forceinline__ void bwd_wb_tile(const float* __restrict__ Xb, const float* __restrict__ rb, int pa0,
-                                            int pb0, int moff, float2 (&accd)[4][4], float2 (&accx)[4][4],
-                                            float (&h)[8], float2 (&macc)[2]) {
+                                            int pb0, const int (&moff)[2], float2 (&accd)[4][4],
+                                            float2 (&accx)[4][4], float (&h)[8], float2 (&macc)[2]) {
     using C = Bwd<DP>;
     constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, H1 = 4 * C::NB;  // second half of a chunk
 #pragma unroll UNROLL
@@ -868,7 +873,9 @@ __device__ __forceinline__ void bwd_wb_tile(const float* __restrict__ Xb, const 
                 h[4 + i] = hb[i];
             }
         } else {
-            macc[0] = __ffma2_rn(r2, *reinterpret_cast<const float2*>(row + moff), macc[0]);
+#pragma unroll
+            for (int t = 0; t < MT; ++t)
+                macc[t] = __ffma2_rn(r2, *reinterpret_cast<const float2*>(row + moff[t]), macc[t]);
             const float4 b0 = *reinterpret_cast<const float4*>(row + pb0);
             const float4 b1 = *reinterpret_cast<const float4*>(row + pb0 + H1);
             bwd_block_update<false>(r2, a0, a1, b0, b1, accd, accx);
@@ -927,12 +934,21 @@ __device__ __forceinline__ void gmm_bwd_wb_body(const float* __restrict__ x, int
     }
     const bool active = kg0 + kk < k;
     const int pa0 = bwd_pos<NB>(8 * a), pb0 = bwd_pos<NB>(8 * b);
-    // m / R task of an off-diagonal thread (one per block at D > 32); a
-    // diagonal block's task is its chunk's first pair (bwd_mtask), which the
-    // diagonal threads sum from their scaled row values instead of a load
-    static_assert(MP == 1, "one m / R task per block");
-    const int mt = diag ? -1 : bwd_mtask<NB>(a, b, 0);
-    const int moff = mt < 0 || mt == DP ? DP : bwd_pos<NB>(mt);
+    // m / R tasks. The diagonal threads sum the first pair (8c, 8c+1) of
+    // their chunks c from their scaled row values (no load). The other 3 NB
+    // pairs (8c + 2s, s = 1..3) and R (the constant 1.0 pair at DP) go to the
+    // off-diagonal threads of warps on the schedulers without a diagonal warp
+    // (warp w on scheduler w % 4), C::MTL tasks per thread, so that each
+    // scheduler carries about the same packed FMAs per point.
+    const bool light = !diag && (warp & 3) >= C::NDW;
+    const int mtask0 = light ? ((warp >> 2) * (4 - C::NDW) + (warp & 3) - C::NDW) * C::BPW + slot : -1;
+    int mco[2], moff[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int q = mtask0 < 0 || t >= C::MTL ? -1 : mtask0 * C::MTL + t;  // task id
+        mco[t] = q < 0 || q > 3 * NB ? -1 : q == 3 * NB ? DP : 8 * (q / 3) + 2 * (q % 3 + 1);
+        moff[t] = mco[t] < 0 || mco[t] == DP ? DP : bwd_pos<NB>(mco[t]);
+    }
 
     // Pipeline, one block barrier per tile. At the top of tile t: the points
     // of t in X[t % 2] and their r in R[t % 3]; the points of t+1 and the
@@ -1021,9 +1037,11 @@ __device__ __forceinline__ void gmm_bwd_wb_body(const float* __restrict__ x, int
         const float* Xb = Xs + b2 * TPB * XST;
         const float* rb = rs + b3 * TPB * GC + kk;
         if (diag)  // warp-uniform
-            bwd_wb_tile<DP, true, UNROLL>(Xb, rb, pa0, pb0, moff, accd, accx, h, macc);
+            bwd_wb_tile<DP, true, 0, UNROLL>(Xb, rb, pa0, pb0, moff, accd, accx, h, macc);
+        else if (light)
+            bwd_wb_tile<DP, false, C::MTL, UNROLL>(Xb, rb, pa0, pb0, moff, accd, accx, h, macc);
         else
-            bwd_wb_tile<DP, false, UNROLL>(Xb, rb, pa0, pb0, moff, accd, accx, h, macc);
+            bwd_wb_tile<DP, false, 0, UNROLL>(Xb, rb, pa0, pb0, moff, accd, accx, h, macc);
         const int n2 = b2 ^ 1, n3a = b3 == 2 ? 0 : b3 + 1, n3b = n3a == 2 ? 0 : n3a + 1;
         cp_async_wait_all();  // this thread's copies of x(t+1) and lj(t+2) have landed
         __syncthreads();      // x(t+1), lj(t+2) complete; nobody reads X[b2], R[b3] any more
@@ -1073,11 +1091,14 @@ __device__ __forceinline__ void gmm_bwd_wb_body(const float* __restrict__ x, int
         M[mb + 1] += macc[1].y;
     } else {
         bwd_store_block(Sk + (int64_t)(a * (a + 1) / 2 + b) * 64, false, accd, accx);
-        if (mt == DP) {
-            M[DP] += macc[0].x;
-        } else if (mt >= 0) {
-            M[mt] += macc[0].x;
-            M[mt + 1] += macc[0].y;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (mco[t] == DP) {
+                M[DP] += macc[t].x;
+            } else if (mco[t] >= 0) {
+                M[mco[t]] += macc[t].x;
+                M[mco[t] + 1] += macc[t].y;
+            }
         }
     }
 }
