@@ -908,7 +908,7 @@ __device__ __forceinline__ void gmm_bwd_wb_body(const float* __restrict__ x, int
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
                    float* __restrict__ partM, unsigned bx, unsigned by) {
     using C = Bwd<DP>;
-    constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, NB = C::NB, NBLK = C::NBLK, MP = C::MP;
+    constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, NB = C::NB, NBLK = C::NBLK;
     constexpr int NT = C::THREADS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* Xs = reinterpret_cast<float*>(smem_raw);  // [2][TPB][XST]
@@ -958,7 +958,13 @@ __device__ __forceinline__ void gmm_bwd_wb_body(const float* __restrict__ x, int
         const int64_t p0 = t * TPB;
         const int nv = (int)min64(TPB, n - p0);
         float* X = Xs + buf * TPB * XST;
-        if (v4) {
+        if (v4 && d == DP) {  // full rows: constant divisor
+            constexpr int Q4 = DP / 4;
+            for (int e = tid; e < nv * Q4; e += NT) {
+                const int p = e / Q4, c = 4 * (e - p * Q4);
+                cp_async16(X + p * XST + bwd_pos<NB>(c), x + (p0 + p) * DP + c);
+            }
+        } else if (v4) {
             const int q4 = d >> 2;
             for (int e = tid; e < nv * q4; e += NT) {
                 const int p = e / q4, c = 4 * (e - p * q4);
