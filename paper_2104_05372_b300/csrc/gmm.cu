@@ -457,5 +457,5 @@ extern "C" int gmm_vjp_finalize(const float* alpha, const float* mu, const float
     A.alpha = alpha; A.mu = mu; A.q = q; A.l = l; A.n = n_total; A.d = d; A.k = k; A.gamma = gamma; A.m = m;
     A.seed = seed; A.out = out; A.d_alpha = d_alpha; A.d_mu = d_mu; A.d_q = d_q; A.d_l = d_l;
     A.status = dev_status; A.exch_in = exch;
-    return finalize_from_exchange(A, L, (char*)ws, prec == GPA_PREC_BF16_TC ? 1 : 0, (cudaStream_t)stream);
+    return finalize_from_exchange(A, L, (char*)ws, 0, (cudaStream_t)stream);  // raw moments from either path
 }

@@ -280,81 +280,133 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 // ---- backward -----------------------------------------------------------------
-constexpr int BSLOT = 4;                        // 128-row blocks per CTA (4 x 128 TMEM columns)
-constexpr int BPROD = 512;                      // producer threads (16 warps, a quarter of the points each)
-constexpr int BTHREADS = BPROD + 32;            // + the MMA warp
+// The Accum sums of the reverse pass as one contraction over the points. With
+// r_ik = seed exp(s_ik - lse_i) and, per point, the vector of products
+//   y_i = [x_ia x_ib (a >= b), x_ia (a < d), 1]      (d(d+1)/2 + d + 1 entries),
+// the sums S_k = sum_i r_ik x_i x_i^T (lower triangle), m_k = sum_i r_ik x_i and
+// R_k = sum_i r_ik are the rows of  Y^T R  (Y: points x products, R: points x
+// components), so a single BF16 MMA stream with FP32 accumulation computes all
+// of them, each product exactly once (the triangle is not mirrored). Y is
+// shared by every component and built on the CUDA cores per point tile; R is
+// written once per call in BF16 (gmm_tc_r_kernel) and read by TMA.
+//
+// CTA: 256 product rows (two 128-row MMA blocks) x up to 256 components x a
+// chunk of the points. Warps 0-15 build the Y tiles (64 points, K-major,
+// 128-byte swizzle) and at the end copy the accumulators from tensor memory
+// into the per-chunk partial sums; warp 16 loads the R tiles (TMA); one lane of
+// warp 17 issues the MMAs (M = 128 products, N = components, K = 16 points).
+constexpr int GTM = 64;                         // points per tile (4 MMA K steps)
+constexpr int GMB = 2;                          // 128-row MMA blocks per CTA
+constexpr int GPROD = 512;                      // producer threads
+constexpr int GTHREADS = GPROD + 64;            // + TMA warp + MMA warp
+constexpr int GKMAX = 256;                      // components per CTA (MMA N)
+constexpr int GRB_POINTS = 1 << 18;             // points of R held at a time
+constexpr uint32_t GYB = GMB * 128 * 128;       // one Y tile: 256 rows x 64 points bf16
+
+// Transposed point tile: row c (a coordinate; row d = ones, d + 1 = zeros)
+// holds the tile's 64 points, the 16-byte group g of 4 points at position
+// g ^ (c & 7), so that a warp reading one group of 32 different rows, or
+// writing 8 rows x 4 points, spreads over all banks.
+__host__ __device__ __forceinline__ int gram_xpos(int c, int p) { return c * GTM + ((((p >> 2) ^ c) & 15) << 2) + (p & 3); }
+
 template <int TDP>
-struct BwdSm {
-    static constexpr int BGC = BSLOT * Tc<TDP>::CPR;                // components per CTA
-    static constexpr int NUB = 4;                                   // U buffers (cycled over the 4 blocks)
-    static constexpr uint32_t U = 0;                                // [NUB] tiles of 32 KB
-    static constexpr uint32_t XS = U + NUB * 2 * ATOM;              // point tile [TM][d] float
-    static constexpr uint32_t LJ = XS + TM * TDP * 4;               // log-joint [2][BGC][TM] float
-    static constexpr uint32_t LS = LJ + 2 * BGC * TM * 4;           // lse [2][TM] float
-    static constexpr uint32_t SR = LS + 2 * TM * 4;                 // sqrt(r) [BGC][TM] float
-    static constexpr uint32_t MU = SR + BGC * TM * 4;               // mu [BSLOT][128] float
-    static constexpr uint32_t MRED = MU + BSLOT * 128 * 4;          // m' of quarters 1..3 [3][BSLOT][128] float
-    static constexpr uint32_t RSUM = MRED + 3 * BSLOT * 128 * 4;    // R per component [BGC] float
-    static constexpr uint32_t BAR = RSUM + BGC * 4;                 // u_full[NUB], u_empty[NUB], done
-    static constexpr uint32_t TMEMP = BAR + 16 * 8;
-    static constexpr uint32_t FLAG = TMEMP + 8;  // abort flag, then the producers' decision slot
+struct GramSm {
+    static constexpr int XR = TDP + 2;          // rows of a transposed point tile
+    static constexpr int XS = TDP == 64 ? 3 : 2;  // point-tile stages (copies run XS - 1 tiles ahead)
+    // R-tile stages: the TMA runs RS - 1 tiles ahead of the MMAs, which covers
+    // the latency of a 26-32 KB load from L2 / HBM
+    static constexpr int RS = 3;
+    static constexpr uint32_t Y = 0;                              // [2] Y tiles
+    static constexpr uint32_t R = Y + 2 * GYB;                    // [RS] R tiles (<= 256 rows x 128 B)
+    static constexpr uint32_t XT = R + RS * GKMAX * 128;          // [XS][XR][GTM] float
+    static constexpr uint32_t BAR = XT + XS * XR * GTM * 4;  // y_full[2], y_empty[2], r_full[RS], r_empty[RS],
+                                                             // x_full[XS], x_empty[XS], done
+    static_assert(4 + 2 * RS + 2 * XS + 1 <= 24, "barrier slots");
+    static constexpr uint32_t TMEMP = BAR + 24 * 8;
+    static constexpr uint32_t FLAG = TMEMP + 8;                   // abort flag
     static constexpr uint32_t END = FLAG + 8;
     static constexpr size_t SMEM = END + 1024;
-    static_assert(SMEM <= 227 * 1024, "backward shared memory");
+    static_assert(SMEM <= 227 * 1024, "gram shared memory");
 };
 
-__device__ __forceinline__ void producers_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(BPROD) : "memory");
+__device__ __forceinline__ void gram_producers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(GPROD) : "memory");
+}
+
+// Product row i of y (0 <= i < np = d(d+1)/2 + d + 1; padding rows beyond):
+// the two coordinates whose product it is (d = the constant 1, d + 1 = 0).
+__device__ __forceinline__ void gram_row(int i, int d, int& u, int& v) {
+    const int T = d * (d + 1) / 2;
+    if (i < T) {
+        int a = (int)((sqrtf(8.f * (float)i + 1.f) - 1.f) * 0.5f);
+        while (a * (a + 1) / 2 > i) --a;
+        while ((a + 1) * (a + 2) / 2 <= i) ++a;
+        u = a;
+        v = i - a * (a + 1) / 2;
+    } else if (i < T + d) {
+        u = i - T;
+        v = d;
+    } else if (i == T + d) {
+        u = v = d;
+    } else {
+        u = v = d + 1;
+    }
 }
 
 template <int TDP>
-__global__ void __launch_bounds__(BTHREADS, 1)
-    gmm_tc_bwd_kernel(const float* __restrict__ x, int64_t n, int k, const float* __restrict__ mu,
-                      int d, const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
-                      float seed, int64_t tiles_per_chunk, float* __restrict__ partS, float* __restrict__ partM,
-                      int nblk64, int32_t* __restrict__ status) {
-    using T = Tc<TDP>;
-    using S = BwdSm<TDP>;
-    constexpr int BGC = S::BGC, NUB = S::NUB;
+__global__ void __launch_bounds__(GTHREADS, 1)
+    gmm_tc_gram_kernel(const __grid_constant__ CUtensorMap tmr, const float* __restrict__ xt_g, int64_t n, int d,
+                       int k, int kn, int ngroups, int64_t tiles_per_chunk, float* __restrict__ partS,
+                       float* __restrict__ partM, int nblk64, int32_t* __restrict__ status) {
+    using S = GramSm<TDP>;
+    constexpr int XS = S::XS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::BAR);
-    uint64_t* u_full = bars;
-    uint64_t* u_empty = bars + NUB;
-    uint64_t* done = bars + 2 * NUB;
+    uint64_t* y_full = bars;
+    uint64_t* y_empty = bars + 2;
+    constexpr int RS = S::RS;
+    uint64_t* r_full = bars + 4;
+    uint64_t* r_empty = bars + 4 + RS;
+    uint64_t* x_full = bars + 4 + 2 * RS;
+    uint64_t* x_empty = bars + 4 + 2 * RS + XS;
+    uint64_t* done = bars + 4 + 2 * RS + 2 * XS;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sm + S::TMEMP);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + S::FLAG);
-    float* xs = reinterpret_cast<float*>(sm + S::XS);
-    float* ljs = reinterpret_cast<float*>(sm + S::LJ);
-    float* lss = reinterpret_cast<float*>(sm + S::LS);
-    float* sr = reinterpret_cast<float*>(sm + S::SR);
-    float* mus = reinterpret_cast<float*>(sm + S::MU);
-    float* mred = reinterpret_cast<float*>(sm + S::MRED);
-    float* rsum = reinterpret_cast<float*>(sm + S::RSUM);
+    float* xt = reinterpret_cast<float*>(sm + S::XT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tid = threadIdx.x;
-    const int kg0 = blockIdx.x * BGC;
-    const int64_t ntiles = (n + TM - 1) / TM;
+    const int g = blockIdx.x % ngroups;           // product-row group
+    const int kg0 = (blockIdx.x / ngroups) * GKMAX;  // first component
+    const int row0 = g * GMB * 128;
+    const int64_t ntiles = (n + GTM - 1) / GTM;
     const int64_t t_begin = (int64_t)blockIdx.y * tiles_per_chunk;
     const int64_t t_end = min64(ntiles, t_begin + tiles_per_chunk);
 
     if (tid == 0) {
-        for (int c = 0; c < NUB; ++c) {
-            mbar_init(&u_full[c], BPROD / 32);
-            mbar_init(&u_empty[c], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&y_full[b], GPROD / 32);
+            mbar_init(&y_empty[b], 1);
+        }
+        for (int b = 0; b < RS; ++b) {
+            mbar_init(&r_full[b], 1);
+            mbar_init(&r_empty[b], 1);
+        }
+        for (int b = 0; b < XS; ++b) {
+            mbar_init(&x_full[b], 1);
+            mbar_init(&x_empty[b], GPROD / 32);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    // mean of the component owning row a' of block c
-    for (int e = tid; e < BSLOT * 128; e += BTHREADS) {
-        const int c = e / 128, ar = e % 128;
-        const int kg = kg0 + c * T::CPR + ar / TDP, a = ar % TDP;
-        mus[e] = (kg < k && a < d) ? mu[(size_t)kg * d + a] : 0.f;
+    // constant rows of the transposed point tiles: ones at row d, zeros at d + 1
+    for (int e = tid; e < XS * GTM; e += GTHREADS) {
+        const int b = e / GTM, p = e % GTM;
+        xt[b * S::XR * GTM + d * GTM + p] = 1.f;
+        xt[b * S::XR * GTM + (d + 1) * GTM + p] = 0.f;
     }
-    for (int e = tid; e < BGC; e += BTHREADS) rsum[e] = 0.f;
-    if (warp == BPROD / 32) {
+    if (warp == GPROD / 32 + 1) {
         tc::tmem_alloc(tmem_holder, 512);
         tc::tmem_relinquish();
     }
@@ -362,202 +414,145 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
+    const uint32_t rbytes = (uint32_t)kn * 128u;  // one R tile: kn components x 64 points bf16
 
-    if (warp == BPROD / 32) {
-        // MMA issuer: block c of tile `it` uses U buffer c % NUB, its use number
-        // u = it * (BSLOT / NUB) + c / NUB giving the barrier phases
+    if (warp == GPROD / 32) {
+        // per tile: the transposed point tile (one bulk copy of d rows x 64
+        // points) and the R tile (TMA: components kg0 .. kg0 + kn - 1, zero rows
+        // past K, 64 points)
         if (lane == 0) {
+            const uint32_t xbytes = (uint32_t)d * GTM * 4u;
+            int it = 0;
+            for (int64_t t = t_begin; t < t_end; ++t, ++it) {
+                const int xb = it % XS, b = it % RS;
+                const uint32_t ux = (uint32_t)(it / XS), u = (uint32_t)(it / RS);
+                if (!mbar_wait(&x_empty[xb], (ux & 1u) ^ 1u, status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                mbar_arrive_expect_tx(&x_full[xb], xbytes);
+                bulk_g2s(xt + xb * S::XR * GTM, xt_g + t * (int64_t)d * GTM, xbytes, &x_full[xb]);
+                if (!mbar_wait(&r_empty[b], (u & 1u) ^ 1u, status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                mbar_arrive_expect_tx(&r_full[b], rbytes);
+                tc::tma_load_2d(sm + S::R + b * GKMAX * 128, &tmr, (int)(t * GTM), kg0, &r_full[b]);
+            }
+        }
+        __syncwarp();
+    } else if (warp == GPROD / 32 + 1) {
+        // MMA issuer: D[mb] (tensor-memory columns 256 mb ..) += Y[mb] R^T
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(128, kn);
             bool ok = true;
             int it = 0;
             for (int64_t t = t_begin; ok && t < t_end; ++t, ++it) {
-                for (int c = 0; c < BSLOT; ++c) {
-                    const int b = c % NUB;
-                    const uint32_t use = (uint32_t)(it * (BSLOT / NUB) + c / NUB);
-                    if (!mbar_wait(&u_full[b], use & 1u, status)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
-                    const uint32_t ua = smem_u32(sm + S::U + b * 2 * ATOM);
-#pragma unroll
-                    for (int j = 0; j < TM / 16; ++j) {
-                        const uint64_t dsc = tc::desc_sw128(ua + (uint32_t)(j >> 2) * ATOM + (uint32_t)(j & 3) * 32u);
-                        tc::mma_bf16(tmem + (uint32_t)(c * 128), dsc, dsc, IDESC, (it > 0 || j > 0) ? 1u : 0u);
-                    }
-                    tc::mma_commit(&u_empty[b]);
+                const int b = it & 1, rb = it % RS;
+                const uint32_t u = (uint32_t)(it >> 1), ur = (uint32_t)(it / RS);
+                if (!mbar_wait(&y_full[b], u & 1u, status) || !mbar_wait(&r_full[rb], ur & 1u, status)) {
+                    ok = false;
+                    break;
                 }
+                tc::fence_after_sync();
+                const uint32_t ya = smem_u32(sm + S::Y + b * GYB), ra = smem_u32(sm + S::R + rb * GKMAX * 128);
+#pragma unroll
+                for (int mb = 0; mb < GMB; ++mb)
+#pragma unroll
+                    for (int j = 0; j < GTM / 16; ++j)
+                        tc::mma_bf16(tmem + (uint32_t)(mb * 256), tc::desc_sw128(ya + mb * 128 * 128 + j * 32),
+                                     tc::desc_sw128(ra + j * 32), idesc, (it > 0 || j > 0) ? 1u : 0u);
+                tc::mma_commit(&y_empty[b]);
+                tc::mma_commit(&r_empty[rb]);
             }
             if (!ok) *abort_flag = 1;
             tc::mma_commit(done);
         }
         __syncwarp();
     } else {
-        // producers: thread owns row a' of every block (component a'/TDP of the
-        // block, dimension a'%TDP) and a quarter of the tile's points. Tile t+1
-        // (points, log-joint, lse) is copied into shared memory while tile t is
-        // built: the point tile has one buffer, free once every thread holds its
-        // column of it in registers.
-        const int ar = tid & 127;
-        const int jr = ar / TDP, a = ar % TDP;
-        const int qp = tid >> 7;  // points 32 qp .. 32 qp + 31 of the tile
-        const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-        auto issue = [&](int64_t t, int buf) {
-            const int64_t p0 = t * TM;
-            const int nv = (int)min64(TM, n - p0);
-            float* X = xs;
-            const float* src = x + p0 * d;
-            if (vec) {
-                for (int e = tid; e < nv * d / 4; e += BPROD) cp_async16(X + 4 * e, src + 4 * e);
-            } else {
-                for (int e = tid; e < nv * d; e += BPROD) cp_async4(X + e, src + e);
-            }
-            float* L = ljs + buf * BGC * TM;
-            for (int e = tid; e < BGC * TM; e += BPROD) {
-                const int c = e / TM, p = e % TM;
-                if (p < nv && kg0 + c < k) cp_async4(L + e, lj + (int64_t)(kg0 + c) * lj_ld + p0 + p);
-            }
-            for (int p = tid; p < nv; p += BPROD) cp_async4(lss + buf * TM + p, lse + p0 + p);
-        };
-        float2 macc[BSLOT];  // m' of this thread's row per block, two partial sums
+        // producers: thread = one product row (u, v) of one MMA block, points
+        // 32 h .. 32 h + 31 of each tile; a warp takes 32 consecutive rows, so
+        // its loads of x_u are broadcasts and its 32 rows x_v fall in distinct
+        // bank groups (row stride 68 floats)
+        const int lrow = tid & 255, h = tid >> 8;
+        int u, v;
+        gram_row(row0 + lrow, d, u, v);
+        const int mb = lrow >> 7, r7 = lrow & 127;
+        // this thread's read offsets in a point tile (groups 8h .. 8h + 7 of
+        // rows u and v) and write offsets in a Y tile (chunks 4h .. 4h + 3)
+        int ou[8], ov[8];
 #pragma unroll
-        for (int c = 0; c < BSLOT; ++c) macc[c] = make_float2(0.f, 0.f);
-        float racc[BGC * TM / BPROD];
+        for (int gg = 0; gg < 8; ++gg) {
+            ou[gg] = gram_xpos(u, 4 * (8 * h + gg));
+            ov[gg] = gram_xpos(v, 4 * (8 * h + gg));
+        }
+        uint32_t oy[4];
 #pragma unroll
-        for (int u = 0; u < BGC * TM / BPROD; ++u) racc[u] = 0.f;
-        volatile int* decision = abort_flag + 1;  // written by thread 0 before a barrier, read after it
-        if (t_begin < t_end) issue(t_begin, 0);
-        cp_async_commit();
+        for (int c = 0; c < 4; ++c) oy[c] = (uint32_t)(mb * 128 * 128) + tc::sw128_offset((uint32_t)r7, (uint32_t)(4 * h + c));
         int it = 0;
         for (int64_t t = t_begin; t < t_end; ++t, ++it) {
-            const int buf = it & 1;
-            const int64_t p0 = t * TM;
-            cp_async_wait_all();  // this thread's copies of tile t have landed
-            if (tid == 0) *decision = *abort_flag;
-            // every thread's copies of tile t are visible, every thread is done with
-            // tile t-1 (its sqrt(r) may be overwritten); decision published
-            producers_sync();
-            if (*decision) break;  // uniform over all producer threads
-            const float* X = xs;
-            const float* L = ljs + buf * BGC * TM;
-            const float* Ls = lss + buf * TM;
-#pragma unroll
-            for (int u = 0; u < BGC * TM / BPROD; ++u) {
-                const int e = tid + u * BPROD;
-                const int c = e / TM, p = e % TM;
-                float v = 0.f;
-                if (p0 + p < n && kg0 + c < k) v = expf(0.5f * (L[e] - Ls[p]));
-                sr[e] = v;
-                racc[u] += v * v;
+            const int b = it & 1, xb = it % XS;
+            const uint32_t use = (uint32_t)(it >> 1), ux = (uint32_t)(it / XS);
+            if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;  // a wait elsewhere gave up (waits are bounded anyway)
+            if (!mbar_wait_warp(&x_full[xb], ux & 1u, status) ||
+                !mbar_wait_warp(&y_empty[b], (use & 1u) ^ 1u, status)) {
+                *abort_flag = 1;
+                break;
             }
-            // x values of this thread: points p0 + 32 qp + 0..31, dimension a (0 past
-            // the end), as pairs of consecutive points
-            float2 xv[16];
-            if (a < d && p0 + TM <= n) {  // a full tile: no per-point tests
-                const float* xa = X + qp * 32 * d + a;
+            const float* X = xt + xb * S::XR * GTM;
+            uint8_t* yt = sm + S::Y + b * GYB;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) xv[j] = make_float2(xa[(2 * j) * d], xa[(2 * j + 1) * d]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int p = qp * 32 + 2 * j;
-                    xv[j] = make_float2((p0 + p < n && a < d) ? X[p * d + a] : 0.f,
-                                        (p0 + p + 1 < n && a < d) ? X[(p + 1) * d + a] : 0.f);
-                }
+            for (int c = 0; c < 4; ++c) {  // 8 points per 16-byte chunk of the Y row
+                const float4 u0 = *reinterpret_cast<const float4*>(X + ou[2 * c]);
+                const float4 u1 = *reinterpret_cast<const float4*>(X + ou[2 * c + 1]);
+                const float4 v0 = *reinterpret_cast<const float4*>(X + ov[2 * c]);
+                const float4 v1 = *reinterpret_cast<const float4*>(X + ov[2 * c + 1]);
+                const float2 p0 = __fmul2_rn(make_float2(u0.x, u0.y), make_float2(v0.x, v0.y));
+                const float2 p1 = __fmul2_rn(make_float2(u0.z, u0.w), make_float2(v0.z, v0.w));
+                const float2 p2 = __fmul2_rn(make_float2(u1.x, u1.y), make_float2(v1.x, v1.y));
+                const float2 p3 = __fmul2_rn(make_float2(u1.z, u1.w), make_float2(v1.z, v1.w));
+                *reinterpret_cast<uint4*>(yt + oy[c]) =
+                    make_uint4(tc::pack_bf16x2(p0.x, p0.y), tc::pack_bf16x2(p1.x, p1.y),
+                               tc::pack_bf16x2(p2.x, p2.y), tc::pack_bf16x2(p3.x, p3.y));
             }
-            producers_sync();     // sqrt(r) of tile t complete, the point tile read by all
-            if (t + 1 < t_end) issue(t + 1, buf ^ 1);  // log-joint buffer buf ^ 1 last read in tile t-1
-            cp_async_commit();
-#pragma unroll 1
-            for (int c = 0; c < BSLOT; ++c) {
-                const int b = c % NUB;
-                const uint32_t use = (uint32_t)(it * (BSLOT / NUB) + c / NUB);
-                // sqrt(r) of this block's 32 points and the mean, loaded before the
-                // wait for the U buffer so that the wait covers their latency
-                const float4* src = reinterpret_cast<const float4*>(sr + (c * T::CPR + jr) * TM + qp * 32);
-                float4 sv4[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) sv4[q] = src[q];
-                const float mcs = mus[c * 128 + ar];
-                if (!mbar_wait_warp(&u_empty[b], (use & 1u) ^ 1u, status)) {
-                    *abort_flag = 1;  // skip the work; the next decision point stops every warp
-                    continue;
-                }
-                // points 32 qp .. +31 are chunks 4 (qp & 1) .. +3 of K atom qp >> 1
-                uint8_t* ut = sm + S::U + b * 2 * ATOM + (qp >> 1) * ATOM;
-                const float2 mc = make_float2(mcs, mcs);
-                // u = sqrt(r) (x - mu) for two points per packed op; m' += sqrt(r) u in
-                // four independent partial sums (no serial chain through the slot)
-                float2 mq[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
-                                make_float2(0.f, 0.f)};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float4 sa = sv4[2 * j], sb = sv4[2 * j + 1];
-                    const float2 sp[4] = {make_float2(sa.x, sa.y), make_float2(sa.z, sa.w), make_float2(sb.x, sb.y),
-                                          make_float2(sb.z, sb.w)};
-                    uint32_t w4[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float2 u = __fmul2_rn(sp[i], __fadd2_rn(xv[4 * j + i], make_float2(-mc.x, -mc.y)));
-                        mq[i] = __ffma2_rn(sp[i], u, mq[i]);
-                        w4[i] = tc::pack_bf16x2(u.x, u.y);
-                    }
-                    *reinterpret_cast<uint4*>(ut + tc::sw128_offset((uint32_t)ar, (uint32_t)(4 * (qp & 1) + j))) =
-                        make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                }
-                macc[c] = __fadd2_rn(macc[c], __fadd2_rn(__fadd2_rn(mq[0], mq[1]), __fadd2_rn(mq[2], mq[3])));
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&u_full[b]);
+            fence_proxy_async_smem();  // the Y writes before the MMAs read them; the point-tile reads before its refill
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(&y_full[b]);
+                tc::mbar_arrive(&x_empty[xb]);
             }
         }
-        cp_async_wait_all();  // no copy may land after the block exits
-        // m' of quarters 1..3 for quarter 0 to add
-        if (qp > 0)
-            for (int c = 0; c < BSLOT; ++c) mred[(qp - 1) * BSLOT * 128 + c * 128 + ar] = macc[c].x + macc[c].y;
-        // R per component
-#pragma unroll
-        for (int u = 0; u < BGC * TM / BPROD; ++u) {
-            const float rv = warp_sum(racc[u]);
-            if (lane == 0) atomicAdd(&rsum[(tid + u * BPROD) / TM], rv);
-        }
-        producers_sync();
-        const int64_t cbase = (int64_t)blockIdx.y * k;
-        if (qp == 0) {
-            for (int c = 0; c < BSLOT; ++c) {
-                const int kg = kg0 + c * T::CPR + jr;
-                if (kg >= k) continue;
-                float* M = partM + (cbase + kg) * (TDP + 1);
-                const float* mr = mred + c * 128 + ar;
-                M[a] += seed * ((macc[c].x + macc[c].y) + mr[0] + mr[BSLOT * 128] + mr[2 * BSLOT * 128]);
-                if (a == 0) M[TDP] += seed * rsum[c * T::CPR + jr];
-            }
-        }
-        // accumulators: warp w reads TMEM lanes of its quarter w % 4 for block w / 4;
-        // row a' = lane index, the component's columns are [jr*TDP, jr*TDP + TDP)
+        // accumulators: warp w reads the tensor-memory lanes of its quarter w % 4
+        // (product rows 32 (w % 4) .. of block mb) for column chunks w / 4, +4, ...
         const bool fin = mbar_wait_warp(done, 0, status);
         if (!fin) *abort_flag = 1;
         tc::fence_after_sync();
-        producers_sync();  // every warp has seen `done` (or given up) before reading the flag
-        const int aborted = __shfl_sync(0xffffffffu, *abort_flag, 0);  // one value per warp
-        if (!aborted && t_begin < t_end) {  // a CTA without tiles issued no MMA: TMEM holds nothing
+        gram_producers_sync();  // every warp has seen `done` (or given up) before reading the flag
+        const int aborted = __shfl_sync(0xffffffffu, *abort_flag, 0);
+        if (!aborted && t_begin < t_end) {
             const int qtr = warp & 3;
-            const int row = qtr * 32 + lane;      // row a' of the block
-            const int jw = row / TDP, aw = row % TDP;  // the same jw for the whole warp
-            const int c = warp >> 2;
-            const int kg = kg0 + c * T::CPR + jw;
-            if (kg < k) {
-                float* Sp = partS + (cbase + kg) * (int64_t)nblk64;
-#pragma unroll 1
-                for (int ch = 0; ch < TDP / 32; ++ch) {
-                    float v[32];
-                    tc::tmem_ld32_wait(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(c * 128 + jw * TDP + ch * 32), v);
+            const int nch = GMB * (kn / 16);  // chunks of 16 columns over both blocks
+            for (int cc = warp >> 2; cc < nch; cc += 4) {
+                const int eb = cc / (kn / 16), c0 = (cc % (kn / 16)) * 16;
+                float vals[16];
+                tc::tmem_ld16_wait(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(eb * 256 + c0), vals);
+                int eu, ev;
+                gram_row(row0 + eb * 128 + qtr * 32 + lane, d, eu, ev);
+                if (ev > d) continue;  // padding row
+                const int64_t cbase = (int64_t)blockIdx.y * k;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int b = ch * 32 + i;
-                        if (b <= aw) {
-                            const int A = aw >> 3, B = b >> 3;
-                            Sp[(A * (A + 1) / 2 + B) * 64 + (aw & 7) * 8 + (b & 7)] += seed * v[i];
-                        }
+                for (int i = 0; i < 16; ++i) {
+                    const int kk = kg0 + c0 + i;
+                    if (kk >= k) break;
+                    const float val = vals[i];
+                    if (ev < d) {          // S entry (eu, ev), eu >= ev
+                        const int A = eu >> 3, B = ev >> 3;
+                        partS[(cbase + kk) * (int64_t)nblk64 + (A * (A + 1) / 2 + B) * 64 + (eu & 7) * 8 + (ev & 7)] +=
+                            val;
+                    } else if (eu < d) {   // m entry
+                        partM[(cbase + kk) * (TDP + 1) + eu] += val;
+                    } else {               // R
+                        partM[(cbase + kk) * (TDP + 1) + TDP] += val;
                     }
                 }
             }
@@ -565,9 +560,53 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == BPROD / 32) {
+    if (warp == GPROD / 32 + 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// Point tiles for the gram kernel: tile t (points 64 t .. 64 t + 63, zero past
+// n) as d rows of 64 floats, row c holding coordinate c of the tile's points in
+// the order of gram_xpos, so that one bulk copy brings a tile into shared
+// memory in the layout the gram kernel reads. One CTA per tile.
+__global__ void __launch_bounds__(256) gmm_tc_xt_kernel(const float* __restrict__ x, int64_t n, int d,
+                                                        float* __restrict__ xt) {
+    __shared__ float tile[GTM][129];
+    const int64_t t = blockIdx.x;
+    const int64_t p0 = t * GTM;
+    for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
+        const int p = e / d, c = e - p * d;
+        tile[p][c] = p0 + p < n ? __ldg(x + (p0 + p) * d + c) : 0.f;
+    }
+    __syncthreads();
+    float* out = xt + t * (int64_t)d * GTM;
+    for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
+        const int c = e / GTM, p = e % GTM;
+        out[gram_xpos(c, p)] = tile[p][c];
+    }
+}
+
+// r[c][p] = seed exp(lj[c][p] - lse[p]) in BF16 for c < k, p < n; zero for the
+// padding rows k <= c < kr and points n <= p < npad. 8 points per thread.
+__global__ void __launch_bounds__(256) gmm_tc_r_kernel(const float* __restrict__ lj, int64_t lj_ld,
+                                                       const float* __restrict__ lse, int64_t n, int k, int kr,
+                                                       int64_t npad, float seed, __nv_bfloat16* __restrict__ rb) {
+    const int64_t per_row = npad / 8;
+    const int64_t total = (int64_t)kr * per_row;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int c = (int)(e / per_row);
+        const int64_t p0 = (e - (int64_t)c * per_row) * 8;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t p = p0 + j;
+            v[j] = (c < k && p < n) ? seed * expf(__ldg(lj + (int64_t)c * lj_ld + p) - __ldg(lse + p)) : 0.f;
+        }
+        *reinterpret_cast<uint4*>(rb + (int64_t)c * npad + p0) =
+            make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]), tc::pack_bf16x2(v[4], v[5]),
+                       tc::pack_bf16x2(v[6], v[7]));
     }
 }
 
@@ -613,21 +652,31 @@ size_t a1024(size_t v) { return (v + 1023) & ~(size_t)1023; }
 
 int tc_dp(int d) { return d <= 64 ? 64 : 128; }
 
+// BF16 rows of R: the components rounded up to a multiple of 16 (the MMA's N
+// granularity); rows past K are zero.
+int tc_r_rows(int k) { return (k + 15) / 16 * 16; }
+
+// Points of R held in the workspace at a time.
+int64_t tc_r_points(int64_t npad) { return npad < GRB_POINTS ? npad : (int64_t)GRB_POINTS; }
+
 struct TcLayout {
-    size_t off_xb, off_xl, off_qb, off_ql, fixed;
-    int64_t npad;
+    size_t off_xb, off_xl, off_qb, off_ql, off_rb, off_xt, fixed;
+    int64_t npad, rpoints;
 };
 
 TcLayout tc_layout(const GmmLayout& L, int64_t n, int d, int k) {
     const int tdp = tc_dp(d);
     TcLayout T;
     T.npad = ((n + TM - 1) / TM) * TM;
+    T.rpoints = tc_r_points(T.npad);
     const size_t xbytes = a1024((size_t)T.npad * tdp * 2), qbytes = a1024((size_t)k * tdp * tdp * 2);
     T.off_xb = a1024(L.fixed);
     T.off_xl = T.off_xb + xbytes;
     T.off_qb = T.off_xl + xbytes;
     T.off_ql = T.off_qb + qbytes;
-    T.fixed = T.off_ql + qbytes;
+    T.off_rb = T.off_ql + qbytes;
+    T.off_xt = T.off_rb + a1024((size_t)tc_r_rows(k) * T.rpoints * 2);
+    T.fixed = T.off_xt + a1024((size_t)T.npad * d * 4);
     return T;
 }
 
@@ -654,6 +703,20 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int tdp) {
     cuuint64_t dims[2] = {(cuuint64_t)tdp, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)tdp * 2};
     cuuint32_t box[2] = {64, (cuuint32_t)TM};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// R in BF16 [kr][npad_r], box 64 points x kn components, 128-byte swizzle;
+// rows past kr read as zero.
+bool make_map_r(CUtensorMap* m, const void* base, int64_t npad_r, int kr, int kn) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)npad_r, (cuuint64_t)kr};
+    cuuint64_t strides[1] = {(cuuint64_t)npad_r * 2};
+    cuuint32_t box[2] = {(cuuint32_t)GTM, (cuuint32_t)kn};
     cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -703,9 +766,18 @@ int launch_tc_fwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char*
     return GPA_OK;
 }
 
-int tc_bwd_chunks(int k, int bgc, int64_t ntiles) {
-    const int slots = sm_count_tc();  // one CTA per SM (all of TMEM)
-    const int groups = (k + bgc - 1) / bgc;
+// Product rows of y (gram kernel): d(d+1)/2 + d + 1, in groups of 256.
+int gram_groups(int d) { return (d * (d + 1) / 2 + d + 1 + GMB * 128 - 1) / (GMB * 128); }
+
+// Point chunks of the gram grid: one wave of CTAs (one per SM: the kernel
+// holds all of tensor memory) when that fills at least 85 % of the SMs, so
+// that each CTA accumulates over as many tiles as possible before its
+// write-out; otherwise the chunk count with the best wave efficiency.
+int tc_bwd_chunks(int groups, int64_t ntiles) {
+    const int slots = sm_count_tc();
+    const int64_t one_wave = (int64_t)(slots / groups);
+    if (one_wave >= 1 && groups * one_wave >= (int64_t)(0.85 * slots))
+        return (int)min64(min64(one_wave, kGmmMaxChunks), ntiles);
     int best = 1;
     double best_eff = -1.0;
     for (int c = 1; c <= kGmmMaxChunks && c <= ntiles; ++c) {
@@ -720,18 +792,32 @@ int tc_bwd_chunks(int k, int bgc, int64_t ntiles) {
     return best;
 }
 
+// Reverse-pass sums of points row0 .. row0 + n_local - 1 (n_local <= the R
+// capacity): R in BF16 from the log-joint chunk, then the gram kernel.
 template <int TDP>
-int launch_tc_bwd(const GmmArgs& A, const GmmLayout& L, char* ws, int64_t row0, int64_t n_local, const float* lj,
-                  int64_t lj_ld, const float* lse, int nchunks, cudaStream_t s) {
-    auto kern = gmm_tc_bwd_kernel<TDP>;
-    if (!set_smem_tc(kern, BwdSm<TDP>::SMEM)) return GPA_ERR_CUDA;
-    const int64_t ntiles = (n_local + TM - 1) / TM;
+int launch_tc_bwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char* ws, int64_t row0, int64_t n_local,
+                  const float* lj, int64_t lj_ld, const float* lse, int nchunks, cudaStream_t s) {
+    const int kr = tc_r_rows(A.k), kn = kr < GKMAX ? kr : GKMAX;
+    const int64_t npad_r = (n_local + GTM - 1) / GTM * GTM;
+    __nv_bfloat16* rb = (__nv_bfloat16*)(ws + T.off_rb);
+    const int64_t work = (int64_t)kr * (npad_r / 8);
+    const int64_t want = (work + 255) / 256, cap = (int64_t)sm_count_tc() * 16;
+    GPA_LAUNCH("gmm_tc_r", s,
+               gmm_tc_r_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
+                   lj, lj_ld, lse, n_local, A.k, kr, npad_r, (float)A.seed, rb));
+    CUtensorMap tmr;
+    if (!make_map_r(&tmr, rb, npad_r, kr, kn)) return GPA_ERR_CUDA;
+    auto kern = gmm_tc_gram_kernel<TDP>;
+    if (!set_smem_tc(kern, GramSm<TDP>::SMEM)) return GPA_ERR_CUDA;
+    const int ng = gram_groups(A.d), nkg = (kr + GKMAX - 1) / GKMAX;
+    const int64_t ntiles = (n_local + GTM - 1) / GTM;
     const int64_t tpc = (ntiles + nchunks - 1) / nchunks;
-    dim3 grid((A.k + BwdSm<TDP>::BGC - 1) / BwdSm<TDP>::BGC, nchunks);
+    dim3 grid((unsigned)(ng * nkg), (unsigned)nchunks);
     GPA_LAUNCH("gmm_tc_bwd", s,
-               kern<<<grid, BTHREADS, BwdSm<TDP>::SMEM, s>>>(
-                   A.x + row0 * A.d, n_local, A.k, A.mu, A.d, lj, lj_ld, lse, (float)A.seed, tpc,
-                   (float*)(ws + L.off_bS), (float*)(ws + L.off_bM), gmm_bwd_partial_entries(TDP), A.status));
+               kern<<<grid, GTHREADS, GramSm<TDP>::SMEM, s>>>(tmr, (const float*)(ws + T.off_xt) + row0 * A.d, n_local,
+                                                                A.d, A.k, kn, ng, tpc,
+                                                         (float*)(ws + L.off_bS), (float*)(ws + L.off_bM),
+                                                         gmm_bwd_partial_entries(TDP), A.status));
     return GPA_OK;
 }
 
@@ -750,8 +836,10 @@ template <int TDP>
 int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s) {
     const TcLayout T = tc_layout(L, A.n, A.d, A.k);
     if (ws_bytes < T.fixed) return GPA_ERR_WORKSPACE;
-    const int64_t ntiles = (A.n + TM - 1) / TM;
-    const int nchunks = tc_bwd_chunks(A.k, BwdSm<TDP>::BGC, ntiles);
+    const int kr = tc_r_rows(A.k);
+    const int64_t RP = T.rpoints;  // points per backward launch (a multiple of 128)
+    const int nchunks = tc_bwd_chunks(gram_groups(A.d) * ((kr + GKMAX - 1) / GKMAX),
+                                      (((A.n < RP ? A.n : RP) + GTM - 1) / GTM));
     const int nent = gmm_bwd_partial_entries(TDP);
     if (cudaMemsetAsync(ws + L.off_bS, 0, sizeof(float) * (size_t)nchunks * A.k * nent, s) != cudaSuccess ||
         cudaMemsetAsync(ws + L.off_bM, 0, sizeof(float) * (size_t)nchunks * A.k * (TDP + 1), s) != cudaSuccess)
@@ -759,8 +847,20 @@ int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cud
     int rc = gmm_run_prep(A, L, ws, s);
     if (rc) return rc;
     if ((rc = convert_inputs<TDP>(A, L, T, ws, s))) return rc;
+    GPA_LAUNCH("gmm_tc_xt", s,
+               gmm_tc_xt_kernel<<<(unsigned)(T.npad / GTM), 256, 0, s>>>(A.x, A.n, A.d, (float*)(ws + T.off_xt)));
+    // the backward runs over at most RP points at a time (the R buffer), with
+    // the same chunk grid each time so that the partial sums keep one order
+    auto bwd_range = [&](int64_t c0, int64_t nl, const float* lj, int64_t lj_ld, const float* lse) {
+        for (int64_t o = 0; o < nl; o += RP) {
+            const int64_t m = min64(RP, nl - o);
+            const int r = launch_tc_bwd<TDP>(A, L, T, ws, c0 + o, m, lj + o, lj_ld, lse + o, nchunks, s);
+            if (r) return r;
+        }
+        return (int)GPA_OK;
+    };
     if (A.lj_in) {
-        if ((rc = launch_tc_bwd<TDP>(A, L, ws, 0, A.n, A.lj_in, A.n, A.lse_in, nchunks, s))) return rc;
+        if ((rc = bwd_range(0, A.n, A.lj_in, A.n, A.lse_in))) return rc;
         if ((A.out || A.exch_out) && (rc = gmm_run_lse_sum(A.lse_in, A.n, L, ws, s))) return rc;
     } else {
         // log-joint chunk after the tensor-core area, as large as the workspace allows
@@ -775,11 +875,11 @@ int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cud
             const int64_t nl = min64(P, A.n - c0);
             // lj / lse are chunk-local: the forward writes them at p0 + row, p0 local
             if ((rc = launch_tc_fwd<TDP>(A, L, T, ws, c0, nl, lj, P, lse, s))) return rc;
-            if ((rc = launch_tc_bwd<TDP>(A, L, ws, c0, nl, lj, P, lse, nchunks, s))) return rc;
+            if ((rc = bwd_range(c0, nl, lj, P, lse))) return rc;
         }
     }
     if (A.exch_out) return gmm_run_exchange(A, L, ws, nchunks, s);
-    if ((rc = gmm_run_finalize(A, L, ws, nchunks, 1, s))) return rc;
+    if ((rc = gmm_run_finalize(A, L, ws, nchunks, 0, s))) return rc;  // raw moments, as the FP32 path
     if (A.out) return gmm_run_objective(A, L, ws, s);
     return GPA_OK;
 }
@@ -791,7 +891,8 @@ bool gmm_tc_supported(int d) { return d > 32 && d <= 128; }
 size_t gmm_tc_extra_bytes(int64_t n, int d, int k) {
     const int tdp = tc_dp(d);
     const int64_t npad = ((n + TM - 1) / TM) * TM;
-    return 2 * a1024((size_t)npad * tdp * 2) + 2 * a1024((size_t)k * tdp * tdp * 2) + 2048;
+    return 2 * a1024((size_t)npad * tdp * 2) + 2 * a1024((size_t)k * tdp * tdp * 2) +
+           a1024((size_t)tc_r_rows(k) * tc_r_points(npad) * 2) + a1024((size_t)npad * d * 4) + 2048;
 }
 
 int gmm_tc_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s) {
