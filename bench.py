@@ -461,6 +461,26 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
         gbs = BYTES_PER_OBS_VJP * RP_M / (ms / 1e3) / 1e9
         out[f"vjp_{strat}"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms, "hbm_gbs_algorithmic": gbs,
                                "frac": gbs / peaks["hbm_gbs"]}
+    # cotangents kept in the plan's camera-sorted order (e.g. residuals written
+    # in plan order by the previous step): read contiguously, no permutation
+    from paper_2104_05372_b300._lib import plan_arrays
+    perm = plan_arrays(plan, RP_M, RP_C)[1].long()
+    w_plan = w[perm].contiguous()
+    tgt_plan = tgt[perm].contiguous()
+    del perm
+    ms = timed(lambda: gpa.reproj_vjp(cams, pts, obs, w_plan, d_cams=dcm, d_pts=dpt, strat="sort", plan=plan,
+                                      obs_order="plan", ws=ws))
+    gbs = BYTES_PER_OBS_VJP * RP_M / (ms / 1e3) / 1e9
+    out["vjp_sort_plan_order"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms, "hbm_gbs_algorithmic": gbs,
+                                  "frac": gbs / peaks["hbm_gbs"],
+                                  "note": "cotangent rows in the plan's camera-sorted order (obs_order plan)"}
+    ms = timed(lambda: gpa.reproj_residual_vjp(cams, pts, obs, tgt_plan, 1.0, res=res, d_cams=dcm, d_pts=dpt,
+                                               strat="sort", plan=plan, obs_order="plan", ws=ws))
+    out["fused_residual_vjp_sort_plan_order"] = {
+        "obs_per_s": RP_M / (ms / 1e3), "ms": ms,
+        "hbm_gbs_algorithmic": BYTES_PER_OBS_FUSED * RP_M / (ms / 1e3) / 1e9,
+        "note": "targets kept permuted into plan order once, residuals written in plan order"}
+    del w_plan, tgt_plan
     ms = timed(lambda: gpa.reproj_residual(cams, pts, obs, tgt, res=res, ws=ws))
     out["residual"] = {"obs_per_s": RP_M / (ms / 1e3), "ms": ms,
                        "hbm_gbs_algorithmic": 25.6 * RP_M / (ms / 1e3) / 1e9}
@@ -497,7 +517,7 @@ def run_reproj(args, gpa, _lib, dev, stream, rank):
                                            "repays it after about ms / (ms_atomic - ms_sort) calls"}
     del pws, pbuf
     out["timing"] = ", ".join(sorted(modes)) + " (one call per timed iteration)"
-    best = max(("sort", "atomic", "warpagg"), key=lambda s_: out[f"vjp_{s_}"]["obs_per_s"])
+    best = max(("sort", "atomic", "warpagg", "sort_plan_order"), key=lambda s_: out[f"vjp_{s_}"]["obs_per_s"])
     out["metric"] = "reproj VJP obs/s"
     out["value"] = out[f"vjp_{best}"]["obs_per_s"]
     out["best_strategy"] = best

@@ -295,15 +295,25 @@ GPA_API int reproj_residual(const float* cams, const float* pts, const int32_t* 
                     int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, void* ws,
                     size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
 
+/* Order of the per-observation arrays (w, tgt, res) of the SORT strategy:
+ * GPA_OBS_INPUT: row j belongs to observation j (obs[j]);
+ * GPA_OBS_PLAN:  row i belongs to the observation at position i of the plan's
+ *                camera-sorted order (plan perm[i]). The kernels then read and
+ *                write these arrays contiguously instead of through the
+ *                permutation, e.g. for a least-squares loop that keeps its
+ *                targets permuted once and its residuals in plan order. */
+typedef enum { GPA_OBS_INPUT = 0, GPA_OBS_PLAN = 1 } gpa_obs_order;
+
 /* reproj_residual computed in the camera-sorted order of a plan built from obs
  * by gpa_obs_plan_build (each camera's record is read once per run of its
- * observations instead of once per observation); res is still written in
- * input order, and every entry equals reproj_residual's bit for bit. obs is
- * checked (non-null, 8-byte aligned) but not read: the plan carries the
- * indices. Invalid indices: NaN rows and GPA_ERR_INDEX, as above. */
+ * observations instead of once per observation); with obs_order
+ * GPA_OBS_INPUT, res is written in input order and every entry equals
+ * reproj_residual's bit for bit; with GPA_OBS_PLAN, tgt and res are in plan
+ * order. obs is checked (non-null, 8-byte aligned) but not read: the plan
+ * carries the indices. Invalid indices: NaN rows and GPA_ERR_INDEX, as above. */
 GPA_API int reproj_residual_sorted(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
-                    int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, const void* plan, void* ws,
-                    size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
+                    int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, const void* plan, int32_t obs_order,
+                    void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
 
 /*
  * VJP of the residual with cotangent w [M][2]: d_cams[c] += J_cam^T w_j and
@@ -312,12 +322,13 @@ GPA_API int reproj_residual_sorted(const float* cams, const float* pts, const in
  * segmented reduction (histogram pattern, Sec. 6.1.3; LetIndexingTranspose,
  * Fig. "transpose"). strat selects how the Accum is carried out; SORT needs
  * `plan` from gpa_obs_plan_build on the same obs (nullable otherwise).
+ * obs_order (gpa_obs_order): the order of w; GPA_OBS_PLAN needs SORT.
  * Atomic strategies give float32 sums whose rounding depends on the order.
  */
 GPA_API int reproj_vjp(const float* cams, const float* pts, const int32_t* obs, const float* w,
                int32_t n_cams, int32_t n_pts, int64_t n_obs, float* d_cams, float* d_pts,
-               int32_t strat, const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
-               gpa_stream_t stream);
+               int32_t strat, const void* plan, int32_t obs_order, void* ws, size_t ws_bytes,
+               int32_t* dev_status, gpa_stream_t stream);
 
 /*
  * Gauss-Newton normal equations of the residual, the blocks of J^T J and J^T r
@@ -363,11 +374,12 @@ GPA_API int reproj_jvp(const float* cams, const float* pts, const int32_t* obs, 
 
 /* Fused residual + VJP in one pass over the observations: res as
  * reproj_residual, then d_cams / d_pts += J^T (wscale * res) (the Gauss-Newton
- * gradient of wscale * |res|^2 / 2 when wscale = 1). */
+ * gradient of wscale * |res|^2 / 2 when wscale = 1). obs_order: the order of
+ * tgt and res (GPA_OBS_PLAN needs SORT). */
 GPA_API int reproj_residual_vjp(const float* cams, const float* pts, const int32_t* obs,
                         const float* tgt, int32_t n_cams, int32_t n_pts, int64_t n_obs,
                         float wscale, float* res, float* d_cams, float* d_pts, int32_t strat,
-                        const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
+                        const void* plan, int32_t obs_order, void* ws, size_t ws_bytes, int32_t* dev_status,
                         gpa_stream_t stream);
 
 /*

@@ -51,10 +51,11 @@ _SIGS = {
                                      _P], _I32),
     "gpa_reproj_workspace_bytes": ([_I32, _I32, _I64], _SZ),
     "reproj_residual": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
-    "reproj_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
-    "reproj_residual_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _F, _P, _P, _P, _I32, _P, _P, _SZ, _P, _P], _I32),
+    "reproj_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _I32, _P, _SZ, _P, _P], _I32),
+    "reproj_residual_vjp": ([_P, _P, _P, _P, _I32, _I32, _I64, _F, _P, _P, _P, _I32, _P, _I32, _P, _SZ, _P, _P],
+                            _I32),
     "reproj_jvp": ([_P, _P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _SZ, _P, _P], _I32),
-    "reproj_residual_sorted": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _P, _SZ, _P, _P], _I32),
+    "reproj_residual_sorted": ([_P, _P, _P, _P, _I32, _I32, _I64, _P, _P, _I32, _P, _SZ, _P, _P], _I32),
     "gpa_reproj_gn_workspace_bytes": ([_I32, _I32, _I64], _SZ),
     "reproj_normal_eqs": ([_P] * 4 + [_I32, _I32, _I64] + [_P] * 3 + [_I32, _I32] + [_P] * 3 + [_I32, _P, _P, _SZ, _P, _P],
                           _I32),
@@ -394,9 +395,23 @@ def _reproj_params(cams, pts, obs):
     return cams.shape[0], pts.shape[0], obs.shape[0]
 
 
-def reproj_residual(cams, pts, obs, tgt, res=None, plan=None, ws=None, status=None, stream=None):
+OBS_ORDERS = {"input": 0, "plan": 1}
+
+
+def _obs_order(order):
+    if order not in OBS_ORDERS:
+        raise ValueError(f"obs_order must be 'input' or 'plan', got {order!r}")
+    return OBS_ORDERS[order]
+
+
+def reproj_residual(cams, pts, obs, tgt, res=None, plan=None, obs_order="input", ws=None, status=None,
+                    stream=None):
     """res [M, 2] = projection - target; with a plan (gpa_obs_plan_build) the
-    observations are visited in camera-sorted order (reproj_residual_sorted)."""
+    observations are visited in camera-sorted order (reproj_residual_sorted),
+    and obs_order "plan" takes tgt and writes res in the plan's order."""
+    order = _obs_order(obs_order)
+    if order and plan is None:
+        raise ValueError("obs_order 'plan' needs a plan")
     nc, npt, no = _reproj_params(cams, pts, obs)
     _check(tgt, torch.float32, "tgt", (no, 2))
     res = torch.empty(no, 2, dtype=torch.float32, device=cams.device) if res is None else res
@@ -408,13 +423,15 @@ def reproj_residual(cams, pts, obs, tgt, res=None, plan=None, ws=None, status=No
         _ok(rc, "reproj_residual")
     else:
         rc = load().reproj_residual_sorted(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, _ptr(res),
-                                           _ptr(plan), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+                                           _ptr(plan), order, _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
         _ok(rc, "reproj_residual_sorted")
     return res
 
 
-def reproj_vjp(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=None, ws=None, status=None,
-               stream=None):
+def reproj_vjp(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=None, obs_order="input", ws=None,
+               status=None, stream=None):
+    """d_cams, d_pts += J^T w; obs_order "plan" (SORT) takes w in the plan's order."""
+    order = _obs_order(obs_order)
     nc, npt, no = _reproj_params(cams, pts, obs)
     _check(w, torch.float32, "w", (no, 2))
     d_cams = torch.zeros(nc, 11, dtype=torch.float32, device=cams.device) if d_cams is None else d_cams
@@ -424,7 +441,7 @@ def reproj_vjp(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto", plan=No
     ws = workspace(gpa_reproj_workspace_bytes(nc, npt, no), cams.device) if ws is None else ws
     st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
     rc = load().reproj_vjp(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(w), nc, npt, no, _ptr(d_cams), _ptr(d_pts), st,
-                           _ptr(plan), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+                           _ptr(plan), order, _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "reproj_vjp")
     return d_cams, d_pts
 
@@ -512,7 +529,10 @@ def reproj_vjp_noalloc(cams, pts, obs, w, d_cams=None, d_pts=None, strat="auto",
 
 
 def reproj_residual_vjp(cams, pts, obs, tgt, wscale=1.0, res=None, d_cams=None, d_pts=None, strat="auto",
-                        plan=None, ws=None, status=None, stream=None):
+                        plan=None, obs_order="input", ws=None, status=None, stream=None):
+    """res and d_cams, d_pts += J^T (wscale res) in one pass; obs_order "plan"
+    (SORT) takes tgt and writes res in the plan's order."""
+    order = _obs_order(obs_order)
     nc, npt, no = _reproj_params(cams, pts, obs)
     _check(tgt, torch.float32, "tgt", (no, 2))
     res = torch.empty(no, 2, dtype=torch.float32, device=cams.device) if res is None else res
@@ -521,8 +541,8 @@ def reproj_residual_vjp(cams, pts, obs, tgt, wscale=1.0, res=None, d_cams=None, 
     ws = workspace(gpa_reproj_workspace_bytes(nc, npt, no), cams.device) if ws is None else ws
     st = STRATEGIES[strat] if isinstance(strat, str) else int(strat)
     rc = load().reproj_residual_vjp(_ptr(cams), _ptr(pts), _ptr(obs), _ptr(tgt), nc, npt, no, float(wscale),
-                                    _ptr(res), _ptr(d_cams), _ptr(d_pts), st, _ptr(plan), _ptr(ws), ws.numel(),
-                                    _ptr(status), _stream(stream))
+                                    _ptr(res), _ptr(d_cams), _ptr(d_pts), st, _ptr(plan), order, _ptr(ws),
+                                    ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "reproj_residual_vjp")
     return res, d_cams, d_pts
 

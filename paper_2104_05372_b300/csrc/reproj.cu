@@ -503,7 +503,10 @@ __device__ __forceinline__ void seg_scan11(float (&v)[11], int key) {
 }
 
 // VJP = false (with FUSED): the residual alone, in camera-sorted order.
-template <bool FUSED, bool VJP = true>
+// PORD: the per-observation arrays (w, tgt, res) are indexed by plan position
+// (row i belongs to observation perm[i]) instead of by observation: they are
+// read and written contiguously and the permutation is not read at all.
+template <bool FUSED, bool VJP = true, bool PORD = false>
 __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
     const float* __restrict__ rec, const float* __restrict__ pts, const float4* __restrict__ pts4,
     const float2* __restrict__ wv,
@@ -520,7 +523,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
         if (pos0 + kOpt <= n_obs) {  // plan arrays are 256-byte aligned, pos0 a multiple of 8
 #pragma unroll
             for (int h = 0; h < kOpt / 4; ++h) {
-                const int4 e4 = __ldg(reinterpret_cast<const int4*>(perm + pos0) + h);
+                const int4 e4 = PORD ? make_int4(0, 0, 0, 0) : __ldg(reinterpret_cast<const int4*>(perm + pos0) + h);
                 const int4 c4 = __ldg(reinterpret_cast<const int4*>(key_s + pos0) + h);
                 const int4 p4 = __ldg(reinterpret_cast<const int4*>(aux_s + pos0) + h);
                 ev[4 * h] = e4.x; ev[4 * h + 1] = e4.y; ev[4 * h + 2] = e4.z; ev[4 * h + 3] = e4.w;
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
 #pragma unroll
             for (int i = 0; i < kOpt; ++i) {
                 const bool in = pos0 + i < n_obs;
-                ev[i] = in ? __ldg(perm + pos0 + i) : -1;
+                ev[i] = !in ? -1 : PORD ? 0 : __ldg(perm + pos0 + i);
                 cv[i] = in ? __ldg(key_s + pos0 + i) : -1;
                 pv[i] = in ? __ldg(aux_s + pos0 + i) : -1;
             }
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
             wq[i] = make_float2(0.f, 0.f);
             if (ok) {
                 load_point_any(pts4, pts, pv[i], pts8, xq[i][0], xq[i][1], xq[i][2]);
-                wq[i] = __ldg((FUSED ? tgt : wv) + ev[i]);
+                wq[i] = __ldg((FUSED ? tgt : wv) + (PORD ? pos0 + i : (int64_t)ev[i]));
             }
         }
         float gc[11];
@@ -558,7 +561,8 @@ __global__ void __launch_bounds__(256) reproj_vjp_sorted_kernel(
 #pragma unroll
         for (int i = 0; i < kOpt; ++i) {
             if (pos0 + i >= n_obs) break;
-            const int e = ev[i], ci = cv[i], pi = pv[i];
+            const int ci = cv[i], pi = pv[i];
+            const int64_t e = PORD ? pos0 + i : (int64_t)ev[i];  // row of the per-observation arrays
             const bool e_ok = e >= 0 && e < n_obs;
             if (!e_ok || ci < 0 || ci >= n_cams || pi < 0 || pi >= n_pts) {
                 if (FUSED && e_ok) res[e] = make_float2(NAN, NAN);
@@ -840,13 +844,21 @@ static int launch_vjp(const float* rec, const float* pts, const float4* pts4, co
 template <bool FUSED>
 static int launch_vjp_sorted(const float* rec, const float* pts, const float4* pts4, const float* w, const float* tgt, float wscale,
                              int n_cams, int n_pts, int64_t n_obs, const PlanView& pv, float* d_cams, float* d_pts,
-                             float4* d_pts4, float* res, int32_t* status, cudaStream_t s) {
+                             float4* d_pts4, float* res, int32_t* status, cudaStream_t s, int obs_order = 0) {
     const int64_t want = (n_obs + 256 * kOpt - 1) / (256 * kOpt), cap = (int64_t)sm_count() * 8;
-    GPA_LAUNCH(FUSED ? "reproj_residual_vjp" : "reproj_vjp", s,
-               reproj_vjp_sorted_kernel<FUSED><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
-                   rec, pts, pts4, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts, n_obs, pv.perm,
-                   pv.key_sorted, pv.aux_sorted, d_cams, d_pts, d_pts4, (float2*)res, status, al_dev(pts, 8) ? 1 : 0,
-                   al_dev(d_pts, 8) ? 1 : 0));
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    if (obs_order)
+        GPA_LAUNCH(FUSED ? "reproj_residual_vjp" : "reproj_vjp", s,
+                   (reproj_vjp_sorted_kernel<FUSED, true, true><<<grid, 256, 0, s>>>(
+                       rec, pts, pts4, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts, n_obs, pv.perm,
+                       pv.key_sorted, pv.aux_sorted, d_cams, d_pts, d_pts4, (float2*)res, status,
+                       al_dev(pts, 8) ? 1 : 0, al_dev(d_pts, 8) ? 1 : 0)));
+    else
+        GPA_LAUNCH(FUSED ? "reproj_residual_vjp" : "reproj_vjp", s,
+                   reproj_vjp_sorted_kernel<FUSED><<<grid, 256, 0, s>>>(
+                       rec, pts, pts4, (const float2*)w, (const float2*)tgt, wscale, n_cams, n_pts, n_obs, pv.perm,
+                       pv.key_sorted, pv.aux_sorted, d_cams, d_pts, d_pts4, (float2*)res, status,
+                       al_dev(pts, 8) ? 1 : 0, al_dev(d_pts, 8) ? 1 : 0));
     return GPA_OK;
 }
 
@@ -858,7 +870,7 @@ static int dispatch_vjp(int strat, const float* rec, const float* pts, const flo
                         const float* w,
                         const float* tgt, float wscale, int n_cams, int n_pts, int64_t n_obs,
                         const PlanView& pv, float* d_cams, float* d_pts, float4* d_pts4, float* res,
-                        int32_t* status, cudaStream_t s) {
+                        int32_t* status, cudaStream_t s, int obs_order = 0) {
     int rc = GPA_ERR_ARG;
     switch (strat) {
         case GPA_SCATTER_ATOMIC:
@@ -871,7 +883,7 @@ static int dispatch_vjp(int strat, const float* rec, const float* pts, const flo
             break;
         case GPA_SCATTER_SORT:
             rc = launch_vjp_sorted<FUSED>(rec, pts, pts4, w, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams, d_pts, d_pts4,
-                                          res, status, s);
+                                          res, status, s, obs_order);
             break;
     }
     if (rc || !d_pts4) return rc;
@@ -943,10 +955,11 @@ extern "C" int reproj_residual(const float* cams, const float* pts, const int32_
 
 extern "C" int reproj_residual_sorted(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
                                       int32_t n_cams, int32_t n_pts, int64_t n_obs, float* res, const void* plan,
-                                      void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
+                                      int32_t obs_order, void* ws, size_t ws_bytes, int32_t* dev_status,
+                                      gpa_stream_t stream) {
     int rc = reproj_check(cams, pts, obs, n_cams, n_pts, n_obs, ws, ws_bytes);
     if (rc) return rc;
-    if (!tgt || !res || !plan) return GPA_ERR_ARG;
+    if (!tgt || !res || !plan || (obs_order != 0 && obs_order != 1)) return GPA_ERR_ARG;
     if (!al(tgt, 8) || !al(res, 8)) return GPA_ERR_ALIGN;
     cudaStream_t s = (cudaStream_t)stream;
     float* rec = (float*)ws;
@@ -955,10 +968,17 @@ extern "C" int reproj_residual_sorted(const float* cams, const float* pts, const
     if (rc) return rc;
     const PlanView pv = plan_view(plan, n_obs, n_cams);
     const int64_t want = (n_obs + 256 * kOpt - 1) / (256 * kOpt), cap = (int64_t)sm_count() * 8;
-    GPA_LAUNCH("reproj_residual_sorted", s,
-               (reproj_vjp_sorted_kernel<true, false><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(
-                   rec, pts, pts4, nullptr, (const float2*)tgt, 1.f, n_cams, n_pts, n_obs, pv.perm, pv.key_sorted,
-                   pv.aux_sorted, nullptr, nullptr, nullptr, (float2*)res, dev_status, al_dev(pts, 8) ? 1 : 0, 0)));
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    if (obs_order)
+        GPA_LAUNCH("reproj_residual_sorted", s,
+                   (reproj_vjp_sorted_kernel<true, false, true><<<grid, 256, 0, s>>>(
+                       rec, pts, pts4, nullptr, (const float2*)tgt, 1.f, n_cams, n_pts, n_obs, pv.perm, pv.key_sorted,
+                       pv.aux_sorted, nullptr, nullptr, nullptr, (float2*)res, dev_status, al_dev(pts, 8) ? 1 : 0, 0)));
+    else
+        GPA_LAUNCH("reproj_residual_sorted", s,
+                   (reproj_vjp_sorted_kernel<true, false><<<grid, 256, 0, s>>>(
+                       rec, pts, pts4, nullptr, (const float2*)tgt, 1.f, n_cams, n_pts, n_obs, pv.perm, pv.key_sorted,
+                       pv.aux_sorted, nullptr, nullptr, nullptr, (float2*)res, dev_status, al_dev(pts, 8) ? 1 : 0, 0)));
     return GPA_OK;
 }
 
@@ -969,14 +989,15 @@ static int resolve_strat(int strat, const void* plan) {
 
 extern "C" int reproj_vjp(const float* cams, const float* pts, const int32_t* obs, const float* w,
                           int32_t n_cams, int32_t n_pts, int64_t n_obs, float* d_cams, float* d_pts,
-                          int32_t strat, const void* plan, void* ws, size_t ws_bytes, int32_t* dev_status,
-                          gpa_stream_t stream) {
+                          int32_t strat, const void* plan, int32_t obs_order, void* ws, size_t ws_bytes,
+                          int32_t* dev_status, gpa_stream_t stream) {
     int rc = reproj_check(cams, pts, obs, n_cams, n_pts, n_obs, ws, ws_bytes);
     if (rc) return rc;
     if (!w || !d_cams || !d_pts) return GPA_ERR_ARG;
     if (!al(w, 8)) return GPA_ERR_ALIGN;
     strat = resolve_strat(strat, plan);
     if (strat < GPA_SCATTER_ATOMIC || strat > GPA_SCATTER_SORT) return GPA_ERR_ARG;
+    if (obs_order != 0 && (obs_order != 1 || strat != GPA_SCATTER_SORT)) return GPA_ERR_ARG;
     PlanView pv{};
     if (strat == GPA_SCATTER_SORT) {
         if (!plan) return GPA_ERR_ARG;
@@ -989,7 +1010,7 @@ extern "C" int reproj_vjp(const float* cams, const float* pts, const int32_t* ob
     rc = vjp_prep(cams, n_cams, rec, pts, n_pts, pts4, acc, s);
     if (rc) return rc;
     return dispatch_vjp<false>(strat, rec, pts, pts4, obs, w, nullptr, 1.f, n_cams, n_pts, n_obs, pv, d_cams, d_pts,
-                               acc, nullptr, dev_status, s);
+                               acc, nullptr, dev_status, s, obs_order);
 }
 
 extern "C" int reproj_jvp(const float* cams, const float* pts, const int32_t* obs, const float* v_cams,
@@ -1012,14 +1033,15 @@ extern "C" int reproj_jvp(const float* cams, const float* pts, const int32_t* ob
 
 extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const int32_t* obs, const float* tgt,
                                    int32_t n_cams, int32_t n_pts, int64_t n_obs, float wscale, float* res,
-                                   float* d_cams, float* d_pts, int32_t strat, const void* plan, void* ws,
-                                   size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
+                                   float* d_cams, float* d_pts, int32_t strat, const void* plan, int32_t obs_order,
+                                   void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
     int rc = reproj_check(cams, pts, obs, n_cams, n_pts, n_obs, ws, ws_bytes);
     if (rc) return rc;
     if (!tgt || !res || !d_cams || !d_pts) return GPA_ERR_ARG;
     if (!al(tgt, 8) || !al(res, 8)) return GPA_ERR_ALIGN;
     strat = resolve_strat(strat, plan);
     if (strat < GPA_SCATTER_ATOMIC || strat > GPA_SCATTER_SORT) return GPA_ERR_ARG;
+    if (obs_order != 0 && (obs_order != 1 || strat != GPA_SCATTER_SORT)) return GPA_ERR_ARG;
     PlanView pv{};
     if (strat == GPA_SCATTER_SORT) {
         if (!plan) return GPA_ERR_ARG;
@@ -1032,7 +1054,7 @@ extern "C" int reproj_residual_vjp(const float* cams, const float* pts, const in
     rc = vjp_prep(cams, n_cams, rec, pts, n_pts, pts4, acc, s);
     if (rc) return rc;
     return dispatch_vjp<true>(strat, rec, pts, pts4, obs, nullptr, tgt, wscale, n_cams, n_pts, n_obs, pv, d_cams,
-                              d_pts, acc, res, dev_status, s);
+                              d_pts, acc, res, dev_status, s, obs_order);
 }
 
 extern "C" size_t gpa_reproj_gn_workspace_bytes(int32_t n_cams, int32_t n_pts, int64_t n_obs) {

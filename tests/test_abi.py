@@ -78,8 +78,13 @@ def test_host_argument_errors_return_before_any_launch(lib):
                              1 << 20, None, None) == 7
     # reprojection: non-positive sizes, bad strategy, SORT without a plan
     assert lib.reproj_residual(fake, fake, fake, fake, 0, 1, 1, fake, fake, 1 << 20, None, None) == 1
-    assert lib.reproj_vjp(fake, fake, fake, fake, 2, 2, 2, fake, fake, 9, None, fake, 1 << 20, None, None) == 1
-    assert lib.reproj_vjp(fake, fake, fake, fake, 2, 2, 2, fake, fake, 3, None, fake, 1 << 20, None, None) == 1
+    assert lib.reproj_vjp(fake, fake, fake, fake, 2, 2, 2, fake, fake, 9, None, 0, fake, 1 << 20, None, None) == 1
+    assert lib.reproj_vjp(fake, fake, fake, fake, 2, 2, 2, fake, fake, 3, None, 0, fake, 1 << 20, None, None) == 1
+    # plan-ordered cotangents need the SORT strategy; orders other than 0, 1
+    assert lib.reproj_vjp(fake, fake, fake, fake, 2, 2, 2, fake, fake, 1, None, 1, fake, 1 << 20, None, None) == 1
+    assert lib.reproj_vjp(fake, fake, fake, fake, 2, 2, 2, fake, fake, 3, fake, 2, fake, 1 << 20, None, None) == 1
+    assert lib.reproj_residual_vjp(fake, fake, fake, fake, 2, 2, 2, 1.0, fake, fake, fake, 2, None, 1, fake,
+                                   1 << 20, None, None) == 1
     # scatter: w out of range, bad dtype
     assert lib.accum_scatter_add(fake, fake, 10, 65, 0, fake, 4, 1, None, None, None) == 1
     assert lib.accum_scatter_add(fake, fake, 10, 1, 2, fake, 4, 1, None, None, None) == 1

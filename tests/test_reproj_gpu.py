@@ -352,3 +352,34 @@ def test_point_arrays_aligned_to_four_bytes_only(strat):
         assert rel_norm(host(a), b) <= TOL_GRAD_FP32
     ref32, _ = oracle.reproj_jvp(r, vc.astype(np.float32).astype(np.float64), vp.astype(np.float32).astype(np.float64))
     assert rel_norm(jv, ref32) <= 1e-5
+
+
+def test_plan_ordered_arrays_match_input_order():
+    """obs_order 'plan': the cotangents, targets and residuals indexed by plan
+    position (row i = observation perm[i]) give the same cotangent sums as the
+    input order, and the residuals are the input-order residuals permuted."""
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300._lib import plan_arrays
+    r = synth.reproj_inputs(300, 4000, 60013, seed=31)
+    obs = r.obs.copy()
+    obs[[5, 77]] = [[300, 1], [2, 4000]]  # two observations outside their index sets
+    cams, pts, o, tgt, w = dev(r.cams), dev(r.pts), dev(obs), dev(r.tgt), dev(r.w)
+    plan = gpa.gpa_obs_plan_build(o, 300, 4000)
+    perm = plan_arrays(plan, r.n_obs, 300)[1].long()
+    ref_c, ref_p = gpa.reproj_vjp(cams, pts, o, w, strat="sort", plan=plan)
+    st = status()
+    got_c, got_p = gpa.reproj_vjp(cams, pts, o, w[perm].contiguous(), strat="sort", plan=plan, obs_order="plan",
+                                  status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 2  # GPA_ERR_INDEX for the two bad observations
+    assert rel_norm(host(got_c), host(ref_c)) <= 1e-6 and rel_norm(host(got_p), host(ref_p)) <= 1e-6
+    res = gpa.reproj_residual(cams, pts, o, tgt)
+    res_p = gpa.reproj_residual(cams, pts, o, tgt[perm].contiguous(), plan=plan, obs_order="plan")
+    assert np.array_equal(host(res_p), host(res)[host(perm)], equal_nan=True)
+    rf, fc, fp = gpa.reproj_residual_vjp(cams, pts, o, tgt, 0.5, strat="sort", plan=plan)
+    rfp, fcp, fpp = gpa.reproj_residual_vjp(cams, pts, o, tgt[perm].contiguous(), 0.5, strat="sort", plan=plan,
+                                            obs_order="plan")
+    assert np.array_equal(host(rfp), host(rf)[host(perm)], equal_nan=True)
+    assert rel_norm(host(fcp), host(fc)) <= 1e-6 and rel_norm(host(fpp), host(fp)) <= 1e-6
+    with pytest.raises(gpa.GpaError):
+        gpa.reproj_vjp(cams, pts, o, w, strat="atomic", obs_order="plan")
