@@ -2,35 +2,13 @@
 // contractions run as tcgen05 MMAs with BF16 operands in shared memory and FP32
 // accumulators in tensor memory; logsumexp, exponentials and every sum over
 // points stay FP32 / FP64 on the CUDA cores. Padded dimension TDP = 64
-// (32 < D <= 64) or 128 (64 < D <= 128). Every MMA is M = N = 128: with TDP = 64
-// two components share one 128-row operand (CPR = 128 / TDP components per
-// block of rows).
+// (32 < D <= 64) or 128 (64 < D <= 128).
 //
-// Forward (A1): Z = X Q_k^T per 128-point tile, with split-BF16 operands:
-// x = x_hi + x_lo and Q = Q_hi + Q_lo (each part BF16), and three MMAs per K
-// step (hi*hi + lo*hi + hi*lo), which keeps about 16 bits of the FP32 inputs --
-// a single BF16 pass leaves log-joint errors of ~0.4 at D = 128, i.e. ~40 %
-// errors in the responsibilities exp(s - lse). Warp roles in a 192-thread CTA:
-// warp 0 issues TMA loads (the point tile once, then each round's Q rows and
-// the b_k / constants through a ring of FQ stages: four at TDP = 64, two at
-// TDP = 128, where shared memory holds no more), warp 1 owns the TMEM allocation
-// and one of its lanes issues the MMAs (M=128 points, N=128 rows of CPR
-// components, K=TDP in steps of 16, 3 passes each) into a double-buffered
-// accumulator, warps 2-5 read the accumulator back (TMEM lane = point, one
-// thread per point) and fold |z - b_k|^2 into the log-joint and an online
-// logsumexp.
-//
-// Backward (A2): the Accum sums of a component, centred on its mean,
-//   C_k = sum_i r_ik (x_i - mu_k)(x_i - mu_k)^T,  m'_k = sum_i r_ik (x_i - mu_k),
-//   R_k = sum_i r_ik,
-// with C_k = U_k^T U_k for U_k[p][a] = sqrt(r_pk) (x_p - mu_k)[a] (x read in
-// FP32, U rounded once to BF16; r from the forward's log-joint). Sixteen
-// producer warps build the 128-row blocks [U_k^T; ...] (CPR components stacked,
-// points contiguous) directly in the 128-byte-swizzled layout the MMA reads; one
-// MMA thread accumulates D += U^T U (A and B the same tile) in TMEM for four
-// blocks across every tile of a point chunk, of which the diagonal TDP x TDP
-// blocks are the C_k. The partial sums go to the same buffers the FP32 finalize
-// reads (centred mode).
+// Forward (A1): z_ik = Q_k x_i - b_k for a 128-point tile against every
+// component, as N = 256 MMAs over the nonzero blocks of the triangular Q_k with
+// split-BF16 operands (gmm_tc_fwd_kernel). Backward (A2): the Accum sums of the
+// reverse pass as the single contraction Y^T R over the points
+// (gmm_tc_gram_kernel). Each kernel's comment gives its layout and warp roles.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -50,15 +28,10 @@ namespace {
 
 constexpr int TM = 128;                          // points per tile; rows of every MMA operand
 constexpr uint32_t ATOM = TM * 128;              // one 64-wide K slice of a 128-row operand: 16 KB
-constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 128);
 
 template <int TDP>
 struct Tc {
-    static constexpr int NA = TDP / 64;                  // 64-wide K slices per row
-    static constexpr int CPR = 128 / TDP;                // components per 128-row block
-    static constexpr uint32_t TILE = NA * ATOM;          // a 128-row operand of K = TDP
     static constexpr int REC = TDP * TDP + TDP + 4;      // FP32 prep record (b at TDP*TDP, cst after)
-    static constexpr uint32_t TAIL = (TDP + 4) * 4;      // b_k, constant, pad
 };
 
 // The dynamic shared array advanced to the next 1024-byte boundary (the
@@ -70,199 +43,282 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 }
 
 // ---- forward ------------------------------------------------------------------
+// Z = X Q_k^T per 128-point tile with split-BF16 operands: x = x_hi + x_lo and
+// Q = Q_hi + Q_lo (each part BF16), three products per K step (x_hi Q_hi,
+// x_lo Q_hi, x_hi Q_lo), which keeps about 16 bits of the FP32 inputs -- a
+// single BF16 pass leaves log-joint errors of ~0.4 at D = 128, i.e. ~40 %
+// errors in the responsibilities exp(s - lse).
+//
+// Q_k is lower triangular, so the first half of the rows of z = Q_k x (RPC =
+// TDP / 2 rows) needs only the first half of the columns of Q_k. A round takes
+// CR = 256 / RPC components (4 at TDP = 128, 8 at TDP = 64) and stacks their
+// rows into two 256-row MMA operands: L = the first RPC rows of each component
+// over K = 0 .. RPC - 1, H = the last RPC rows of each over K = 0 .. TDP - 1.
+// The zero blocks are never multiplied, and every MMA is M = 128, N = 256: a
+// single issuing thread needs about 100 cycles per tcgen05.mma, more than an
+// N = 128 MMA takes to execute (64 cycles), so narrower MMAs leave the tensor
+// pipe ~40 % idle.
+//
+// Pipeline stages are 32 KB operand atoms (256 rows x 64 columns; CR TMA boxes
+// of RPC rows), 2 + 2 NA per round (NA = TDP / 64 column atoms): L of Q_hi, L
+// of Q_lo, then H of Q_hi and of Q_lo per column atom. The L phase
+// accumulates in TMEM columns 0..255 and the H phase in 256..511 (component c
+// at RPC c within each), so the epilogue reads the L phase of a round while
+// the MMAs of its H phase run, and the H phase while the next round's L phase
+// runs. The b_k tails of a round travel with its first stage into a ring of
+// FT slots, which the epilogue releases; the Q stages are released by the MMAs.
+//
+// Warp roles (320 threads): warp 0 issues the TMA loads, one lane of warp 1
+// the MMAs (warp 1 also owns the TMEM allocation), warps 2-9 read the
+// accumulators back, one thread per point (TMEM lane) and half of the round's
+// components, and fold |z - b_k|^2 into the log-joint and an online logsumexp.
 template <int TDP>
 struct FwdSm {
-    using T = Tc<TDP>;
-    // Q stages (hi and lo parts and the b_k tails each). A stage is refilled
-    // only after the epilogue has read its tails, so the ring must cover the
-    // epilogue's lag plus a TMA round trip: four stages where shared memory
-    // allows (TDP = 64), two at TDP = 128.
-    static constexpr int FQ = TDP == 64 ? 4 : 2;
-    static constexpr uint32_t X = 0;                            // x_hi, x_lo tiles
-    static constexpr uint32_t Q = X + 2 * T::TILE;              // [FQ] x (Q_hi, Q_lo)
-    static constexpr uint32_t B = Q + FQ * 2 * T::TILE;         // [FQ][CPR] tails
-    static constexpr uint32_t RED = B + FQ * T::CPR * T::TAIL;
-    static constexpr uint32_t BAR = RED + 8 * 8;  // x_full, q_full[FQ], q_empty[FQ], acc_full[2], acc_empty[2]
-    static_assert(1 + 2 * FQ + 4 <= 16, "barrier slots");
-    static constexpr uint32_t TMEMP = BAR + 16 * 8;
+    static constexpr int NA = TDP / 64;                           // 64-wide column atoms of a Q row
+    static constexpr int RPC = TDP / 2;                           // rows per component in L and in H
+    static constexpr int CR = 256 / RPC;                          // components per round
+    static constexpr int LK = RPC / 16;                           // K steps of the L phase
+    static constexpr int NS = 2 + 2 * NA;                         // stages per round
+    static constexpr int FQ = TDP == 64 ? 5 : 4;                  // Q stages
+    static constexpr int FT = 4;                                  // tail slots (rounds)
+    static constexpr int EW = 8;                                  // epilogue warps
+    static constexpr uint32_t STG = 2 * ATOM;                     // 256 rows x 128 bytes
+    static constexpr uint32_t TAIL = (TDP + 4) * 4;               // b_k, constant, pad
+    static constexpr uint32_t X = 0;                              // x_hi, x_lo tiles (NA atoms each)
+    static constexpr uint32_t Q = X + 2 * NA * ATOM;              // [FQ] stages
+    static constexpr uint32_t B = Q + FQ * STG;                   // [FT][CR] tails
+    static constexpr uint32_t RED = B + FT * CR * TAIL;
+    static constexpr uint32_t MRG = RED + 8 * 8;                  // [128] (max, sum) of warps 6-9
+    static constexpr uint32_t BAR = MRG + 128 * 8;  // x_full, q_full[FQ], q_empty[FQ], l_full, l_empty, h_full,
+                                                    // h_empty, t_empty[FT]
+    static_assert(1 + 2 * FQ + 4 + FT <= 32, "barrier slots");
+    static constexpr uint32_t TMEMP = BAR + 32 * 8;
     static constexpr uint32_t FLAG = TMEMP + 8;
     static constexpr uint32_t END = FLAG + 8;
-    static constexpr size_t SMEM = END + 1024;  // + alignment slack
+    static constexpr size_t SMEM = END + 1024;
     static_assert(SMEM <= 227 * 1024, "forward shared memory");
+    static_assert(Q % 1024 == 0 && STG % 1024 == 0 && TAIL % 16 == 0, "operand and copy alignment");
+    static_assert(CR * RPC == 256 && (CR / 2) * RPC == 128, "a round fills N = 256; each epilogue warp 128 columns");
 };
 
+// a shared-memory descriptor advanced by `bytes` (the start address field is
+// addr >> 4 in 14 bits; operands stay below 256 KB, so the sum never carries
+// into the next field)
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+
+// sum over CNT rows (columns off .. of a 64-column TMEM chunk) of (z - b)^2,
+// z as raw FP32 bits from tcgen05.ld; off must fold to a constant where this
+// is inlined (every caller's loop is unrolled), so v stays in registers
+template <int CNT>
+__device__ __forceinline__ float sumsq_rows(const uint32_t (&v)[64], int off, const float* __restrict__ b) {
+    const float2 neg1 = make_float2(-1.f, -1.f);
+    float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int i = 0; i < CNT; i += 4) {
+        const float4 b4 = *reinterpret_cast<const float4*>(b + i);
+        const float2 z0 = __ffma2_rn(make_float2(b4.x, b4.y), neg1,
+                                     make_float2(__uint_as_float(v[off + i]), __uint_as_float(v[off + i + 1])));
+        const float2 z1 = __ffma2_rn(make_float2(b4.z, b4.w), neg1,
+                                     make_float2(__uint_as_float(v[off + i + 2]), __uint_as_float(v[off + i + 3])));
+        acc[(i >> 2) & 1] = __ffma2_rn(z0, z0, acc[(i >> 2) & 1]);
+        acc[2 + ((i >> 2) & 1)] = __ffma2_rn(z1, z1, acc[2 + ((i >> 2) & 1)]);
+    }
+    const float2 t = __fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3]));
+    return t.x + t.y;
+}
+
 template <int TDP>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
     gmm_tc_fwd_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmxl,
                       const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmql,
                       const float* __restrict__ rec, int64_t n, int64_t xrow0, int k, float* __restrict__ lj,
                       int64_t lj_ld, float* __restrict__ lse_out, double* __restrict__ part, int64_t tile0,
                       int32_t* __restrict__ status) {
-    using T = Tc<TDP>;
     using S = FwdSm<TDP>;
-    constexpr int FQ = S::FQ;
+    constexpr int FQ = S::FQ, FT = S::FT, NA = S::NA, RPC = S::RPC, CR = S::CR, NS = S::NS;
+    constexpr int REC = Tc<TDP>::REC;
+    constexpr uint32_t IDESC256 = tc::idesc_bf16_f32(128, 256);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::BAR);
     uint64_t* x_full = bars;
     uint64_t* q_full = bars + 1;
     uint64_t* q_empty = bars + 1 + FQ;
-    uint64_t* acc_full = bars + 1 + 2 * FQ;
-    uint64_t* acc_empty = bars + 3 + 2 * FQ;
+    uint64_t* l_full = bars + 1 + 2 * FQ;
+    uint64_t* l_empty = l_full + 1;
+    uint64_t* h_full = l_full + 2;
+    uint64_t* h_empty = l_full + 3;
+    uint64_t* t_empty = l_full + 4;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sm + S::TMEMP);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + S::FLAG);
     double* red = reinterpret_cast<double*>(sm + S::RED);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t p0 = (int64_t)blockIdx.x * TM;
-    const int rounds = (k + T::CPR - 1) / T::CPR;
+    const int rounds = (k + CR - 1) / CR;
 
     if (threadIdx.x == 0) {
         mbar_init(x_full, 1);
         for (int s = 0; s < FQ; ++s) {
             mbar_init(&q_full[s], 1);
-            mbar_init(&q_empty[s], 1 + 4);  // MMA commit + 4 epilogue warps (they read b_k)
+            mbar_init(&q_empty[s], 1);  // MMA commit
         }
-        for (int a = 0; a < 2; ++a) {
-            mbar_init(&acc_full[a], 1);
-            mbar_init(&acc_empty[a], 4);
-        }
+        mbar_init(l_full, 1);
+        mbar_init(h_full, 1);
+        mbar_init(l_empty, S::EW);
+        mbar_init(h_empty, S::EW);
+        for (int t = 0; t < FT; ++t) mbar_init(&t_empty[t], S::EW);
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 1) {
-        tc::tmem_alloc(tmem_holder, 256);
+        tc::tmem_alloc(tmem_holder, 512);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
+    Lse st;  // epilogue threads: online logsumexp over the components they read
+    st.init();
 
     if (warp == 0) {
         if (lane == 0) {
-            mbar_arrive_expect_tx(x_full, 2 * T::TILE);
-            for (int a = 0; a < T::NA; ++a) {
+            mbar_arrive_expect_tx(x_full, 2 * NA * ATOM);
+            for (int a = 0; a < NA; ++a) {
                 tc::tma_load_2d(sm + S::X + a * ATOM, &tmx, 64 * a, (int)(xrow0 + p0), x_full);
-                tc::tma_load_2d(sm + S::X + T::TILE + a * ATOM, &tmxl, 64 * a, (int)(xrow0 + p0), x_full);
+                tc::tma_load_2d(sm + S::X + (NA + a) * ATOM, &tmxl, 64 * a, (int)(xrow0 + p0), x_full);
             }
-            for (int r = 0; r < rounds; ++r) {
-                const int s = r % FQ;
-                const uint32_t ph = (uint32_t)(r / FQ) & 1u;
-                if (!mbar_wait(&q_empty[s], ph ^ 1u, status)) {
+            // stage g: atom a = g % NS of round g / NS -- L of Q_hi, L of Q_lo,
+            // H of Q_hi per column atom, H of Q_lo per column atom
+            for (int g = 0; g < NS * rounds; ++g) {
+                const int r = g / NS, a = g - NS * r, s = g % FQ, ts = r % FT;
+                const uint32_t ph = (uint32_t)(g / FQ) & 1u, tph = (uint32_t)(r / FT) & 1u;
+                if (!mbar_wait(&q_empty[s], ph ^ 1u, status) ||
+                    (a == 0 && !mbar_wait(&t_empty[ts], tph ^ 1u, status))) {
                     *abort_flag = 1;
                     break;
                 }
-                const int c0 = r * T::CPR;
-                const int nc = min(T::CPR, k - c0);
-                mbar_arrive_expect_tx(&q_full[s], 2 * T::TILE + nc * T::TAIL);
-                uint8_t* qd = sm + S::Q + s * 2 * T::TILE;
-                for (int a = 0; a < T::NA; ++a) {
-                    tc::tma_load_2d(qd + a * ATOM, &tmq, 64 * a, r * TM, &q_full[s]);
-                    tc::tma_load_2d(qd + T::TILE + a * ATOM, &tmql, 64 * a, r * TM, &q_full[s]);
-                }
-                for (int j = 0; j < nc; ++j)
-                    bulk_g2s(sm + S::B + (s * T::CPR + j) * T::TAIL, rec + (size_t)(c0 + j) * T::REC + TDP * TDP,
-                             T::TAIL, &q_full[s]);
+                const int c0 = CR * r;
+                const int nc = min(CR, k - c0);
+                mbar_arrive_expect_tx(&q_full[s], S::STG + (a == 0 ? (uint32_t)nc * S::TAIL : 0u));
+                const bool lo = a == 1 || a >= 2 + NA;
+                const CUtensorMap* m = lo ? &tmql : &tmq;
+                const int col = a < 2 ? 0 : 64 * ((a - 2) % NA), roff = a < 2 ? 0 : RPC;
+                uint8_t* stg = sm + S::Q + s * S::STG;
+                for (int c = 0; c < CR; ++c)  // components past K read as zero
+                    tc::tma_load_2d(stg + c * RPC * 128, m, col, (c0 + c) * TDP + roff, &q_full[s]);
+                if (a == 0)
+                    for (int c = 0; c < nc; ++c)
+                        bulk_g2s(sm + S::B + (ts * CR + c) * S::TAIL, rec + (size_t)(c0 + c) * REC + TDP * TDP,
+                                 S::TAIL, &q_full[s]);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = mbar_wait(x_full, 0, status);
+            const uint64_t dxh = tc::desc_sw128(smem_u32(sm + S::X)), dxl = desc_add(dxh, NA * ATOM);
+            const uint64_t dq0 = tc::desc_sw128(smem_u32(sm + S::Q));
             for (int r = 0; ok && r < rounds; ++r) {
-                const int s = r % FQ;
-                const uint32_t ph = (uint32_t)(r / FQ) & 1u;
-                const int as = r & 1;
-                const uint32_t aph = (uint32_t)(r >> 1) & 1u;
-                if (!mbar_wait(&q_full[s], ph, status) || !mbar_wait(&acc_empty[as], aph ^ 1u, status)) {
-                    ok = false;
-                    break;
-                }
-                tc::fence_after_sync();
-                const uint32_t xh = smem_u32(sm + S::X), xl = xh + T::TILE;
-                const uint32_t qh = smem_u32(sm + S::Q + s * 2 * T::TILE), ql = qh + T::TILE;
-                const uint32_t dt = tmem + (uint32_t)(as * TM);
+                const uint32_t rph = (uint32_t)r & 1u;
+                for (int a = 0; a < NS; ++a) {
+                    const int g = NS * r + a, s = g % FQ;
+                    const uint32_t ph = (uint32_t)(g / FQ) & 1u;
+                    if ((a == 0 && !mbar_wait(l_empty, rph ^ 1u, status)) ||
+                        (a == 2 && !mbar_wait(h_empty, rph ^ 1u, status)) || !mbar_wait(&q_full[s], ph, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const bool hi = !(a == 1 || a >= 2 + NA);
+                    const uint32_t d = a < 2 ? tmem : tmem + 256u;
+                    const uint32_t xo = a < 2 ? 0u : (uint32_t)((a - 2) % NA) * ATOM;  // x column atom
+                    const uint32_t acc0 = (a == 0 || a == 2) ? 0u : 1u;                // first product into L / H
+                    const int ksteps = a < 2 ? S::LK : 4;
+                    const uint64_t bq = desc_add(dq0, (uint32_t)s * S::STG);
+                    const uint64_t ah = desc_add(dxh, xo), al = desc_add(dxl, xo);
 #pragma unroll
-                for (int j = 0; j < TDP / 16; ++j) {
-                    const uint32_t off = (uint32_t)(j >> 2) * ATOM + (uint32_t)(j & 3) * 32u;
-                    tc::mma_bf16(dt, tc::desc_sw128(xh + off), tc::desc_sw128(qh + off), IDESC, j > 0 ? 1u : 0u);
-                    tc::mma_bf16(dt, tc::desc_sw128(xl + off), tc::desc_sw128(qh + off), IDESC, 1u);
-                    tc::mma_bf16(dt, tc::desc_sw128(xh + off), tc::desc_sw128(ql + off), IDESC, 1u);
+                    for (int ks = 0; ks < 4; ++ks) {
+                        if (ks >= ksteps) break;
+                        const uint32_t ko = (uint32_t)ks * 32u;
+                        tc::mma_bf16(d, desc_add(ah, ko), desc_add(bq, ko), IDESC256, ks == 0 ? acc0 : 1u);
+                        if (hi) tc::mma_bf16(d, desc_add(al, ko), desc_add(bq, ko), IDESC256, 1u);
+                    }
+                    tc::mma_commit(&q_empty[s]);
+                    if (a == 1) tc::mma_commit(l_full);
+                    if (a == NS - 1) tc::mma_commit(h_full);
                 }
-                tc::mma_commit(&acc_full[as]);
-                tc::mma_commit(&q_empty[s]);
             }
             if (!ok) *abort_flag = 1;
         }
         __syncwarp();
     } else {
-        // epilogue: one thread per point (TMEM lane)
+        // epilogue: one thread per point (TMEM lane). Warp w reads TMEM lanes
+        // 32 (w % 4) ..; warps 2-5 take the first CR / 2 components of each
+        // round, warps 6-9 the others: 128 columns per warp and phase, read
+        // as two 64-column chunks of 64 / RPC components each.
+        constexpr int HC = CR / 2, PCH = 64 / RPC;  // components per warp, per chunk
         const int qtr = warp & 3;
+        const int jw = (warp - 2) >> 2;
         const int row = qtr * 32 + lane;
         const bool valid = p0 + row < n;
-        Lse st;
-        st.init();
+        const uint32_t tl = tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(128 * jw);
         for (int r = 0; r < rounds; ++r) {
-            const int s = r % FQ;
-            const int as = r & 1;
-            const uint32_t aph = (uint32_t)(r >> 1) & 1u;
-            if (!mbar_wait_warp(&acc_full[as], aph, status)) {
-                *abort_flag = 1;
-                break;
-            }
-            tc::fence_after_sync();
-            float sv[Tc<TDP>::CPR], cst[Tc<TDP>::CPR];
-            // |z - b|^2 per component: z - b and the squares as packed pairs into
-            // four independent partial sums (no serial chain through one register)
-            const float2 neg1 = make_float2(-1.f, -1.f);
-#pragma unroll
-            for (int j = 0; j < T::CPR; ++j) {
-                const float* bb = reinterpret_cast<const float*>(sm + S::B + (s * T::CPR + j) * T::TAIL);
-                float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
-                                 make_float2(0.f, 0.f)};
-#pragma unroll
-                for (int h = 0; h < TDP / 64; ++h) {  // 64 columns: two loads in flight, one wait
-                    float v[2][32];
-                    tc::tmem_ld64_wait(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(as * TM + j * TDP + h * 64),
-                                       v[0], v[1]);
-#pragma unroll
-                    for (int ch = 0; ch < 2; ++ch)
-#pragma unroll
-                        for (int i = 0; i < 32; i += 4) {
-                            const float4 b4 = *reinterpret_cast<const float4*>(bb + h * 64 + ch * 32 + i);
-                            const float2 z0 =
-                                __ffma2_rn(make_float2(b4.x, b4.y), neg1, make_float2(v[ch][i], v[ch][i + 1]));
-                            const float2 z1 =
-                                __ffma2_rn(make_float2(b4.z, b4.w), neg1, make_float2(v[ch][i + 2], v[ch][i + 3]));
-                            acc[(i >> 2) & 1] = __ffma2_rn(z0, z0, acc[(i >> 2) & 1]);
-                            acc[2 + ((i >> 2) & 1)] = __ffma2_rn(z1, z1, acc[2 + ((i >> 2) & 1)]);
-                        }
+            const uint32_t rph = (uint32_t)r & 1u;
+            const int ts = r % FT;
+            const float* bw = reinterpret_cast<const float*>(sm + S::B + (ts * CR + jw * HC) * S::TAIL);
+            constexpr int TF = S::TAIL / 4;  // floats per tail
+            float sv[HC];
+            uint32_t rv[2][64];
+            // phase L (the first RPC rows of z), then phase H (the rest): the
+            // second chunk's load is in flight while the first is summed
+            for (int ph = 0; ph < 2; ++ph) {
+                if (!mbar_wait_warp(ph == 0 ? l_full : h_full, rph, status)) {
+                    *abort_flag = 1;
+                    break;
                 }
-                const float2 t = __fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3]));
-                sv[j] = t.x + t.y;
-                cst[j] = bb[TDP];
-            }
-            // The stage's b_k tail was read through the generic proxy and the
-            // producer refills it with a bulk copy (async proxy) once q_empty
-            // completes: order the reads before that write.
-            fence_proxy_async_smem();
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) {
-                tc::mbar_arrive(&acc_empty[as]);
-                tc::mbar_arrive(&q_empty[s]);
-            }
+                tc::fence_after_sync();
+                const uint32_t ta = tl + (ph == 0 ? 0u : 256u);
+                tc::tmem_ld64_issue(ta, rv[0]);
+                tc::tmem_ld64_tied_wait(rv[0]);
+                tc::tmem_ld64_issue(ta + 64u, rv[1]);
+                float s2[HC];
 #pragma unroll
-            for (int j = 0; j < T::CPR; ++j) {
-                const int kk = r * T::CPR + j;
+                for (int u = 0; u < PCH; ++u) s2[u] = sumsq_rows<RPC>(rv[0], u * RPC, bw + u * TF + ph * RPC);
+                tc::tmem_ld64_tied_wait(rv[1]);
+#pragma unroll
+                for (int u = 0; u < PCH; ++u)
+                    s2[PCH + u] = sumsq_rows<RPC>(rv[1], u * RPC, bw + (PCH + u) * TF + ph * RPC);
+#pragma unroll
+                for (int u = 0; u < HC; ++u) sv[u] = ph == 0 ? s2[u] : sv[u] + s2[u];
+                if (ph == 1) fence_proxy_async_smem();  // tails read through the generic proxy
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) {
+                    tc::mbar_arrive(ph == 0 ? l_empty : h_empty);
+                    if (ph == 1) tc::mbar_arrive(&t_empty[ts]);
+                }
+            }
+            if (*abort_flag) break;
+#pragma unroll
+            for (int u = 0; u < HC; ++u) {
+                const int kk = CR * r + HC * jw + u;
                 if (kk < k && valid) {
-                    const float v = cst[j] - 0.5f * sv[j];
+                    const float v = bw[u * TF + TDP] - 0.5f * sv[u];
                     if (lj) lj[(int64_t)kk * lj_ld + p0 + row] = v;
                     st.add(v);
                 }
             }
         }
+        if (jw == 1) reinterpret_cast<float2*>(sm + S::MRG)[row] = make_float2(st.m, st.l);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp >= 2 && warp < 6) {  // each point's two partial logsumexps
+        const int row = (warp & 3) * 32 + lane;
+        const float2 o = reinterpret_cast<const float2*>(sm + S::MRG)[row];
+        st.merge(o.x, o.y);
         double v = 0.0;
-        if (valid && !*abort_flag) {
+        if (p0 + row < n && !*abort_flag) {
             const float lv = st.value();
             if (lse_out) lse_out[p0 + row] = lv;
             v = (double)lv;
@@ -270,12 +326,11 @@ __global__ void __launch_bounds__(192, 1)
         v = warp_sum(v);
         if (lane == 0) red[warp - 2] = v;
     }
-    tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x == 64) part[tile0 + blockIdx.x] = *abort_flag ? NAN : red[0] + red[1] + red[2] + red[3];
     if (warp == 1) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem, 256);
+        tc::tmem_dealloc(tmem, 512);
     }
 }
 
@@ -696,13 +751,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D bf16 tensor [rows][tdp], box 64 x 128 rows, 128-byte swizzle.
-bool make_map(CUtensorMap* m, const void* base, int64_t rows, int tdp) {
+// 2-D bf16 tensor [rows][tdp], box 64 x box_rows rows, 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int tdp, int box_rows = TM) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)tdp, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)tdp * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)TM};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -751,16 +806,17 @@ int convert_inputs(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char
 template <int TDP>
 int launch_tc_fwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char* ws, int64_t row0, int64_t n_local,
                   float* lj, int64_t lj_ld, float* lse, cudaStream_t s) {
+    using S = FwdSm<TDP>;
     CUtensorMap tmx, tmxl, tmq, tmql;
     if (!make_map(&tmx, ws + T.off_xb, A.n, TDP) || !make_map(&tmxl, ws + T.off_xl, A.n, TDP) ||
-        !make_map(&tmq, ws + T.off_qb, (int64_t)A.k * TDP, TDP) ||
-        !make_map(&tmql, ws + T.off_ql, (int64_t)A.k * TDP, TDP))
+        !make_map(&tmq, ws + T.off_qb, (int64_t)A.k * TDP, TDP, S::RPC) ||
+        !make_map(&tmql, ws + T.off_ql, (int64_t)A.k * TDP, TDP, S::RPC))
         return GPA_ERR_CUDA;
-    auto kern = gmm_tc_fwd_kernel<TDP>;
-    if (!set_smem_tc(kern, FwdSm<TDP>::SMEM)) return GPA_ERR_CUDA;
     const int64_t tiles = (n_local + TM - 1) / TM;
+    auto kern = gmm_tc_fwd_kernel<TDP>;
+    if (!set_smem_tc(kern, S::SMEM)) return GPA_ERR_CUDA;
     GPA_LAUNCH("gmm_tc_fwd", s,
-               kern<<<(unsigned)tiles, 192, FwdSm<TDP>::SMEM, s>>>(
+               kern<<<(unsigned)tiles, 64 + 32 * S::EW, S::SMEM, s>>>(
                    tmx, tmxl, tmq, tmql, (const float*)(ws + L.off_rec), n_local, row0, A.k, lj, lj_ld, lse,
                    (double*)(ws + L.off_fwd), row0 / TM, A.status));
     return GPA_OK;

@@ -122,6 +122,37 @@ __device__ __forceinline__ void tmem_ld64_wait(uint32_t taddr, float (&v0)[32], 
         v1[i] = __uint_as_float(r[32 + i]);
     }
 }
+// Split form of tmem_ld64_wait for software pipelining: tmem_ld64_issue starts
+// the two 32-column loads into r, tmem_ld64_tied_wait waits for every load of
+// this thread. The wait takes r as read-write operands, so the compiler can
+// neither read r (the undefined destinations of a load in flight) before the
+// wait nor move the wait after a use of r.
+#define GPA_R64(o) GPA_R32(o), GPA_R32(o + 32)
+__device__ __forceinline__ void tmem_ld64_issue(uint32_t taddr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];"
+        : GPA_R64(0)
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+}
+#define GPA_T32(o)                                                                                            \
+    "+r"(r[o + 0]), "+r"(r[o + 1]), "+r"(r[o + 2]), "+r"(r[o + 3]), "+r"(r[o + 4]), "+r"(r[o + 5]),           \
+        "+r"(r[o + 6]), "+r"(r[o + 7]), "+r"(r[o + 8]), "+r"(r[o + 9]), "+r"(r[o + 10]), "+r"(r[o + 11]),     \
+        "+r"(r[o + 12]), "+r"(r[o + 13]), "+r"(r[o + 14]), "+r"(r[o + 15]), "+r"(r[o + 16]), "+r"(r[o + 17]), \
+        "+r"(r[o + 18]), "+r"(r[o + 19]), "+r"(r[o + 20]), "+r"(r[o + 21]), "+r"(r[o + 22]), "+r"(r[o + 23]), \
+        "+r"(r[o + 24]), "+r"(r[o + 25]), "+r"(r[o + 26]), "+r"(r[o + 27]), "+r"(r[o + 28]), "+r"(r[o + 29]), \
+        "+r"(r[o + 30]), "+r"(r[o + 31])
+__device__ __forceinline__ void tmem_ld64_tied_wait(uint32_t (&r)[64]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : GPA_T32(0), GPA_T32(32) : : "memory");
+}
+#undef GPA_T32
+#undef GPA_R64
+
 // 32 lanes x 32-bit, 16 consecutive columns per thread, with its wait.
 __device__ __forceinline__ void tmem_ld16_wait(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
