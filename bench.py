@@ -632,16 +632,26 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256, fp32_steps=1):
     sample = np.random.default_rng(7).choice(n, 4096, replace=False)
     pairs = n * k
     kern = {kk: {"launches": c, "ms_per_launch": round(v / c, 4)} for kk, (c, v) in tr.items()}
-    fwd = tr.get("gmm_tc_fwd", (1, float("nan")))
-    bwd = tr.get("gmm_tc_bwd", (1, float("nan")))
-    fwd_ms, bwd_ms = fwd[1] / fwd[0], bwd[1] / bwd[0]
+    # per-step device time of each kernel (a step may launch one over several
+    # point ranges), so that flops per step / ms per step is the kernel's rate
+    fwd_ms = tr.get("gmm_tc_fwd", (1, float("nan")))[1] / args.steps
+    bwd_ms = tr.get("gmm_tc_bwd", (1, float("nan")))[1] / args.steps
     dom, dom_ms = ("gmm_tc_fwd", fwd_ms) if fwd_ms >= bwd_ms else ("gmm_tc_bwd", bwd_ms)
-    alg = (d * d + 3 * d) * pairs / (dom_ms / 1e3) / 1e12  # algorithmic flops of the dominant kernel
     tdp = 64 if d <= 64 else 128
-    # executed MMA flops per (point, component): forward 3 passes of 2 TDP^2;
-    # backward one 128 x 128 block per 128 / TDP components over the points
-    per_pair = 3 * 2 * tdp * tdp if dom == "gmm_tc_fwd" else 2 * 128 * tdp
-    dense = per_pair * pairs / (dom_ms / 1e3) / 1e12
+    # executed MMA flops per step. Forward: rounds of 512 / TDP components, the
+    # first TDP / 2 rows of each over K = TDP / 2 and the rest over K = TDP,
+    # three split passes: 4.5 TDP^2 per (point, padded component). Backward:
+    # Y^T R with the products padded to groups of 256 rows and the components
+    # to a multiple of 16.
+    cr = 512 // tdp
+    k_fwd = -(-k // cr) * cr
+    groups = -(-(d * (d + 1) // 2 + d + 1) // 256)
+    k_bwd = -(-k // 16) * 16
+    executed = {"gmm_tc_fwd": 4.5 * tdp * tdp * n * k_fwd, "gmm_tc_bwd": 2.0 * groups * 256 * k_bwd * n}
+    # algorithmic flops per (point, component): the forward's 2 D^2 split
+    # evenly over the two kernels (D^2 + 3D each, as the FP32 roofline counts)
+    alg = (d * d + 3 * d) * pairs / (dom_ms / 1e3) / 1e12
+    dense = executed[dom] / (dom_ms / 1e3) / 1e12
     return {
         "workload": f"GMM objective+gradient, N={n}, D={d}, K={k}, tensor cores (split-BF16 forward, BF16 "
                     "backward, FP32 accumulate)",
@@ -654,8 +664,11 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256, fp32_steps=1):
                      "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": round(alg / peaks["bf16_tflops"], 4),
                      "executed_mma_tflops": round(dense, 1),
                      "executed_frac": round(dense / peaks["bf16_tflops"], 4), "peak_source": src,
+                     "ms_per_step": round(dom_ms, 4),
                      "note": "achieved counts D^2 + 3D flops per (point, component); executed counts every "
-                             "MMA (128x128 tiles of the padded dimension, 3 passes in the forward)"},
+                             "MMA as issued (forward: 4.5 TDP^2 per point and padded component, the nonzero "
+                             "blocks of Q_k in 3 split passes; backward: 256-row product groups x components "
+                             "padded to 16)"},
         "errors_vs_fp32_path": dict(vs_fp32, note="every output at full size against the FP32 CUDA-core path on "
                                                   "the same inputs (normwise per gradient block; lse per point "
                                                   "relative to max(|lse|, 1)); the FP32 path's own error against "

@@ -62,13 +62,16 @@ int gc_of(int dp) { return dp == 16 ? Bwd<16>::GC : dp == 32 ? Bwd<32>::GC : dp 
 struct Plan {
     std::vector<BInst> inst;
     std::vector<BItem> items[kClasses][kPhases];
-    std::vector<int> tc;  // instances on the tensor-core path, run one after another
+    std::vector<int> tc;          // instances on the tensor-core path
+    std::vector<size_t> tc_off;   // their workspace regions (per instance, indexed like tc)
     size_t off_desc, off_items[kClasses][kPhases], off_counters, off_partials, partial_bytes, off_regions;
-    size_t off_tc, tc_bytes, total;
+    size_t total;
 };
 
 // Workspace of one tensor-core instance: the per-call layout with the whole
-// log-joint resident.
+// log-joint resident. Every tensor-core instance has a region of its own, so
+// that its parameter expansion and finalize run in the class's persistent
+// kernels before and after the contractions (which go one instance per launch).
 size_t tc_instance_bytes(const gpa_gmm_instance& I) {
     return gpa_gmm_workspace_bytes(I.n, I.d, I.k, GPA_PREC_BF16_TC, 0);
 }
@@ -117,10 +120,6 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
     for (int i = 0; i < n_inst; ++i) {
         const gpa_gmm_instance& I = in[i];
         if (I.n < 1 || I.d < 1 || I.d > 128 || I.k < 1 || I.k > 4096 || !(I.gamma > 0.0)) return false;
-        if (I.prec == GPA_PREC_BF16_TC) {
-            P.tc.push_back(i);
-            continue;
-        }
         const int dp = gmm_dp(I.d), c = class_of(dp);
         BInst& B = P.inst[i];
         B.n = I.n;
@@ -132,6 +131,14 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
         B.cw = gmm_prior_const(I.d, I.m, I.gamma);
         B.seed = I.seed;
         B.ntiles128 = (int)((I.n + 127) / 128);
+        if (I.prec == GPA_PREC_BF16_TC) {  // prep and finalize items only; pointers bound below
+            P.tc.push_back(i);
+            B.nchunks = gmm_tc_bwd_nchunks(I.n, I.d, I.k);
+            for (int kk = 0; kk < I.k; ++kk) P.items[c][0].push_back({i, kk, 0, 0});
+            for (int kk = 0; kk < I.k; ++kk) P.items[c][3].push_back({i, kk, 0, 0});
+            P.items[c][3].push_back({i, -1, 0, 0});  // objective
+            continue;
+        }
         const int64_t ntiles64 = (I.n + bwd_tpb(dp) - 1) / bwd_tpb(dp);  // backward tiles
         int nch = (int)((I.n + chunk_points - 1) / chunk_points);
         nch = std::max(1, std::min(nch, kGmmMaxChunks));
@@ -192,17 +199,34 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
         B.lse = (float*)(base + off);   off = a256(off + sizeof(float) * (size_t)B.n);
         B.lj = (float*)(base + off);    off = a256(off + sizeof(float) * (size_t)B.n * B.k);
     }
-    // one region per stream lane, each reused by the instances of its lane in turn
-    P.off_tc = off;
-    P.tc_bytes = 0;
-    for (int i : P.tc) P.tc_bytes = std::max(P.tc_bytes, a256(tc_instance_bytes(in[i])));
-    off += P.tc_bytes * (size_t)std::min<int>(kTcLanes, (int)P.tc.size());
+    // tensor-core regions: the per-call layout of each instance; the batched
+    // prep and finalize read and write its records, scalars and partial sums there
+    for (int i : P.tc) {
+        const gpa_gmm_instance& I = in[i];
+        BInst& B = P.inst[i];
+        const GmmLayout L = gmm_layout(I.n, I.d, I.k, 0);
+        char* r = base + off;
+        P.tc_off.push_back(off);
+        B.x = I.x; B.alpha = I.alpha; B.mu = I.mu; B.q = I.q; B.l = I.l;
+        B.d_alpha = I.d_alpha; B.d_mu = I.d_mu; B.d_q = I.d_q; B.d_l = I.d_l; B.out = I.out;
+        B.rec = (float*)(r + L.off_rec);
+        B.scal = (double*)(r + L.off_scal);
+        B.lpk = (double*)(r + L.off_lpk);
+        B.fwd = (double*)(r + L.off_fwd);
+        B.bS = (float*)(r + L.off_bS);
+        B.bM = (float*)(r + L.off_bM);
+        B.lse = nullptr;
+        B.lj = nullptr;
+        off = a256(off + tc_instance_bytes(I));
+    }
     P.total = off;
     return true;
 }
 
-// Fork the lanes from s and enqueue the tensor-core instances on them; the
-// caller enqueues the FP32 classes on s meanwhile and then calls tc_join.
+// Fork the lanes from s and enqueue the contractions of the tensor-core
+// instances on them (their prep ran before, their finalize runs after the
+// join); the caller enqueues the FP32 classes on s meanwhile and then calls
+// tc_join.
 int tc_fork_and_run(const gpa_gmm_instance* in, const Plan& P, char* ws, int32_t* status, cudaStream_t s) {
     if (P.tc.empty()) return GPA_OK;
     TcLanes* T = tc_lanes(false);
@@ -212,19 +236,21 @@ int tc_fork_and_run(const gpa_gmm_instance* in, const Plan& P, char* ws, int32_t
     for (int j = 0; j < lanes; ++j)
         if (cudaStreamWaitEvent(T->st[j], T->fork, 0) != cudaSuccess) return GPA_ERR_CUDA;
     // longest instances first, dealt round-robin over the lanes
-    std::vector<int> order(P.tc);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int u, int v) { return in[u].n * in[u].k > in[v].n * in[v].k; });
+    std::vector<int> order(P.tc.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+        return in[P.tc[u]].n * in[P.tc[u]].k > in[P.tc[v]].n * in[P.tc[v]].k;
+    });
     int rc = GPA_OK;
     for (size_t t = 0; t < order.size() && rc == GPA_OK; ++t) {
         const int j = (int)(t % lanes);
-        const gpa_gmm_instance& I = in[order[t]];
+        const gpa_gmm_instance& I = in[P.tc[order[t]]];
         GmmArgs A{};
         A.x = I.x; A.alpha = I.alpha; A.mu = I.mu; A.q = I.q; A.l = I.l; A.n = I.n; A.d = I.d; A.k = I.k;
         A.gamma = I.gamma; A.m = I.m; A.seed = I.seed; A.out = I.out; A.status = status;
         A.d_alpha = I.d_alpha; A.d_mu = I.d_mu; A.d_q = I.d_q; A.d_l = I.d_l;
         const GmmLayout L = gmm_layout(I.n, I.d, I.k, 0);
-        rc = gmm_tc_vjp_run(A, L, ws + P.off_tc + (size_t)j * P.tc_bytes, P.tc_bytes, T->st[j]);
+        rc = gmm_tc_vjp_run(A, L, ws + P.tc_off[order[t]], tc_instance_bytes(I), T->st[j], kGmmStageCore);
     }
     return rc;
 }
@@ -340,48 +366,52 @@ unsigned persistent_grid(K kern, int threads, size_t smem, int n_items, int ctas
     return (unsigned)std::max(1, std::min(n_items, sms() * occ));
 }
 
+// The four phases of one class: prep and finalize also cover the class's
+// tensor-core instances, forward and backward only its FP32 ones.
 template <int DP>
-int run_class(const Plan& P, char* ws, int c, int ctas_per_sm, int32_t* status, cudaStream_t s) {
-    const BInst* inst = (const BInst*)(ws + P.off_desc);
-    int* counters = (int*)(ws + P.off_counters);
-    const BItem* it[kPhases];
-    int n[kPhases];
-    for (int ph = 0; ph < kPhases; ++ph) {
-        it[ph] = (const BItem*)(ws + P.off_items[c][ph]);
-        n[ph] = (int)P.items[c][ph].size();
-    }
-    if (n[1] == 0) return GPA_OK;
-    {
+struct ClassRun {
+    const Plan& P;
+    char* ws;
+    int c;
+    const BInst* inst() const { return (const BInst*)(ws + P.off_desc); }
+    int* counter(int ph) const { return (int*)(ws + P.off_counters) + c * kPhases + ph; }
+    const BItem* items(int ph) const { return (const BItem*)(ws + P.off_items[c][ph]); }
+    int count(int ph) const { return (int)P.items[c][ph].size(); }
+
+    int prep(cudaStream_t s) const {
+        if (count(0) == 0) return GPA_OK;
         auto k = batched_prep_kernel<DP>;
-        const unsigned g = persistent_grid(k, 128, 0, n[0], 0);
-        GPA_LAUNCH("gmm_batched_prep", s, k<<<g, 128, 0, s>>>(inst, it[0], n[0], counters + c * kPhases + 0));
+        const unsigned g = persistent_grid(k, 128, 0, count(0), 0);
+        GPA_LAUNCH("gmm_batched_prep", s, k<<<g, 128, 0, s>>>(inst(), items(0), count(0), counter(0)));
+        return GPA_OK;
     }
-    {
-        auto k = batched_fwd_kernel<DP>;
-        if (!smem_attr(k, Fwd<DP>::SMEM)) return GPA_ERR_CUDA;
-        const unsigned g = persistent_grid(k, Fwd<DP>::THREADS, Fwd<DP>::SMEM, n[1], ctas_per_sm);
-        GPA_LAUNCH("gmm_batched_fwd", s,
-                   k<<<g, Fwd<DP>::THREADS, Fwd<DP>::SMEM, s>>>(inst, it[1], n[1], counters + c * kPhases + 1,
-                                                               status));
-    }
-    {
+    int core(int ctas_per_sm, int32_t* status, cudaStream_t s) const {
+        if (count(1) == 0) return GPA_OK;
+        {
+            auto k = batched_fwd_kernel<DP>;
+            if (!smem_attr(k, Fwd<DP>::SMEM)) return GPA_ERR_CUDA;
+            const unsigned g = persistent_grid(k, Fwd<DP>::THREADS, Fwd<DP>::SMEM, count(1), ctas_per_sm);
+            GPA_LAUNCH("gmm_batched_fwd", s,
+                       k<<<g, Fwd<DP>::THREADS, Fwd<DP>::SMEM, s>>>(inst(), items(1), count(1), counter(1), status));
+        }
         auto k = batched_bwd_kernel<DP>;
         if (!smem_attr(k, Bwd<DP>::SMEM)) return GPA_ERR_CUDA;
-        const unsigned g = persistent_grid(k, Bwd<DP>::THREADS, Bwd<DP>::SMEM, n[2], ctas_per_sm);
+        const unsigned g = persistent_grid(k, Bwd<DP>::THREADS, Bwd<DP>::SMEM, count(2), ctas_per_sm);
         GPA_LAUNCH("gmm_batched_bwd", s,
-                   k<<<g, Bwd<DP>::THREADS, Bwd<DP>::SMEM, s>>>(inst, it[2], n[2], counters + c * kPhases + 2));
+                   k<<<g, Bwd<DP>::THREADS, Bwd<DP>::SMEM, s>>>(inst(), items(2), count(2), counter(2)));
+        return GPA_OK;
     }
-    {
+    int fin(cudaStream_t s) const {
+        if (count(3) == 0) return GPA_OK;
         constexpr int NB = (DP / 8) * (DP / 8 + 1) / 2;
         const size_t smem = sizeof(double) * (NB * 64 + 3 * DP + 1) + sizeof(float) * 2 * DP * DP + 64;
         auto k = batched_fin_kernel<DP>;
         if (!smem_attr(k, smem)) return GPA_ERR_CUDA;
-        const unsigned g = persistent_grid(k, 256, smem, n[3], 0);
-        GPA_LAUNCH("gmm_batched_finalize", s,
-                   k<<<g, 256, smem, s>>>(inst, it[3], n[3], counters + c * kPhases + 3));
+        const unsigned g = persistent_grid(k, 256, smem, count(3), 0);
+        GPA_LAUNCH("gmm_batched_finalize", s, k<<<g, 256, smem, s>>>(inst(), items(3), count(3), counter(3)));
+        return GPA_OK;
     }
-    return GPA_OK;
-}
+};
 
 int check_instances(const gpa_gmm_instance* in, int n_inst) {
     if (!in || n_inst < 1 || n_inst > (1 << 20)) return GPA_ERR_ARG;
@@ -452,12 +482,22 @@ extern "C" int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int
     if (cudaMemsetAsync((char*)ws + P.off_counters, 0, sizeof(int) * kClasses * kPhases, s) != cudaSuccess ||
         cudaMemsetAsync((char*)ws + P.off_partials, 0, P.partial_bytes, s) != cudaSuccess)
         return GPA_ERR_CUDA;
-    // tensor-core instances on the forked lanes, concurrently with the FP32 classes on s
-    rc = tc_fork_and_run(inst, P, (char*)ws, dev_status, s);
-    if (!rc) rc = run_class<16>(P, (char*)ws, 0, ctas_per_sm, dev_status, s);
-    if (!rc) rc = run_class<32>(P, (char*)ws, 1, ctas_per_sm, dev_status, s);
-    if (!rc) rc = run_class<64>(P, (char*)ws, 2, ctas_per_sm, dev_status, s);
-    if (!rc) rc = run_class<128>(P, (char*)ws, 3, ctas_per_sm, dev_status, s);
+    char* w = (char*)ws;
+    const ClassRun<16> c16{P, w, 0};
+    const ClassRun<32> c32{P, w, 1};
+    const ClassRun<64> c64{P, w, 2};
+    const ClassRun<128> c128{P, w, 3};
+    // parameter expansion of every instance, then the tensor-core contractions
+    // on the forked lanes concurrently with the FP32 classes on s, then every
+    // instance's finalize
+    if ((rc = c16.prep(s)) || (rc = c32.prep(s)) || (rc = c64.prep(s)) || (rc = c128.prep(s))) return rc;
+    rc = tc_fork_and_run(inst, P, w, dev_status, s);
+    if (!rc) rc = c16.core(ctas_per_sm, dev_status, s);
+    if (!rc) rc = c32.core(ctas_per_sm, dev_status, s);
+    if (!rc) rc = c64.core(ctas_per_sm, dev_status, s);
+    if (!rc) rc = c128.core(ctas_per_sm, dev_status, s);
     const int jr = tc_join(P, s);
-    return rc ? rc : jr;
+    if (rc || jr) return rc ? rc : jr;
+    if ((rc = c16.fin(s)) || (rc = c32.fin(s)) || (rc = c64.fin(s)) || (rc = c128.fin(s))) return rc;
+    return GPA_OK;
 }

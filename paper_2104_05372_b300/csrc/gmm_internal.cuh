@@ -66,7 +66,13 @@ int gmm_run_exchange(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks
 bool gmm_tc_supported(int d);
 size_t gmm_tc_extra_bytes(int64_t n, int d, int k);
 int gmm_tc_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s);
-int gmm_tc_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s);
+// Stages of a reverse pass: parameter expansion, the contractions, the
+// finalize (gradient and objective). The batched form runs the first and last
+// in its persistent kernels and asks the tensor-core path for the middle only.
+enum : int { kGmmStagePrep = 1, kGmmStageCore = 2, kGmmStageFinish = 4, kGmmStagesAll = 7 };
+int gmm_tc_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s,
+                   int stages = kGmmStagesAll);
+int gmm_tc_bwd_nchunks(int64_t n, int d, int k);  // point chunks (partial sums) of the reverse pass
 
 // The data-independent part of each component's Wishart log-prior, for
 // n = d + m + 1 degrees of freedom: n d log(gamma) - (n d / 2) log 2 - log

@@ -792,12 +792,16 @@ int sm_count_tc() {
 
 template <int TDP>
 int convert_inputs(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char* ws, cudaStream_t s) {
-    const unsigned g = (unsigned)sm_count_tc() * 8;
+    // grid-stride kernels: one element pair (x) or element (Q) per thread and
+    // step, the grid as large as the work up to 8 CTAs per SM
+    const int64_t cap = (int64_t)sm_count_tc() * 8;
+    const unsigned gx = (unsigned)min64(cap, (A.n * (TDP / 2) + 255) / 256);
+    const unsigned gq = (unsigned)min64(cap, ((int64_t)A.k * TDP * TDP + 255) / 256);
     GPA_LAUNCH("gmm_tc_convert_x", s,
-               tc_convert_x_kernel<TDP><<<g, 256, 0, s>>>(A.x, A.n, A.d, (__nv_bfloat16*)(ws + T.off_xb),
-                                                          (__nv_bfloat16*)(ws + T.off_xl)));
+               tc_convert_x_kernel<TDP><<<gx, 256, 0, s>>>(A.x, A.n, A.d, (__nv_bfloat16*)(ws + T.off_xb),
+                                                           (__nv_bfloat16*)(ws + T.off_xl)));
     GPA_LAUNCH("gmm_tc_convert_q", s,
-               tc_convert_q_kernel<TDP><<<g, 256, 0, s>>>((const float*)(ws + L.off_rec), A.k,
+               tc_convert_q_kernel<TDP><<<gq, 256, 0, s>>>((const float*)(ws + L.off_rec), A.k,
                                                           (__nv_bfloat16*)(ws + T.off_qb),
                                                           (__nv_bfloat16*)(ws + T.off_ql)));
     return GPA_OK;
@@ -831,12 +835,18 @@ int gram_groups(int d) { return (d * (d + 1) / 2 + d + 1 + GMB * 128 - 1) / (GMB
 // write-out; otherwise the chunk count with the best wave efficiency.
 int tc_bwd_chunks(int groups, int64_t ntiles) {
     const int slots = sm_count_tc();
+    // at least kMinTiles point tiles per chunk: a CTA's set-up and write-out
+    // of its partial sums cost about as much as that many tiles, and a small
+    // problem spread over every SM would keep the others (the concurrent
+    // instances of a batch) waiting for little work
+    constexpr int64_t kMinTiles = 8;
+    const int64_t cap = ntiles / kMinTiles > 1 ? ntiles / kMinTiles : 1;
     const int64_t one_wave = (int64_t)(slots / groups);
     if (one_wave >= 1 && groups * one_wave >= (int64_t)(0.85 * slots))
-        return (int)min64(min64(one_wave, kGmmMaxChunks), ntiles);
+        return (int)min64(min64(one_wave, kGmmMaxChunks), cap);
     int best = 1;
     double best_eff = -1.0;
-    for (int c = 1; c <= kGmmMaxChunks && c <= ntiles; ++c) {
+    for (int c = 1; c <= kGmmMaxChunks && c <= cap; ++c) {
         const int64_t total = (int64_t)groups * c;
         const int64_t waves = (total + slots - 1) / slots;
         const double eff = (double)total / (double)(waves * slots);
@@ -888,20 +898,27 @@ int objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_byte
     return gmm_run_objective(A, L, ws, s);
 }
 
+// point chunks of the gram grid for n points (the backward runs over at most
+// rpoints at a time, with the same chunk grid each time)
 template <int TDP>
-int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s) {
+int vjp_chunks(int64_t n, int d, int k, int64_t rpoints) {
+    return tc_bwd_chunks(gram_groups(d) * ((tc_r_rows(k) + GKMAX - 1) / GKMAX),
+                         (((n < rpoints ? n : rpoints) + GTM - 1) / GTM));
+}
+
+template <int TDP>
+int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s, int stages) {
     const TcLayout T = tc_layout(L, A.n, A.d, A.k);
     if (ws_bytes < T.fixed) return GPA_ERR_WORKSPACE;
-    const int kr = tc_r_rows(A.k);
     const int64_t RP = T.rpoints;  // points per backward launch (a multiple of 128)
-    const int nchunks = tc_bwd_chunks(gram_groups(A.d) * ((kr + GKMAX - 1) / GKMAX),
-                                      (((A.n < RP ? A.n : RP) + GTM - 1) / GTM));
+    const int nchunks = vjp_chunks<TDP>(A.n, A.d, A.k, RP);
+    int rc = GPA_OK;
+    if ((stages & kGmmStagePrep) && (rc = gmm_run_prep(A, L, ws, s))) return rc;
+    if (!(stages & kGmmStageCore)) return GPA_OK;
     const int nent = gmm_bwd_partial_entries(TDP);
     if (cudaMemsetAsync(ws + L.off_bS, 0, sizeof(float) * (size_t)nchunks * A.k * nent, s) != cudaSuccess ||
         cudaMemsetAsync(ws + L.off_bM, 0, sizeof(float) * (size_t)nchunks * A.k * (TDP + 1), s) != cudaSuccess)
         return GPA_ERR_CUDA;
-    int rc = gmm_run_prep(A, L, ws, s);
-    if (rc) return rc;
     if ((rc = convert_inputs<TDP>(A, L, T, ws, s))) return rc;
     GPA_LAUNCH("gmm_tc_xt", s,
                gmm_tc_xt_kernel<<<(unsigned)(T.npad / GTM), 256, 0, s>>>(A.x, A.n, A.d, (float*)(ws + T.off_xt)));
@@ -934,6 +951,7 @@ int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cud
             if ((rc = bwd_range(c0, nl, lj, P, lse))) return rc;
         }
     }
+    if (!(stages & kGmmStageFinish)) return GPA_OK;
     if (A.exch_out) return gmm_run_exchange(A, L, ws, nchunks, s);
     if ((rc = gmm_run_finalize(A, L, ws, nchunks, 0, s))) return rc;  // raw moments, as the FP32 path
     if (A.out) return gmm_run_objective(A, L, ws, s);
@@ -955,8 +973,14 @@ int gmm_tc_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t 
     return tc_dp(A.d) == 64 ? objective_run<64>(A, L, ws, ws_bytes, s) : objective_run<128>(A, L, ws, ws_bytes, s);
 }
 
-int gmm_tc_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s) {
-    return tc_dp(A.d) == 64 ? vjp_run<64>(A, L, ws, ws_bytes, s) : vjp_run<128>(A, L, ws, ws_bytes, s);
+int gmm_tc_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s, int stages) {
+    return tc_dp(A.d) == 64 ? vjp_run<64>(A, L, ws, ws_bytes, s, stages) : vjp_run<128>(A, L, ws, ws_bytes, s, stages);
+}
+
+int gmm_tc_bwd_nchunks(int64_t n, int d, int k) {
+    const GmmLayout L = gmm_layout(n, d, k, 0);
+    const TcLayout T = tc_layout(L, n, d, k);
+    return tc_dp(d) == 64 ? vjp_chunks<64>(n, d, k, T.rpoints) : vjp_chunks<128>(n, d, k, T.rpoints);
 }
 
 }  // namespace gpa
