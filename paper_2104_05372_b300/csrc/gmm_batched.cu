@@ -47,17 +47,27 @@ struct BItem {
     int inst, a, b, pad;
 };
 
-constexpr int kClasses = 4;  // padded dimension 16, 32, 64, 128
+constexpr int kClasses = 5;  // padded dimension 8, 16, 32, 64, 128
 constexpr int kPhases = 4;   // prep, forward, backward, finalize
-int class_of(int dp) { return dp == 16 ? 0 : dp == 32 ? 1 : dp == 64 ? 2 : 3; }
+int class_of(int dp) { return dp == 8 ? 0 : dp == 16 ? 1 : dp == 32 ? 2 : dp == 64 ? 3 : 4; }
+// D <= 8 has a class of its own here (the per-call path pads it to 16)
+int batched_dp(int d) { return d <= 8 ? 8 : gmm_dp(d); }
 
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// D <= 8 kernels: 128 points per forward item (one per thread); backward items
+// of up to 16 components over 128-point tiles
+constexpr int kD8Points = 128, kD8Group = 16, kD8Rec = 8 * 8 + 8 + 4, kD8Stage = 64;
+
 int nblk(int dp) { return (dp / 8) * (dp / 8 + 1) / 2; }
 int bwd_tpb(int dp) {
-    return dp == 16 ? Bwd<16>::TPB : dp == 32 ? Bwd<32>::TPB : dp == 64 ? Bwd<64>::TPB : Bwd<128>::TPB;
+    return dp == 8 ? kD8Points : dp == 16 ? Bwd<16>::TPB : dp == 32 ? Bwd<32>::TPB : dp == 64 ? Bwd<64>::TPB
+                                                                                               : Bwd<128>::TPB;
 }
-int gc_of(int dp) { return dp == 16 ? Bwd<16>::GC : dp == 32 ? Bwd<32>::GC : dp == 64 ? Bwd<64>::GC : Bwd<128>::GC; }
+int gc_of(int dp) {
+    return dp == 8 ? kD8Group : dp == 16 ? Bwd<16>::GC : dp == 32 ? Bwd<32>::GC : dp == 64 ? Bwd<64>::GC
+                                                                                           : Bwd<128>::GC;
+}
 
 struct Plan {
     std::vector<BInst> inst;
@@ -120,7 +130,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
     for (int i = 0; i < n_inst; ++i) {
         const gpa_gmm_instance& I = in[i];
         if (I.n < 1 || I.d < 1 || I.d > 128 || I.k < 1 || I.k > 4096 || !(I.gamma > 0.0)) return false;
-        const int dp = gmm_dp(I.d), c = class_of(dp);
+        const int dp = I.prec == GPA_PREC_BF16_TC ? gmm_dp(I.d) : batched_dp(I.d), c = class_of(dp);
         BInst& B = P.inst[i];
         B.n = I.n;
         B.d = I.d;
@@ -343,6 +353,168 @@ __global__ void __launch_bounds__(256) batched_fin_kernel(const BInst* __restric
     }
 }
 
+// ---- D <= 8 ------------------------------------------------------------------------
+// Forward: one thread per point, the point's 8 coordinates in registers, the
+// component records (Q^T, b, constant) staged kD8Stage at a time in shared
+// memory and read as broadcasts. z = Q x - b in packed pairs of rows over the
+// lower triangle (column c touches rows c.. only), then the log-joint and the
+// online logsumexp as in the other forward kernels.
+__global__ void __launch_bounds__(128) batched_fwd8_kernel(const BInst* __restrict__ inst,
+                                                           const BItem* __restrict__ items, int n_items,
+                                                           int* counter) {
+    __shared__ __align__(16) float qs[kD8Stage * kD8Rec];
+    __shared__ double wsum[4];
+    for (;;) {
+        const int it = next_item(counter);
+        if (it >= n_items) break;
+        const BItem w = items[it];
+        const BInst& B = inst[w.inst];
+        const int64_t p = (int64_t)w.a * kD8Points + threadIdx.x;
+        const bool valid = p < B.n;
+        float xv[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) xv[c] = (valid && c < B.d) ? __ldg(B.x + p * B.d + c) : 0.f;
+        Lse st;
+        st.init();
+        for (int c0 = 0; c0 < B.k; c0 += kD8Stage) {
+            const int nc = min(kD8Stage, B.k - c0);
+            __syncthreads();  // the previous stage's readers are done
+            const float4* src = reinterpret_cast<const float4*>(B.rec + (size_t)c0 * kD8Rec);
+            for (int e = threadIdx.x; e < nc * (kD8Rec / 4); e += 128)
+                reinterpret_cast<float4*>(qs)[e] = __ldg(src + e);
+            __syncthreads();
+            for (int j = 0; j < nc; ++j) {
+                const float* R = qs + j * kD8Rec;  // Qt[c][r] at 8 c + r, b at 64, constant at 72
+                const float4 b0 = *reinterpret_cast<const float4*>(R + 64);
+                const float4 b1 = *reinterpret_cast<const float4*>(R + 68);
+                float2 z[4] = {make_float2(-b0.x, -b0.y), make_float2(-b0.z, -b0.w), make_float2(-b1.x, -b1.y),
+                               make_float2(-b1.z, -b1.w)};
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float4 q0 = *reinterpret_cast<const float4*>(R + 8 * c);
+                    const float4 q1 = *reinterpret_cast<const float4*>(R + 8 * c + 4);
+                    const float2 qp[4] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                                          make_float2(q1.z, q1.w)};
+                    const float2 x2 = make_float2(xv[c], xv[c]);
+#pragma unroll
+                    for (int i = c / 2; i < 4; ++i) z[i] = __ffma2_rn(x2, qp[i], z[i]);
+                }
+                float2 s2 = __fmul2_rn(z[0], z[0]);
+#pragma unroll
+                for (int i = 1; i < 4; ++i) s2 = __ffma2_rn(z[i], z[i], s2);
+                const float v = R[72] - 0.5f * (s2.x + s2.y);
+                if (valid) {
+                    if (B.lj) B.lj[(int64_t)(c0 + j) * B.n + p] = v;
+                    st.add(v);
+                }
+            }
+        }
+        double v = 0.0;
+        if (valid) {
+            const float lv = st.value();
+            if (B.lse) B.lse[p] = lv;
+            v = (double)lv;
+        }
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) B.fwd[w.a] = wsum[0] + wsum[1] + wsum[2] + wsum[3];
+    }
+}
+
+// Backward Accum: item (instance, group of up to kD8Group components, point
+// chunk). The nc components of the group share the CTA's 128 threads: thread
+// t takes component t % nc and every ps-th point of each tile from t / nc
+// (ps = 128 / nc slices), so a group of few components still keeps most
+// threads busy. Per point and component: r = seed exp(s - lse), y = r x,
+// S += y x^T (lower triangle, 36 sums), m += y, R += r. The slices' sums are
+// then combined in slice order and added into the chunk's partial sums.
+constexpr int kD8Sums = 36 + 8 + 1;
+__global__ void __launch_bounds__(128) batched_bwd8_kernel(const BInst* __restrict__ inst,
+                                                           const BItem* __restrict__ items, int n_items,
+                                                           int* counter) {
+    __shared__ __align__(16) float xs[kD8Points * 8];
+    __shared__ float rs[kD8Points * kD8Group];
+    __shared__ float lse_s[kD8Points];
+    __shared__ float red[128 * kD8Sums];
+    const int tid = threadIdx.x;
+    for (;;) {
+        const int it = next_item(counter);
+        if (it >= n_items) break;
+        const BItem w = items[it];
+        const BInst& B = inst[w.inst];
+        const int kg0 = w.a * kD8Group, nc = min(kD8Group, B.k - kg0), ps = 128 / nc;
+        const int c = tid % nc, sl = tid / nc;
+        const bool active = sl < ps;
+        const int64_t ntiles = (B.n + kD8Points - 1) / kD8Points;
+        const int64_t t0 = (int64_t)w.b * B.tiles_per_chunk, t1 = min64(ntiles, t0 + B.tiles_per_chunk);
+        const float seed = (float)B.seed;
+        float S[36], m[8], R = 0.f;
+#pragma unroll
+        for (int e = 0; e < 36; ++e) S[e] = 0.f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m[e] = 0.f;
+        for (int64_t t = t0; t < t1; ++t) {
+            const int64_t p0 = t * kD8Points;
+            __syncthreads();  // the previous tile's readers are done
+            for (int e = tid; e < kD8Points * 8; e += 128) {
+                const int pp = e >> 3, cc = e & 7;
+                xs[e] = (p0 + pp < B.n && cc < B.d) ? __ldg(B.x + (p0 + pp) * B.d + cc) : 0.f;
+            }
+            lse_s[tid] = p0 + tid < B.n ? __ldg(B.lse + p0 + tid) : 0.f;
+            __syncthreads();
+            for (int e = tid; e < nc * kD8Points; e += 128) {
+                const int cc = e / kD8Points, pp = e % kD8Points;
+                float r = 0.f;
+                if (p0 + pp < B.n) r = seed * expf(__ldg(B.lj + (int64_t)(kg0 + cc) * B.n + p0 + pp) - lse_s[pp]);
+                rs[pp * kD8Group + cc] = r;
+            }
+            __syncthreads();
+            if (active)
+                for (int pp = sl; pp < kD8Points; pp += ps) {
+                    const float r = rs[pp * kD8Group + c];
+                    const float4 xa = *reinterpret_cast<const float4*>(xs + pp * 8);
+                    const float4 xb = *reinterpret_cast<const float4*>(xs + pp * 8 + 4);
+                    const float x[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                    R += r;
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) {
+                        const float y = r * x[a];
+                        m[a] += y;
+#pragma unroll
+                        for (int b = 0; b <= a; ++b) S[a * (a + 1) / 2 + b] = fmaf(y, x[b], S[a * (a + 1) / 2 + b]);
+                    }
+                }
+        }
+        __syncthreads();
+        if (active) {
+            float* o = red + (sl * nc + c) * kD8Sums;
+#pragma unroll
+            for (int e = 0; e < 36; ++e) o[e] = S[e];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) o[36 + e] = m[e];
+            o[44] = R;
+        }
+        __syncthreads();
+        for (int e2 = tid; e2 < nc * kD8Sums; e2 += 128) {
+            const int cc = e2 / kD8Sums, e = e2 % kD8Sums;
+            float v = 0.f;
+            for (int s2 = 0; s2 < ps; ++s2) v += red[(s2 * nc + cc) * kD8Sums + e];
+            const int64_t base = (int64_t)w.b * B.k + kg0 + cc;
+            if (e < 36) {
+                int a = 0, b = e;
+                while (b > a) {
+                    ++a;
+                    b -= a;
+                }
+                B.bS[base * 64 + a * 8 + b] += v;
+            } else {
+                B.bM[base * 9 + (e - 36)] += v;  // m at 0..7, R at 8
+            }
+        }
+    }
+}
+
 // ---- host -------------------------------------------------------------------------
 template <typename K>
 bool smem_attr(K kern, size_t bytes) {
@@ -387,18 +559,27 @@ struct ClassRun {
     }
     int core(int ctas_per_sm, int32_t* status, cudaStream_t s) const {
         if (count(1) == 0) return GPA_OK;
-        {
-            auto k = batched_fwd_kernel<DP>;
-            if (!smem_attr(k, Fwd<DP>::SMEM)) return GPA_ERR_CUDA;
-            const unsigned g = persistent_grid(k, Fwd<DP>::THREADS, Fwd<DP>::SMEM, count(1), ctas_per_sm);
+        if constexpr (DP == 8) {
+            (void)status;
+            auto kf = batched_fwd8_kernel;
+            const unsigned gf = persistent_grid(kf, 128, 0, count(1), ctas_per_sm);
+            GPA_LAUNCH("gmm_batched_fwd", s, kf<<<gf, 128, 0, s>>>(inst(), items(1), count(1), counter(1)));
+            auto kb = batched_bwd8_kernel;
+            const unsigned gb = persistent_grid(kb, 128, 0, count(2), ctas_per_sm);
+            GPA_LAUNCH("gmm_batched_bwd", s, kb<<<gb, 128, 0, s>>>(inst(), items(2), count(2), counter(2)));
+        } else {
+            auto kf = batched_fwd_kernel<DP>;
+            if (!smem_attr(kf, Fwd<DP>::SMEM)) return GPA_ERR_CUDA;
+            const unsigned gf = persistent_grid(kf, Fwd<DP>::THREADS, Fwd<DP>::SMEM, count(1), ctas_per_sm);
             GPA_LAUNCH("gmm_batched_fwd", s,
-                       k<<<g, Fwd<DP>::THREADS, Fwd<DP>::SMEM, s>>>(inst(), items(1), count(1), counter(1), status));
+                       kf<<<gf, Fwd<DP>::THREADS, Fwd<DP>::SMEM, s>>>(inst(), items(1), count(1), counter(1),
+                                                                      status));
+            auto kb = batched_bwd_kernel<DP>;
+            if (!smem_attr(kb, Bwd<DP>::SMEM)) return GPA_ERR_CUDA;
+            const unsigned gb = persistent_grid(kb, Bwd<DP>::THREADS, Bwd<DP>::SMEM, count(2), ctas_per_sm);
+            GPA_LAUNCH("gmm_batched_bwd", s,
+                       kb<<<gb, Bwd<DP>::THREADS, Bwd<DP>::SMEM, s>>>(inst(), items(2), count(2), counter(2)));
         }
-        auto k = batched_bwd_kernel<DP>;
-        if (!smem_attr(k, Bwd<DP>::SMEM)) return GPA_ERR_CUDA;
-        const unsigned g = persistent_grid(k, Bwd<DP>::THREADS, Bwd<DP>::SMEM, count(2), ctas_per_sm);
-        GPA_LAUNCH("gmm_batched_bwd", s,
-                   k<<<g, Bwd<DP>::THREADS, Bwd<DP>::SMEM, s>>>(inst(), items(2), count(2), counter(2)));
         return GPA_OK;
     }
     int fin(cudaStream_t s) const {
@@ -483,21 +664,25 @@ extern "C" int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int
         cudaMemsetAsync((char*)ws + P.off_partials, 0, P.partial_bytes, s) != cudaSuccess)
         return GPA_ERR_CUDA;
     char* w = (char*)ws;
-    const ClassRun<16> c16{P, w, 0};
-    const ClassRun<32> c32{P, w, 1};
-    const ClassRun<64> c64{P, w, 2};
-    const ClassRun<128> c128{P, w, 3};
+    const ClassRun<8> c8{P, w, 0};
+    const ClassRun<16> c16{P, w, 1};
+    const ClassRun<32> c32{P, w, 2};
+    const ClassRun<64> c64{P, w, 3};
+    const ClassRun<128> c128{P, w, 4};
     // parameter expansion of every instance, then the tensor-core contractions
     // on the forked lanes concurrently with the FP32 classes on s, then every
     // instance's finalize
-    if ((rc = c16.prep(s)) || (rc = c32.prep(s)) || (rc = c64.prep(s)) || (rc = c128.prep(s))) return rc;
+    if ((rc = c8.prep(s)) || (rc = c16.prep(s)) || (rc = c32.prep(s)) || (rc = c64.prep(s)) || (rc = c128.prep(s)))
+        return rc;
     rc = tc_fork_and_run(inst, P, w, dev_status, s);
+    if (!rc) rc = c8.core(ctas_per_sm, dev_status, s);
     if (!rc) rc = c16.core(ctas_per_sm, dev_status, s);
     if (!rc) rc = c32.core(ctas_per_sm, dev_status, s);
     if (!rc) rc = c64.core(ctas_per_sm, dev_status, s);
     if (!rc) rc = c128.core(ctas_per_sm, dev_status, s);
     const int jr = tc_join(P, s);
     if (rc || jr) return rc ? rc : jr;
-    if ((rc = c16.fin(s)) || (rc = c32.fin(s)) || (rc = c64.fin(s)) || (rc = c128.fin(s))) return rc;
+    if ((rc = c8.fin(s)) || (rc = c16.fin(s)) || (rc = c32.fin(s)) || (rc = c64.fin(s)) || (rc = c128.fin(s)))
+        return rc;
     return GPA_OK;
 }

@@ -12,12 +12,13 @@
 namespace gpa {
 
 // ---------------------------------------------------------------------------
-// Configuration per padded dimension DP (16, 32, 64, 128)
+// Configuration per padded dimension DP (16, 32, 64, 128; the batched form
+// also has a class DP = 8 with kernels of its own, sharing only REC and NBLK)
 // ---------------------------------------------------------------------------
 template <int DP>
 struct Fwd {
     static constexpr int NB = DP / 8;         // 8-row blocks of Q
-    static constexpr int NWC = DP / 16;       // warps per component (pairs of row blocks)
+    static constexpr int NWC = DP >= 16 ? DP / 16 : 1;  // warps per component (pairs of row blocks)
     static constexpr int NS = 8 / NWC;        // components processed at once per CTA
     static constexpr int TP = 128;            // points per tile (4 per lane)
     static constexpr int XST = TP + 4;        // row stride of the transposed tile Xs[c][p]

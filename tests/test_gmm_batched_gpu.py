@@ -167,3 +167,21 @@ def test_tensor_core_instance_outside_its_range_is_rejected():
     inst[0]["prec"] = 1
     with pytest.raises(gpa.GpaError):
         GmmBatch(inst).prepare()
+
+
+@pytest.mark.parametrize("shapes", [[(257, 8, 17), (300, 2, 16), (129, 7, 15), (5000, 8, 33)],
+                                    [(128, 8, 1), (1, 4, 3), (4096, 6, 64)]])
+def test_batched_d8_class_matches_oracle(shapes):
+    """D <= 8 instances run in kernels of their own (one thread per point in
+    the forward; component groups of up to 16 split over point slices in the
+    backward): group sizes around 16, a single point, ragged tiles."""
+    from paper_2104_05372_b300._lib import GmmBatch
+    gs, inst = _instances(shapes, seed=21)
+    for chunk in (128, 4096):
+        b = GmmBatch(inst, chunk_points=chunk)
+        b.prepare()
+        st = status()
+        b.run(status=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        _check(gs, inst, b)
