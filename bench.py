@@ -694,18 +694,16 @@ def run_batched(args, gpa, _lib, dev, stream, rank):
                  l=torch.from_numpy(g.l).to(dev), gamma=g.gamma, m=g.m, seed=1.0) for g in gs]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def graph_time(instances):
-        tune = autotune.tune_batched(instances, reps=2)
-        b = _lib.GmmBatch(instances, chunk_points=tune["chunk_points"])
+    def graph_time(instances, opts):
+        b = _lib.GmmBatch(instances, opts=opts)
         b.prepare()
-        cps = tune["ctas_per_sm"]
         b.zero_grads()
-        b.run(cps)
+        b.run()
         torch.cuda.synchronize(dev)
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
             b.zero_grads()
-            b.run(cps)
+            b.run()
         for _ in range(args.warmup):
             graph.replay()
         torch.cuda.synchronize(dev)
@@ -718,11 +716,34 @@ def run_batched(args, gpa, _lib, dev, stream, rank):
         pairs = b.pairs
         del graph, b
         torch.cuda.empty_cache()
-        return ms, pairs, {k: tune[k] for k in ("chunk_points", "ctas_per_sm", "ms")}
+        return ms, pairs
 
-    ms_fp32, pairs, tune_fp32 = graph_time(inst)
+    tune_fp32 = autotune.tune_batched(inst, reps=2)
+    ms_fp32, pairs = graph_time(inst, tune_fp32["opts"])
     mixed = [dict(i, prec=1) if 32 < int(i["x"].shape[1]) <= 128 else i for i in inst]
-    ms_b, _, tune = graph_time(mixed)
+    tune = autotune.tune_batched(mixed, reps=2)
+    ms_b, _ = graph_time(mixed, tune["opts"])
+    # per class: its instances alone with the tuned settings; roofline against
+    # the FP32 ALU peak (FP32 classes) or the BF16 tensor peak (tensor cores),
+    # algorithmic flops 2 D^2 + 6 D per (point, component) as in the headline
+    peaks, src = measured_peaks()
+    fp32_peak = fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count,
+                                 float(peaks.get("sm_max_mhz", 2032.0)))  # at the maximum SM clock
+    per_class = {}
+    for c in range(_lib.BATCH_CLASSES):
+        sub = [i for i in mixed if autotune.class_of(i) == c]
+        if not sub:
+            continue
+        ms_c, pairs_c = graph_time(sub, tune["opts"])
+        flops = sum((2 * int(i["x"].shape[1]) ** 2 + 6 * int(i["x"].shape[1])) * int(i["x"].shape[0]) *
+                    int(i["alpha"].shape[0]) for i in sub)
+        tc = any(int(i.get("prec", 0)) == 1 for i in sub)
+        peak = peaks["bf16_tflops"] if tc else fp32_peak
+        ach = flops / (ms_c / 1e3) / 1e12
+        per_class[f"D<={_lib.BATCH_CLASS_DP[c]}"] = {
+            "instances": len(sub), "pairs": pairs_c, "ms": round(ms_c, 3), "achieved_tflops": round(ach, 2),
+            "peak_tflops": round(peak, 1), "bound": "tensor" if tc else "alu", "frac": round(ach / peak, 4),
+            "settings": tune["opts"].get(c, "tensor-core contractions per instance (prep and finalize batched)")}
     # plain path: one gmm_vjp call per instance (its own workspace, allocated beforehand)
     wss = [_lib.workspace(gpa.gpa_gmm_workspace_bytes(g.n, g.d, g.k, 0, 0), dev) for g in gs]
     grads = [gpa.gmm_vjp(i["x"], i["alpha"], i["mu"], i["q"], i["l"], i["gamma"], i["m"], ws=w)
@@ -746,10 +767,12 @@ def run_batched(args, gpa, _lib, dev, stream, rank):
     return {"workload": "512 GMM instances, N log-uniform [1e3,2e5], D in {8,16,32,64}, K log-uniform [4,128]; "
                         f"FP32, BF16 tensor-core contraction for the {n_tc} instances with 32 < D <= 128",
             "metric": METRIC, "unit": UNIT, "pairs": pairs, "value": pairs / (ms_b / 1e3), "ms_per_step": ms_b,
-            "all_fp32_batched": {"value": pairs / (ms_fp32 / 1e3), "ms_per_step": ms_fp32, "autotune": tune_fp32},
+            "all_fp32_batched": {"value": pairs / (ms_fp32 / 1e3), "ms_per_step": ms_fp32,
+                                 "autotune": {str(c): v for c, v in tune_fp32["opts"].items()}},
+            "per_class_alone": per_class,
             "per_instance_launches": {"value": pairs / (ms_loop / 1e3), "ms_per_step": ms_loop},
             "speedup_vs_per_instance": ms_loop / ms_b, "speedup_vs_all_fp32_batched": ms_fp32 / ms_b,
-            "autotune": tune}
+            "autotune": {str(c): v for c, v in tune["opts"].items()}}
 
 
 # ---------------------------------------------------------------------------

@@ -250,20 +250,55 @@ GPA_API int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst, in
                                 void* ws, size_t ws_bytes, gpa_stream_t stream);
 
 /* Objective and seed * gradient of every prepared instance: per padded
- * dimension class (D <= 16, 32, 64, 128) four persistent kernels whose CTAs
- * pull work items from an atomic counter (flattened loops, Sec. 6.1.1), plus
- * two memsets. Enqueues device work only, so the call can be captured in a
+ * dimension class (D <= 8, 16, 32, 64, 128) up to five persistent kernels
+ * (prep, forward, backward in default and small component groups, finalize)
+ * whose CTAs pull work items from an atomic counter (flattened loops, Sec.
+ * 6.1.1), plus two memsets. Enqueues device work only, so the call can be captured in a
  * CUDA graph and replayed while the inputs live at the same addresses.
  * ctas_per_sm caps resident CTAs per SM (0 = as many as fit). `inst`,
  * n_inst, chunk_points must equal the gmm_batched_prepare arguments. FP32
  * CUDA-core arithmetic, deterministic like gmm_vjp. Instances with prec =
- * GPA_PREC_BF16_TC run the tensor-core path of gmm_vjp instead, spread over 8
- * library streams forked from `stream` with events and joined back into it
- * (capturable in the same graph); their R sums use shared-memory float atomics,
- * so their last bits may differ between runs. */
+ * GPA_PREC_BF16_TC run the contractions of the tensor-core path of gmm_vjp
+ * instead (their prep and finalize run in the class's persistent kernels),
+ * spread over 8 library streams forked from `stream` with events and joined
+ * back into it (capturable in the same graph); each has a workspace region
+ * of its own (gmm_vjp's tensor-core workspace for its n, d, k). */
 GPA_API int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
                             int32_t ctas_per_sm, void* ws, size_t ws_bytes, int32_t* dev_status,
                             gpa_stream_t stream);
+
+/* Per-class settings of the batched form. The classes are the padded
+ * dimensions 8 (D <= 8), 16, 32, 64 and 128, index 0..4. For each class:
+ *   chunk_points  points per backward work item (>= 64);
+ *   ctas_per_sm   resident persistent CTAs per SM of its forward and backward
+ *                 kernels (0 = as many as fit);
+ *   small_groups  1: an FP32 instance whose component count K fills the
+ *                 class's small component group (10 components at D <= 16, 6 at
+ *                 D <= 32) with fewer idle threads than the default group (42,
+ *                 25) takes its backward work items in that group size; 0: the
+ *                 default groups only. Ignored for the other classes.
+ * gmm_batched_prepare / gmm_batched_vjp / gpa_gmm_batched_workspace_bytes
+ * are the _opts calls with every class set to (chunk_points, ctas_per_sm, 0).
+ * The results do not depend on the settings beyond the order of the float32
+ * sums of the backward (which the settings fix, so every run with the same
+ * settings gives the same bits). */
+#define GPA_BATCH_CLASSES 5
+typedef struct {
+    int64_t chunk_points[GPA_BATCH_CLASSES];
+    int32_t ctas_per_sm[GPA_BATCH_CLASSES];
+    int32_t small_groups[GPA_BATCH_CLASSES];
+} gpa_batched_opts;
+
+/* As gpa_gmm_batched_workspace_bytes, gmm_batched_prepare, gmm_batched_vjp
+ * with per-class settings (host struct, read during the call; the same
+ * settings for all three). GPA_ERR_ARG (0 bytes) for a null opts, a
+ * chunk_points below 64 or a negative ctas_per_sm. */
+GPA_API size_t gpa_gmm_batched_workspace_bytes_opts(const gpa_gmm_instance* inst, int32_t n_inst,
+                                                    const gpa_batched_opts* opts);
+GPA_API int gmm_batched_prepare_opts(const gpa_gmm_instance* inst, int32_t n_inst, const gpa_batched_opts* opts,
+                                     void* ws, size_t ws_bytes, gpa_stream_t stream);
+GPA_API int gmm_batched_vjp_opts(const gpa_gmm_instance* inst, int32_t n_inst, const gpa_batched_opts* opts,
+                                 void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
 
 /* ========================================================================= */
 /* Camera reprojection (bundle adjustment residual)                          */

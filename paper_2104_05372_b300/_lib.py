@@ -68,6 +68,9 @@ _SIGS = {
     "gpa_gmm_batched_workspace_bytes": ([_P, _I32, _I64], _SZ),
     "gmm_batched_prepare": ([_P, _I32, _I64, _P, _SZ, _P], _I32),
     "gmm_batched_vjp": ([_P, _I32, _I64, _I32, _P, _SZ, _P, _P], _I32),
+    "gpa_gmm_batched_workspace_bytes_opts": ([_P, _I32, _P], _SZ),
+    "gmm_batched_prepare_opts": ([_P, _I32, _P, _P, _SZ, _P], _I32),
+    "gmm_batched_vjp_opts": ([_P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "gpa_check_bounded_wait": ([_I64, _P, _P, _P], _I32),
     "gpa_trace_enable": ([_I32], None),
     "gpa_trace_summary": ([C.c_char_p, _SZ], _I32),
@@ -314,6 +317,37 @@ class GmmInstance(C.Structure):
                 ("gamma", C.c_double), ("m", C.c_int32), ("seed", C.c_double), ("prec", C.c_int32)]
 
 
+BATCH_CLASSES = 5  # padded dimension 8, 16, 32, 64, 128 (GPA_BATCH_CLASSES)
+BATCH_CLASS_DP = (8, 16, 32, 64, 128)
+
+
+def batch_class(d: int, prec: int = 0) -> int:
+    """Class index of an instance of dimension d in the batched form (the
+    tensor-core instances by their padded dimension 64 / 128)."""
+    if prec == PREC_BF16_TC:
+        return 3 if d <= 64 else 4
+    return 0 if d <= 8 else 1 if d <= 16 else 2 if d <= 32 else 3 if d <= 64 else 4
+
+
+class BatchedOpts(C.Structure):
+    """C layout of gpa_batched_opts (include/gpa.h): per class chunk_points,
+    ctas_per_sm, small_groups."""
+    _fields_ = [("chunk_points", C.c_int64 * BATCH_CLASSES), ("ctas_per_sm", C.c_int32 * BATCH_CLASSES),
+                ("small_groups", C.c_int32 * BATCH_CLASSES)]
+
+    @classmethod
+    def make(cls, per_class):
+        """per_class: {class index: {"chunk_points", "ctas_per_sm", "small_groups"}}; classes not
+        given take (4096, 0, 0)."""
+        o = cls()
+        for c in range(BATCH_CLASSES):
+            v = per_class.get(c, per_class.get(str(c), {}))
+            o.chunk_points[c] = int(v.get("chunk_points", 4096))
+            o.ctas_per_sm[c] = int(v.get("ctas_per_sm", 0))
+            o.small_groups[c] = int(v.get("small_groups", 0))
+        return o
+
+
 class GmmBatch:
     """Device tensors and descriptors of a batch of GMM instances.
 
@@ -323,8 +357,12 @@ class GmmBatch:
     allocated here.
     """
 
-    def __init__(self, instances, chunk_points=4096):
+    def __init__(self, instances, chunk_points=4096, opts=None):
+        """opts: None (every class at chunk_points, CTAs per SM as given to
+        run) or {class index: {"chunk_points", "ctas_per_sm", "small_groups"}}
+        (the _opts entry points; run's ctas_per_sm is then ignored)."""
         self.chunk_points = int(chunk_points)
+        self.opts = None if opts is None else BatchedOpts.make(opts)
         dev = instances[0]["x"].device
         shapes = [_gmm_params(i["x"], i["alpha"], i["mu"], i["q"], i["l"]) for i in instances]
         # every gradient and objective of the batch in one buffer: one memset clears them
@@ -351,19 +389,30 @@ class GmmBatch:
         self.desc = arr
         self.n_inst = len(instances)
         self.pairs = sum(n * k for n, d, k in shapes)
-        nb = int(load().gpa_gmm_batched_workspace_bytes(C.byref(arr), self.n_inst, self.chunk_points))
+        if self.opts is None:
+            nb = int(load().gpa_gmm_batched_workspace_bytes(C.byref(arr), self.n_inst, self.chunk_points))
+        else:
+            nb = int(load().gpa_gmm_batched_workspace_bytes_opts(C.byref(arr), self.n_inst, C.byref(self.opts)))
         if nb == 0:
             raise GpaError(ERR_ARG, "gpa_gmm_batched_workspace_bytes")
         self.ws = workspace(nb, dev)
 
     def prepare(self, stream=None):
-        rc = load().gmm_batched_prepare(C.byref(self.desc), self.n_inst, self.chunk_points, _ptr(self.ws),
-                                        self.ws.numel(), _stream(stream))
+        if self.opts is None:
+            rc = load().gmm_batched_prepare(C.byref(self.desc), self.n_inst, self.chunk_points, _ptr(self.ws),
+                                            self.ws.numel(), _stream(stream))
+        else:
+            rc = load().gmm_batched_prepare_opts(C.byref(self.desc), self.n_inst, C.byref(self.opts),
+                                                 _ptr(self.ws), self.ws.numel(), _stream(stream))
         _ok(rc, "gmm_batched_prepare")
 
     def run(self, ctas_per_sm=0, status=None, stream=None):
-        rc = load().gmm_batched_vjp(C.byref(self.desc), self.n_inst, self.chunk_points, int(ctas_per_sm),
-                                    _ptr(self.ws), self.ws.numel(), _ptr(status), _stream(stream))
+        if self.opts is None:
+            rc = load().gmm_batched_vjp(C.byref(self.desc), self.n_inst, self.chunk_points, int(ctas_per_sm),
+                                        _ptr(self.ws), self.ws.numel(), _ptr(status), _stream(stream))
+        else:
+            rc = load().gmm_batched_vjp_opts(C.byref(self.desc), self.n_inst, C.byref(self.opts), _ptr(self.ws),
+                                             self.ws.numel(), _ptr(status), _stream(stream))
         _ok(rc, "gmm_batched_vjp")
 
     def zero_grads(self):

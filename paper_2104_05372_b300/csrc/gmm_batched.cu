@@ -48,7 +48,9 @@ struct BItem {
 };
 
 constexpr int kClasses = 5;  // padded dimension 8, 16, 32, 64, 128
-constexpr int kPhases = 4;   // prep, forward, backward, finalize
+static_assert(kClasses == GPA_BATCH_CLASSES, "classes of gpa_batched_opts");
+// phases: prep, forward, backward in default groups, backward in small groups, finalize
+constexpr int kPhPrep = 0, kPhFwd = 1, kPhBwd = 2, kPhBwdSmall = 3, kPhFin = 4, kPhases = 5;
 int class_of(int dp) { return dp == 8 ? 0 : dp == 16 ? 1 : dp == 32 ? 2 : dp == 64 ? 3 : 4; }
 // D <= 8 has a class of its own here (the per-call path pads it to 16)
 int batched_dp(int d) { return d <= 8 ? 8 : gmm_dp(d); }
@@ -67,6 +69,20 @@ int bwd_tpb(int dp) {
 int gc_of(int dp) {
     return dp == 8 ? kD8Group : dp == 16 ? Bwd<16>::GC : dp == 32 ? Bwd<32>::GC : dp == 64 ? Bwd<64>::GC
                                                                                            : Bwd<128>::GC;
+}
+// small component groups (sequential layout): components and threads per CTA
+constexpr int kSmallGc16 = 10, kSmallGc32 = 6;
+int small_gc_of(int dp) { return dp == 16 ? kSmallGc16 : dp == 32 ? kSmallGc32 : 0; }
+int small_threads_of(int dp) {
+    return dp == 16 ? Bwd<16, kSmallGc16>::THREADS : dp == 32 ? Bwd<32, kSmallGc32>::THREADS : 0;
+}
+int bwd_threads_of(int dp) { return dp == 16 ? Bwd<16>::THREADS : dp == 32 ? Bwd<32>::THREADS : 0; }
+// the small groups for this instance: fewer thread slots per point over its components
+bool use_small_groups(int dp, int k) {
+    const int gs = small_gc_of(dp);
+    if (gs == 0) return false;
+    const int gb = gc_of(dp);
+    return (int64_t)((k + gs - 1) / gs) * small_threads_of(dp) < (int64_t)((k + gb - 1) / gb) * bwd_threads_of(dp);
 }
 
 struct Plan {
@@ -121,7 +137,7 @@ TcLanes* tc_lanes(bool create) {
 }
 
 // Deterministic plan: workspace offsets are relative (base = 0) until bound.
-bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, char* base, Plan& P) {
+bool make_plan(const gpa_gmm_instance* in, int n_inst, const gpa_batched_opts& O, char* base, Plan& P) {
     P.inst.resize(n_inst);
     size_t off = 256;  // header
     P.off_desc = off;
@@ -144,24 +160,27 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
         if (I.prec == GPA_PREC_BF16_TC) {  // prep and finalize items only; pointers bound below
             P.tc.push_back(i);
             B.nchunks = gmm_tc_bwd_nchunks(I.n, I.d, I.k);
-            for (int kk = 0; kk < I.k; ++kk) P.items[c][0].push_back({i, kk, 0, 0});
-            for (int kk = 0; kk < I.k; ++kk) P.items[c][3].push_back({i, kk, 0, 0});
-            P.items[c][3].push_back({i, -1, 0, 0});  // objective
+            for (int kk = 0; kk < I.k; ++kk) P.items[c][kPhPrep].push_back({i, kk, 0, 0});
+            for (int kk = 0; kk < I.k; ++kk) P.items[c][kPhFin].push_back({i, kk, 0, 0});
+            P.items[c][kPhFin].push_back({i, -1, 0, 0});  // objective
             continue;
         }
         const int64_t ntiles64 = (I.n + bwd_tpb(dp) - 1) / bwd_tpb(dp);  // backward tiles
+        const int64_t chunk_points = O.chunk_points[c];
         int nch = (int)((I.n + chunk_points - 1) / chunk_points);
         nch = std::max(1, std::min(nch, kGmmMaxChunks));
         nch = (int)std::min<int64_t>(nch, ntiles64);
         B.tiles_per_chunk = (ntiles64 + nch - 1) / nch;
         B.nchunks = (int)((ntiles64 + B.tiles_per_chunk - 1) / B.tiles_per_chunk);
-        const int groups = (I.k + gc_of(dp) - 1) / gc_of(dp);
-        for (int kk = 0; kk < I.k; ++kk) P.items[c][0].push_back({i, kk, 0, 0});
-        for (int t = 0; t < B.ntiles128; ++t) P.items[c][1].push_back({i, t, 0, 0});
+        const bool small = O.small_groups[c] && use_small_groups(dp, I.k);
+        const int gc = small ? small_gc_of(dp) : gc_of(dp);
+        const int groups = (I.k + gc - 1) / gc;
+        for (int kk = 0; kk < I.k; ++kk) P.items[c][kPhPrep].push_back({i, kk, 0, 0});
+        for (int t = 0; t < B.ntiles128; ++t) P.items[c][kPhFwd].push_back({i, t, 0, 0});
         for (int g = 0; g < groups; ++g)
-            for (int ch = 0; ch < B.nchunks; ++ch) P.items[c][2].push_back({i, g, ch, 0});
-        for (int kk = 0; kk < I.k; ++kk) P.items[c][3].push_back({i, kk, 0, 0});
-        P.items[c][3].push_back({i, -1, 0, 0});  // objective
+            for (int ch = 0; ch < B.nchunks; ++ch) P.items[c][small ? kPhBwdSmall : kPhBwd].push_back({i, g, ch, 0});
+        for (int kk = 0; kk < I.k; ++kk) P.items[c][kPhFin].push_back({i, kk, 0, 0});
+        P.items[c][kPhFin].push_back({i, -1, 0, 0});  // objective
     }
     // longest-processing-time order for the forward and backward lists
     for (int c = 0; c < kClasses; ++c) {
@@ -172,10 +191,11 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, int64_t chunk_points, cha
             const int64_t t0 = (int64_t)w.b * B.tiles_per_chunk;
             return (double)std::max<int64_t>(0, std::min<int64_t>(ntiles64, t0 + B.tiles_per_chunk) - t0);
         };
-        std::stable_sort(P.items[c][1].begin(), P.items[c][1].end(),
+        std::stable_sort(P.items[c][kPhFwd].begin(), P.items[c][kPhFwd].end(),
                          [&](const BItem& u, const BItem& v) { return cost_f(u) > cost_f(v); });
-        std::stable_sort(P.items[c][2].begin(), P.items[c][2].end(),
-                         [&](const BItem& u, const BItem& v) { return cost_b(u) > cost_b(v); });
+        for (int ph : {kPhBwd, kPhBwdSmall})
+            std::stable_sort(P.items[c][ph].begin(), P.items[c][ph].end(),
+                             [&](const BItem& u, const BItem& v) { return cost_b(u) > cost_b(v); });
     }
     for (int c = 0; c < kClasses; ++c)
         for (int ph = 0; ph < kPhases; ++ph) {
@@ -317,8 +337,8 @@ __global__ void __launch_bounds__(256, (DP <= 64 ? 2 : 1))
     }
 }
 
-template <int DP>
-__global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
+template <int DP, int GCX = 0>
+__global__ void __launch_bounds__(Bwd<DP, GCX>::THREADS, Bwd<DP, GCX>::MINB)
     batched_bwd_kernel(const BInst* __restrict__ inst, const BItem* __restrict__ items, int n_items,
                        int* counter) {
     for (;;) {
@@ -326,9 +346,9 @@ __global__ void __launch_bounds__(Bwd<DP>::THREADS, Bwd<DP>::MINB)
         if (it >= n_items) break;
         const BItem w = items[it];
         const BInst& B = inst[w.inst];
-        gmm_bwd_kernel_body<DP, Bwd<DP>::UNROLL_BATCHED>(B.x, B.n, B.d, B.k, B.lj, B.n, B.lse, (float)B.seed,
-                                                     B.tiles_per_chunk, B.bS, B.bM,
-                                (unsigned)w.a, (unsigned)w.b);
+        gmm_bwd_kernel_body<DP, Bwd<DP>::UNROLL_BATCHED, GCX>(B.x, B.n, B.d, B.k, B.lj, B.n, B.lse, (float)B.seed,
+                                                            B.tiles_per_chunk, B.bS, B.bM, (unsigned)w.a,
+                                                            (unsigned)w.b);
         __syncthreads();
     }
 }
@@ -538,7 +558,7 @@ unsigned persistent_grid(K kern, int threads, size_t smem, int n_items, int ctas
     return (unsigned)std::max(1, std::min(n_items, sms() * occ));
 }
 
-// The four phases of one class: prep and finalize also cover the class's
+// The phases of one class: prep and finalize also cover the class's
 // tensor-core instances, forward and backward only its FP32 ones.
 template <int DP>
 struct ClassRun {
@@ -551,45 +571,59 @@ struct ClassRun {
     int count(int ph) const { return (int)P.items[c][ph].size(); }
 
     int prep(cudaStream_t s) const {
-        if (count(0) == 0) return GPA_OK;
+        if (count(kPhPrep) == 0) return GPA_OK;
         auto k = batched_prep_kernel<DP>;
-        const unsigned g = persistent_grid(k, 128, 0, count(0), 0);
-        GPA_LAUNCH("gmm_batched_prep", s, k<<<g, 128, 0, s>>>(inst(), items(0), count(0), counter(0)));
+        const unsigned g = persistent_grid(k, 128, 0, count(kPhPrep), 0);
+        GPA_LAUNCH("gmm_batched_prep", s,
+                   k<<<g, 128, 0, s>>>(inst(), items(kPhPrep), count(kPhPrep), counter(kPhPrep)));
+        return GPA_OK;
+    }
+    template <int GCX>
+    int bwd(int ph, int ctas_per_sm, cudaStream_t s) const {
+        if (count(ph) == 0) return GPA_OK;
+        using C = Bwd<DP, GCX>;
+        auto kb = batched_bwd_kernel<DP, GCX>;
+        if (!smem_attr(kb, C::SMEM)) return GPA_ERR_CUDA;
+        const unsigned gb = persistent_grid(kb, C::THREADS, C::SMEM, count(ph), ctas_per_sm);
+        GPA_LAUNCH("gmm_batched_bwd", s, kb<<<gb, C::THREADS, C::SMEM, s>>>(inst(), items(ph), count(ph), counter(ph)));
         return GPA_OK;
     }
     int core(int ctas_per_sm, int32_t* status, cudaStream_t s) const {
-        if (count(1) == 0) return GPA_OK;
+        if (count(kPhFwd) == 0) return GPA_OK;
         if constexpr (DP == 8) {
             (void)status;
             auto kf = batched_fwd8_kernel;
-            const unsigned gf = persistent_grid(kf, 128, 0, count(1), ctas_per_sm);
-            GPA_LAUNCH("gmm_batched_fwd", s, kf<<<gf, 128, 0, s>>>(inst(), items(1), count(1), counter(1)));
+            const unsigned gf = persistent_grid(kf, 128, 0, count(kPhFwd), ctas_per_sm);
+            GPA_LAUNCH("gmm_batched_fwd", s,
+                       kf<<<gf, 128, 0, s>>>(inst(), items(kPhFwd), count(kPhFwd), counter(kPhFwd)));
             auto kb = batched_bwd8_kernel;
-            const unsigned gb = persistent_grid(kb, 128, 0, count(2), ctas_per_sm);
-            GPA_LAUNCH("gmm_batched_bwd", s, kb<<<gb, 128, 0, s>>>(inst(), items(2), count(2), counter(2)));
+            const unsigned gb = persistent_grid(kb, 128, 0, count(kPhBwd), ctas_per_sm);
+            GPA_LAUNCH("gmm_batched_bwd", s,
+                       kb<<<gb, 128, 0, s>>>(inst(), items(kPhBwd), count(kPhBwd), counter(kPhBwd)));
+            return GPA_OK;
         } else {
             auto kf = batched_fwd_kernel<DP>;
             if (!smem_attr(kf, Fwd<DP>::SMEM)) return GPA_ERR_CUDA;
-            const unsigned gf = persistent_grid(kf, Fwd<DP>::THREADS, Fwd<DP>::SMEM, count(1), ctas_per_sm);
+            const unsigned gf = persistent_grid(kf, Fwd<DP>::THREADS, Fwd<DP>::SMEM, count(kPhFwd), ctas_per_sm);
             GPA_LAUNCH("gmm_batched_fwd", s,
-                       kf<<<gf, Fwd<DP>::THREADS, Fwd<DP>::SMEM, s>>>(inst(), items(1), count(1), counter(1),
-                                                                      status));
-            auto kb = batched_bwd_kernel<DP>;
-            if (!smem_attr(kb, Bwd<DP>::SMEM)) return GPA_ERR_CUDA;
-            const unsigned gb = persistent_grid(kb, Bwd<DP>::THREADS, Bwd<DP>::SMEM, count(2), ctas_per_sm);
-            GPA_LAUNCH("gmm_batched_bwd", s,
-                       kb<<<gb, Bwd<DP>::THREADS, Bwd<DP>::SMEM, s>>>(inst(), items(2), count(2), counter(2)));
+                       kf<<<gf, Fwd<DP>::THREADS, Fwd<DP>::SMEM, s>>>(inst(), items(kPhFwd), count(kPhFwd),
+                                                                      counter(kPhFwd), status));
+            int rc = bwd<0>(kPhBwd, ctas_per_sm, s);
+            if (rc) return rc;
+            if constexpr (DP == 16) return bwd<kSmallGc16>(kPhBwdSmall, ctas_per_sm, s);
+            if constexpr (DP == 32) return bwd<kSmallGc32>(kPhBwdSmall, ctas_per_sm, s);
+            return GPA_OK;
         }
-        return GPA_OK;
     }
     int fin(cudaStream_t s) const {
-        if (count(3) == 0) return GPA_OK;
+        if (count(kPhFin) == 0) return GPA_OK;
         constexpr int NB = (DP / 8) * (DP / 8 + 1) / 2;
         const size_t smem = sizeof(double) * (NB * 64 + 3 * DP + 1) + sizeof(float) * 2 * DP * DP + 64;
         auto k = batched_fin_kernel<DP>;
         if (!smem_attr(k, smem)) return GPA_ERR_CUDA;
-        const unsigned g = persistent_grid(k, 256, smem, count(3), 0);
-        GPA_LAUNCH("gmm_batched_finalize", s, k<<<g, 256, smem, s>>>(inst(), items(3), count(3), counter(3)));
+        const unsigned g = persistent_grid(k, 256, smem, count(kPhFin), 0);
+        GPA_LAUNCH("gmm_batched_finalize", s,
+                   k<<<g, 256, smem, s>>>(inst(), items(kPhFin), count(kPhFin), counter(kPhFin)));
         return GPA_OK;
     }
 };
@@ -614,22 +648,40 @@ int check_instances(const gpa_gmm_instance* in, int n_inst) {
 
 using namespace gpa;
 
-extern "C" size_t gpa_gmm_batched_workspace_bytes(const gpa_gmm_instance* inst, int32_t n_inst,
-                                                  int64_t chunk_points) {
-    if (check_instances(inst, n_inst) || chunk_points < 64) return 0;
+namespace {
+gpa_batched_opts uniform_opts(int64_t chunk_points, int32_t ctas_per_sm) {
+    gpa_batched_opts O;
+    for (int c = 0; c < kClasses; ++c) {
+        O.chunk_points[c] = chunk_points;
+        O.ctas_per_sm[c] = ctas_per_sm;
+        O.small_groups[c] = 0;
+    }
+    return O;
+}
+bool opts_ok(const gpa_batched_opts* O) {
+    if (!O) return false;
+    for (int c = 0; c < kClasses; ++c)
+        if (O->chunk_points[c] < 64 || O->ctas_per_sm[c] < 0) return false;
+    return true;
+}
+}  // namespace
+
+extern "C" size_t gpa_gmm_batched_workspace_bytes_opts(const gpa_gmm_instance* inst, int32_t n_inst,
+                                                       const gpa_batched_opts* opts) {
+    if (check_instances(inst, n_inst) || !opts_ok(opts)) return 0;
     Plan P;
-    if (!make_plan(inst, n_inst, chunk_points, nullptr, P)) return 0;
+    if (!make_plan(inst, n_inst, *opts, nullptr, P)) return 0;
     return P.total + 256;
 }
 
-extern "C" int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points, void* ws,
-                                   size_t ws_bytes, gpa_stream_t stream) {
+extern "C" int gmm_batched_prepare_opts(const gpa_gmm_instance* inst, int32_t n_inst, const gpa_batched_opts* opts,
+                                        void* ws, size_t ws_bytes, gpa_stream_t stream) {
     int rc = check_instances(inst, n_inst);
     if (rc) return rc;
-    if (!ws || chunk_points < 64) return GPA_ERR_ARG;
+    if (!ws || !opts_ok(opts)) return GPA_ERR_ARG;
     if (((uintptr_t)ws) & 255) return GPA_ERR_ALIGN;
     Plan P;
-    if (!make_plan(inst, n_inst, chunk_points, (char*)ws, P)) return GPA_ERR_ARG;
+    if (!make_plan(inst, n_inst, *opts, (char*)ws, P)) return GPA_ERR_ARG;
     if (ws_bytes < P.total) return GPA_ERR_WORKSPACE;
     if (!P.tc.empty() && !tc_lanes(true)) return GPA_ERR_CUDA;
     // host image of descriptors and work lists, copied in one transfer
@@ -649,21 +701,21 @@ extern "C" int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst,
     return GPA_OK;
 }
 
-extern "C" int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
-                               int32_t ctas_per_sm, void* ws, size_t ws_bytes, int32_t* dev_status,
-                               gpa_stream_t stream) {
+extern "C" int gmm_batched_vjp_opts(const gpa_gmm_instance* inst, int32_t n_inst, const gpa_batched_opts* opts,
+                                    void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream) {
     int rc = check_instances(inst, n_inst);
     if (rc) return rc;
-    if (!ws || chunk_points < 64 || ctas_per_sm < 0) return GPA_ERR_ARG;
+    if (!ws || !opts_ok(opts)) return GPA_ERR_ARG;
     if (((uintptr_t)ws) & 255) return GPA_ERR_ALIGN;
     Plan P;
-    if (!make_plan(inst, n_inst, chunk_points, (char*)ws, P)) return GPA_ERR_ARG;
+    if (!make_plan(inst, n_inst, *opts, (char*)ws, P)) return GPA_ERR_ARG;
     if (ws_bytes < P.total) return GPA_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync((char*)ws + P.off_counters, 0, sizeof(int) * kClasses * kPhases, s) != cudaSuccess ||
         cudaMemsetAsync((char*)ws + P.off_partials, 0, P.partial_bytes, s) != cudaSuccess)
         return GPA_ERR_CUDA;
     char* w = (char*)ws;
+    const int* cps = opts->ctas_per_sm;
     const ClassRun<8> c8{P, w, 0};
     const ClassRun<16> c16{P, w, 1};
     const ClassRun<32> c32{P, w, 2};
@@ -675,14 +727,34 @@ extern "C" int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int
     if ((rc = c8.prep(s)) || (rc = c16.prep(s)) || (rc = c32.prep(s)) || (rc = c64.prep(s)) || (rc = c128.prep(s)))
         return rc;
     rc = tc_fork_and_run(inst, P, w, dev_status, s);
-    if (!rc) rc = c8.core(ctas_per_sm, dev_status, s);
-    if (!rc) rc = c16.core(ctas_per_sm, dev_status, s);
-    if (!rc) rc = c32.core(ctas_per_sm, dev_status, s);
-    if (!rc) rc = c64.core(ctas_per_sm, dev_status, s);
-    if (!rc) rc = c128.core(ctas_per_sm, dev_status, s);
+    if (!rc) rc = c8.core(cps[0], dev_status, s);
+    if (!rc) rc = c16.core(cps[1], dev_status, s);
+    if (!rc) rc = c32.core(cps[2], dev_status, s);
+    if (!rc) rc = c64.core(cps[3], dev_status, s);
+    if (!rc) rc = c128.core(cps[4], dev_status, s);
     const int jr = tc_join(P, s);
     if (rc || jr) return rc ? rc : jr;
     if ((rc = c8.fin(s)) || (rc = c16.fin(s)) || (rc = c32.fin(s)) || (rc = c64.fin(s)) || (rc = c128.fin(s)))
         return rc;
     return GPA_OK;
+}
+
+extern "C" size_t gpa_gmm_batched_workspace_bytes(const gpa_gmm_instance* inst, int32_t n_inst,
+                                                  int64_t chunk_points) {
+    const gpa_batched_opts O = uniform_opts(chunk_points, 0);
+    return gpa_gmm_batched_workspace_bytes_opts(inst, n_inst, &O);
+}
+
+extern "C" int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points, void* ws,
+                                   size_t ws_bytes, gpa_stream_t stream) {
+    const gpa_batched_opts O = uniform_opts(chunk_points, 0);
+    return gmm_batched_prepare_opts(inst, n_inst, &O, ws, ws_bytes, stream);
+}
+
+extern "C" int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
+                               int32_t ctas_per_sm, void* ws, size_t ws_bytes, int32_t* dev_status,
+                               gpa_stream_t stream) {
+    if (ctas_per_sm < 0) return GPA_ERR_ARG;
+    const gpa_batched_opts O = uniform_opts(chunk_points, ctas_per_sm);
+    return gmm_batched_vjp_opts(inst, n_inst, &O, ws, ws_bytes, dev_status, stream);
 }

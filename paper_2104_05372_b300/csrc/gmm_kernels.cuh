@@ -53,12 +53,16 @@ __host__ __device__ __forceinline__ int bwd_swz(int c) {
 //     halves; the other NOW warps hold one off-diagonal block per lane. The 16
 //     warps (4 per scheduler) carry equal work except the diagonal warps'
 //     one-third extra, spread over different schedulers.
-template <int DP>
+// GCX (sequential layout only): components per CTA other than the default,
+// for the batched form's small component groups (instances with few
+// components, where a default group would leave most threads idle).
+template <int DP, int GCX = 0>
 struct Bwd {
     static constexpr int NB = DP / 8;
     static constexpr int NBLK = NB * (NB + 1) / 2;     // lower blocks incl. diagonal
     static constexpr bool WB = DP >= 64;
-    static constexpr int GC = DP == 16 ? 42 : DP == 32 ? 25 : DP == 64 ? 16 : 4;  // components per CTA
+    static_assert(GCX == 0 || !WB, "small component groups: sequential layout only");
+    static constexpr int GC = GCX ? GCX : DP == 16 ? 42 : DP == 32 ? 25 : DP == 64 ? 16 : 4;  // components per CTA
     static constexpr int BPW = WB ? 32 / GC : 0;                 // slots per warp (lanes per slot = GC)
     static constexpr int NDW = WB ? (NB / 2) * GC / 32 : 0;      // warps on pairs of diagonal blocks
     static constexpr int NOW = WB ? (NBLK - NB) * GC / 32 : 0;   // warps on off-diagonal blocks
@@ -72,7 +76,9 @@ struct Bwd {
     static constexpr int MP = NB == 2 ? 3 : NB == 4 ? 2 : 1;  // m / R pairs per thread and block
     static constexpr int NACT = GC * NBLK;               // threads with a block (sequential layout)
     static constexpr int THREADS = WB ? 32 * (NDW + NOW) : ((NACT + 31) / 32) * 32;
-    static constexpr int MINB = DP == 16 ? 3 : DP == 32 ? 2 : 1;  // resident CTAs per SM
+    // resident CTAs per SM: as many threads per SM as the default group has
+    static constexpr int MINB_DEF = DP == 16 ? 3 : DP == 32 ? 2 : 1;
+    static constexpr int MINB = GCX ? MINB_DEF * (Bwd<DP>::THREADS / THREADS) : MINB_DEF;
     static constexpr int XST = DP + 4;  // row stride of the point tiles; floats DP, DP+1 hold 1.0
     // point-loop unroll of the per-call kernel and of the persistent batched
     // kernel, as far as the register budget of MINB resident CTAs allows
@@ -579,12 +585,12 @@ static __global__ void __launch_bounds__(256) gmm_objective_finalize_kernel(
 // UNROLL: point-loop unroll, registers permitting (the plain kernel takes 4
 // for padded dimensions up to 64, the persistent batched kernel 2): the next
 // points' shared loads overlap the FMAs.
-template <int DP, int UNROLL = 1>
+template <int DP, int UNROLL = 1, int GCX = 0>
 __device__ __forceinline__ void gmm_bwd_seq_body(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
                    float* __restrict__ partM, unsigned bx, unsigned by) {
-    using C = Bwd<DP>;
+    using C = Bwd<DP, GCX>;
     constexpr int TPB = C::TPB, XST = C::XST, GC = C::GC, NB = C::NB, NBLK = C::NBLK, MP = C::MP;
     constexpr int NT = C::THREADS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1110,7 +1116,7 @@ __device__ __forceinline__ void gmm_bwd_wb_body(const float* __restrict__ x, int
     }
 }
 
-template <int DP, int UNROLL = 1>
+template <int DP, int UNROLL = 1, int GCX = 0>
 __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x, int64_t n, int d, int k,
                    const float* __restrict__ lj, int64_t lj_ld, const float* __restrict__ lse,
                    float seed, int64_t tiles_per_chunk, float* __restrict__ partS,
@@ -1118,7 +1124,8 @@ __device__ __forceinline__ void gmm_bwd_kernel_body(const float* __restrict__ x,
     if constexpr (Bwd<DP>::WB)
         gmm_bwd_wb_body<DP, UNROLL>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM, bx, by);
     else
-        gmm_bwd_seq_body<DP, UNROLL>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM, bx, by);
+        gmm_bwd_seq_body<DP, UNROLL, GCX>(x, n, d, k, lj, lj_ld, lse, seed, tiles_per_chunk, partS, partM, bx,
+                                          by);
 }
 
 template <int DP>

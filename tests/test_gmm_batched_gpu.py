@@ -87,14 +87,47 @@ def test_graph_capture_and_replay():
             assert np.array_equal(host(u), v)
 
 
-def test_autotuner_picks_and_caches(tmp_path):
+def test_autotuner_picks_per_class_and_caches(tmp_path):
+    """SHAPES[:5] holds classes D <= 8 (three instances), D <= 16 and D <= 32:
+    each is tuned on its own instances, the two with small component groups
+    over both group sizes."""
     from paper_2104_05372_b300 import autotune
     _, inst = _instances(SHAPES[:5], seed=3)
     path = str(tmp_path / "tune.json")
     r1 = autotune.tune_batched(inst, chunks=(256, 4096), ctas=(0,), reps=1, cache_path=path)
-    assert r1["chunk_points"] in (256, 4096) and len(r1["table"]) == 2
+    assert sorted(r1["opts"]) == [0, 1, 2]
+    assert [len(r1["classes"][c]["table"]) for c in (0, 1, 2)] == [2, 4, 4]
+    for c, o in r1["opts"].items():
+        assert o["chunk_points"] in (256, 4096) and o["ctas_per_sm"] == 0
+        assert o["small_groups"] in ((0, 1) if c in (1, 2) else (0,))
     r2 = autotune.tune_batched(inst, chunks=(256, 4096), ctas=(0,), reps=1, cache_path=path)
     assert r2 == r1
+
+
+@pytest.mark.parametrize("small", [0, 1])
+def test_batched_per_class_options_match_oracle(small):
+    """Per-class settings (chunk sizes, CTAs per SM, the small component
+    groups of D <= 16 and D <= 32): every instance against the oracle, and
+    against the uniform-settings run within float32 rounding."""
+    from paper_2104_05372_b300._lib import GmmBatch
+    shapes = SHAPES + [(600, 14, 3), (2000, 30, 7), (333, 16, 11), (1500, 24, 31)]
+    gs, inst = _instances(shapes, seed=13)
+    opts = {0: {"chunk_points": 256}, 1: {"chunk_points": 1024, "ctas_per_sm": 1, "small_groups": small},
+            2: {"chunk_points": 128, "small_groups": small}, 3: {"chunk_points": 4096}, 4: {"chunk_points": 64}}
+    b = GmmBatch(inst, opts=opts)
+    b.prepare()
+    st = status()
+    b.run(status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    _check(gs, inst, b)
+    u = GmmBatch(inst, chunk_points=2048)
+    u.prepare()
+    u.run()
+    for (_, g1), (_, g2) in zip(b.results(), u.results()):
+        for a, c in zip(g1, g2):
+            if a.numel():
+                assert rel_norm(host(a), host(c)) <= 1e-5
 
 
 @pytest.mark.slow
