@@ -82,7 +82,7 @@ struct Bwd {
     static constexpr int XST = DP + 4;  // row stride of the point tiles; floats DP, DP+1 hold 1.0
     // point-loop unroll of the per-call kernel and of the persistent batched
     // kernel, as far as the register budget of MINB resident CTAs allows
-    static constexpr int UNROLL = DP == 128 ? 2 : 4;
+    static constexpr int UNROLL = DP == 128 ? 2 : DP == 64 ? 8 : 4;
     static constexpr int UNROLL_BATCHED = DP == 128 ? 1 : 2;
     // point tiles double-buffered; raw log-joint, lse and the cotangents r
     // triple-buffered
