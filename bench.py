@@ -743,7 +743,7 @@ def run_batched(args, gpa, _lib, dev, stream, rank):
         per_class[f"D<={_lib.BATCH_CLASS_DP[c]}"] = {
             "instances": len(sub), "pairs": pairs_c, "ms": round(ms_c, 3), "achieved_tflops": round(ach, 2),
             "peak_tflops": round(peak, 1), "bound": "tensor" if tc else "alu", "frac": round(ach / peak, 4),
-            "settings": tune["opts"].get(c, "tensor-core contractions per instance (prep and finalize batched)")}
+            "settings": tune["opts"].get(c)}
     # plain path: one gmm_vjp call per instance (its own workspace, allocated beforehand)
     wss = [_lib.workspace(gpa.gpa_gmm_workspace_bytes(g.n, g.d, g.k, 0, 0), dev) for g in gs]
     grads = [gpa.gmm_vjp(i["x"], i["alpha"], i["mu"], i["q"], i["l"], i["gamma"], i["m"], ws=w)

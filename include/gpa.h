@@ -259,10 +259,14 @@ GPA_API int gmm_batched_prepare(const gpa_gmm_instance* inst, int32_t n_inst, in
  * n_inst, chunk_points must equal the gmm_batched_prepare arguments. FP32
  * CUDA-core arithmetic, deterministic like gmm_vjp. Instances with prec =
  * GPA_PREC_BF16_TC run the contractions of the tensor-core path of gmm_vjp
- * instead (their prep and finalize run in the class's persistent kernels),
- * spread over 8 library streams forked from `stream` with events and joined
- * back into it (capturable in the same graph); each has a workspace region
- * of its own (gmm_vjp's tensor-core workspace for its n, d, k). */
+ * instead (their prep and finalize run in the class's persistent kernels):
+ * those of one padded dimension (64 or 128) as one concatenated class, each
+ * stage one launch over all their tiles, when their BF16 responsibilities
+ * (rows: the largest K rounded up to 16; columns: the sum of their n rounded
+ * up to 128) fit 8 GiB; otherwise instance by instance, spread over 8 library
+ * streams forked from `stream` with events and joined back into it
+ * (capturable in the same graph), each in a workspace region of its own
+ * (gmm_vjp's tensor-core workspace for its n, d, k). */
 GPA_API int gmm_batched_vjp(const gpa_gmm_instance* inst, int32_t n_inst, int64_t chunk_points,
                             int32_t ctas_per_sm, void* ws, size_t ws_bytes, int32_t* dev_status,
                             gpa_stream_t stream);

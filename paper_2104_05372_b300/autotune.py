@@ -13,10 +13,10 @@ own instances alone. Its settings (gpa_batched_opts in include/gpa.h):
   components per CTA instead of 42 and 25), where that leaves fewer threads
   idle.
 
-For each class with FP32 instances the tuner times every candidate with CUDA
-events (best of `reps` runs after a warm-up) and keeps the fastest; classes
-with tensor-core instances only have nothing to tune (their contractions run
-per instance). Results are cached in a JSON file keyed by the device name and a
+For each class the tuner times every candidate with CUDA events (best of
+`reps` runs after a warm-up) and keeps the fastest; a class of tensor-core
+instances only (its stages one launch each over all its instances) has only
+its backward chunk size to tune. Results are cached in a JSON file keyed by the device name and a
 digest of the instance shapes, so the search runs once per workload and
 device. Default cache: $GPA_TUNE_CACHE, else ~/.cache/gpa_autotune.json.
 """
@@ -30,7 +30,7 @@ import torch
 
 from . import _lib
 
-CHUNKS = (1024, 2048, 4096, 8192, 16384)
+CHUNKS = (1024, 2048, 4096, 8192, 16384, 65536)
 CTAS = (0, 1)
 SMALL_CLASSES = (1, 2)  # D <= 16, D <= 32
 
@@ -68,9 +68,9 @@ def _time(batch, reps):
     return best
 
 
-def _tune_class(c, sub, chunks, ctas, reps):
+def _tune_class(c, sub, chunks, ctas, reps, small=True):
     table = []
-    smalls = (0, 1) if c in SMALL_CLASSES else (0,)
+    smalls = (0, 1) if small and c in SMALL_CLASSES else (0,)
     for cp in chunks:
         for sg in smalls:
             for ct in ctas:
@@ -101,10 +101,11 @@ def tune_batched(instances, chunks=CHUNKS, ctas=CTAS, reps=3, cache_path=None, r
     opts, classes = {}, {}
     for c in range(_lib.BATCH_CLASSES):
         sub = [i for i in instances if class_of(i) == c]
-        fp32 = [i for i in sub if int(i.get("prec", 0)) == _lib.PREC_FP32]
-        if not fp32:
+        if not sub:
             continue
-        opts[c], ms, table = _tune_class(c, sub, chunks, ctas, reps)
+        fp32 = any(int(i.get("prec", 0)) == _lib.PREC_FP32 for i in sub)
+        # a class of tensor-core instances only has its backward chunk size to tune
+        opts[c], ms, table = _tune_class(c, sub, chunks, ctas if fp32 else (0,), reps, small=fp32)
         classes[c] = {"n": len(sub), "ms": ms, "table": table}
     result = {"opts": opts, "classes": classes}
     cache[key] = result

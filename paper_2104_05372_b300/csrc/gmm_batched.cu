@@ -85,11 +85,31 @@ bool use_small_groups(int dp, int k) {
     return (int64_t)((k + gs - 1) / gs) * small_threads_of(dp) < (int64_t)((k + gb - 1) / gb) * bwd_threads_of(dp);
 }
 
+// Tensor-core instances of one padded dimension run as a concatenated class
+// (gmm_tc_cat_run: one launch per stage over all their tiles) when the
+// class's BF16 responsibilities fit kCatRBytes; otherwise each instance runs
+// the per-call stages in a workspace region of its own, on the forked streams.
+constexpr size_t kCatRBytes = (size_t)8 << 30;
+struct CatPlan {
+    bool on = false;
+    int tdp = 0;
+    std::vector<int> members;  // instance indices
+    std::vector<TcCatInst> cinst;
+    std::vector<int> tile_inst;
+    std::vector<int2> fwd_tiles;
+    std::vector<int4> gram_items;
+    int64_t np = 0, kc = 0, kr = 0;
+    size_t off_cinst = 0, off_tile_inst = 0, off_fwd_tiles = 0, off_gram_items = 0;
+    size_t off_rec = 0, off_xb = 0, off_xl = 0, off_qb = 0, off_ql = 0, off_rb = 0, off_xt = 0, off_lse = 0,
+           off_lj = 0;
+};
+
 struct Plan {
     std::vector<BInst> inst;
     std::vector<BItem> items[kClasses][kPhases];
-    std::vector<int> tc;          // instances on the tensor-core path
+    std::vector<int> tc;          // instances on the per-instance tensor-core path
     std::vector<size_t> tc_off;   // their workspace regions (per instance, indexed like tc)
+    CatPlan cat[2];               // concatenated tensor-core classes: padded dimension 64, 128
     size_t off_desc, off_items[kClasses][kPhases], off_counters, off_partials, partial_bytes, off_regions;
     size_t total;
 };
@@ -158,8 +178,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, const gpa_batched_opts& O
         B.seed = I.seed;
         B.ntiles128 = (int)((I.n + 127) / 128);
         if (I.prec == GPA_PREC_BF16_TC) {  // prep and finalize items only; pointers bound below
-            P.tc.push_back(i);
-            B.nchunks = gmm_tc_bwd_nchunks(I.n, I.d, I.k);
+            P.cat[dp == 64 ? 0 : 1].members.push_back(i);
             for (int kk = 0; kk < I.k; ++kk) P.items[c][kPhPrep].push_back({i, kk, 0, 0});
             for (int kk = 0; kk < I.k; ++kk) P.items[c][kPhFin].push_back({i, kk, 0, 0});
             P.items[c][kPhFin].push_back({i, -1, 0, 0});  // objective
@@ -197,17 +216,96 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, const gpa_batched_opts& O
             std::stable_sort(P.items[c][ph].begin(), P.items[c][ph].end(),
                              [&](const BItem& u, const BItem& v) { return cost_b(u) > cost_b(v); });
     }
+    // tensor-core instances: a concatenated class per padded dimension where
+    // its responsibilities fit, else the per-instance path
+    for (int q = 0; q < 2; ++q) {
+        CatPlan& C = P.cat[q];
+        C.tdp = q == 0 ? 64 : 128;
+        if (C.members.empty()) continue;
+        int64_t np = 0, kr = 0;
+        for (int i : C.members) {
+            np += (in[i].n + 127) / 128 * 128;
+            kr = std::max<int64_t>(kr, (in[i].k + 15) / 16 * 16);
+        }
+        C.on = (size_t)kr * (size_t)np * 2 <= kCatRBytes;
+        if (!C.on) {
+            for (int i : C.members) {
+                P.tc.push_back(i);
+                P.inst[i].nchunks = gmm_tc_bwd_nchunks(in[i].n, in[i].d, in[i].k);
+            }
+            continue;
+        }
+        C.np = np;
+        C.kr = kr;
+        const int64_t chunk_points = O.chunk_points[class_of(C.tdp)];
+        int64_t xoff = 0, xtoff = 0, koff = 0;
+        for (int m = 0; m < (int)C.members.size(); ++m) {
+            const int i = C.members[m];
+            const gpa_gmm_instance& I = in[i];
+            BInst& B = P.inst[i];
+            TcCatInst T{};
+            T.n = I.n;
+            T.d = I.d;
+            T.k = I.k;
+            T.xoff = xoff;
+            T.xtoff = xtoff;
+            T.koff = (int)koff;
+            const int krr = (I.k + 15) / 16 * 16;
+            T.kn = krr < 256 ? krr : 256;
+            T.seed = (float)I.seed;
+            const int gg = gmm_tc_cat_gram_groups(I.d, I.k);  // product groups x component groups
+            const int nkg = (krr + 255) / 256;
+            T.ng = gg / nkg;
+            const int64_t ntiles64 = (I.n + 63) / 64;
+            int nch = (int)std::min<int64_t>(std::max<int64_t>(1, (I.n + chunk_points - 1) / chunk_points),
+                                             kGmmMaxChunks);
+            nch = (int)std::min<int64_t>(nch, ntiles64);
+            T.tpc = (ntiles64 + nch - 1) / nch;
+            T.nchunks = (int)((ntiles64 + T.tpc - 1) / T.tpc);
+            B.nchunks = T.nchunks;
+            const int64_t npad = (I.n + 127) / 128 * 128;
+            for (int64_t t = 0; t < npad / 128; ++t) C.tile_inst.push_back(m);
+            for (int t = 0; t < B.ntiles128; ++t) C.fwd_tiles.push_back(make_int2(m, t));
+            for (int bx = 0; bx < gg; ++bx)
+                for (int ch = 0; ch < T.nchunks; ++ch) C.gram_items.push_back(make_int4(m, bx, ch, 0));
+            C.cinst.push_back(T);
+            xoff += npad;
+            xtoff += npad * I.d;
+            koff += I.k;
+        }
+        C.kc = koff;
+        // longest first: forward tiles by rounds (components), gram items by tiles per chunk
+        std::stable_sort(C.fwd_tiles.begin(), C.fwd_tiles.end(),
+                         [&](int2 u, int2 v) { return C.cinst[u.x].k > C.cinst[v.x].k; });
+        std::stable_sort(C.gram_items.begin(), C.gram_items.end(),
+                         [&](int4 u, int4 v) { return C.cinst[u.x].tpc > C.cinst[v.x].tpc; });
+    }
     for (int c = 0; c < kClasses; ++c)
         for (int ph = 0; ph < kPhases; ++ph) {
             P.off_items[c][ph] = off;
             off = a256(off + sizeof(BItem) * P.items[c][ph].size());
         }
+    for (CatPlan& C : P.cat) {
+        if (!C.on) continue;
+        C.off_cinst = off;
+        off = a256(off + sizeof(TcCatInst) * C.cinst.size());
+        C.off_tile_inst = off;
+        off = a256(off + sizeof(int) * C.tile_inst.size());
+        C.off_fwd_tiles = off;
+        off = a256(off + sizeof(int2) * C.fwd_tiles.size());
+        C.off_gram_items = off;
+        off = a256(off + sizeof(int4) * C.gram_items.size());
+    }
     P.off_counters = off;
     off = a256(off + sizeof(int) * kClasses * kPhases);
     // Accum partials of every instance, contiguous so that one memset clears them
     P.off_partials = off;
+    auto in_cat = [&](int i) {
+        if (in[i].prec != GPA_PREC_BF16_TC) return false;
+        return P.cat[P.inst[i].dp == 64 ? 0 : 1].on;
+    };
     for (int i = 0; i < n_inst; ++i) {
-        if (in[i].prec == GPA_PREC_BF16_TC) continue;
+        if (in[i].prec == GPA_PREC_BF16_TC && !in_cat(i)) continue;
         BInst& B = P.inst[i];
         B.bS = (float*)(base + off);
         off = a256(off + sizeof(float) * (size_t)B.nchunks * B.k * nblk(B.dp) * 64);
@@ -228,6 +326,47 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, const gpa_batched_opts& O
         B.fwd = (double*)(base + off);  off = a256(off + sizeof(double) * (size_t)B.ntiles128);
         B.lse = (float*)(base + off);   off = a256(off + sizeof(float) * (size_t)B.n);
         B.lj = (float*)(base + off);    off = a256(off + sizeof(float) * (size_t)B.n * B.k);
+    }
+    // concatenated tensor-core classes: shared buffers, per-instance scalars
+    for (CatPlan& C : P.cat) {
+        if (!C.on) continue;
+        const int tdp = C.tdp, rec_len = tdp * tdp + tdp + 4;
+        int64_t pairs = 0, xtf = 0;
+        for (int i : C.members) {
+            pairs += in[i].n * (int64_t)in[i].k;
+            xtf += (in[i].n + 127) / 128 * 128 * (int64_t)in[i].d;
+        }
+        C.off_rec = off; off = a256(off + sizeof(float) * (size_t)C.kc * rec_len);
+        C.off_xb = off;  off = a256(off + 2 * (size_t)C.np * tdp);
+        C.off_xl = off;  off = a256(off + 2 * (size_t)C.np * tdp);
+        C.off_qb = off;  off = a256(off + 2 * (size_t)C.kc * tdp * tdp);
+        C.off_ql = off;  off = a256(off + 2 * (size_t)C.kc * tdp * tdp);
+        C.off_rb = off;  off = a256(off + 2 * (size_t)C.kr * C.np);
+        C.off_xt = off;  off = a256(off + sizeof(float) * (size_t)xtf);
+        C.off_lse = off; off = a256(off + sizeof(float) * (size_t)C.np);
+        C.off_lj = off;  off = a256(off + sizeof(float) * (size_t)pairs);
+        int64_t ljo = 0;
+        for (int m = 0; m < (int)C.members.size(); ++m) {
+            const int i = C.members[m];
+            const gpa_gmm_instance& I = in[i];
+            BInst& B = P.inst[i];
+            TcCatInst& T = C.cinst[m];
+            B.x = I.x; B.alpha = I.alpha; B.mu = I.mu; B.q = I.q; B.l = I.l;
+            B.d_alpha = I.d_alpha; B.d_mu = I.d_mu; B.d_q = I.d_q; B.d_l = I.d_l; B.out = I.out;
+            B.rec = (float*)(base + C.off_rec) + (size_t)T.koff * rec_len;
+            B.scal = (double*)(base + off); off = a256(off + sizeof(double) * 8);
+            B.lpk = (double*)(base + off);  off = a256(off + sizeof(double) * (size_t)B.k);
+            B.fwd = (double*)(base + off);  off = a256(off + sizeof(double) * (size_t)B.ntiles128);
+            B.lse = (float*)(base + C.off_lse) + T.xoff;
+            B.lj = (float*)(base + C.off_lj) + ljo;
+            ljo += I.n * (int64_t)I.k;
+            T.x = I.x;
+            T.lj = B.lj;
+            T.lse = B.lse;
+            T.fwd = B.fwd;
+            T.bS = B.bS;
+            T.bM = B.bM;
+        }
     }
     // tensor-core regions: the per-call layout of each instance; the batched
     // prep and finalize read and write its records, scalars and partial sums there
@@ -692,6 +831,13 @@ extern "C" int gmm_batched_prepare_opts(const gpa_gmm_instance* inst, int32_t n_
             if (!P.items[c][ph].empty())
                 memcpy(img.data() + P.off_items[c][ph], P.items[c][ph].data(),
                        sizeof(BItem) * P.items[c][ph].size());
+    for (const CatPlan& C : P.cat) {
+        if (!C.on) continue;
+        memcpy(img.data() + C.off_cinst, C.cinst.data(), sizeof(TcCatInst) * C.cinst.size());
+        memcpy(img.data() + C.off_tile_inst, C.tile_inst.data(), sizeof(int) * C.tile_inst.size());
+        memcpy(img.data() + C.off_fwd_tiles, C.fwd_tiles.data(), sizeof(int2) * C.fwd_tiles.size());
+        memcpy(img.data() + C.off_gram_items, C.gram_items.data(), sizeof(int4) * C.gram_items.size());
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemcpyAsync(ws, img.data(), P.off_partials, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -727,6 +873,29 @@ extern "C" int gmm_batched_vjp_opts(const gpa_gmm_instance* inst, int32_t n_inst
     if ((rc = c8.prep(s)) || (rc = c16.prep(s)) || (rc = c32.prep(s)) || (rc = c64.prep(s)) || (rc = c128.prep(s)))
         return rc;
     rc = tc_fork_and_run(inst, P, w, dev_status, s);
+    for (const CatPlan& C : P.cat) {  // concatenated tensor-core classes, one launch per stage
+        if (rc || !C.on) continue;
+        TcCatClass T{};
+        T.tdp = C.tdp;
+        T.np = C.np;
+        T.kc = C.kc;
+        T.kr = C.kr;
+        T.inst = (const TcCatInst*)(w + C.off_cinst);
+        T.tile_inst = (const int*)(w + C.off_tile_inst);
+        T.fwd_tiles = (const int2*)(w + C.off_fwd_tiles);
+        T.gram_items = (const int4*)(w + C.off_gram_items);
+        T.n_fwd = (int)C.fwd_tiles.size();
+        T.n_gram = (int)C.gram_items.size();
+        T.rec = (const float*)(w + C.off_rec);
+        T.xb = w + C.off_xb;
+        T.xl = w + C.off_xl;
+        T.qb = w + C.off_qb;
+        T.ql = w + C.off_ql;
+        T.rb = w + C.off_rb;
+        T.xt = (float*)(w + C.off_xt);
+        T.status = dev_status;
+        rc = gmm_tc_cat_run(T, s);
+    }
     if (!rc) rc = c8.core(cps[0], dev_status, s);
     if (!rc) rc = c16.core(cps[1], dev_status, s);
     if (!rc) rc = c32.core(cps[2], dev_status, s);

@@ -74,6 +74,38 @@ int gmm_tc_vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_byt
                    int stages = kGmmStagesAll);
 int gmm_tc_bwd_nchunks(int64_t n, int d, int k);  // point chunks (partial sums) of the reverse pass
 
+// Batched form, tensor-core instances of one padded dimension run together:
+// their points, Q records, BF16 responsibilities and transposed point tiles
+// live in concatenated buffers (each instance's points at a row offset that is
+// a multiple of 128), and each stage is one launch over every instance's
+// tiles. Device descriptors, built on the host by the batched plan.
+struct TcCatInst {
+    const float* x;              // [n][d] points
+    float* lj;                   // [k][n] log-joint
+    float* lse;                  // [n] per-point logsumexp
+    double* fwd;                 // [ceil(n / 128)] per-tile sums of lse
+    float *bS, *bM;              // partial sums [nchunks][k][...] (zeroed by the caller)
+    int64_t n, xoff, xtoff;      // points; first row in x / R; float offset of its point tiles
+    int64_t tpc;                 // 64-point tiles per backward chunk
+    int d, k, koff, kn, ng, nchunks;
+    float seed;
+};
+struct TcCatClass {
+    int tdp;
+    int64_t np, kc, kr;          // rows of x / columns of R; components; rows of R
+    const TcCatInst* inst;       // [instances]
+    const int* tile_inst;        // [np / 128] instance of each 128-row tile
+    const int2* fwd_tiles;       // [n_fwd] (instance, tile within it), longest first
+    const int4* gram_items;      // [n_gram] (instance, product/component group, chunk, 0), longest first
+    int n_fwd, n_gram;
+    const float* rec;            // [kc] prep records
+    void *xb, *xl, *qb, *ql, *rb;  // bf16 x_hi, x_lo [np][tdp]; Q_hi, Q_lo [kc][tdp][tdp]; R [kr][np]
+    float* xt;                   // point tiles
+    int32_t* status;
+};
+int gmm_tc_cat_run(const TcCatClass& C, cudaStream_t s);
+int gmm_tc_cat_gram_groups(int d, int k);  // product x component groups of one instance
+
 // The data-independent part of each component's Wishart log-prior, for
 // n = d + m + 1 degrees of freedom: n d log(gamma) - (n d / 2) log 2 - log
 // Gamma_d(n/2), with log Gamma_d(a) = d (d - 1) / 4 log(pi) + sum_{j<d}

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
                       const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmql,
                       const float* __restrict__ rec, int64_t n, int64_t xrow0, int k, float* __restrict__ lj,
                       int64_t lj_ld, float* __restrict__ lse_out, double* __restrict__ part, int64_t tile0,
+                      const TcCatInst* __restrict__ cat, const int2* __restrict__ cat_tiles,
                       int32_t* __restrict__ status) {
     using S = FwdSm<TDP>;
     constexpr int FQ = S::FQ, FT = S::FT, NA = S::NA, RPC = S::RPC, CR = S::CR, NS = S::NS;
@@ -153,7 +154,25 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + S::FLAG);
     double* red = reinterpret_cast<double*>(sm + S::RED);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t p0 = (int64_t)blockIdx.x * TM;
+    // this CTA's tile: tile blockIdx.x of the call, or, in a concatenated
+    // class of the batched form, tile cat_tiles[blockIdx.x] of its instance
+    // (its points from row xoff, its components from Q row block koff)
+    int64_t p0 = (int64_t)blockIdx.x * TM, pidx = tile0 + blockIdx.x;
+    int koff = 0;
+    if (cat) {
+        const int2 tt = cat_tiles[blockIdx.x];
+        const TcCatInst& I = cat[tt.x];
+        n = I.n;
+        xrow0 = I.xoff;
+        k = I.k;
+        koff = I.koff;
+        lj = I.lj;
+        lj_ld = I.n;
+        lse_out = I.lse;
+        part = I.fwd;
+        p0 = (int64_t)tt.y * TM;
+        pidx = tt.y;
+    }
     const int rounds = (k + CR - 1) / CR;
 
     if (threadIdx.x == 0) {
@@ -206,10 +225,10 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
                 const int col = a < 2 ? 0 : 64 * ((a - 2) % NA), roff = a < 2 ? 0 : RPC;
                 uint8_t* stg = sm + S::Q + s * S::STG;
                 for (int c = 0; c < CR; ++c)  // components past K read as zero
-                    tc::tma_load_2d(stg + c * RPC * 128, m, col, (c0 + c) * TDP + roff, &q_full[s]);
+                    tc::tma_load_2d(stg + c * RPC * 128, m, col, (koff + c0 + c) * TDP + roff, &q_full[s]);
                 if (a == 0)
                     for (int c = 0; c < nc; ++c)
-                        bulk_g2s(sm + S::B + (ts * CR + c) * S::TAIL, rec + (size_t)(c0 + c) * REC + TDP * TDP,
+                        bulk_g2s(sm + S::B + (ts * CR + c) * S::TAIL, rec + (size_t)(koff + c0 + c) * REC + TDP * TDP,
                                  S::TAIL, &q_full[s]);
             }
         }
@@ -327,7 +346,7 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
         if (lane == 0) red[warp - 2] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 64) part[tile0 + blockIdx.x] = *abort_flag ? NAN : red[0] + red[1] + red[2] + red[3];
+    if (threadIdx.x == 64) part[pidx] = *abort_flag ? NAN : red[0] + red[1] + red[2] + red[3];
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
@@ -412,7 +431,8 @@ template <int TDP>
 __global__ void __launch_bounds__(GTHREADS, 1)
     gmm_tc_gram_kernel(const __grid_constant__ CUtensorMap tmr, const float* __restrict__ xt_g, int64_t n, int d,
                        int k, int kn, int ngroups, int64_t tiles_per_chunk, float* __restrict__ partS,
-                       float* __restrict__ partM, int nblk64, int32_t* __restrict__ status) {
+                       float* __restrict__ partM, int nblk64, int rbox, const TcCatInst* __restrict__ cat,
+                       const int4* __restrict__ cat_items, int32_t* __restrict__ status) {
     using S = GramSm<TDP>;
     constexpr int XS = S::XS;
     extern __shared__ uint8_t smem_raw[];
@@ -431,11 +451,32 @@ __global__ void __launch_bounds__(GTHREADS, 1)
     float* xt = reinterpret_cast<float*>(sm + S::XT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tid = threadIdx.x;
-    const int g = blockIdx.x % ngroups;           // product-row group
-    const int kg0 = (blockIdx.x / ngroups) * GKMAX;  // first component
+    // this CTA's work: (group blockIdx.x, chunk blockIdx.y) of the call, or, in
+    // a concatenated class of the batched form, item cat_items[blockIdx.x] of
+    // its instance (its points' R columns from xoff, its point tiles at xtoff)
+    int bx = blockIdx.x, chunk = blockIdx.y;
+    int64_t roff = 0;
+    if (cat) {
+        const int4 it = cat_items[blockIdx.x];
+        const TcCatInst& I = cat[it.x];
+        xt_g += I.xtoff;
+        n = I.n;
+        d = I.d;
+        k = I.k;
+        kn = I.kn;
+        ngroups = I.ng;
+        tiles_per_chunk = I.tpc;
+        partS = I.bS;
+        partM = I.bM;
+        roff = I.xoff;
+        bx = it.y;
+        chunk = it.z;
+    }
+    const int g = bx % ngroups;           // product-row group
+    const int kg0 = (bx / ngroups) * GKMAX;  // first component
     const int row0 = g * GMB * 128;
     const int64_t ntiles = (n + GTM - 1) / GTM;
-    const int64_t t_begin = (int64_t)blockIdx.y * tiles_per_chunk;
+    const int64_t t_begin = (int64_t)chunk * tiles_per_chunk;
     const int64_t t_end = min64(ntiles, t_begin + tiles_per_chunk);
 
     if (tid == 0) {
@@ -492,7 +533,9 @@ __global__ void __launch_bounds__(GTHREADS, 1)
                     break;
                 }
                 mbar_arrive_expect_tx(&r_full[b], rbytes);
-                tc::tma_load_2d(sm + S::R + b * GKMAX * 128, &tmr, (int)(t * GTM), kg0, &r_full[b]);
+                for (int j = 0; j < kn; j += rbox)  // boxes of rbox components (kn / rbox of them)
+                    tc::tma_load_2d(sm + S::R + b * GKMAX * 128 + j * 128, &tmr, (int)(t * GTM + roff), kg0 + j,
+                                    &r_full[b]);
             }
         }
         __syncwarp();
@@ -594,7 +637,7 @@ __global__ void __launch_bounds__(GTHREADS, 1)
                 int eu, ev;
                 gram_row(row0 + eb * 128 + qtr * 32 + lane, d, eu, ev);
                 if (ev > d) continue;  // padding row
-                const int64_t cbase = (int64_t)blockIdx.y * k;
+                const int64_t cbase = (int64_t)chunk * k;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int kk = kg0 + c0 + i;
@@ -625,10 +668,9 @@ __global__ void __launch_bounds__(GTHREADS, 1)
 // n) as d rows of 64 floats, row c holding coordinate c of the tile's points in
 // the order of gram_xpos, so that one bulk copy brings a tile into shared
 // memory in the layout the gram kernel reads. One CTA per tile.
-__global__ void __launch_bounds__(256) gmm_tc_xt_kernel(const float* __restrict__ x, int64_t n, int d,
-                                                        float* __restrict__ xt) {
+__device__ __forceinline__ void gmm_tc_xt_tile(const float* __restrict__ x, int64_t n, int d,
+                                               float* __restrict__ xt, int64_t t) {
     __shared__ float tile[GTM][129];
-    const int64_t t = blockIdx.x;
     const int64_t p0 = t * GTM;
     for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
         const int p = e / d, c = e - p * d;
@@ -639,6 +681,46 @@ __global__ void __launch_bounds__(256) gmm_tc_xt_kernel(const float* __restrict_
     for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
         const int c = e / GTM, p = e % GTM;
         out[gram_xpos(c, p)] = tile[p][c];
+    }
+}
+
+__global__ void __launch_bounds__(256) gmm_tc_xt_kernel(const float* __restrict__ x, int64_t n, int d,
+                                                        float* __restrict__ xt) {
+    gmm_tc_xt_tile(x, n, d, xt, blockIdx.x);
+}
+
+// The same for every instance of a concatenated class: CTA t makes 64-point
+// tile t of the concatenated rows, i.e. tile t - xoff / 64 of its instance.
+__global__ void __launch_bounds__(256) tc_cat_xt_kernel(const TcCatInst* __restrict__ cat,
+                                                        const int* __restrict__ tile_inst, float* __restrict__ xt) {
+    const TcCatInst& I = cat[tile_inst[blockIdx.x / 2]];
+    gmm_tc_xt_tile(I.x, I.n, I.d, xt + I.xtoff, (int64_t)blockIdx.x - I.xoff / GTM);
+}
+
+// R of every instance of a concatenated class, [kr][np]: row c, column xoff + p
+// holds seed exp(lj[c][p] - lse[p]) of the instance whose rows those are, for
+// c < k and p < n; zero elsewhere (padding rows and points). 8 points per
+// thread (never across a 128-point tile).
+__global__ void __launch_bounds__(256) tc_cat_r_kernel(const TcCatInst* __restrict__ cat,
+                                                       const int* __restrict__ tile_inst, int64_t np, int kr,
+                                                       __nv_bfloat16* __restrict__ rb) {
+    const int64_t per_row = np / 8;
+    const int64_t total = (int64_t)kr * per_row;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int c = (int)(e / per_row);
+        const int64_t q0 = (e - (int64_t)c * per_row) * 8;
+        const TcCatInst& I = cat[tile_inst[q0 / TM]];
+        const int64_t p0 = q0 - I.xoff;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t p = p0 + j;
+            v[j] = (c < I.k && p < I.n) ? I.seed * expf(__ldg(I.lj + (int64_t)c * I.n + p) - __ldg(I.lse + p)) : 0.f;
+        }
+        *reinterpret_cast<uint4*>(rb + (int64_t)c * np + q0) =
+            make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]), tc::pack_bf16x2(v[4], v[5]),
+                       tc::pack_bf16x2(v[6], v[7]));
     }
 }
 
@@ -681,6 +763,30 @@ __global__ void __launch_bounds__(256) tc_convert_x_kernel(const float* __restri
         const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
         reinterpret_cast<__nv_bfloat162*>(xb + i * TDP)[c / 2] = h;
         reinterpret_cast<__nv_bfloat162*>(xl + i * TDP)[c / 2] =
+            __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+    }
+}
+
+// the same for the concatenated rows of a class: row r belongs to the instance
+// of its 128-row tile (zero past that instance's n)
+template <int TDP>
+__global__ void __launch_bounds__(256) tc_cat_convert_x_kernel(const TcCatInst* __restrict__ cat,
+                                                               const int* __restrict__ tile_inst, int64_t np,
+                                                               __nv_bfloat16* __restrict__ xb,
+                                                               __nv_bfloat16* __restrict__ xl) {
+    const int64_t total = np * (TDP / 2);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int64_t r = e / (TDP / 2);
+        const int c = (int)(e % (TDP / 2)) * 2;
+        const TcCatInst& I = cat[tile_inst[r / TM]];
+        const int64_t i = r - I.xoff;
+        const bool in = i < I.n;
+        const float v0 = in && c < I.d ? __ldg(I.x + i * I.d + c) : 0.f;
+        const float v1 = in && c + 1 < I.d ? __ldg(I.x + i * I.d + c + 1) : 0.f;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        reinterpret_cast<__nv_bfloat162*>(xb + r * TDP)[c / 2] = h;
+        reinterpret_cast<__nv_bfloat162*>(xl + r * TDP)[c / 2] =
             __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
     }
 }
@@ -822,7 +928,7 @@ int launch_tc_fwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char*
     GPA_LAUNCH("gmm_tc_fwd", s,
                kern<<<(unsigned)tiles, 64 + 32 * S::EW, S::SMEM, s>>>(
                    tmx, tmxl, tmq, tmql, (const float*)(ws + L.off_rec), n_local, row0, A.k, lj, lj_ld, lse,
-                   (double*)(ws + L.off_fwd), row0 / TM, A.status));
+                   (double*)(ws + L.off_fwd), row0 / TM, nullptr, nullptr, A.status));
     return GPA_OK;
 }
 
@@ -883,7 +989,8 @@ int launch_tc_bwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char*
                kern<<<grid, GTHREADS, GramSm<TDP>::SMEM, s>>>(tmr, (const float*)(ws + T.off_xt) + row0 * A.d, n_local,
                                                                 A.d, A.k, kn, ng, tpc,
                                                          (float*)(ws + L.off_bS), (float*)(ws + L.off_bM),
-                                                         gmm_bwd_partial_entries(TDP), A.status));
+                                                         gmm_bwd_partial_entries(TDP), kn, nullptr, nullptr,
+                                                         A.status));
     return GPA_OK;
 }
 
@@ -958,7 +1065,59 @@ int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cud
     return GPA_OK;
 }
 
+// One concatenated class of the batched form: every stage one launch over all
+// its instances' tiles (prep before and finalize after run in the batched
+// class kernels).
+template <int TDP>
+int cat_run(const TcCatClass& C, cudaStream_t s) {
+    using S = FwdSm<TDP>;
+    const int64_t cap = (int64_t)sm_count_tc() * 8;
+    auto* xb = (__nv_bfloat16*)C.xb;
+    auto* xl = (__nv_bfloat16*)C.xl;
+    auto* qb = (__nv_bfloat16*)C.qb;
+    auto* ql = (__nv_bfloat16*)C.ql;
+    auto* rb = (__nv_bfloat16*)C.rb;
+    GPA_LAUNCH("gmm_tc_convert_x", s,
+               tc_cat_convert_x_kernel<TDP><<<(unsigned)min64(cap, (C.np * (TDP / 2) + 255) / 256), 256, 0, s>>>(
+                   C.inst, C.tile_inst, C.np, xb, xl));
+    GPA_LAUNCH("gmm_tc_convert_q", s,
+               tc_convert_q_kernel<TDP><<<(unsigned)min64(cap, (C.kc * TDP * TDP + 255) / 256), 256, 0, s>>>(
+                   C.rec, (int)C.kc, qb, ql));
+    GPA_LAUNCH("gmm_tc_xt", s, tc_cat_xt_kernel<<<(unsigned)(C.np / GTM), 256, 0, s>>>(C.inst, C.tile_inst, C.xt));
+    CUtensorMap tmx, tmxl, tmq, tmql, tmr;
+    if (!make_map(&tmx, xb, C.np, TDP) || !make_map(&tmxl, xl, C.np, TDP) ||
+        !make_map(&tmq, qb, C.kc * TDP, TDP, S::RPC) || !make_map(&tmql, ql, C.kc * TDP, TDP, S::RPC) ||
+        !make_map_r(&tmr, rb, C.np, (int)C.kr, 16))
+        return GPA_ERR_CUDA;
+    auto kf = gmm_tc_fwd_kernel<TDP>;
+    if (!set_smem_tc(kf, S::SMEM)) return GPA_ERR_CUDA;
+    if (C.n_fwd > 0)
+        GPA_LAUNCH("gmm_tc_fwd", s,
+                   kf<<<(unsigned)C.n_fwd, 64 + 32 * S::EW, S::SMEM, s>>>(tmx, tmxl, tmq, tmql, C.rec, 0, 0, 0,
+                                                                          nullptr, 0, nullptr, nullptr, 0, C.inst,
+                                                                          C.fwd_tiles, C.status));
+    const int64_t rwork = C.kr * (C.np / 8);
+    GPA_LAUNCH("gmm_tc_r", s,
+               tc_cat_r_kernel<<<(unsigned)min64((int64_t)sm_count_tc() * 16, (rwork + 255) / 256), 256, 0, s>>>(
+                   C.inst, C.tile_inst, C.np, (int)C.kr, rb));
+    auto kg = gmm_tc_gram_kernel<TDP>;
+    if (!set_smem_tc(kg, GramSm<TDP>::SMEM)) return GPA_ERR_CUDA;
+    if (C.n_gram > 0)
+        GPA_LAUNCH("gmm_tc_bwd", s,
+                   kg<<<(unsigned)C.n_gram, GTHREADS, GramSm<TDP>::SMEM, s>>>(
+                       tmr, C.xt, 0, 0, 0, 16, 1, 1, nullptr, nullptr, gmm_bwd_partial_entries(TDP), 16, C.inst,
+                       C.gram_items, C.status));
+    return GPA_OK;
+}
+
 }  // namespace
+
+int gmm_tc_cat_run(const TcCatClass& C, cudaStream_t s) {
+    if (C.np % TM || C.np <= 0 || C.kc <= 0 || C.kr % 16 || C.kr <= 0) return GPA_ERR_ARG;
+    return C.tdp == 64 ? cat_run<64>(C, s) : C.tdp == 128 ? cat_run<128>(C, s) : GPA_ERR_UNSUPPORTED;
+}
+
+int gmm_tc_cat_gram_groups(int d, int k) { return gram_groups(d) * ((tc_r_rows(k) + GKMAX - 1) / GKMAX); }
 
 bool gmm_tc_supported(int d) { return d > 32 && d <= 128; }
 

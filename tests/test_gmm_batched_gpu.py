@@ -218,3 +218,31 @@ def test_batched_d8_class_matches_oracle(shapes):
         torch.cuda.synchronize()
         assert int(st.item()) == 0
         _check(gs, inst, b)
+
+
+def test_concatenated_tensor_core_class_equals_per_call_path():
+    """The batched form runs its tensor-core instances of one padded dimension
+    as one concatenated class (shared operand buffers, one launch per stage):
+    every instance's objective and gradient equal the per-call tensor-core
+    path's within float32 summation order (the backward's chunking differs)."""
+    import paper_2104_05372_b300 as gpa
+    from paper_2104_05372_b300._lib import GmmBatch
+    shapes = [(5000, 64, 33), (64, 40, 2), (1, 48, 9), (3000, 33, 120), (900, 100, 3), (129, 128, 7),
+              (2500, 65, 40), (300, 128, 260)]
+    gs, inst = _instances(shapes, seed=31)
+    inst = _tensor_cores_where_supported(inst)
+    b = GmmBatch(inst, chunk_points=512)
+    b.prepare()
+    st = status()
+    b.run(status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    _check(gs, inst, b)
+    for (out, grads), i in zip(b.results(), inst):
+        o1 = torch.empty(1, dtype=torch.float64, device="cuda")
+        single = gpa.gmm_vjp(i["x"], i["alpha"], i["mu"], i["q"], i["l"], i["gamma"], i["m"], 1, seed=i["seed"],
+                             out=o1)
+        assert abs(float(out.item()) - float(o1.item())) <= 1e-6 * abs(float(o1.item()))
+        for u, v in zip(grads, single):
+            if u.numel():
+                assert rel_norm(host(u), host(v)) <= 1e-4
