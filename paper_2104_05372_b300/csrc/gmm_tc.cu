@@ -668,8 +668,14 @@ __global__ void __launch_bounds__(GTHREADS, 1)
 // n) as d rows of 64 floats, row c holding coordinate c of the tile's points in
 // the order of gram_xpos, so that one bulk copy brings a tile into shared
 // memory in the layout the gram kernel reads. One CTA per tile.
+// With XB (the forward's operands, TDP > 0): the same tile's rows also split
+// into x_hi + x_lo (BF16, rows of TDP, zero padded) at rows xrow .. xrow + 63
+// of xb / xl, from the one read of x.
+template <int TDP = 0>
 __device__ __forceinline__ void gmm_tc_xt_tile(const float* __restrict__ x, int64_t n, int d,
-                                               float* __restrict__ xt, int64_t t) {
+                                               float* __restrict__ xt, int64_t t,
+                                               __nv_bfloat16* __restrict__ xb = nullptr,
+                                               __nv_bfloat16* __restrict__ xl = nullptr, int64_t xrow = 0) {
     __shared__ float tile[GTM][129];
     const int64_t p0 = t * GTM;
     for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
@@ -682,19 +688,38 @@ __device__ __forceinline__ void gmm_tc_xt_tile(const float* __restrict__ x, int6
         const int c = e / GTM, p = e % GTM;
         out[gram_xpos(c, p)] = tile[p][c];
     }
+    if constexpr (TDP > 0) {
+        for (int e = threadIdx.x; e < GTM * (TDP / 2); e += blockDim.x) {
+            const int p = e / (TDP / 2), c = (e % (TDP / 2)) * 2;
+            const float v0 = c < d ? tile[p][c] : 0.f, v1 = c + 1 < d ? tile[p][c + 1] : 0.f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            reinterpret_cast<__nv_bfloat162*>(xb + (xrow + p) * TDP)[c / 2] = h;
+            reinterpret_cast<__nv_bfloat162*>(xl + (xrow + p) * TDP)[c / 2] =
+                __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+        }
+    }
 }
 
-__global__ void __launch_bounds__(256) gmm_tc_xt_kernel(const float* __restrict__ x, int64_t n, int d,
-                                                        float* __restrict__ xt) {
-    gmm_tc_xt_tile(x, n, d, xt, blockIdx.x);
+// Point tiles and forward operands of one call from one read of x: CTA t makes
+// point tile t and rows 64 t .. 64 t + 63 of x_hi, x_lo.
+template <int TDP>
+__global__ void __launch_bounds__(256) gmm_tc_xtb_kernel(const float* __restrict__ x, int64_t n, int d,
+                                                         float* __restrict__ xt, __nv_bfloat16* __restrict__ xb,
+                                                         __nv_bfloat16* __restrict__ xl) {
+    gmm_tc_xt_tile<TDP>(x, n, d, xt, blockIdx.x, xb, xl, (int64_t)blockIdx.x * GTM);
 }
 
 // The same for every instance of a concatenated class: CTA t makes 64-point
-// tile t of the concatenated rows, i.e. tile t - xoff / 64 of its instance.
+// tile t of the concatenated rows, i.e. tile t - xoff / 64 of its instance,
+// and those rows of x_hi, x_lo.
+template <int TDP>
 __global__ void __launch_bounds__(256) tc_cat_xt_kernel(const TcCatInst* __restrict__ cat,
-                                                        const int* __restrict__ tile_inst, float* __restrict__ xt) {
+                                                        const int* __restrict__ tile_inst, float* __restrict__ xt,
+                                                        __nv_bfloat16* __restrict__ xb,
+                                                        __nv_bfloat16* __restrict__ xl) {
     const TcCatInst& I = cat[tile_inst[blockIdx.x / 2]];
-    gmm_tc_xt_tile(I.x, I.n, I.d, xt + I.xtoff, (int64_t)blockIdx.x - I.xoff / GTM);
+    gmm_tc_xt_tile<TDP>(I.x, I.n, I.d, xt + I.xtoff, (int64_t)blockIdx.x - I.xoff / GTM, xb, xl,
+                        (int64_t)blockIdx.x * GTM);
 }
 
 // R of every instance of a concatenated class, [kr][np]: row c, column xoff + p
@@ -763,30 +788,6 @@ __global__ void __launch_bounds__(256) tc_convert_x_kernel(const float* __restri
         const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
         reinterpret_cast<__nv_bfloat162*>(xb + i * TDP)[c / 2] = h;
         reinterpret_cast<__nv_bfloat162*>(xl + i * TDP)[c / 2] =
-            __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
-    }
-}
-
-// the same for the concatenated rows of a class: row r belongs to the instance
-// of its 128-row tile (zero past that instance's n)
-template <int TDP>
-__global__ void __launch_bounds__(256) tc_cat_convert_x_kernel(const TcCatInst* __restrict__ cat,
-                                                               const int* __restrict__ tile_inst, int64_t np,
-                                                               __nv_bfloat16* __restrict__ xb,
-                                                               __nv_bfloat16* __restrict__ xl) {
-    const int64_t total = np * (TDP / 2);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-        const int64_t r = e / (TDP / 2);
-        const int c = (int)(e % (TDP / 2)) * 2;
-        const TcCatInst& I = cat[tile_inst[r / TM]];
-        const int64_t i = r - I.xoff;
-        const bool in = i < I.n;
-        const float v0 = in && c < I.d ? __ldg(I.x + i * I.d + c) : 0.f;
-        const float v1 = in && c + 1 < I.d ? __ldg(I.x + i * I.d + c + 1) : 0.f;
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        reinterpret_cast<__nv_bfloat162*>(xb + r * TDP)[c / 2] = h;
-        reinterpret_cast<__nv_bfloat162*>(xl + r * TDP)[c / 2] =
             __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
     }
 }
@@ -896,16 +897,25 @@ int sm_count_tc() {
     return sms;
 }
 
+// The forward's operands x_hi, x_lo and Q_hi, Q_lo; with_xt: x_hi, x_lo come
+// with the backward's transposed point tiles from one read of x.
 template <int TDP>
-int convert_inputs(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char* ws, cudaStream_t s) {
+int convert_inputs(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char* ws, cudaStream_t s,
+                   bool with_xt = false) {
     // grid-stride kernels: one element pair (x) or element (Q) per thread and
     // step, the grid as large as the work up to 8 CTAs per SM
     const int64_t cap = (int64_t)sm_count_tc() * 8;
     const unsigned gx = (unsigned)min64(cap, (A.n * (TDP / 2) + 255) / 256);
     const unsigned gq = (unsigned)min64(cap, ((int64_t)A.k * TDP * TDP + 255) / 256);
-    GPA_LAUNCH("gmm_tc_convert_x", s,
-               tc_convert_x_kernel<TDP><<<gx, 256, 0, s>>>(A.x, A.n, A.d, (__nv_bfloat16*)(ws + T.off_xb),
-                                                           (__nv_bfloat16*)(ws + T.off_xl)));
+    if (with_xt)
+        GPA_LAUNCH("gmm_tc_xt", s,
+                   gmm_tc_xtb_kernel<TDP><<<(unsigned)(T.npad / GTM), 256, 0, s>>>(
+                       A.x, A.n, A.d, (float*)(ws + T.off_xt), (__nv_bfloat16*)(ws + T.off_xb),
+                       (__nv_bfloat16*)(ws + T.off_xl)));
+    else
+        GPA_LAUNCH("gmm_tc_convert_x", s,
+                   tc_convert_x_kernel<TDP><<<gx, 256, 0, s>>>(A.x, A.n, A.d, (__nv_bfloat16*)(ws + T.off_xb),
+                                                               (__nv_bfloat16*)(ws + T.off_xl)));
     GPA_LAUNCH("gmm_tc_convert_q", s,
                tc_convert_q_kernel<TDP><<<gq, 256, 0, s>>>((const float*)(ws + L.off_rec), A.k,
                                                           (__nv_bfloat16*)(ws + T.off_qb),
@@ -1026,9 +1036,7 @@ int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cud
     if (cudaMemsetAsync(ws + L.off_bS, 0, sizeof(float) * (size_t)nchunks * A.k * nent, s) != cudaSuccess ||
         cudaMemsetAsync(ws + L.off_bM, 0, sizeof(float) * (size_t)nchunks * A.k * (TDP + 1), s) != cudaSuccess)
         return GPA_ERR_CUDA;
-    if ((rc = convert_inputs<TDP>(A, L, T, ws, s))) return rc;
-    GPA_LAUNCH("gmm_tc_xt", s,
-               gmm_tc_xt_kernel<<<(unsigned)(T.npad / GTM), 256, 0, s>>>(A.x, A.n, A.d, (float*)(ws + T.off_xt)));
+    if ((rc = convert_inputs<TDP>(A, L, T, ws, s, true))) return rc;
     // the backward runs over at most RP points at a time (the R buffer), with
     // the same chunk grid each time so that the partial sums keep one order
     auto bwd_range = [&](int64_t c0, int64_t nl, const float* lj, int64_t lj_ld, const float* lse) {
@@ -1077,13 +1085,11 @@ int cat_run(const TcCatClass& C, cudaStream_t s) {
     auto* qb = (__nv_bfloat16*)C.qb;
     auto* ql = (__nv_bfloat16*)C.ql;
     auto* rb = (__nv_bfloat16*)C.rb;
-    GPA_LAUNCH("gmm_tc_convert_x", s,
-               tc_cat_convert_x_kernel<TDP><<<(unsigned)min64(cap, (C.np * (TDP / 2) + 255) / 256), 256, 0, s>>>(
-                   C.inst, C.tile_inst, C.np, xb, xl));
     GPA_LAUNCH("gmm_tc_convert_q", s,
                tc_convert_q_kernel<TDP><<<(unsigned)min64(cap, (C.kc * TDP * TDP + 255) / 256), 256, 0, s>>>(
                    C.rec, (int)C.kc, qb, ql));
-    GPA_LAUNCH("gmm_tc_xt", s, tc_cat_xt_kernel<<<(unsigned)(C.np / GTM), 256, 0, s>>>(C.inst, C.tile_inst, C.xt));
+    GPA_LAUNCH("gmm_tc_xt", s,
+               tc_cat_xt_kernel<TDP><<<(unsigned)(C.np / GTM), 256, 0, s>>>(C.inst, C.tile_inst, C.xt, xb, xl));
     CUtensorMap tmx, tmxl, tmq, tmql, tmr;
     if (!make_map(&tmx, xb, C.np, TDP) || !make_map(&tmxl, xl, C.np, TDP) ||
         !make_map(&tmq, qb, C.kc * TDP, TDP, S::RPC) || !make_map(&tmql, ql, C.kc * TDP, TDP, S::RPC) ||
