@@ -336,15 +336,45 @@ def run_ours(args):
 
 
 def run_e2e(args, gpa, _lib, g, dev, ws, stream, exch, n_total):
-    """The headline step through the public API from pinned host buffers: the
-    parameters are copied in, the points stream to the device in chunks of
-    2^19 (data_parallel.gmm_vjp_from_host: the copy of chunk c + 1 overlaps the
-    work on chunk c; 2^19 measured best of 2^17..2^19), and the gradient and
-    objective are copied back."""
+    """The headline step end to end from pinned host buffers. One rank: the C
+    entry gmm_vjp_host (parameters copied in, the points streamed to the
+    device in chunks of 2^19 with the copy of chunk c + 1 overlapping the work
+    on chunk c, the gradient and objective copied back to host memory). Several
+    ranks: the same streaming from the binding (data_parallel.gmm_vjp_from_host),
+    whose Accum vectors are all-reduced between the two halves."""
     import torch
+    import torch.distributed as dist
     chunk = int(os.environ.get("GPA_E2E_CHUNK", 1 << 19))
     xh = torch.from_numpy(g.x).pin_memory()
     host = [torch.from_numpy(t).pin_memory() for t in (g.alpha, g.mu, g.q, g.l)]
+    if not (dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1):
+        wsh = _lib.workspace(gpa.gpa_gmm_vjp_host_workspace_bytes(GMM_N, GMM_D, GMM_K, 0, chunk), dev)
+        t = GMM_D * (GMM_D - 1) // 2
+        hgrads = [torch.empty(sh, dtype=torch.float32).pin_memory() for sh in ((GMM_K,), (GMM_K, GMM_D),
+                                                                              (GMM_K, GMM_D), (GMM_K, t))]
+        hout = torch.empty(1, dtype=torch.float64).pin_memory()
+
+        def step_c():
+            gpa.gmm_vjp_host(xh, *host, g.gamma, g.m, 0, seed=1.0, chunk_points=chunk, d_alpha=hgrads[0],
+                             d_mu=hgrads[1], d_q=hgrads[2], d_l=hgrads[3], out=hout, ws=wsh, device=dev,
+                             stream=stream)
+        for _ in range(max(1, args.warmup)):
+            step_c()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_c()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        h2d = xh.numel() * xh.element_size() + sum(h.numel() * h.element_size() for h in host)
+        d2h = sum(h.numel() * h.element_size() for h in hgrads) + 8
+        del wsh
+        return {"value": GMM_N * GMM_K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "note": f"C entry gmm_vjp_host on pinned host buffers: points streamed in "
+                                                   f"chunks of {chunk}, copies overlapping the computation, gradient "
+                                                   "and objective copied back to host memory"}
     dbuf = [torch.empty(t.shape, dtype=t.dtype, device=dev) for t in host]
     staging = [torch.empty(chunk, GMM_D, device=dev) for _ in range(2)]
     wsc = _lib.workspace(gpa.gpa_gmm_workspace_bytes(chunk, GMM_D, GMM_K, 0, 0), dev)
@@ -380,7 +410,6 @@ def run_e2e(args, gpa, _lib, g, dev, ws, stream, exch, n_total):
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
     world = 1
-    import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
         world = dist.get_world_size()
         tt = torch.tensor([ms], device=dev)

@@ -183,10 +183,10 @@ GPA_API int gmm_jvp(const float* x, const float* alpha, const float* mu, const f
  *
  * Exchange vector: float64, gpa_gmm_exchange_len(d, k) entries; per component
  * the sums [S (lower 8x8 blocks of the padded dimension) | m | R] of the
- * reverse pass (raw moments for GPA_PREC_FP32, moments centred on mu_k for
- * GPA_PREC_BF16_TC: every rank must use the same prec), then the sum over
- * the shard's points of logsumexp_k s_ik. Its layout is internal; only its
- * length and its additivity are part of the interface.
+ * reverse pass (raw moments, S = sum r x x^T, m = sum r x, R = sum r, for both
+ * precisions; every rank must use the same prec), then the sum over the
+ * shard's points of logsumexp_k s_ik. Its layout is internal; only its length
+ * and its additivity are part of the interface.
  */
 GPA_API int64_t gpa_gmm_exchange_len(int32_t d, int32_t k); /* 0 on bad arguments */
 
@@ -213,6 +213,36 @@ GPA_API int gmm_vjp_finalize(const float* alpha, const float* mu, const float* q
                              double seed, const double* exch, float* d_alpha, float* d_mu, float* d_q,
                              float* d_l, double* out, void* ws, size_t ws_bytes, int32_t* dev_status,
                              gpa_stream_t stream);
+
+/* ------------------------------------------------------------------------- */
+/* GMM from host memory                                                       */
+/* ------------------------------------------------------------------------- */
+/* Objective and seed * gradient of a mixture whose points and parameters are
+ * in HOST memory, the results written to HOST memory: the end-to-end form of
+ * gmm_vjp. x [n][d], alpha, mu, q, l as in gmm_vjp but host pointers, best
+ * page-locked (cudaHostAlloc / cudaHostRegister) so that the copies run
+ * asynchronously; pageable memory works with slower, blocking copies. The
+ * parameters are copied in on `stream`; the points go to the device in chunks
+ * of chunk_points (a multiple of 128; 0 = 2^19; the first chunk a quarter of
+ * that) through two staging buffers in ws, each chunk's copy issued on a
+ * library stream (one per device, made on first use) so that it overlaps the
+ * reverse pass on the previous chunk (gmm_vjp_partial on `stream`); the
+ * chunks' exchange vectors add up in ws and gmm_vjp_finalize finishes them.
+ * d_alpha, d_mu, d_q, d_l (host, d_l ignored for d = 1) receive seed * grad f
+ * (WRITTEN, not added) and *out (host, nullable) the objective, by copies on
+ * `stream`: they hold the results once `stream` has completed the call's work
+ * (synchronize it before reading them). Device memory: ws only, of
+ * gpa_gmm_vjp_host_workspace_bytes(n, d, k, prec, chunk_points) bytes (two
+ * chunks of points, the parameters, gradients, exchange vector and a chunk's
+ * gmm_vjp workspace), 256-byte aligned. Calls on one device share the library
+ * stream: concurrent calls from several host threads are ordered by it.
+ * Errors as gmm_vjp. */
+GPA_API size_t gpa_gmm_vjp_host_workspace_bytes(int64_t n, int32_t d, int32_t k, int32_t prec,
+                                                int64_t chunk_points); /* 0 on bad arguments */
+GPA_API int gmm_vjp_host(const float* x, const float* alpha, const float* mu, const float* q, const float* l,
+                         int64_t n, int32_t d, int32_t k, double gamma, int32_t m, int32_t prec, double seed,
+                         float* d_alpha, float* d_mu, float* d_q, float* d_l, double* out, int64_t chunk_points,
+                         void* ws, size_t ws_bytes, int32_t* dev_status, gpa_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
 /* Batched GMM: many instances of uneven N, D, K in persistent kernels        */

@@ -69,6 +69,8 @@ _SIGS = {
     "gmm_batched_prepare": ([_P, _I32, _I64, _P, _SZ, _P], _I32),
     "gmm_batched_vjp": ([_P, _I32, _I64, _I32, _P, _SZ, _P, _P], _I32),
     "gpa_gmm_batched_workspace_bytes_opts": ([_P, _I32, _P], _SZ),
+    "gpa_gmm_vjp_host_workspace_bytes": ([_I64, _I32, _I32, _I32, _I64], _SZ),
+    "gmm_vjp_host": ([_P] * 5 + [_I64, _I32, _I32, _D, _I32, _I32, _D] + [_P] * 5 + [_I64, _P, _SZ, _P, _P], _I32),
     "gmm_batched_prepare_opts": ([_P, _I32, _P, _P, _SZ, _P], _I32),
     "gmm_batched_vjp_opts": ([_P, _I32, _P, _P, _SZ, _P, _P], _I32),
     "gpa_check_bounded_wait": ([_I64, _P, _P, _P], _I32),
@@ -276,6 +278,64 @@ def gmm_vjp_partial(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, logjoint
                                 ws.numel(), _ptr(status), _stream(stream))
     _ok(rc, "gmm_vjp_partial")
     return exch
+
+
+def _check_host(t, name, shape):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.is_cuda:
+        raise ValueError(f"{name} must be in host memory")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be torch.float32, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+def gpa_gmm_vjp_host_workspace_bytes(n, d, k, prec=PREC_FP32, chunk_points=0) -> int:
+    return int(load().gpa_gmm_vjp_host_workspace_bytes(int(n), int(d), int(k), int(prec), int(chunk_points)))
+
+
+def gmm_vjp_host(x, alpha, mu, q, l, gamma=1.0, m=0, prec=PREC_FP32, seed=1.0, chunk_points=0, d_alpha=None,
+                 d_mu=None, d_q=None, d_l=None, out=None, ws=None, device=None, status=None, stream=None):
+    """gmm_vjp_host: points and parameters in host memory (pinned for
+    asynchronous copies), seed * grad f and the objective WRITTEN to host
+    tensors (pinned ones allocated if not given). The results are complete once
+    ``stream`` (default: the current stream of ``device``) has run the call;
+    returns (d_alpha, d_mu, d_q, d_l, out)."""
+    n, d = x.shape
+    k = alpha.shape[0]
+    t = d * (d - 1) // 2
+    for v, name, shape in ((x, "x", (n, d)), (alpha, "alpha", (k,)), (mu, "mu", (k, d)), (q, "q", (k, d)),
+                           (l, "l", (k, t))):
+        _check_host(v, name, shape)
+
+    def host_out(v, name, shape):
+        return torch.empty(shape, dtype=torch.float32).pin_memory() if v is None else _check_host(v, name, shape)
+    d_alpha = host_out(d_alpha, "d_alpha", (k,))
+    d_mu = host_out(d_mu, "d_mu", (k, d))
+    d_q = host_out(d_q, "d_q", (k, d))
+    d_l = host_out(d_l, "d_l", (k, t))
+    out = torch.empty(1, dtype=torch.float64).pin_memory() if out is None else out
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if ws is None:
+        nb = gpa_gmm_vjp_host_workspace_bytes(n, d, k, prec, chunk_points)
+        if nb == 0:
+            raise GpaError(ERR_ARG, "gpa_gmm_vjp_host_workspace_bytes")
+        ws = workspace(nb, dev)
+    s = torch.cuda.current_stream(dev) if stream is None else stream
+    rc = load().gmm_vjp_host(_hptr(x), _hptr(alpha), _hptr(mu), _hptr(q), _hptr(l), n, d, k, float(gamma), int(m),
+                             int(prec), float(seed), _hptr(d_alpha), _hptr(d_mu), _hptr(d_q), _hptr(d_l), _hptr(out),
+                             int(chunk_points), _ptr(ws), ws.numel(), _ptr(status), C.c_void_p(s.cuda_stream))
+    _ok(rc, "gmm_vjp_host")
+    return d_alpha, d_mu, d_q, d_l, out
+
+
+def _hptr(t):
+    """Host address of a CPU tensor's data (None for an empty tensor)."""
+    return C.c_void_p(t.data_ptr()) if t.numel() else None
 
 
 def gmm_vjp_finalize(alpha, mu, q, l, n_total, exch, gamma=1.0, m=0, prec=PREC_FP32, seed=1.0, d_alpha=None,
