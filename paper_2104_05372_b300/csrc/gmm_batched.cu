@@ -100,8 +100,8 @@ struct CatPlan {
     std::vector<int4> gram_items;
     int64_t np = 0, kc = 0, kr = 0;
     size_t off_cinst = 0, off_tile_inst = 0, off_fwd_tiles = 0, off_gram_items = 0;
-    size_t off_rec = 0, off_xb = 0, off_xl = 0, off_qb = 0, off_ql = 0, off_rb = 0, off_xt = 0, off_lse = 0,
-           off_lj = 0;
+    size_t off_rec = 0, off_tails = 0, off_xb = 0, off_xl = 0, off_qb = 0, off_ql = 0, off_rb = 0, off_xt = 0,
+           off_lse = 0, off_lj = 0;
 };
 
 struct Plan {
@@ -337,6 +337,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, const gpa_batched_opts& O
             xtf += (in[i].n + 127) / 128 * 128 * (int64_t)in[i].d;
         }
         C.off_rec = off; off = a256(off + sizeof(float) * (size_t)C.kc * rec_len);
+        C.off_tails = off; off = a256(off + sizeof(float) * (size_t)C.kc * (tdp + 4));
         C.off_xb = off;  off = a256(off + 2 * (size_t)C.np * tdp);
         C.off_xl = off;  off = a256(off + 2 * (size_t)C.np * tdp);
         C.off_qb = off;  off = a256(off + 2 * (size_t)C.kc * tdp * tdp);
@@ -887,6 +888,7 @@ extern "C" int gmm_batched_vjp_opts(const gpa_gmm_instance* inst, int32_t n_inst
         T.n_fwd = (int)C.fwd_tiles.size();
         T.n_gram = (int)C.gram_items.size();
         T.rec = (const float*)(w + C.off_rec);
+        T.tails = (float*)(w + C.off_tails);
         T.xb = w + C.off_xb;
         T.xl = w + C.off_xl;
         T.qb = w + C.off_qb;

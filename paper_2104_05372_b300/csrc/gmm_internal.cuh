@@ -99,7 +99,8 @@ struct TcCatClass {
     const int4* gram_items;      // [n_gram] (instance, product/component group, chunk, 0), longest first
     int n_fwd, n_gram;
     const float* rec;            // [kc] prep records
-    void *xb, *xl, *qb, *ql, *rb;  // bf16 x_hi, x_lo [np][tdp]; Q_hi, Q_lo [kc][tdp][tdp]; R [kr][np]
+    float* tails;                // [kc][tdp + 4] b_k and constants
+    void *xb, *xl, *qb, *ql, *rb;  // bf16 x_hi, x_lo [np][tdp]; Q_hi, Q_lo (kc * tdp * tdp each); R [kr][np]
     float* xt;                   // point tiles
     int32_t* status;
 };

@@ -130,14 +130,14 @@ __device__ __forceinline__ float sumsq_rows(const uint32_t (&v)[64], int off, co
 template <int TDP>
 __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
     gmm_tc_fwd_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmxl,
-                      const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmql,
-                      const float* __restrict__ rec, int64_t n, int64_t xrow0, int k, float* __restrict__ lj,
+                      const __grid_constant__ CUtensorMap tmqL, const __grid_constant__ CUtensorMap tmqLl,
+                      const __grid_constant__ CUtensorMap tmqH, const __grid_constant__ CUtensorMap tmqHl,
+                      const float* __restrict__ tails, int64_t n, int64_t xrow0, int k, float* __restrict__ lj,
                       int64_t lj_ld, float* __restrict__ lse_out, double* __restrict__ part, int64_t tile0,
                       const TcCatInst* __restrict__ cat, const int2* __restrict__ cat_tiles,
                       int32_t* __restrict__ status) {
     using S = FwdSm<TDP>;
     constexpr int FQ = S::FQ, FT = S::FT, NA = S::NA, RPC = S::RPC, CR = S::CR, NS = S::NS;
-    constexpr int REC = Tc<TDP>::REC;
     constexpr uint32_t IDESC256 = tc::idesc_bf16_f32(128, 256);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
@@ -221,15 +221,14 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
                 const int nc = min(CR, k - c0);
                 mbar_arrive_expect_tx(&q_full[s], S::STG + (a == 0 ? (uint32_t)nc * S::TAIL : 0u));
                 const bool lo = a == 1 || a >= 2 + NA;
-                const CUtensorMap* m = lo ? &tmql : &tmq;
-                const int col = a < 2 ? 0 : 64 * ((a - 2) % NA), roff = a < 2 ? 0 : RPC;
-                uint8_t* stg = sm + S::Q + s * S::STG;
-                for (int c = 0; c < CR; ++c)  // components past K read as zero
-                    tc::tma_load_2d(stg + c * RPC * 128, m, col, (koff + c0 + c) * TDP + roff, &q_full[s]);
+                // one 256-row box: RPC rows of each of the round's CR components
+                // (rows past the last component read as zero)
+                const CUtensorMap* m = a < 2 ? (lo ? &tmqLl : &tmqL) : (lo ? &tmqHl : &tmqH);
+                const int col = a < 2 ? 0 : 64 * ((a - 2) % NA);
+                tc::tma_load_2d(sm + S::Q + s * S::STG, m, col, (koff + c0) * RPC, &q_full[s]);
                 if (a == 0)
-                    for (int c = 0; c < nc; ++c)
-                        bulk_g2s(sm + S::B + (ts * CR + c) * S::TAIL, rec + (size_t)(koff + c0 + c) * REC + TDP * TDP,
-                                 S::TAIL, &q_full[s]);
+                    bulk_g2s(sm + S::B + ts * CR * S::TAIL, tails + (size_t)(koff + c0) * (TDP + 4),
+                             (uint32_t)nc * S::TAIL, &q_full[s]);
             }
         }
     } else if (warp == 1) {
@@ -792,21 +791,41 @@ __global__ void __launch_bounds__(256) tc_convert_x_kernel(const float* __restri
     }
 }
 
-// prep record Qt[c][r] -> Q_hi + Q_lo, each qb[k][r][c] bf16
+// prep record Qt[c][r] -> Q_hi + Q_lo (bf16) in the forward's phase-major
+// layout, and the b_k tails. Each of qb, ql holds two parts: L = [k][RPC][64]
+// (the first RPC = TDP / 2 rows of each Q_k, first 64 columns: the forward's L
+// operand needs no more) and, after it, H = [k][RPC][TDP] (the other rows), so
+// that the rows of CR = 256 / RPC consecutive components form one 256-row TMA
+// box. tails: [k][TDP + 4] floats (b_k, the constant, padding), contiguous
+// over the components so that a round's tails are one copy.
 template <int TDP>
 __global__ void __launch_bounds__(256) tc_convert_q_kernel(const float* __restrict__ rec, int k,
                                                            __nv_bfloat16* __restrict__ qb,
-                                                           __nv_bfloat16* __restrict__ ql) {
-    const int64_t total = (int64_t)k * TDP * TDP;
+                                                           __nv_bfloat16* __restrict__ ql,
+                                                           float* __restrict__ tails) {
+    constexpr int RPC = TDP / 2;
+    const int64_t nl = (int64_t)k * RPC * 64, total = nl + (int64_t)k * RPC * TDP;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-        const int64_t kk = e / (TDP * TDP);
-        const int r = (int)((e / TDP) % TDP), c = (int)(e % TDP);
+        int64_t kk;
+        int r, c;
+        if (e < nl) {
+            kk = e / (RPC * 64);
+            r = (int)((e / 64) % RPC);
+            c = (int)(e % 64);
+        } else {
+            const int64_t f = e - nl;
+            kk = f / (RPC * TDP);
+            r = RPC + (int)((f / TDP) % RPC);
+            c = (int)(f % TDP);
+        }
         const float v = rec[kk * Tc<TDP>::REC + (int64_t)c * TDP + r];
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         qb[e] = h;
         ql[e] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)k * (TDP + 4); e += stride)
+        tails[e] = rec[(e / (TDP + 4)) * Tc<TDP>::REC + TDP * TDP + e % (TDP + 4)];
 }
 
 // ---- host ---------------------------------------------------------------------------
@@ -822,7 +841,7 @@ int tc_r_rows(int k) { return (k + 15) / 16 * 16; }
 int64_t tc_r_points(int64_t npad) { return npad < GRB_POINTS ? npad : (int64_t)GRB_POINTS; }
 
 struct TcLayout {
-    size_t off_xb, off_xl, off_qb, off_ql, off_rb, off_xt, fixed;
+    size_t off_xb, off_xl, off_qb, off_ql, off_tails, off_rb, off_xt, fixed;
     int64_t npad, rpoints;
 };
 
@@ -836,7 +855,8 @@ TcLayout tc_layout(const GmmLayout& L, int64_t n, int d, int k) {
     T.off_xl = T.off_xb + xbytes;
     T.off_qb = T.off_xl + xbytes;
     T.off_ql = T.off_qb + qbytes;
-    T.off_rb = T.off_ql + qbytes;
+    T.off_tails = T.off_ql + qbytes;
+    T.off_rb = T.off_tails + a1024((size_t)k * (tdp + 4) * 4);
     T.off_xt = T.off_rb + a1024((size_t)tc_r_rows(k) * T.rpoints * 2);
     T.fixed = T.off_xt + a1024((size_t)T.npad * d * 4);
     return T;
@@ -919,26 +939,38 @@ int convert_inputs(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char
     GPA_LAUNCH("gmm_tc_convert_q", s,
                tc_convert_q_kernel<TDP><<<gq, 256, 0, s>>>((const float*)(ws + L.off_rec), A.k,
                                                           (__nv_bfloat16*)(ws + T.off_qb),
-                                                          (__nv_bfloat16*)(ws + T.off_ql)));
+                                                          (__nv_bfloat16*)(ws + T.off_ql),
+                                                          (float*)(ws + T.off_tails)));
     return GPA_OK;
+}
+
+// Tensor maps of the forward's Q operands (hi, lo) in the phase-major layout
+// of tc_convert_q_kernel: L part [k * RPC rows][64], H part [k * RPC][TDP],
+// 256-row boxes.
+template <int TDP>
+bool make_q_maps(CUtensorMap (&m)[4], const void* qb, const void* ql, int64_t k) {
+    constexpr int RPC = FwdSm<TDP>::RPC;
+    const size_t hoff = (size_t)k * RPC * 64 * 2;
+    return make_map(&m[0], qb, k * RPC, 64, 256) && make_map(&m[1], ql, k * RPC, 64, 256) &&
+           make_map(&m[2], (const char*)qb + hoff, k * RPC, TDP, 256) &&
+           make_map(&m[3], (const char*)ql + hoff, k * RPC, TDP, 256);
 }
 
 template <int TDP>
 int launch_tc_fwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char* ws, int64_t row0, int64_t n_local,
                   float* lj, int64_t lj_ld, float* lse, cudaStream_t s) {
     using S = FwdSm<TDP>;
-    CUtensorMap tmx, tmxl, tmq, tmql;
+    CUtensorMap tmx, tmxl, tq[4];
     if (!make_map(&tmx, ws + T.off_xb, A.n, TDP) || !make_map(&tmxl, ws + T.off_xl, A.n, TDP) ||
-        !make_map(&tmq, ws + T.off_qb, (int64_t)A.k * TDP, TDP, S::RPC) ||
-        !make_map(&tmql, ws + T.off_ql, (int64_t)A.k * TDP, TDP, S::RPC))
+        !make_q_maps<TDP>(tq, ws + T.off_qb, ws + T.off_ql, A.k))
         return GPA_ERR_CUDA;
     const int64_t tiles = (n_local + TM - 1) / TM;
     auto kern = gmm_tc_fwd_kernel<TDP>;
     if (!set_smem_tc(kern, S::SMEM)) return GPA_ERR_CUDA;
     GPA_LAUNCH("gmm_tc_fwd", s,
                kern<<<(unsigned)tiles, 64 + 32 * S::EW, S::SMEM, s>>>(
-                   tmx, tmxl, tmq, tmql, (const float*)(ws + L.off_rec), n_local, row0, A.k, lj, lj_ld, lse,
-                   (double*)(ws + L.off_fwd), row0 / TM, nullptr, nullptr, A.status));
+                   tmx, tmxl, tq[0], tq[1], tq[2], tq[3], (const float*)(ws + T.off_tails), n_local, row0, A.k, lj,
+                   lj_ld, lse, (double*)(ws + L.off_fwd), row0 / TM, nullptr, nullptr, A.status));
     return GPA_OK;
 }
 
@@ -1087,21 +1119,20 @@ int cat_run(const TcCatClass& C, cudaStream_t s) {
     auto* rb = (__nv_bfloat16*)C.rb;
     GPA_LAUNCH("gmm_tc_convert_q", s,
                tc_convert_q_kernel<TDP><<<(unsigned)min64(cap, (C.kc * TDP * TDP + 255) / 256), 256, 0, s>>>(
-                   C.rec, (int)C.kc, qb, ql));
+                   C.rec, (int)C.kc, qb, ql, C.tails));
     GPA_LAUNCH("gmm_tc_xt", s,
                tc_cat_xt_kernel<TDP><<<(unsigned)(C.np / GTM), 256, 0, s>>>(C.inst, C.tile_inst, C.xt, xb, xl));
-    CUtensorMap tmx, tmxl, tmq, tmql, tmr;
-    if (!make_map(&tmx, xb, C.np, TDP) || !make_map(&tmxl, xl, C.np, TDP) ||
-        !make_map(&tmq, qb, C.kc * TDP, TDP, S::RPC) || !make_map(&tmql, ql, C.kc * TDP, TDP, S::RPC) ||
+    CUtensorMap tmx, tmxl, tq[4], tmr;
+    if (!make_map(&tmx, xb, C.np, TDP) || !make_map(&tmxl, xl, C.np, TDP) || !make_q_maps<TDP>(tq, qb, ql, C.kc) ||
         !make_map_r(&tmr, rb, C.np, (int)C.kr, 16))
         return GPA_ERR_CUDA;
     auto kf = gmm_tc_fwd_kernel<TDP>;
     if (!set_smem_tc(kf, S::SMEM)) return GPA_ERR_CUDA;
     if (C.n_fwd > 0)
         GPA_LAUNCH("gmm_tc_fwd", s,
-                   kf<<<(unsigned)C.n_fwd, 64 + 32 * S::EW, S::SMEM, s>>>(tmx, tmxl, tmq, tmql, C.rec, 0, 0, 0,
-                                                                          nullptr, 0, nullptr, nullptr, 0, C.inst,
-                                                                          C.fwd_tiles, C.status));
+                   kf<<<(unsigned)C.n_fwd, 64 + 32 * S::EW, S::SMEM, s>>>(tmx, tmxl, tq[0], tq[1], tq[2], tq[3],
+                                                                          C.tails, 0, 0, 0, nullptr, 0, nullptr,
+                                                                          nullptr, 0, C.inst, C.fwd_tiles, C.status));
     const int64_t rwork = C.kr * (C.np / 8);
     GPA_LAUNCH("gmm_tc_r", s,
                tc_cat_r_kernel<<<(unsigned)min64((int64_t)sm_count_tc() * 16, (rwork + 255) / 256), 256, 0, s>>>(
@@ -1131,7 +1162,8 @@ size_t gmm_tc_extra_bytes(int64_t n, int d, int k) {
     const int tdp = tc_dp(d);
     const int64_t npad = ((n + TM - 1) / TM) * TM;
     return 2 * a1024((size_t)npad * tdp * 2) + 2 * a1024((size_t)k * tdp * tdp * 2) +
-           a1024((size_t)tc_r_rows(k) * tc_r_points(npad) * 2) + a1024((size_t)npad * d * 4) + 2048;
+           a1024((size_t)k * (tdp + 4) * 4) + a1024((size_t)tc_r_rows(k) * tc_r_points(npad) * 2) +
+           a1024((size_t)npad * d * 4) + 2048;
 }
 
 int gmm_tc_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s) {
