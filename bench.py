@@ -667,16 +667,17 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256, fp32_steps=1):
     bwd_ms = tr.get("gmm_tc_bwd", (1, float("nan")))[1] / args.steps
     dom, dom_ms = ("gmm_tc_fwd", fwd_ms) if fwd_ms >= bwd_ms else ("gmm_tc_bwd", bwd_ms)
     tdp = 64 if d <= 64 else 128
-    # executed MMA flops per step. Forward: rounds of 512 / TDP components, the
-    # first TDP / 2 rows of each over K = TDP / 2 and the rest over K = TDP,
-    # three split passes: 4.5 TDP^2 per (point, padded component). Backward:
-    # Y^T R with the products padded to groups of 256 rows and the components
-    # to a multiple of 16.
-    cr = 512 // tdp
-    k_fwd = -(-k // cr) * cr
+    # executed MMA flops per step. Forward: sets of G rows of z (G = 16 at TDP
+    # = 128, 32 at TDP = 64), set j over K = G (j + 1), N = G per component
+    # (no padding), three split passes: 6 G^2 NSET (NSET + 1) / 2 per (point,
+    # component), NSET = TDP / G. Backward: Y^T R with the products padded to
+    # groups of 256 rows and the components to a multiple of 16.
+    gset = 16 if tdp == 128 else 32
+    nset = tdp // gset
     groups = -(-(d * (d + 1) // 2 + d + 1) // 256)
     k_bwd = -(-k // 16) * 16
-    executed = {"gmm_tc_fwd": 4.5 * tdp * tdp * n * k_fwd, "gmm_tc_bwd": 2.0 * groups * 256 * k_bwd * n}
+    executed = {"gmm_tc_fwd": 6.0 * gset * gset * nset * (nset + 1) / 2 * n * k,
+                "gmm_tc_bwd": 2.0 * groups * 256 * k_bwd * n}
     # algorithmic flops per (point, component): the forward's 2 D^2 split
     # evenly over the two kernels (D^2 + 3D each, as the FP32 roofline counts)
     alg = (d * d + 3 * d) * pairs / (dom_ms / 1e3) / 1e12
@@ -695,8 +696,8 @@ def run_gmm_tc(args, gpa, _lib, dev, stream, rank, d=128, k=256, fp32_steps=1):
                      "executed_frac": round(dense / peaks["bf16_tflops"], 4), "peak_source": src,
                      "ms_per_step": round(dom_ms, 4),
                      "note": "achieved counts D^2 + 3D flops per (point, component); executed counts every "
-                             "MMA as issued (forward: 4.5 TDP^2 per point and padded component, the nonzero "
-                             "blocks of Q_k in 3 split passes; backward: 256-row product groups x components "
+                             "MMA as issued (forward: the nonzero row blocks of Q_k in 3 split passes, "
+                             "3.375 TDP^2 per pair at TDP = 128, 4.5 TDP^2 at 64; backward: 256-row product groups x components "
                              "padded to 16)"},
         "errors_vs_fp32_path": dict(vs_fp32, note="every output at full size against the FP32 CUDA-core path on "
                                                   "the same inputs (normwise per gradient block; lse per point "

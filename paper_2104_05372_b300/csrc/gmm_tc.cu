@@ -49,24 +49,24 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 // single BF16 pass leaves log-joint errors of ~0.4 at D = 128, i.e. ~40 %
 // errors in the responsibilities exp(s - lse).
 //
-// Q_k is lower triangular, so the first half of the rows of z = Q_k x (RPC =
-// TDP / 2 rows) needs only the first half of the columns of Q_k. A round takes
-// CR = 256 / RPC components (4 at TDP = 128, 8 at TDP = 64) and stacks their
-// rows into two 256-row MMA operands: L = the first RPC rows of each component
-// over K = 0 .. RPC - 1, H = the last RPC rows of each over K = 0 .. TDP - 1.
-// The zero blocks are never multiplied, and every MMA is M = 128, N = 256: a
-// single issuing thread needs about 100 cycles per tcgen05.mma, more than an
-// N = 128 MMA takes to execute (64 cycles), so narrower MMAs leave the tensor
-// pipe ~40 % idle.
+// Q_k is lower triangular, so rows jG .. jG + G - 1 of z = Q_k x (one set)
+// need only the first (j + 1) G columns of Q_k. A round takes CR = 256 / G
+// components and runs NSET = TDP / G sets: set j stacks rows jG .. of each of
+// the round's components into one 256-row MMA operand over K = 0 .. (j + 1) G
+// - 1, so the zero blocks above the diagonal blocks are never multiplied. G =
+// 16 at TDP = 128 (8 sets, 16 components per round, 9/16 of the dense MMA
+// work), G = 32 at TDP = 64 (2 sets, 8 components, 3/4). Every MMA is M = 128
+// and N = G nc (nc = the round's components: 256 but in a last, partial
+// round): a single issuing thread needs about 100 cycles per tcgen05.mma, more
+// than an N = 128 MMA takes to execute (64 cycles), so narrower MMAs would
+// leave the tensor pipe idle.
 //
-// Pipeline stages are 32 KB operand atoms (256 rows x 64 columns; CR TMA boxes
-// of RPC rows), 2 + 2 NA per round (NA = TDP / 64 column atoms): L of Q_hi, L
-// of Q_lo, then H of Q_hi and of Q_lo per column atom. The L phase
-// accumulates in TMEM columns 0..255 and the H phase in 256..511 (component c
-// at RPC c within each), so the epilogue reads the L phase of a round while
-// the MMAs of its H phase run, and the H phase while the next round's L phase
-// runs. The b_k tails of a round travel with its first stage into a ring of
-// FT slots, which the epilogue releases; the Q stages are released by the MMAs.
+// Pipeline stages are 32 KB operand atoms (256 rows x 64 columns, one TMA
+// box), per set its NA_j = ceil((j + 1) G / 64) atoms of Q_hi, then of Q_lo.
+// Set j accumulates in TMEM columns 256 (j % 2) .. (component c at 16 c), so
+// the epilogue reads one set while the MMAs of the next run. The b_k tails of
+// a round travel with its first stage into a ring of FT slots, which the
+// epilogue releases; the Q stages are released by the MMAs.
 //
 // Warp roles (320 threads): warp 0 issues the TMA loads, one lane of warp 1
 // the MMAs (warp 1 also owns the TMEM allocation), warps 2-9 read the
@@ -75,12 +75,19 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 template <int TDP>
 struct FwdSm {
     static constexpr int NA = TDP / 64;                           // 64-wide column atoms of a Q row
-    static constexpr int RPC = TDP / 2;                           // rows per component in L and in H
-    static constexpr int CR = 256 / RPC;                          // components per round
-    static constexpr int LK = RPC / 16;                           // K steps of the L phase
-    static constexpr int NS = 2 + 2 * NA;                         // stages per round
+    // rows of z per set: 16 (one MMA K step) at TDP = 128; at TDP = 64 sets of
+    // 32 rows (two sets, 8 components per round) measured faster (3.00
+    // against 3.21 ms at N = 2^20, K = 200): the shorter sets of 16 rows left
+    // the MMAs waiting on the epilogue
+    static constexpr int G = TDP == 64 ? 32 : 16;
+    static constexpr int NSET = TDP / G;                          // sets per round
+    static constexpr int CR = 256 / G;                            // components per round
+    // column atoms of set j (its stages: these atoms of Q_hi, then of Q_lo)
+    static constexpr __host__ __device__ int atoms(int j) { return ((j + 1) * G + 63) / 64; }
     static constexpr int FQ = TDP == 64 ? 5 : 4;                  // Q stages
-    static constexpr int FT = 4;                                  // tail slots (rounds)
+    // tail slots (rounds): enough that the producer, FQ stages ahead of the
+    // MMAs, never waits for the epilogue to finish a round
+    static constexpr int FT = G >= 32 ? 4 : 3;
     static constexpr int EW = 8;                                  // epilogue warps
     static constexpr uint32_t STG = 2 * ATOM;                     // 256 rows x 128 bytes
     static constexpr uint32_t TAIL = (TDP + 4) * 4;               // b_k, constant, pad
@@ -89,8 +96,8 @@ struct FwdSm {
     static constexpr uint32_t B = Q + FQ * STG;                   // [FT][CR] tails
     static constexpr uint32_t RED = B + FT * CR * TAIL;
     static constexpr uint32_t MRG = RED + 8 * 8;                  // [128] (max, sum) of warps 6-9
-    static constexpr uint32_t BAR = MRG + 128 * 8;  // x_full, q_full[FQ], q_empty[FQ], l_full, l_empty, h_full,
-                                                    // h_empty, t_empty[FT]
+    static constexpr uint32_t BAR = MRG + 128 * 8;  // x_full, q_full[FQ], q_empty[FQ], a_full[2], a_empty[2],
+                                                    // t_empty[FT]
     static_assert(1 + 2 * FQ + 4 + FT <= 32, "barrier slots");
     static constexpr uint32_t TMEMP = BAR + 32 * 8;
     static constexpr uint32_t FLAG = TMEMP + 8;
@@ -98,13 +105,9 @@ struct FwdSm {
     static constexpr size_t SMEM = END + 1024;
     static_assert(SMEM <= 227 * 1024, "forward shared memory");
     static_assert(Q % 1024 == 0 && STG % 1024 == 0 && TAIL % 16 == 0, "operand and copy alignment");
-    static_assert(CR * RPC == 256 && (CR / 2) * RPC == 128, "a round fills N = 256; each epilogue warp 128 columns");
+    static_assert(CR * G == 256 && (CR / 2) * G == 128 && NSET % 2 == 0,
+                  "a round fills N = 256; each epilogue warp 128 columns");
 };
-
-// a shared-memory descriptor advanced by `bytes` (the start address field is
-// addr >> 4 in 14 bits; operands stay below 256 KB, so the sum never carries
-// into the next field)
-__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
 
 // sum over CNT rows (columns off .. of a 64-column TMEM chunk) of (z - b)^2,
 // z as raw FP32 bits from tcgen05.ld; off must fold to a constant where this
@@ -127,29 +130,110 @@ __device__ __forceinline__ float sumsq_rows(const uint32_t (&v)[64], int off, co
     return t.x + t.y;
 }
 
+// ---- the forward's MMA issue -------------------------------------------------
+// One thread issues every MMA of a CTA; its loop is straight-line code (the
+// sets, atoms and K steps of a round unrolled at compile time) so that
+// consecutive tcgen05.mma instructions are a few independent integer adds
+// apart. Descriptors are handled as low words (start address >> 4: a K step
+// of 32 bytes adds 2, an atom of 16 KB adds 1024; the field has 14 bits and
+// operands stay below 256 KB, so a sum never carries into the next field)
+// with one shared high word.
+struct FwdIssue {
+    uint64_t* q_full;
+    uint64_t* q_empty;
+    uint64_t* a_full;
+    uint64_t* a_empty;
+    int32_t* status;
+    uint32_t tmem, xh, xl, q0, dhi, idesc;
+    uint32_t s, ph;  // next Q stage slot and the parity of its fill
+};
+
+// The MMAs of one stage: NK K steps of its column atom. HI: x_hi and x_lo
+// against Q_hi (two MMAs per step), else x_hi against Q_lo; `first` starts
+// the set's accumulator.
+template <int NK, bool HI>
+__device__ __forceinline__ void fwd_stage_mmas(const FwdIssue& I, uint32_t d, uint32_t ah, uint32_t al, uint32_t bq,
+                                               bool first) {
+#pragma unroll
+    for (int ks = 0; ks < NK; ++ks) {
+        tc::mma_bf16_w(d, ah + 2u * ks, bq + 2u * ks, I.dhi, I.idesc, (first && ks == 0) ? 0u : 1u);
+        if (HI) tc::mma_bf16_w(d, al + 2u * ks, bq + 2u * ks, I.dhi, I.idesc, 1u);
+    }
+}
+
+template <bool HI>
+__device__ __forceinline__ void fwd_stage_dispatch(const FwdIssue& I, int nk, uint32_t d, uint32_t ah, uint32_t al,
+                                                   uint32_t bq, bool first) {
+    switch (nk) {
+        case 1: fwd_stage_mmas<1, HI>(I, d, ah, al, bq, first); break;
+        case 2: fwd_stage_mmas<2, HI>(I, d, ah, al, bq, first); break;
+        case 3: fwd_stage_mmas<3, HI>(I, d, ah, al, bq, first); break;
+        default: fwd_stage_mmas<4, HI>(I, d, ah, al, bq, first); break;
+    }
+}
+
+// Set J of a round (set number q of the CTA: TMEM half q % 2): its atoms of
+// Q_hi, then of Q_lo, each one stage. False when a wait gave up.
+template <int TDP, int J>
+__device__ __forceinline__ bool fwd_set_mmas(FwdIssue& I, int q) {
+    using S = FwdSm<TDP>;
+    constexpr int NAJ = S::atoms(J), KS = (J + 1) * S::G / 16;
+    const int b = q & 1;
+    if (!mbar_wait(&I.a_empty[b], ((uint32_t)(q >> 1) & 1u) ^ 1u, I.status)) return false;
+    const uint32_t d = I.tmem + 256u * (uint32_t)b;
+#pragma unroll
+    for (int lo = 0; lo < 2; ++lo)
+#pragma unroll
+        for (int at = 0; at < NAJ; ++at) {
+            if (!mbar_wait(&I.q_full[I.s], I.ph, I.status)) return false;
+            tc::fence_after_sync();
+            const uint32_t bq = I.q0 + I.s * (S::STG >> 4);
+            const uint32_t ah = I.xh + (uint32_t)at * (ATOM >> 4), al = I.xl + (uint32_t)at * (ATOM >> 4);
+            const int nk = KS - 4 * at < 4 ? KS - 4 * at : 4;
+            if (lo == 0)
+                fwd_stage_dispatch<true>(I, nk, d, ah, al, bq, at == 0);
+            else
+                fwd_stage_dispatch<false>(I, nk, d, ah, al, bq, false);
+            tc::mma_commit(&I.q_empty[I.s]);
+            if (++I.s == (uint32_t)S::FQ) {
+                I.s = 0;
+                I.ph ^= 1u;
+            }
+        }
+    tc::mma_commit(&I.a_full[b]);
+    return true;
+}
+
+template <int TDP, int J, bool END = (J >= FwdSm<TDP>::NSET)>
+struct FwdSets {
+    __device__ static __forceinline__ bool run(FwdIssue& I, int q) {
+        return fwd_set_mmas<TDP, J>(I, q) && FwdSets<TDP, J + 1>::run(I, q + 1);
+    }
+};
+template <int TDP, int J>
+struct FwdSets<TDP, J, true> {
+    __device__ static __forceinline__ bool run(FwdIssue&, int) { return true; }
+};
+
 template <int TDP>
 __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
     gmm_tc_fwd_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmxl,
-                      const __grid_constant__ CUtensorMap tmqL, const __grid_constant__ CUtensorMap tmqLl,
-                      const __grid_constant__ CUtensorMap tmqH, const __grid_constant__ CUtensorMap tmqHl,
-                      const float* __restrict__ tails, int64_t n, int64_t xrow0, int k, float* __restrict__ lj,
-                      int64_t lj_ld, float* __restrict__ lse_out, double* __restrict__ part, int64_t tile0,
-                      const TcCatInst* __restrict__ cat, const int2* __restrict__ cat_tiles,
+                      const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmql,
+                      const float* __restrict__ tails, int64_t n, int64_t xrow0, int k, int kq,
+                      float* __restrict__ lj, int64_t lj_ld, float* __restrict__ lse_out, double* __restrict__ part,
+                      int64_t tile0, const TcCatInst* __restrict__ cat, const int2* __restrict__ cat_tiles,
                       int32_t* __restrict__ status) {
     using S = FwdSm<TDP>;
-    constexpr int FQ = S::FQ, FT = S::FT, NA = S::NA, RPC = S::RPC, CR = S::CR, NS = S::NS;
-    constexpr uint32_t IDESC256 = tc::idesc_bf16_f32(128, 256);
+    constexpr int FQ = S::FQ, FT = S::FT, NA = S::NA, G = S::G, NSET = S::NSET, CR = S::CR;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::BAR);
     uint64_t* x_full = bars;
     uint64_t* q_full = bars + 1;
     uint64_t* q_empty = bars + 1 + FQ;
-    uint64_t* l_full = bars + 1 + 2 * FQ;
-    uint64_t* l_empty = l_full + 1;
-    uint64_t* h_full = l_full + 2;
-    uint64_t* h_empty = l_full + 3;
-    uint64_t* t_empty = l_full + 4;
+    uint64_t* a_full = bars + 1 + 2 * FQ;  // [2] accumulator halves of TMEM
+    uint64_t* a_empty = a_full + 2;
+    uint64_t* t_empty = a_full + 4;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sm + S::TMEMP);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + S::FLAG);
     double* red = reinterpret_cast<double*>(sm + S::RED);
@@ -181,10 +265,10 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
             mbar_init(&q_full[s], 1);
             mbar_init(&q_empty[s], 1);  // MMA commit
         }
-        mbar_init(l_full, 1);
-        mbar_init(h_full, 1);
-        mbar_init(l_empty, S::EW);
-        mbar_init(h_empty, S::EW);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&a_full[b], 1);
+            mbar_init(&a_empty[b], S::EW);
+        }
         for (int t = 0; t < FT; ++t) mbar_init(&t_empty[t], S::EW);
         *abort_flag = 0;
         fence_mbar_init();
@@ -207,64 +291,45 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
                 tc::tma_load_2d(sm + S::X + a * ATOM, &tmx, 64 * a, (int)(xrow0 + p0), x_full);
                 tc::tma_load_2d(sm + S::X + (NA + a) * ATOM, &tmxl, 64 * a, (int)(xrow0 + p0), x_full);
             }
-            // stage g: atom a = g % NS of round g / NS -- L of Q_hi, L of Q_lo,
-            // H of Q_hi per column atom, H of Q_lo per column atom
-            for (int g = 0; g < NS * rounds; ++g) {
-                const int r = g / NS, a = g - NS * r, s = g % FQ, ts = r % FT;
-                const uint32_t ph = (uint32_t)(g / FQ) & 1u, tph = (uint32_t)(r / FT) & 1u;
-                if (!mbar_wait(&q_empty[s], ph ^ 1u, status) ||
-                    (a == 0 && !mbar_wait(&t_empty[ts], tph ^ 1u, status))) {
-                    *abort_flag = 1;
-                    break;
+            // per round and set j: the set's column atoms of Q_hi, then of
+            // Q_lo; one 256-row box each (G rows of each of the round's
+            // components; rows past the last one are never multiplied)
+            uint32_t g = 0;
+            bool ok = true;
+            for (int r = 0; ok && r < rounds; ++r) {
+                const int c0 = CR * r, nc = min(CR, k - c0), ts = r % FT;
+                const uint32_t tph = (uint32_t)(r / FT) & 1u;
+                for (int j = 0; ok && j < NSET; ++j) {
+                    const int row = (j * kq + koff + c0) * G;
+                    for (int lo = 0; ok && lo < 2; ++lo)
+                        for (int at = 0; at < S::atoms(j); ++at, ++g) {
+                            const int s = (int)(g % FQ);
+                            const uint32_t ph = (g / FQ) & 1u;
+                            const bool first = j == 0 && lo == 0 && at == 0;
+                            if (!mbar_wait(&q_empty[s], ph ^ 1u, status) ||
+                                (first && !mbar_wait(&t_empty[ts], tph ^ 1u, status))) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(&q_full[s], S::STG + (first ? (uint32_t)nc * S::TAIL : 0u));
+                            tc::tma_load_2d(sm + S::Q + s * S::STG, lo ? &tmql : &tmq, 64 * at, row, &q_full[s]);
+                            if (first)
+                                bulk_g2s(sm + S::B + ts * CR * S::TAIL, tails + (size_t)(koff + c0) * (TDP + 4),
+                                         (uint32_t)nc * S::TAIL, &q_full[s]);
+                        }
                 }
-                const int c0 = CR * r;
-                const int nc = min(CR, k - c0);
-                mbar_arrive_expect_tx(&q_full[s], S::STG + (a == 0 ? (uint32_t)nc * S::TAIL : 0u));
-                const bool lo = a == 1 || a >= 2 + NA;
-                // one 256-row box: RPC rows of each of the round's CR components
-                // (rows past the last component read as zero)
-                const CUtensorMap* m = a < 2 ? (lo ? &tmqLl : &tmqL) : (lo ? &tmqHl : &tmqH);
-                const int col = a < 2 ? 0 : 64 * ((a - 2) % NA);
-                tc::tma_load_2d(sm + S::Q + s * S::STG, m, col, (koff + c0) * RPC, &q_full[s]);
-                if (a == 0)
-                    bulk_g2s(sm + S::B + ts * CR * S::TAIL, tails + (size_t)(koff + c0) * (TDP + 4),
-                             (uint32_t)nc * S::TAIL, &q_full[s]);
             }
+            if (!ok) *abort_flag = 1;
         }
     } else if (warp == 1) {
         if (lane == 0) {
             bool ok = mbar_wait(x_full, 0, status);
-            const uint64_t dxh = tc::desc_sw128(smem_u32(sm + S::X)), dxl = desc_add(dxh, NA * ATOM);
-            const uint64_t dq0 = tc::desc_sw128(smem_u32(sm + S::Q));
+            const uint64_t dx = tc::desc_sw128(smem_u32(sm + S::X)), dq = tc::desc_sw128(smem_u32(sm + S::Q));
+            FwdIssue I{q_full, q_empty, a_full, a_empty, status, tmem, (uint32_t)dx,
+                       (uint32_t)dx + (uint32_t)(NA * ATOM >> 4), (uint32_t)dq, (uint32_t)(dx >> 32), 0u, 0u, 0u};
             for (int r = 0; ok && r < rounds; ++r) {
-                const uint32_t rph = (uint32_t)r & 1u;
-                for (int a = 0; a < NS; ++a) {
-                    const int g = NS * r + a, s = g % FQ;
-                    const uint32_t ph = (uint32_t)(g / FQ) & 1u;
-                    if ((a == 0 && !mbar_wait(l_empty, rph ^ 1u, status)) ||
-                        (a == 2 && !mbar_wait(h_empty, rph ^ 1u, status)) || !mbar_wait(&q_full[s], ph, status)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
-                    const bool hi = !(a == 1 || a >= 2 + NA);
-                    const uint32_t d = a < 2 ? tmem : tmem + 256u;
-                    const uint32_t xo = a < 2 ? 0u : (uint32_t)((a - 2) % NA) * ATOM;  // x column atom
-                    const uint32_t acc0 = (a == 0 || a == 2) ? 0u : 1u;                // first product into L / H
-                    const int ksteps = a < 2 ? S::LK : 4;
-                    const uint64_t bq = desc_add(dq0, (uint32_t)s * S::STG);
-                    const uint64_t ah = desc_add(dxh, xo), al = desc_add(dxl, xo);
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        if (ks >= ksteps) break;
-                        const uint32_t ko = (uint32_t)ks * 32u;
-                        tc::mma_bf16(d, desc_add(ah, ko), desc_add(bq, ko), IDESC256, ks == 0 ? acc0 : 1u);
-                        if (hi) tc::mma_bf16(d, desc_add(al, ko), desc_add(bq, ko), IDESC256, 1u);
-                    }
-                    tc::mma_commit(&q_empty[s]);
-                    if (a == 1) tc::mma_commit(l_full);
-                    if (a == NS - 1) tc::mma_commit(h_full);
-                }
+                I.idesc = tc::idesc_bf16_f32(128, G * min(CR, k - CR * r));
+                ok = FwdSets<TDP, 0>::run(I, r * NSET);
             }
             if (!ok) *abort_flag = 1;
         }
@@ -272,56 +337,61 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
     } else {
         // epilogue: one thread per point (TMEM lane). Warp w reads TMEM lanes
         // 32 (w % 4) ..; warps 2-5 take the first CR / 2 components of each
-        // round, warps 6-9 the others: 128 columns per warp and phase, read
-        // as two 64-column chunks of 64 / RPC components each.
-        constexpr int HC = CR / 2, PCH = 64 / RPC;  // components per warp, per chunk
+        // round, warps 6-9 the others: 128 columns per warp and set, read as
+        // two 64-column chunks of 64 / G components each.
+        constexpr int HC = CR / 2, PCH = 64 / G;  // components per warp, per chunk
+        constexpr int TF = S::TAIL / 4;           // floats per tail
         const int qtr = warp & 3;
         const int jw = (warp - 2) >> 2;
         const int row = qtr * 32 + lane;
         const bool valid = p0 + row < n;
         const uint32_t tl = tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(128 * jw);
         for (int r = 0; r < rounds; ++r) {
-            const uint32_t rph = (uint32_t)r & 1u;
             const int ts = r % FT;
             const float* bw = reinterpret_cast<const float*>(sm + S::B + (ts * CR + jw * HC) * S::TAIL);
-            constexpr int TF = S::TAIL / 4;  // floats per tail
             float sv[HC];
+#pragma unroll
+            for (int u = 0; u < HC; ++u) sv[u] = 0.f;
             uint32_t rv[2][64];
-            // phase L (the first RPC rows of z), then phase H (the rest): the
-            // second chunk's load is in flight while the first is summed
-            for (int ph = 0; ph < 2; ++ph) {
-                if (!mbar_wait_warp(ph == 0 ? l_full : h_full, rph, status)) {
+            // set by set: both chunks' loads issued together, one wait (the
+            // two sets of TDP = 64 unrolled)
+            constexpr int JU = NSET <= 2 ? NSET : 1;
+#pragma unroll JU
+            for (int j = 0; j < NSET; ++j) {
+                const int q = r * NSET + j, b = q & 1;
+                if (!mbar_wait_warp(&a_full[b], (uint32_t)(q >> 1) & 1u, status)) {
                     *abort_flag = 1;
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t ta = tl + (ph == 0 ? 0u : 256u);
+                const uint32_t ta = tl + 256u * (uint32_t)b;
+                const float* bj = bw + j * G;
                 tc::tmem_ld64_issue(ta, rv[0]);
-                tc::tmem_ld64_tied_wait(rv[0]);
                 tc::tmem_ld64_issue(ta + 64u, rv[1]);
-                float s2[HC];
+                tc::tmem_ld64_tied_wait(rv[0]);
 #pragma unroll
-                for (int u = 0; u < PCH; ++u) s2[u] = sumsq_rows<RPC>(rv[0], u * RPC, bw + u * TF + ph * RPC);
+                for (int u = 0; u < PCH; ++u) sv[u] += sumsq_rows<G>(rv[0], u * G, bj + u * TF);
                 tc::tmem_ld64_tied_wait(rv[1]);
 #pragma unroll
-                for (int u = 0; u < PCH; ++u)
-                    s2[PCH + u] = sumsq_rows<RPC>(rv[1], u * RPC, bw + (PCH + u) * TF + ph * RPC);
-#pragma unroll
-                for (int u = 0; u < HC; ++u) sv[u] = ph == 0 ? s2[u] : sv[u] + s2[u];
-                if (ph == 1) fence_proxy_async_smem();  // tails read through the generic proxy
+                for (int u = 0; u < PCH; ++u) sv[PCH + u] += sumsq_rows<G>(rv[1], u * G, bj + (PCH + u) * TF);
                 tc::fence_before_sync();
                 __syncwarp();
-                if (lane == 0) {
-                    tc::mbar_arrive(ph == 0 ? l_empty : h_empty);
-                    if (ph == 1) tc::mbar_arrive(&t_empty[ts]);
-                }
+                if (lane == 0) tc::mbar_arrive(&a_empty[b]);
             }
             if (*abort_flag) break;
+            // the round's tail slot goes back to the producer after its last
+            // read (the constants)
+            float cst[HC];
+#pragma unroll
+            for (int u = 0; u < HC; ++u) cst[u] = bw[u * TF + TDP];
+            fence_proxy_async_smem();  // tails read through the generic proxy
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&t_empty[ts]);
 #pragma unroll
             for (int u = 0; u < HC; ++u) {
                 const int kk = CR * r + HC * jw + u;
                 if (kk < k && valid) {
-                    const float v = bw[u * TF + TDP] - 0.5f * sv[u];
+                    const float v = cst[u] - 0.5f * sv[u];
                     if (lj) lj[(int64_t)kk * lj_ld + p0 + row] = v;
                     st.add(v);
                 }
@@ -791,40 +861,32 @@ __global__ void __launch_bounds__(256) tc_convert_x_kernel(const float* __restri
     }
 }
 
-// prep record Qt[c][r] -> Q_hi + Q_lo (bf16) in the forward's phase-major
-// layout, and the b_k tails. Each of qb, ql holds two parts: L = [k][RPC][64]
-// (the first RPC = TDP / 2 rows of each Q_k, first 64 columns: the forward's L
-// operand needs no more) and, after it, H = [k][RPC][TDP] (the other rows), so
-// that the rows of CR = 256 / RPC consecutive components form one 256-row TMA
-// box. tails: [k][TDP + 4] floats (b_k, the constant, padding), contiguous
-// over the components so that a round's tails are one copy.
+// prep record Qt[c][r] -> Q_hi + Q_lo (bf16) in the forward's set-major
+// layout, and the b_k tails. qb and ql each hold NSET parts [kq][G][TDP]: part
+// j has rows jG .. jG + G - 1 of every Q_k, so that the rows of CR = 256 / G
+// consecutive components form one 256-row TMA box. tails: [kq][TDP + 4] floats
+// (b_k, the constant, padding), contiguous over the components so that a
+// round's tails are one copy.
 template <int TDP>
-__global__ void __launch_bounds__(256) tc_convert_q_kernel(const float* __restrict__ rec, int k,
+__global__ void __launch_bounds__(256) tc_convert_q_kernel(const float* __restrict__ rec, int kq,
                                                            __nv_bfloat16* __restrict__ qb,
                                                            __nv_bfloat16* __restrict__ ql,
                                                            float* __restrict__ tails) {
-    constexpr int RPC = TDP / 2;
-    const int64_t nl = (int64_t)k * RPC * 64, total = nl + (int64_t)k * RPC * TDP;
+    constexpr int G = FwdSm<TDP>::G;
+    const int64_t part = (int64_t)kq * G * TDP, total = part * FwdSm<TDP>::NSET;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-        int64_t kk;
-        int r, c;
-        if (e < nl) {
-            kk = e / (RPC * 64);
-            r = (int)((e / 64) % RPC);
-            c = (int)(e % 64);
-        } else {
-            const int64_t f = e - nl;
-            kk = f / (RPC * TDP);
-            r = RPC + (int)((f / TDP) % RPC);
-            c = (int)(f % TDP);
-        }
+        const int j = (int)(e / part);
+        const int64_t f = e - j * part;
+        const int64_t kk = f / (G * TDP);
+        const int r = j * G + (int)((f / TDP) % G);
+        const int c = (int)(f % TDP);
         const float v = rec[kk * Tc<TDP>::REC + (int64_t)c * TDP + r];
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         qb[e] = h;
         ql[e] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)k * (TDP + 4); e += stride)
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)kq * (TDP + 4); e += stride)
         tails[e] = rec[(e / (TDP + 4)) * Tc<TDP>::REC + TDP * TDP + e % (TDP + 4)];
 }
 
@@ -944,23 +1006,18 @@ int convert_inputs(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char
     return GPA_OK;
 }
 
-// Tensor maps of the forward's Q operands (hi, lo) in the phase-major layout
-// of tc_convert_q_kernel: L part [k * RPC rows][64], H part [k * RPC][TDP],
-// 256-row boxes.
+// Tensor maps of the forward's Q operands (hi, lo) in the set-major layout of
+// tc_convert_q_kernel ([kq * TDP rows][TDP]), 256-row boxes.
 template <int TDP>
-bool make_q_maps(CUtensorMap (&m)[4], const void* qb, const void* ql, int64_t k) {
-    constexpr int RPC = FwdSm<TDP>::RPC;
-    const size_t hoff = (size_t)k * RPC * 64 * 2;
-    return make_map(&m[0], qb, k * RPC, 64, 256) && make_map(&m[1], ql, k * RPC, 64, 256) &&
-           make_map(&m[2], (const char*)qb + hoff, k * RPC, TDP, 256) &&
-           make_map(&m[3], (const char*)ql + hoff, k * RPC, TDP, 256);
+bool make_q_maps(CUtensorMap (&m)[2], const void* qb, const void* ql, int64_t kq) {
+    return make_map(&m[0], qb, kq * TDP, TDP, 256) && make_map(&m[1], ql, kq * TDP, TDP, 256);
 }
 
 template <int TDP>
 int launch_tc_fwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char* ws, int64_t row0, int64_t n_local,
                   float* lj, int64_t lj_ld, float* lse, cudaStream_t s) {
     using S = FwdSm<TDP>;
-    CUtensorMap tmx, tmxl, tq[4];
+    CUtensorMap tmx, tmxl, tq[2];
     if (!make_map(&tmx, ws + T.off_xb, A.n, TDP) || !make_map(&tmxl, ws + T.off_xl, A.n, TDP) ||
         !make_q_maps<TDP>(tq, ws + T.off_qb, ws + T.off_ql, A.k))
         return GPA_ERR_CUDA;
@@ -969,8 +1026,8 @@ int launch_tc_fwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char*
     if (!set_smem_tc(kern, S::SMEM)) return GPA_ERR_CUDA;
     GPA_LAUNCH("gmm_tc_fwd", s,
                kern<<<(unsigned)tiles, 64 + 32 * S::EW, S::SMEM, s>>>(
-                   tmx, tmxl, tq[0], tq[1], tq[2], tq[3], (const float*)(ws + T.off_tails), n_local, row0, A.k, lj,
-                   lj_ld, lse, (double*)(ws + L.off_fwd), row0 / TM, nullptr, nullptr, A.status));
+                   tmx, tmxl, tq[0], tq[1], (const float*)(ws + T.off_tails), n_local, row0, A.k, A.k, lj, lj_ld,
+                   lse, (double*)(ws + L.off_fwd), row0 / TM, nullptr, nullptr, A.status));
     return GPA_OK;
 }
 
@@ -1122,7 +1179,7 @@ int cat_run(const TcCatClass& C, cudaStream_t s) {
                    C.rec, (int)C.kc, qb, ql, C.tails));
     GPA_LAUNCH("gmm_tc_xt", s,
                tc_cat_xt_kernel<TDP><<<(unsigned)(C.np / GTM), 256, 0, s>>>(C.inst, C.tile_inst, C.xt, xb, xl));
-    CUtensorMap tmx, tmxl, tq[4], tmr;
+    CUtensorMap tmx, tmxl, tq[2], tmr;
     if (!make_map(&tmx, xb, C.np, TDP) || !make_map(&tmxl, xl, C.np, TDP) || !make_q_maps<TDP>(tq, qb, ql, C.kc) ||
         !make_map_r(&tmr, rb, C.np, (int)C.kr, 16))
         return GPA_ERR_CUDA;
@@ -1130,9 +1187,9 @@ int cat_run(const TcCatClass& C, cudaStream_t s) {
     if (!set_smem_tc(kf, S::SMEM)) return GPA_ERR_CUDA;
     if (C.n_fwd > 0)
         GPA_LAUNCH("gmm_tc_fwd", s,
-                   kf<<<(unsigned)C.n_fwd, 64 + 32 * S::EW, S::SMEM, s>>>(tmx, tmxl, tq[0], tq[1], tq[2], tq[3],
-                                                                          C.tails, 0, 0, 0, nullptr, 0, nullptr,
-                                                                          nullptr, 0, C.inst, C.fwd_tiles, C.status));
+                   kf<<<(unsigned)C.n_fwd, 64 + 32 * S::EW, S::SMEM, s>>>(tmx, tmxl, tq[0], tq[1], C.tails, 0, 0, 0,
+                                                                          (int)C.kc, nullptr, 0, nullptr, nullptr,
+                                                                          0, C.inst, C.fwd_tiles, C.status));
     const int64_t rwork = C.kr * (C.np / 8);
     GPA_LAUNCH("gmm_tc_r", s,
                tc_cat_r_kernel<<<(unsigned)min64((int64_t)sm_count_tc() * 16, (rwork + 255) / 256), 256, 0, s>>>(
