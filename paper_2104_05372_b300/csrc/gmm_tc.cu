@@ -57,9 +57,8 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 // 16 at TDP = 128 (8 sets, 16 components per round, 9/16 of the dense MMA
 // work), G = 32 at TDP = 64 (2 sets, 8 components, 3/4). Every MMA is M = 128
 // and N = G nc (nc = the round's components: 256 but in a last, partial
-// round): a single issuing thread needs about 100 cycles per tcgen05.mma, more
-// than an N = 128 MMA takes to execute (64 cycles), so narrower MMAs would
-// leave the tensor pipe idle.
+// round), the widest single-CTA shape, so that the one issuing thread stays
+// ahead of the tensor pipe.
 //
 // Pipeline stages are 32 KB operand atoms (256 rows x 64 columns, one TMA
 // box), per set its NA_j = ceil((j + 1) G / 64) atoms of Q_hi, then of Q_lo.
@@ -76,9 +75,9 @@ template <int TDP>
 struct FwdSm {
     static constexpr int NA = TDP / 64;                           // 64-wide column atoms of a Q row
     // rows of z per set: 16 (one MMA K step) at TDP = 128; at TDP = 64 sets of
-    // 32 rows (two sets, 8 components per round) measured faster (3.00
-    // against 3.21 ms at N = 2^20, K = 200): the shorter sets of 16 rows left
-    // the MMAs waiting on the epilogue
+    // 32 rows (two sets, 8 components per round) measured faster (2.39
+    // against 2.78 ms at N = 2^20, K = 200): with sets of 16 rows the MMAs
+    // of a set take less time than the epilogue's read of the previous one
     static constexpr int G = TDP == 64 ? 32 : 16;
     static constexpr int NSET = TDP / G;                          // sets per round
     static constexpr int CR = 256 / G;                            // components per round
