@@ -343,7 +343,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, const gpa_batched_opts& O
         C.off_qb = off;  off = a256(off + 2 * (size_t)C.kc * tdp * tdp);
         C.off_ql = off;  off = a256(off + 2 * (size_t)C.kc * tdp * tdp);
         C.off_rb = off;  off = a256(off + 2 * (size_t)C.kr * C.np);
-        C.off_xt = off;  off = a256(off + sizeof(float) * (size_t)xtf);
+        C.off_xt = off;  off = a256(off + 2 * (size_t)xtf);  // bf16
         C.off_lse = off; off = a256(off + sizeof(float) * (size_t)C.np);
         C.off_lj = off;  off = a256(off + sizeof(float) * (size_t)pairs);
         int64_t ljo = 0;
@@ -894,7 +894,7 @@ extern "C" int gmm_batched_vjp_opts(const gpa_gmm_instance* inst, int32_t n_inst
         T.qb = w + C.off_qb;
         T.ql = w + C.off_ql;
         T.rb = w + C.off_rb;
-        T.xt = (float*)(w + C.off_xt);
+        T.xt = w + C.off_xt;
         T.status = dev_status;
         rc = gmm_tc_cat_run(T, s);
     }

@@ -85,7 +85,7 @@ struct TcCatInst {
     float* lse;                  // [n] per-point logsumexp
     double* fwd;                 // [ceil(n / 128)] per-tile sums of lse
     float *bS, *bM;              // partial sums [nchunks][k][...] (zeroed by the caller)
-    int64_t n, xoff, xtoff;      // points; first row in x / R; float offset of its point tiles
+    int64_t n, xoff, xtoff;      // points; first row in x / R; element offset of its point tiles
     int64_t tpc;                 // 64-point tiles per backward chunk
     int d, k, koff, kn, ng, nchunks;
     float seed;
@@ -101,7 +101,7 @@ struct TcCatClass {
     const float* rec;            // [kc] prep records
     float* tails;                // [kc][tdp + 4] b_k and constants
     void *xb, *xl, *qb, *ql, *rb;  // bf16 x_hi, x_lo [np][tdp]; Q_hi, Q_lo (kc * tdp * tdp each); R [kr][np]
-    float* xt;                   // point tiles
+    void* xt;                    // bf16 point tiles
     int32_t* status;
 };
 int gmm_tc_cat_run(const TcCatClass& C, cudaStream_t s);

@@ -445,23 +445,23 @@ constexpr int GKMAX = 256;                      // components per CTA (MMA N)
 constexpr int GRB_POINTS = 1 << 18;             // points of R held at a time
 constexpr uint32_t GYB = GMB * 128 * 128;       // one Y tile: 256 rows x 64 points bf16
 
-// Transposed point tile: row c (a coordinate; row d = ones, d + 1 = zeros)
-// holds the tile's 64 points, the 16-byte group g of 4 points at position
-// g ^ (c & 7), so that a warp reading one group of 32 different rows, or
-// writing 8 rows x 4 points, spreads over all banks.
-__host__ __device__ __forceinline__ int gram_xpos(int c, int p) { return c * GTM + ((((p >> 2) ^ c) & 15) << 2) + (p & 3); }
+// Transposed point tile (BF16): row c (a coordinate; row d = ones, d + 1 =
+// zeros) holds the tile's 64 points in 128 bytes, the 16-byte group g of 8
+// points at position g ^ (c & 7), so that a warp reading one group of 32
+// different rows spreads over all banks.
+__host__ __device__ __forceinline__ int gram_xpos(int c, int p) { return c * GTM + ((((p >> 3) ^ c) & 7) << 3) + (p & 7); }
 
 template <int TDP>
 struct GramSm {
     static constexpr int XR = TDP + 2;          // rows of a transposed point tile
-    static constexpr int XS = TDP == 64 ? 3 : 2;  // point-tile stages (copies run XS - 1 tiles ahead)
+    static constexpr int XS = 3;                // point-tile stages (copies run XS - 1 tiles ahead)
     // R-tile stages: the TMA runs RS - 1 tiles ahead of the MMAs, which covers
     // the latency of a 26-32 KB load from L2 / HBM
     static constexpr int RS = 3;
     static constexpr uint32_t Y = 0;                              // [2] Y tiles
     static constexpr uint32_t R = Y + 2 * GYB;                    // [RS] R tiles (<= 256 rows x 128 B)
-    static constexpr uint32_t XT = R + RS * GKMAX * 128;          // [XS][XR][GTM] float
-    static constexpr uint32_t BAR = XT + XS * XR * GTM * 4;  // y_full[2], y_empty[2], r_full[RS], r_empty[RS],
+    static constexpr uint32_t XT = R + RS * GKMAX * 128;          // [XS][XR][GTM] bf16
+    static constexpr uint32_t BAR = XT + XS * XR * GTM * 2;  // y_full[2], y_empty[2], r_full[RS], r_empty[RS],
                                                              // x_full[XS], x_empty[XS], done
     static_assert(4 + 2 * RS + 2 * XS + 1 <= 24, "barrier slots");
     static constexpr uint32_t TMEMP = BAR + 24 * 8;
@@ -470,6 +470,13 @@ struct GramSm {
     static constexpr size_t SMEM = END + 1024;
     static_assert(SMEM <= 227 * 1024, "gram shared memory");
 };
+
+// Two packed BF16 products, each rounded once to BF16.
+__device__ __forceinline__ uint32_t bf16x2_mul(uint32_t a, uint32_t b) {
+    const __nv_bfloat162 r =
+        __hmul2(*reinterpret_cast<const __nv_bfloat162*>(&a), *reinterpret_cast<const __nv_bfloat162*>(&b));
+    return *reinterpret_cast<const uint32_t*>(&r);
+}
 
 __device__ __forceinline__ void gram_producers_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(GPROD) : "memory");
@@ -497,7 +504,7 @@ __device__ __forceinline__ void gram_row(int i, int d, int& u, int& v) {
 
 template <int TDP>
 __global__ void __launch_bounds__(GTHREADS, 1)
-    gmm_tc_gram_kernel(const __grid_constant__ CUtensorMap tmr, const float* __restrict__ xt_g, int64_t n, int d,
+    gmm_tc_gram_kernel(const __grid_constant__ CUtensorMap tmr, const __nv_bfloat16* __restrict__ xt_g, int64_t n, int d,
                        int k, int kn, int ngroups, int64_t tiles_per_chunk, float* __restrict__ partS,
                        float* __restrict__ partM, int nblk64, int rbox, const TcCatInst* __restrict__ cat,
                        const int4* __restrict__ cat_items, int32_t* __restrict__ status) {
@@ -516,7 +523,7 @@ __global__ void __launch_bounds__(GTHREADS, 1)
     uint64_t* done = bars + 4 + 2 * RS + 2 * XS;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sm + S::TMEMP);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + S::FLAG);
-    float* xt = reinterpret_cast<float*>(sm + S::XT);
+    __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(sm + S::XT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tid = threadIdx.x;
     // this CTA's work: (group blockIdx.x, chunk blockIdx.y) of the call, or, in
@@ -567,8 +574,8 @@ __global__ void __launch_bounds__(GTHREADS, 1)
     // constant rows of the transposed point tiles: ones at row d, zeros at d + 1
     for (int e = tid; e < XS * GTM; e += GTHREADS) {
         const int b = e / GTM, p = e % GTM;
-        xt[b * S::XR * GTM + d * GTM + p] = 1.f;
-        xt[b * S::XR * GTM + (d + 1) * GTM + p] = 0.f;
+        xt[b * S::XR * GTM + d * GTM + p] = __float2bfloat16_rn(1.f);
+        xt[b * S::XR * GTM + (d + 1) * GTM + p] = __float2bfloat16_rn(0.f);
     }
     if (warp == GPROD / 32 + 1) {
         tc::tmem_alloc(tmem_holder, 512);
@@ -585,7 +592,7 @@ __global__ void __launch_bounds__(GTHREADS, 1)
         // points) and the R tile (TMA: components kg0 .. kg0 + kn - 1, zero rows
         // past K, 64 points)
         if (lane == 0) {
-            const uint32_t xbytes = (uint32_t)d * GTM * 4u;
+            const uint32_t xbytes = (uint32_t)d * GTM * 2u;
             int it = 0;
             for (int64_t t = t_begin; t < t_end; ++t, ++it) {
                 const int xb = it % XS, b = it % RS;
@@ -611,6 +618,10 @@ __global__ void __launch_bounds__(GTHREADS, 1)
         // MMA issuer: D[mb] (tensor-memory columns 256 mb ..) += Y[mb] R^T
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(128, kn);
+            // descriptors as low words with one shared high word (as in the
+            // forward): a K step of 32 bytes adds 2
+            const uint64_t dy = tc::desc_sw128(smem_u32(sm + S::Y)), dr = tc::desc_sw128(smem_u32(sm + S::R));
+            const uint32_t dhi = (uint32_t)(dy >> 32);
             bool ok = true;
             int it = 0;
             for (int64_t t = t_begin; ok && t < t_end; ++t, ++it) {
@@ -621,13 +632,14 @@ __global__ void __launch_bounds__(GTHREADS, 1)
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t ya = smem_u32(sm + S::Y + b * GYB), ra = smem_u32(sm + S::R + rb * GKMAX * 128);
+                const uint32_t ya = (uint32_t)dy + (uint32_t)b * (GYB >> 4);
+                const uint32_t ra = (uint32_t)dr + (uint32_t)rb * (GKMAX * 128 >> 4);
 #pragma unroll
                 for (int mb = 0; mb < GMB; ++mb)
 #pragma unroll
                     for (int j = 0; j < GTM / 16; ++j)
-                        tc::mma_bf16(tmem + (uint32_t)(mb * 256), tc::desc_sw128(ya + mb * 128 * 128 + j * 32),
-                                     tc::desc_sw128(ra + j * 32), idesc, (it > 0 || j > 0) ? 1u : 0u);
+                        tc::mma_bf16_w(tmem + (uint32_t)(mb * 256), ya + (uint32_t)(mb * (128 * 128 >> 4) + 2 * j),
+                                       ra + 2u * j, dhi, idesc, (it > 0 || j > 0) ? 1u : 0u);
                 tc::mma_commit(&y_empty[b]);
                 tc::mma_commit(&r_empty[rb]);
             }
@@ -638,23 +650,24 @@ __global__ void __launch_bounds__(GTHREADS, 1)
     } else {
         // producers: thread = one product row (u, v) of one MMA block, points
         // 32 h .. 32 h + 31 of each tile; a warp takes 32 consecutive rows, so
-        // its loads of x_u are broadcasts and its 32 rows x_v fall in distinct
-        // bank groups (row stride 68 floats)
+        // its loads of x_u are broadcasts and its 32 rows x_v spread over all
+        // banks. The coordinates are BF16; each product of two of them is
+        // formed and rounded to BF16 by one packed multiply.
         const int lrow = tid & 255, h = tid >> 8;
         int u, v;
         gram_row(row0 + lrow, d, u, v);
         const int mb = lrow >> 7, r7 = lrow & 127;
-        // this thread's read offsets in a point tile (groups 8h .. 8h + 7 of
-        // rows u and v) and write offsets in a Y tile (chunks 4h .. 4h + 3)
-        int ou[8], ov[8];
-#pragma unroll
-        for (int gg = 0; gg < 8; ++gg) {
-            ou[gg] = gram_xpos(u, 4 * (8 * h + gg));
-            ov[gg] = gram_xpos(v, 4 * (8 * h + gg));
-        }
+        // this thread's read offsets in a point tile (groups 4h .. 4h + 3 of
+        // rows u and v, 8 points each) and write offsets in a Y tile (the same
+        // 16-byte chunks of its row)
+        int ou[4], ov[4];
         uint32_t oy[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) oy[c] = (uint32_t)(mb * 128 * 128) + tc::sw128_offset((uint32_t)r7, (uint32_t)(4 * h + c));
+        for (int c = 0; c < 4; ++c) {
+            ou[c] = gram_xpos(u, 8 * (4 * h + c));
+            ov[c] = gram_xpos(v, 8 * (4 * h + c));
+            oy[c] = (uint32_t)(mb * 128 * 128) + tc::sw128_offset((uint32_t)r7, (uint32_t)(4 * h + c));
+        }
         int it = 0;
         for (int64_t t = t_begin; t < t_end; ++t, ++it) {
             const int b = it & 1, xb = it % XS;
@@ -665,21 +678,15 @@ __global__ void __launch_bounds__(GTHREADS, 1)
                 *abort_flag = 1;
                 break;
             }
-            const float* X = xt + xb * S::XR * GTM;
+            const __nv_bfloat16* X = xt + xb * S::XR * GTM;
             uint8_t* yt = sm + S::Y + b * GYB;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {  // 8 points per 16-byte chunk of the Y row
-                const float4 u0 = *reinterpret_cast<const float4*>(X + ou[2 * c]);
-                const float4 u1 = *reinterpret_cast<const float4*>(X + ou[2 * c + 1]);
-                const float4 v0 = *reinterpret_cast<const float4*>(X + ov[2 * c]);
-                const float4 v1 = *reinterpret_cast<const float4*>(X + ov[2 * c + 1]);
-                const float2 p0 = __fmul2_rn(make_float2(u0.x, u0.y), make_float2(v0.x, v0.y));
-                const float2 p1 = __fmul2_rn(make_float2(u0.z, u0.w), make_float2(v0.z, v0.w));
-                const float2 p2 = __fmul2_rn(make_float2(u1.x, u1.y), make_float2(v1.x, v1.y));
-                const float2 p3 = __fmul2_rn(make_float2(u1.z, u1.w), make_float2(v1.z, v1.w));
+                const uint4 a4 = *reinterpret_cast<const uint4*>(X + ou[c]);
+                const uint4 b4 = *reinterpret_cast<const uint4*>(X + ov[c]);
                 *reinterpret_cast<uint4*>(yt + oy[c]) =
-                    make_uint4(tc::pack_bf16x2(p0.x, p0.y), tc::pack_bf16x2(p1.x, p1.y),
-                               tc::pack_bf16x2(p2.x, p2.y), tc::pack_bf16x2(p3.x, p3.y));
+                    make_uint4(bf16x2_mul(a4.x, b4.x), bf16x2_mul(a4.y, b4.y), bf16x2_mul(a4.z, b4.z),
+                               bf16x2_mul(a4.w, b4.w));
             }
             fence_proxy_async_smem();  // the Y writes before the MMAs read them; the point-tile reads before its refill
             __syncwarp();
@@ -733,15 +740,15 @@ __global__ void __launch_bounds__(GTHREADS, 1)
 }
 
 // Point tiles for the gram kernel: tile t (points 64 t .. 64 t + 63, zero past
-// n) as d rows of 64 floats, row c holding coordinate c of the tile's points in
-// the order of gram_xpos, so that one bulk copy brings a tile into shared
-// memory in the layout the gram kernel reads. One CTA per tile.
+// n) as d rows of 64 BF16 values, row c holding coordinate c of the tile's
+// points in the order of gram_xpos, so that one bulk copy brings a tile into
+// shared memory in the layout the gram kernel reads. One CTA per tile.
 // With XB (the forward's operands, TDP > 0): the same tile's rows also split
 // into x_hi + x_lo (BF16, rows of TDP, zero padded) at rows xrow .. xrow + 63
 // of xb / xl, from the one read of x.
 template <int TDP = 0>
 __device__ __forceinline__ void gmm_tc_xt_tile(const float* __restrict__ x, int64_t n, int d,
-                                               float* __restrict__ xt, int64_t t,
+                                               __nv_bfloat16* __restrict__ xt, int64_t t,
                                                __nv_bfloat16* __restrict__ xb = nullptr,
                                                __nv_bfloat16* __restrict__ xl = nullptr, int64_t xrow = 0) {
     __shared__ float tile[GTM][129];
@@ -751,10 +758,10 @@ __device__ __forceinline__ void gmm_tc_xt_tile(const float* __restrict__ x, int6
         tile[p][c] = p0 + p < n ? __ldg(x + (p0 + p) * d + c) : 0.f;
     }
     __syncthreads();
-    float* out = xt + t * (int64_t)d * GTM;
+    __nv_bfloat16* out = xt + t * (int64_t)d * GTM;
     for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
         const int c = e / GTM, p = e % GTM;
-        out[gram_xpos(c, p)] = tile[p][c];
+        out[gram_xpos(c, p)] = __float2bfloat16_rn(tile[p][c]);
     }
     if constexpr (TDP > 0) {
         for (int e = threadIdx.x; e < GTM * (TDP / 2); e += blockDim.x) {
@@ -772,7 +779,7 @@ __device__ __forceinline__ void gmm_tc_xt_tile(const float* __restrict__ x, int6
 // point tile t and rows 64 t .. 64 t + 63 of x_hi, x_lo.
 template <int TDP>
 __global__ void __launch_bounds__(256) gmm_tc_xtb_kernel(const float* __restrict__ x, int64_t n, int d,
-                                                         float* __restrict__ xt, __nv_bfloat16* __restrict__ xb,
+                                                         __nv_bfloat16* __restrict__ xt, __nv_bfloat16* __restrict__ xb,
                                                          __nv_bfloat16* __restrict__ xl) {
     gmm_tc_xt_tile<TDP>(x, n, d, xt, blockIdx.x, xb, xl, (int64_t)blockIdx.x * GTM);
 }
@@ -782,7 +789,7 @@ __global__ void __launch_bounds__(256) gmm_tc_xtb_kernel(const float* __restrict
 // and those rows of x_hi, x_lo.
 template <int TDP>
 __global__ void __launch_bounds__(256) tc_cat_xt_kernel(const TcCatInst* __restrict__ cat,
-                                                        const int* __restrict__ tile_inst, float* __restrict__ xt,
+                                                        const int* __restrict__ tile_inst, __nv_bfloat16* __restrict__ xt,
                                                         __nv_bfloat16* __restrict__ xb,
                                                         __nv_bfloat16* __restrict__ xl) {
     const TcCatInst& I = cat[tile_inst[blockIdx.x / 2]];
@@ -919,7 +926,7 @@ TcLayout tc_layout(const GmmLayout& L, int64_t n, int d, int k) {
     T.off_tails = T.off_ql + qbytes;
     T.off_rb = T.off_tails + a1024((size_t)k * (tdp + 4) * 4);
     T.off_xt = T.off_rb + a1024((size_t)tc_r_rows(k) * T.rpoints * 2);
-    T.fixed = T.off_xt + a1024((size_t)T.npad * d * 4);
+    T.fixed = T.off_xt + a1024((size_t)T.npad * d * 2);
     return T;
 }
 
@@ -991,7 +998,7 @@ int convert_inputs(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char
     if (with_xt)
         GPA_LAUNCH("gmm_tc_xt", s,
                    gmm_tc_xtb_kernel<TDP><<<(unsigned)(T.npad / GTM), 256, 0, s>>>(
-                       A.x, A.n, A.d, (float*)(ws + T.off_xt), (__nv_bfloat16*)(ws + T.off_xb),
+                       A.x, A.n, A.d, (__nv_bfloat16*)(ws + T.off_xt), (__nv_bfloat16*)(ws + T.off_xb),
                        (__nv_bfloat16*)(ws + T.off_xl)));
     else
         GPA_LAUNCH("gmm_tc_convert_x", s,
@@ -1084,7 +1091,7 @@ int launch_tc_bwd(const GmmArgs& A, const GmmLayout& L, const TcLayout& T, char*
     const int64_t tpc = (ntiles + nchunks - 1) / nchunks;
     dim3 grid((unsigned)(ng * nkg), (unsigned)nchunks);
     GPA_LAUNCH("gmm_tc_bwd", s,
-               kern<<<grid, GTHREADS, GramSm<TDP>::SMEM, s>>>(tmr, (const float*)(ws + T.off_xt) + row0 * A.d, n_local,
+               kern<<<grid, GTHREADS, GramSm<TDP>::SMEM, s>>>(tmr, (const __nv_bfloat16*)(ws + T.off_xt) + row0 * A.d, n_local,
                                                                 A.d, A.k, kn, ng, tpc,
                                                          (float*)(ws + L.off_bS), (float*)(ws + L.off_bM),
                                                          gmm_bwd_partial_entries(TDP), kn, nullptr, nullptr,
@@ -1177,7 +1184,8 @@ int cat_run(const TcCatClass& C, cudaStream_t s) {
                tc_convert_q_kernel<TDP><<<(unsigned)min64(cap, (C.kc * TDP * TDP + 255) / 256), 256, 0, s>>>(
                    C.rec, (int)C.kc, qb, ql, C.tails));
     GPA_LAUNCH("gmm_tc_xt", s,
-               tc_cat_xt_kernel<TDP><<<(unsigned)(C.np / GTM), 256, 0, s>>>(C.inst, C.tile_inst, C.xt, xb, xl));
+               tc_cat_xt_kernel<TDP><<<(unsigned)(C.np / GTM), 256, 0, s>>>(C.inst, C.tile_inst,
+                                                                          (__nv_bfloat16*)C.xt, xb, xl));
     CUtensorMap tmx, tmxl, tq[2], tmr;
     if (!make_map(&tmx, xb, C.np, TDP) || !make_map(&tmxl, xl, C.np, TDP) || !make_q_maps<TDP>(tq, qb, ql, C.kc) ||
         !make_map_r(&tmr, rb, C.np, (int)C.kr, 16))
@@ -1198,7 +1206,7 @@ int cat_run(const TcCatClass& C, cudaStream_t s) {
     if (C.n_gram > 0)
         GPA_LAUNCH("gmm_tc_bwd", s,
                    kg<<<(unsigned)C.n_gram, GTHREADS, GramSm<TDP>::SMEM, s>>>(
-                       tmr, C.xt, 0, 0, 0, 16, 1, 1, nullptr, nullptr, gmm_bwd_partial_entries(TDP), 16, C.inst,
+                       tmr, (const __nv_bfloat16*)C.xt, 0, 0, 0, 16, 1, 1, nullptr, nullptr, gmm_bwd_partial_entries(TDP), 16, C.inst,
                        C.gram_items, C.status));
     return GPA_OK;
 }
@@ -1219,7 +1227,7 @@ size_t gmm_tc_extra_bytes(int64_t n, int d, int k) {
     const int64_t npad = ((n + TM - 1) / TM) * TM;
     return 2 * a1024((size_t)npad * tdp * 2) + 2 * a1024((size_t)k * tdp * tdp * 2) +
            a1024((size_t)k * (tdp + 4) * 4) + a1024((size_t)tc_r_rows(k) * tc_r_points(npad) * 2) +
-           a1024((size_t)npad * d * 4) + 2048;
+           a1024((size_t)npad * d * 2) + 2048;
 }
 
 int gmm_tc_objective_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cudaStream_t s) {
