@@ -753,24 +753,51 @@ __device__ __forceinline__ void gmm_tc_xt_tile(const float* __restrict__ x, int6
                                                __nv_bfloat16* __restrict__ xl = nullptr, int64_t xrow = 0) {
     __shared__ float tile[GTM][129];
     const int64_t p0 = t * GTM;
-    for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
-        const int p = e / d, c = e - p * d;
-        tile[p][c] = p0 + p < n ? __ldg(x + (p0 + p) * d + c) : 0.f;
+    if (d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {  // 16-byte loads of the rows
+        const int d4 = d / 4;
+        for (int e = threadIdx.x; e < GTM * d4; e += blockDim.x) {
+            const int p = e / d4, c = (e - p * d4) * 4;
+            const float4 v = p0 + p < n ? __ldg(reinterpret_cast<const float4*>(x + (p0 + p) * d + c))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+            tile[p][c] = v.x;
+            tile[p][c + 1] = v.y;
+            tile[p][c + 2] = v.z;
+            tile[p][c + 3] = v.w;
+        }
+    } else {
+        for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
+            const int p = e / d, c = e - p * d;
+            tile[p][c] = p0 + p < n ? __ldg(x + (p0 + p) * d + c) : 0.f;
+        }
     }
     __syncthreads();
+    // coordinate row c, 8-point group g: one 16-byte store
     __nv_bfloat16* out = xt + t * (int64_t)d * GTM;
-    for (int e = threadIdx.x; e < GTM * d; e += blockDim.x) {
-        const int c = e / GTM, p = e % GTM;
-        out[gram_xpos(c, p)] = __float2bfloat16_rn(tile[p][c]);
+    for (int e = threadIdx.x; e < d * (GTM / 8); e += blockDim.x) {
+        const int c = e / (GTM / 8), g = e % (GTM / 8);
+        uint4 w;
+        w.x = tc::pack_bf16x2(tile[8 * g][c], tile[8 * g + 1][c]);
+        w.y = tc::pack_bf16x2(tile[8 * g + 2][c], tile[8 * g + 3][c]);
+        w.z = tc::pack_bf16x2(tile[8 * g + 4][c], tile[8 * g + 5][c]);
+        w.w = tc::pack_bf16x2(tile[8 * g + 6][c], tile[8 * g + 7][c]);
+        *reinterpret_cast<uint4*>(out + gram_xpos(c, 8 * g)) = w;
     }
     if constexpr (TDP > 0) {
-        for (int e = threadIdx.x; e < GTM * (TDP / 2); e += blockDim.x) {
-            const int p = e / (TDP / 2), c = (e % (TDP / 2)) * 2;
-            const float v0 = c < d ? tile[p][c] : 0.f, v1 = c + 1 < d ? tile[p][c + 1] : 0.f;
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            reinterpret_cast<__nv_bfloat162*>(xb + (xrow + p) * TDP)[c / 2] = h;
-            reinterpret_cast<__nv_bfloat162*>(xl + (xrow + p) * TDP)[c / 2] =
-                __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+        // point p, columns c .. c + 7: one 16-byte store each of x_hi and x_lo
+        for (int e = threadIdx.x; e < GTM * (TDP / 8); e += blockDim.x) {
+            const int p = e / (TDP / 8), c = (e % (TDP / 8)) * 8;
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float v0 = c + 2 * j < d ? tile[p][c + 2 * j] : 0.f;
+                const float v1 = c + 2 * j + 1 < d ? tile[p][c + 2 * j + 1] : 0.f;
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+                hw[j] = *reinterpret_cast<const uint32_t*>(&h);
+                lw[j] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+            *reinterpret_cast<uint4*>(xb + (xrow + p) * TDP + c) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(xl + (xrow + p) * TDP + c) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
     }
 }
@@ -832,14 +859,26 @@ __global__ void __launch_bounds__(256) gmm_tc_r_kernel(const float* __restrict__
     const int64_t per_row = npad / 8;
     const int64_t total = (int64_t)kr * per_row;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // 16-byte loads where the rows allow them (p0 is a multiple of 8)
+    const bool vec = ((reinterpret_cast<uintptr_t>(lj) | reinterpret_cast<uintptr_t>(lse)) & 15) == 0 && lj_ld % 4 == 0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
         const int c = (int)(e / per_row);
         const int64_t p0 = (e - (int64_t)c * per_row) * 8;
         float v[8];
+        if (vec && c < k && p0 + 8 <= n) {
+            const float4* l4 = reinterpret_cast<const float4*>(lj + (int64_t)c * lj_ld + p0);
+            const float4* s4 = reinterpret_cast<const float4*>(lse + p0);
+            const float4 a0 = __ldcs(l4), a1 = __ldcs(l4 + 1), b0 = __ldg(s4), b1 = __ldg(s4 + 1);
+            v[0] = seed * expf(a0.x - b0.x); v[1] = seed * expf(a0.y - b0.y);
+            v[2] = seed * expf(a0.z - b0.z); v[3] = seed * expf(a0.w - b0.w);
+            v[4] = seed * expf(a1.x - b1.x); v[5] = seed * expf(a1.y - b1.y);
+            v[6] = seed * expf(a1.z - b1.z); v[7] = seed * expf(a1.w - b1.w);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t p = p0 + j;
-            v[j] = (c < k && p < n) ? seed * expf(__ldg(lj + (int64_t)c * lj_ld + p) - __ldg(lse + p)) : 0.f;
+            for (int j = 0; j < 8; ++j) {
+                const int64_t p = p0 + j;
+                v[j] = (c < k && p < n) ? seed * expf(__ldg(lj + (int64_t)c * lj_ld + p) - __ldg(lse + p)) : 0.f;
+            }
         }
         *reinterpret_cast<uint4*>(rb + (int64_t)c * npad + p0) =
             make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]), tc::pack_bf16x2(v[4], v[5]),
