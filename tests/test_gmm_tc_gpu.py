@@ -64,12 +64,14 @@ def test_tc_path_matches_oracle(n, d, k):
         assert v <= TOL_BF16, (name, v)
 
 
-@pytest.mark.parametrize("n,d,k", [(8192, 64, 255), (8229, 64, 254), (4096, 128, 64)])
+@pytest.mark.parametrize("n,d,k", [(8192, 64, 255), (8229, 64, 254), (4096, 128, 64), (3000, 33, 120),
+                                   (6000, 100, 200)])
 def test_tc_forward_is_deterministic_run_to_run(n, d, k):
     """The forward's stages are refilled by bulk copies while the epilogue
     warps still use the previous contents; a missing ordering shows up as
-    values that change from run to run (it did: a component constant read
-    after the refill). Three runs must give bit-identical log-joint and lse."""
+    values that change from run to run (it did, twice: a component constant
+    read after its tail slot was released). Three runs must give bit-identical
+    log-joint and lse, also with a partial last round of components."""
     import paper_2104_05372_b300 as gpa
     g = synth.gmm_inputs(n, d, k, seed=n + d + k)
     x, a, mu, q, l = gmm_dev(g)
