@@ -333,7 +333,8 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, const gpa_batched_opts& O
         const int tdp = C.tdp, rec_len = tdp * tdp + tdp + 4;
         int64_t pairs = 0, xtf = 0;
         for (int i : C.members) {
-            pairs += in[i].n * (int64_t)in[i].k;
+            // log-joint rows padded to whole 128-point tiles (16-byte aligned rows)
+            pairs += (in[i].n + 127) / 128 * 128 * (int64_t)in[i].k;
             xtf += (in[i].n + 127) / 128 * 128 * (int64_t)in[i].d;
         }
         C.off_rec = off; off = a256(off + sizeof(float) * (size_t)C.kc * rec_len);
@@ -360,7 +361,7 @@ bool make_plan(const gpa_gmm_instance* in, int n_inst, const gpa_batched_opts& O
             B.fwd = (double*)(base + off);  off = a256(off + sizeof(double) * (size_t)B.ntiles128);
             B.lse = (float*)(base + C.off_lse) + T.xoff;
             B.lj = (float*)(base + C.off_lj) + ljo;
-            ljo += I.n * (int64_t)I.k;
+            ljo += (I.n + 127) / 128 * 128 * (int64_t)I.k;
             T.x = I.x;
             T.lj = B.lj;
             T.lse = B.lse;

@@ -81,7 +81,7 @@ int gmm_tc_bwd_nchunks(int64_t n, int d, int k);  // point chunks (partial sums)
 // tiles. Device descriptors, built on the host by the batched plan.
 struct TcCatInst {
     const float* x;              // [n][d] points
-    float* lj;                   // [k][n] log-joint
+    float* lj;                   // [k][npad] log-joint (rows of n padded to whole 128-point tiles)
     float* lse;                  // [n] per-point logsumexp
     double* fwd;                 // [ceil(n / 128)] per-tile sums of lse
     float *bS, *bM;              // partial sums [nchunks][k][...] (zeroed by the caller)

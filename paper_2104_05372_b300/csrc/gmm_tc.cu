@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
         k = I.k;
         koff = I.koff;
         lj = I.lj;
-        lj_ld = I.n;
+        lj_ld = (I.n + TM - 1) / TM * TM;
         lse_out = I.lse;
         part = I.fwd;
         p0 = (int64_t)tt.y * TM;
@@ -826,8 +826,9 @@ __global__ void __launch_bounds__(256) tc_cat_xt_kernel(const TcCatInst* __restr
 
 // R of every instance of a concatenated class, [kr][np]: row c, column xoff + p
 // holds seed exp(lj[c][p] - lse[p]) of the instance whose rows those are, for
-// c < k and p < n; zero elsewhere (padding rows and points). 8 points per
-// thread (never across a 128-point tile).
+// c < k and p < n; zero for its padding points and for rows k .. up to the
+// next multiple of 16 (the width of its MMAs); rows beyond that are never
+// read and not written. 8 points per thread (never across a 128-point tile).
 __global__ void __launch_bounds__(256) tc_cat_r_kernel(const TcCatInst* __restrict__ cat,
                                                        const int* __restrict__ tile_inst, int64_t np, int kr,
                                                        __nv_bfloat16* __restrict__ rb) {
@@ -838,12 +839,24 @@ __global__ void __launch_bounds__(256) tc_cat_r_kernel(const TcCatInst* __restri
         const int c = (int)(e / per_row);
         const int64_t q0 = (e - (int64_t)c * per_row) * 8;
         const TcCatInst& I = cat[tile_inst[q0 / TM]];
+        if (c >= (I.k + 15) / 16 * 16) continue;  // rows past the instance's MMA width are never read
         const int64_t p0 = q0 - I.xoff;
+        const int64_t ld = (I.n + TM - 1) / TM * TM;  // log-joint rows padded to whole tiles
         float v[8];
+        if (c < I.k && p0 + 8 <= I.n) {  // 16-byte loads: rows and lse start on tile boundaries
+            const float4* l4 = reinterpret_cast<const float4*>(I.lj + (int64_t)c * ld + p0);
+            const float4* s4 = reinterpret_cast<const float4*>(I.lse + p0);
+            const float4 a0 = __ldcs(l4), a1 = __ldcs(l4 + 1), b0 = __ldg(s4), b1 = __ldg(s4 + 1);
+            v[0] = I.seed * expf(a0.x - b0.x); v[1] = I.seed * expf(a0.y - b0.y);
+            v[2] = I.seed * expf(a0.z - b0.z); v[3] = I.seed * expf(a0.w - b0.w);
+            v[4] = I.seed * expf(a1.x - b1.x); v[5] = I.seed * expf(a1.y - b1.y);
+            v[6] = I.seed * expf(a1.z - b1.z); v[7] = I.seed * expf(a1.w - b1.w);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t p = p0 + j;
-            v[j] = (c < I.k && p < I.n) ? I.seed * expf(__ldg(I.lj + (int64_t)c * I.n + p) - __ldg(I.lse + p)) : 0.f;
+            for (int j = 0; j < 8; ++j) {
+                const int64_t p = p0 + j;
+                v[j] = (c < I.k && p < I.n) ? I.seed * expf(__ldg(I.lj + (int64_t)c * ld + p) - __ldg(I.lse + p)) : 0.f;
+            }
         }
         *reinterpret_cast<uint4*>(rb + (int64_t)c * np + q0) =
             make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]), tc::pack_bf16x2(v[4], v[5]),
