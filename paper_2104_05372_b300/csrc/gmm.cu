@@ -174,8 +174,7 @@ static int launch_bwd(const GmmArgs& A, const GmmLayout& L, char* ws, const floa
 template <int DP>
 static int launch_finalize(const GmmArgs& A, const GmmLayout& L, char* ws, int nchunks, cudaStream_t s,
                            int centered = 0) {
-    constexpr int NBLK = Bwd<DP>::NBLK;
-    const size_t smem = sizeof(double) * (NBLK * 64 + 3 * DP + 1) + sizeof(float) * 2 * DP * DP + 64;
+    const size_t smem = gmm_finalize_smem<DP>();
     auto kern = gmm_finalize_kernel<DP>;
     if (!set_smem(kern, smem)) return GPA_ERR_CUDA;
     GPA_LAUNCH("gmm_finalize", s,

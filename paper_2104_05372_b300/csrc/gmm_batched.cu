@@ -758,8 +758,7 @@ struct ClassRun {
     }
     int fin(cudaStream_t s) const {
         if (count(kPhFin) == 0) return GPA_OK;
-        constexpr int NB = (DP / 8) * (DP / 8 + 1) / 2;
-        const size_t smem = sizeof(double) * (NB * 64 + 3 * DP + 1) + sizeof(float) * 2 * DP * DP + 64;
+        const size_t smem = gmm_finalize_smem<DP>();
         auto k = batched_fin_kernel<DP>;
         if (!smem_attr(k, smem)) return GPA_ERR_CUDA;
         const unsigned g = persistent_grid(k, 256, smem, count(kPhFin), 0);

@@ -1166,6 +1166,12 @@ __device__ __forceinline__ void tri_index(int e, int& r, int& c) {
 // ---------------------------------------------------------------------------
 // A3: finalize gradients per component (fixed-order sums over chunks)
 // ---------------------------------------------------------------------------
+// Dynamic shared memory of gmm_finalize_kernel_body<DP>.
+template <int DP>
+constexpr size_t gmm_finalize_smem() {
+    return sizeof(double) * ((DP / 8) * (DP / 8 + 1) / 2 * 64 + 3 * DP + 1) + sizeof(float) * (2 * DP * DP + 2 * DP) + 64;
+}
+
 template <int DP>
 __device__ __forceinline__ void gmm_finalize_kernel_body(
     const float* __restrict__ alpha, const float* __restrict__ mu, const float* __restrict__ q,
@@ -1184,9 +1190,11 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
     double* Sd = reinterpret_cast<double*>(smem_raw);  // [NBLK*64]
     double* md = Sd + NBLK * 64;                         // [DP+1]
     double* vd = md + DP + 1;                            // [DP]  v = m - R mu
-    double* mud = vd + DP;                               // [DP]  mu, then Q v
+    double* mud = vd + DP;                               // [DP]  mu
     float* Cf = reinterpret_cast<float*>(mud + DP);      // [DP][DP] symmetric
     float* Qf = Cf + DP * DP;                            // [DP][DP] lower
+    float* vf = Qf + DP * DP;                            // [DP]  v in float32
+    float* wf = vf + DP;                                 // [DP]  w = Q v
     const int kk = bx, tid = threadIdx.x;
     const int t = d * (d - 1) / 2;
     const float* qk = q + (size_t)kk * d;
@@ -1210,8 +1218,12 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
     for (int e = tid; e < DP; e += 256) mud[e] = e < d ? (double)mu[(size_t)kk * d + e] : 0.0;
     __syncthreads();
     const double R = md[DP];
-    // v = m - R mu (raw moments) or m (centred sums)
-    for (int j = tid; j < DP; j += 256) vd[j] = centered ? md[j] : md[j] - R * mud[j];
+    // v = m - R mu (raw moments) or m (centred sums): the cancelling
+    // difference in float64, its result rounded once for the float32 products
+    for (int j = tid; j < DP; j += 256) {
+        vd[j] = centered ? md[j] : md[j] - R * mud[j];
+        vf[j] = (float)vd[j];
+    }
     __syncthreads();
     // C = S - mu v^T - m mu^T (= S - mu m^T - m mu^T + R mu mu^T), mirrored
     for (int e = tid; e < DP * (DP + 1) / 2; e += 256) {
@@ -1226,17 +1238,17 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
         Cf[a * DP + b] = (float)c;
         Cf[b * DP + a] = (float)c;
     }
-    __syncthreads();  // last read of mu
-    // w = Q v, stored over mu
+    // w = Q v (float32: the operands are float32 values, no cancellation left)
     for (int r = tid; r < DP; r += 256) {
-        double w = 0.0;
+        float w = 0.f;
         if (r < d)
-            for (int j = 0; j <= r; ++j) w += (double)Qf[r * DP + j] * vd[j];
-        mud[r] = w;
+            for (int j = 0; j <= r; ++j) w = fmaf(Qf[r * DP + j], vf[j], w);
+        wf[r] = w;
     }
     __syncthreads();
     // H = Q C on the lower triangle; dq from its diagonal, dl from the rest
     const int ne = d * (d + 1) / 2;
+    const float sg2 = (float)(seed * gamma * gamma);
     for (int e = tid; e < ne; e += 256) {
         int r, c;
         tri_index(e, r, c);
@@ -1247,14 +1259,14 @@ __device__ __forceinline__ void gmm_finalize_kernel_body(
             d_q[(size_t)kk * d + r] += (float)(R - ev * (double)h + seed * ((double)m - gamma * gamma * ev * ev));
         } else {
             const int li = r * (r - 1) / 2 + c;
-            d_l[(size_t)kk * t + li] += (float)(-(double)h - seed * gamma * gamma * (double)lk[li]);
+            d_l[(size_t)kk * t + li] += fmaf(-sg2, lk[li], -h);
         }
     }
     // d mu = Q^T w
     for (int c = tid; c < d; c += 256) {
-        double s = 0.0;
-        for (int r = c; r < d; ++r) s += (double)Qf[r * DP + c] * mud[r];
-        d_mu[(size_t)kk * d + c] += (float)s;
+        float s = 0.f;
+        for (int r = c; r < d; ++r) s = fmaf(Qf[r * DP + c], wf[r], s);
+        d_mu[(size_t)kk * d + c] += s;
     }
     if (tid == 0) d_alpha[kk] += (float)(R - seed * (double)n * exp((double)alpha[kk] - scal[0]));
 }
