@@ -83,7 +83,9 @@ struct Bwd {
     // point-loop unroll of the per-call kernel and of the persistent batched
     // kernel, as far as the register budget of MINB resident CTAs allows
     static constexpr int UNROLL = DP == 128 ? 2 : DP == 64 ? 8 : 4;
-    static constexpr int UNROLL_BATCHED = DP == 128 ? 1 : 2;
+    // (4 at DP <= 32 measured 3-7 % faster than 2 in the 512-instance batch,
+    // in spite of a few spilled registers)
+    static constexpr int UNROLL_BATCHED = DP == 128 ? 1 : DP <= 32 ? 4 : 2;
     // point tiles double-buffered; raw log-joint, lse and the cotangents r
     // triple-buffered
     static constexpr size_t SMEM = sizeof(float) * (size_t)(2 * TPB * XST + 3 * GC * TPB + 3 * TPB + 3 * TPB * GC);
