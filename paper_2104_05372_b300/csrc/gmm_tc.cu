@@ -71,7 +71,7 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 // the MMAs (warp 1 also owns the TMEM allocation), warps 2-9 read the
 // accumulators back, one thread per point (TMEM lane) and half of the round's
 // components, and fold |z - b_k|^2 into the log-joint and an online logsumexp.
-template <int TDP>
+template <int TDP, bool P = false>
 struct FwdSm {
     static constexpr int NA = TDP / 64;                           // 64-wide column atoms of a Q row
     // rows of z per set: 16 (one MMA K step) at TDP = 128; at TDP = 64 sets of
@@ -83,27 +83,35 @@ struct FwdSm {
     static constexpr int CR = 256 / G;                            // components per round
     // column atoms of set j (its stages: these atoms of Q_hi, then of Q_lo)
     static constexpr __host__ __device__ int atoms(int j) { return ((j + 1) * G + 63) / 64; }
-    static constexpr int FQ = TDP == 64 ? 5 : 4;                  // Q stages
+    // P: the persistent form (one CTA per SM over many tiles), which keeps two
+    // x tiles at TDP = 64 (the next tile's loads while the current one is
+    // multiplied) and so one Q stage fewer
+    static constexpr int XB = P && TDP == 64 ? 2 : 1;              // x tile buffers
+    static constexpr int FQ = TDP == 64 && !P ? 5 : 4;            // Q stages
     // tail slots (rounds): enough that the producer, FQ stages ahead of the
     // MMAs, never waits for the epilogue to finish a round
     static constexpr int FT = G >= 32 ? 4 : 3;
     static constexpr int EW = 8;                                  // epilogue warps
+    static constexpr uint32_t XBYTES = 2 * NA * ATOM;             // x_hi, x_lo tiles (NA atoms each)
     static constexpr uint32_t STG = 2 * ATOM;                     // 256 rows x 128 bytes
     static constexpr uint32_t TAIL = (TDP + 4) * 4;               // b_k, constant, pad
-    static constexpr uint32_t X = 0;                              // x_hi, x_lo tiles (NA atoms each)
-    static constexpr uint32_t Q = X + 2 * NA * ATOM;              // [FQ] stages
+    static constexpr uint32_t X = 0;                              // [XB] x tiles
+    static constexpr uint32_t Q = X + XB * XBYTES;                // [FQ] stages
     static constexpr uint32_t B = Q + FQ * STG;                   // [FT][CR] tails
-    static constexpr uint32_t RED = B + FT * CR * TAIL;
-    static constexpr uint32_t MRG = RED + 8 * 8;                  // [128] (max, sum) of warps 6-9
-    static constexpr uint32_t BAR = MRG + 128 * 8;  // x_full, q_full[FQ], q_empty[FQ], a_full[2], a_empty[2],
-                                                    // t_empty[FT]
-    static_assert(1 + 2 * FQ + 4 + FT <= 32, "barrier slots");
+    static constexpr uint32_t RED = B + FT * CR * TAIL;           // warp sums of lse ([2][4] when P)
+    static constexpr uint32_t MRG = RED + 8 * 8;                  // [128] (max, sum) of warps 6-9 ([2][128] when P)
+    static constexpr uint32_t BAR = MRG + (P ? 2 : 1) * 128 * 8;  // x_full, q_full[FQ], q_empty[FQ], a_full[2],
+                                                                  // a_empty[2], t_empty[FT]; when P also
+                                                                  // x_empty, the second x_full / x_empty, m_full[2],
+                                                                  // r_full[2]
+    static_assert(2 * XB + 2 * FQ + 4 + FT + 4 <= 32, "barrier slots");
     static constexpr uint32_t TMEMP = BAR + 32 * 8;
     static constexpr uint32_t FLAG = TMEMP + 8;
     static constexpr uint32_t END = FLAG + 8;
     static constexpr size_t SMEM = END + 1024;
     static_assert(SMEM <= 227 * 1024, "forward shared memory");
-    static_assert(Q % 1024 == 0 && STG % 1024 == 0 && TAIL % 16 == 0, "operand and copy alignment");
+    static_assert(Q % 1024 == 0 && STG % 1024 == 0 && XBYTES % 1024 == 0 && TAIL % 16 == 0,
+                  "operand and copy alignment");
     static_assert(CR * G == 256 && (CR / 2) * G == 128 && NSET % 2 == 0,
                   "a round fills N = 256; each epilogue warp 128 columns");
 };
@@ -173,9 +181,8 @@ __device__ __forceinline__ void fwd_stage_dispatch(const FwdIssue& I, int nk, ui
 
 // Set J of a round (set number q of the CTA: TMEM half q % 2): its atoms of
 // Q_hi, then of Q_lo, each one stage. False when a wait gave up.
-template <int TDP, int J>
+template <class S, int J>
 __device__ __forceinline__ bool fwd_set_mmas(FwdIssue& I, int q) {
-    using S = FwdSm<TDP>;
     constexpr int NAJ = S::atoms(J), KS = (J + 1) * S::G / 16;
     const int b = q & 1;
     if (!mbar_wait(&I.a_empty[b], ((uint32_t)(q >> 1) & 1u) ^ 1u, I.status)) return false;
@@ -203,14 +210,14 @@ __device__ __forceinline__ bool fwd_set_mmas(FwdIssue& I, int q) {
     return true;
 }
 
-template <int TDP, int J, bool END = (J >= FwdSm<TDP>::NSET)>
+template <class S, int J, bool END = (J >= S::NSET)>
 struct FwdSets {
     __device__ static __forceinline__ bool run(FwdIssue& I, int q) {
-        return fwd_set_mmas<TDP, J>(I, q) && FwdSets<TDP, J + 1>::run(I, q + 1);
+        return fwd_set_mmas<S, J>(I, q) && FwdSets<S, J + 1>::run(I, q + 1);
     }
 };
-template <int TDP, int J>
-struct FwdSets<TDP, J, true> {
+template <class S, int J>
+struct FwdSets<S, J, true> {
     __device__ static __forceinline__ bool run(FwdIssue&, int) { return true; }
 };
 
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
                        (uint32_t)dx + (uint32_t)(NA * ATOM >> 4), (uint32_t)dq, (uint32_t)(dx >> 32), 0u, 0u, 0u};
             for (int r = 0; ok && r < rounds; ++r) {
                 I.idesc = tc::idesc_bf16_f32(128, G * min(CR, k - CR * r));
-                ok = FwdSets<TDP, 0>::run(I, r * NSET);
+                ok = FwdSets<S, 0>::run(I, r * NSET);
             }
             if (!ok) *abort_flag = 1;
         }
@@ -415,6 +422,294 @@ __global__ void __launch_bounds__(64 + 32 * FwdSm<TDP>::EW, 1)
     }
     __syncthreads();
     if (threadIdx.x == 64) part[pidx] = *abort_flag ? NAN : red[0] + red[1] + red[2] + red[3];
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// The forward of a concatenated class of the batched form, persistent: one
+// CTA per SM takes the class's tiles w = blockIdx.x, blockIdx.x + gridDim.x,
+// ... (tile cat_tiles[w] of its instance: its points from row xoff, its
+// components from Q row block koff), so that the CTA start, tensor-memory
+// allocation and pipeline fill and drain of gmm_tc_fwd_kernel are paid once per
+// SM instead of once per tile (the class's tiles are short: about five rounds
+// at its average K). The roles and the round structure are those of
+// gmm_tc_fwd_kernel; in addition the MMA thread releases an x buffer after the
+// last MMA of its tile, and at the end of a tile the two halves of each
+// point's logsumexp merge through shared memory in two buffers by tile
+// parity, each with its own barrier.
+struct FwdItem {
+    int64_t n, xrow0, p0, pidx, lj_ld;
+    int k, koff;
+    float* lj;
+    float* lse_out;
+    double* part;
+};
+
+template <int TDP>
+__global__ void __launch_bounds__(64 + 32 * FwdSm<TDP, true>::EW, 1)
+    gmm_tc_fwd_cat_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmxl,
+                          const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmql,
+                          const float* __restrict__ tails, int kq, int n_items, const TcCatInst* __restrict__ cat,
+                          const int2* __restrict__ cat_tiles, int32_t* __restrict__ status) {
+    using S = FwdSm<TDP, true>;
+    constexpr int FQ = S::FQ, FT = S::FT, NA = S::NA, G = S::G, NSET = S::NSET, CR = S::CR, XB = S::XB;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::BAR);
+    uint64_t* x_full = bars;                 // [XB]
+    uint64_t* x_empty = bars + XB;           // [XB]
+    uint64_t* q_full = bars + 2 * XB;        // [FQ]
+    uint64_t* q_empty = q_full + FQ;         // [FQ]
+    uint64_t* a_full = q_empty + FQ;         // [2] accumulator halves of TMEM
+    uint64_t* a_empty = a_full + 2;          // [2]
+    uint64_t* t_empty = a_full + 4;          // [FT]
+    uint64_t* m_full = t_empty + FT;         // [2] per item parity: second halves of the logsumexps written
+    uint64_t* r_full = m_full + 2;           // [2] per item parity: the tile's four warp sums written
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sm + S::TMEMP);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + S::FLAG);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // persistent: CTA b takes items b, b + gridDim.x, ...
+    auto item = [&](int w) {
+        FwdItem it;
+        const int2 tt = cat_tiles[w];
+        const TcCatInst& I = cat[tt.x];
+        it.n = I.n;
+        it.xrow0 = I.xoff;
+        it.k = I.k;
+        it.koff = I.koff;
+        it.lj = I.lj;
+        it.lj_ld = (I.n + TM - 1) / TM * TM;
+        it.lse_out = I.lse;
+        it.part = I.fwd;
+        it.p0 = (int64_t)tt.y * TM;
+        it.pidx = tt.y;
+        return it;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < XB; ++b) {
+            mbar_init(&x_full[b], 1);
+            mbar_init(&x_empty[b], 1);  // MMA commit after the tile's last MMA
+        }
+        for (int s = 0; s < FQ; ++s) {
+            mbar_init(&q_full[s], 1);
+            mbar_init(&q_empty[s], 1);  // MMA commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&a_full[b], 1);
+            mbar_init(&a_empty[b], S::EW);
+            mbar_init(&m_full[b], S::EW / 2);
+            mbar_init(&r_full[b], S::EW / 2);
+        }
+        for (int t = 0; t < FT; ++t) mbar_init(&t_empty[t], S::EW);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_holder, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // per item: its x tile (into X buffer xt % XB, once the MMAs of the
+            // item that used it are done), then per round and set j the set's
+            // column atoms of Q_hi, then of Q_lo; one 256-row box each (G rows
+            // of each of the round's components; rows past the last one are
+            // never multiplied)
+            uint32_t g = 0;
+            int rr = 0;  // rounds issued (tail slots)
+            bool ok = true;
+            for (int w = blockIdx.x, xt = 0; ok && w < n_items; w += gridDim.x, ++xt) {
+                const FwdItem it = item(w);
+                const int xb = xt % XB;
+                if (!mbar_wait(&x_empty[xb], ((uint32_t)(xt / XB) & 1u) ^ 1u, status)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&x_full[xb], 2 * NA * ATOM);
+                for (int a = 0; a < NA; ++a) {
+                    tc::tma_load_2d(sm + S::X + xb * S::XBYTES + a * ATOM, &tmx, 64 * a, (int)(it.xrow0 + it.p0),
+                                    &x_full[xb]);
+                    tc::tma_load_2d(sm + S::X + xb * S::XBYTES + (NA + a) * ATOM, &tmxl, 64 * a,
+                                    (int)(it.xrow0 + it.p0), &x_full[xb]);
+                }
+                const int rounds = (it.k + CR - 1) / CR;
+                for (int r = 0; ok && r < rounds; ++r, ++rr) {
+                    const int c0 = CR * r, nc = min(CR, it.k - c0), ts = rr % FT;
+                    const uint32_t tph = (uint32_t)(rr / FT) & 1u;
+                    for (int j = 0; ok && j < NSET; ++j) {
+                        const int row = (j * kq + it.koff + c0) * G;
+                        for (int lo = 0; ok && lo < 2; ++lo)
+                            for (int at = 0; at < S::atoms(j); ++at, ++g) {
+                                const int s = (int)(g % FQ);
+                                const uint32_t ph = (g / FQ) & 1u;
+                                const bool first = j == 0 && lo == 0 && at == 0;
+                                if (!mbar_wait(&q_empty[s], ph ^ 1u, status) ||
+                                    (first && !mbar_wait(&t_empty[ts], tph ^ 1u, status))) {
+                                    ok = false;
+                                    break;
+                                }
+                                mbar_arrive_expect_tx(&q_full[s], S::STG + (first ? (uint32_t)nc * S::TAIL : 0u));
+                                tc::tma_load_2d(sm + S::Q + s * S::STG, lo ? &tmql : &tmq, 64 * at, row, &q_full[s]);
+                                if (first)
+                                    bulk_g2s(sm + S::B + ts * CR * S::TAIL,
+                                             tails + (size_t)(it.koff + c0) * (TDP + 4), (uint32_t)nc * S::TAIL,
+                                             &q_full[s]);
+                            }
+                    }
+                }
+            }
+            if (!ok) *abort_flag = 1;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint64_t dx = tc::desc_sw128(smem_u32(sm + S::X)), dq = tc::desc_sw128(smem_u32(sm + S::Q));
+            FwdIssue I{q_full, q_empty, a_full, a_empty, status, tmem, 0u, 0u, (uint32_t)dq, (uint32_t)(dx >> 32),
+                       0u, 0u, 0u};
+            bool ok = true;
+            int q = 0;  // sets issued (TMEM halves)
+            for (int w = blockIdx.x, xt = 0; ok && w < n_items; w += gridDim.x, ++xt) {
+                const int kk = cat[cat_tiles[w].x].k;
+                const int xb = xt % XB;
+                if (!mbar_wait(&x_full[xb], (uint32_t)(xt / XB) & 1u, status)) {
+                    ok = false;
+                    break;
+                }
+                I.xh = (uint32_t)dx + (uint32_t)(xb * (S::XBYTES >> 4));
+                I.xl = I.xh + (uint32_t)(NA * ATOM >> 4);
+                const int rounds = (kk + CR - 1) / CR;
+                for (int r = 0; ok && r < rounds; ++r, q += NSET) {
+                    I.idesc = tc::idesc_bf16_f32(128, G * min(CR, kk - CR * r));
+                    ok = FwdSets<S, 0>::run(I, q);
+                }
+                if (ok) tc::mma_commit(&x_empty[xb]);  // the item's MMAs have read its x tile
+            }
+            if (!ok) *abort_flag = 1;
+        }
+        __syncwarp();
+    } else {
+        // epilogue: one thread per point (TMEM lane). Warp w reads TMEM lanes
+        // 32 (w % 4) ..; warps 2-5 take the first CR / 2 components of each
+        // round, warps 6-9 the others: 128 columns per warp and set, read as
+        // two 64-column chunks of 64 / G components each. At the end of an
+        // item the two halves of each point's logsumexp merge through shared
+        // memory (two buffers by item parity, each with a barrier).
+        constexpr int HC = CR / 2, PCH = 64 / G;  // components per warp, per chunk
+        constexpr int TF = S::TAIL / 4;           // floats per tail
+        const int qtr = warp & 3;
+        const int jw = (warp - 2) >> 2;
+        const int row = qtr * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(128 * jw);
+        int q = 0, rr = 0;
+        for (int w = blockIdx.x, ni = 0; w < n_items && !*abort_flag; w += gridDim.x, ++ni) {
+            const FwdItem it = item(w);
+            const bool valid = it.p0 + row < it.n;
+            Lse st;  // online logsumexp over the components this thread reads
+            st.init();
+            const int rounds = (it.k + CR - 1) / CR;
+            bool ok = true;
+            for (int r = 0; ok && r < rounds; ++r, ++rr) {
+                const int ts = rr % FT;
+                const float* bw = reinterpret_cast<const float*>(sm + S::B + (ts * CR + jw * HC) * S::TAIL);
+                float sv[HC];
+#pragma unroll
+                for (int u = 0; u < HC; ++u) sv[u] = 0.f;
+                uint32_t rv[2][64];
+                // set by set: both chunks' loads issued together, one wait (the
+                // two sets of TDP = 64 unrolled)
+                constexpr int JU = NSET <= 2 ? NSET : 1;
+#pragma unroll JU
+                for (int j = 0; j < NSET; ++j, ++q) {
+                    const int b = q & 1;
+                    if (!mbar_wait_warp(&a_full[b], (uint32_t)(q >> 1) & 1u, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t ta = tl + 256u * (uint32_t)b;
+                    const float* bj = bw + j * G;
+                    tc::tmem_ld64_issue(ta, rv[0]);
+                    tc::tmem_ld64_issue(ta + 64u, rv[1]);
+                    tc::tmem_ld64_tied_wait(rv[0]);
+#pragma unroll
+                    for (int u = 0; u < PCH; ++u) sv[u] += sumsq_rows<G>(rv[0], u * G, bj + u * TF);
+                    tc::tmem_ld64_tied_wait(rv[1]);
+#pragma unroll
+                    for (int u = 0; u < PCH; ++u) sv[PCH + u] += sumsq_rows<G>(rv[1], u * G, bj + (PCH + u) * TF);
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&a_empty[b]);
+                }
+                if (!ok) break;
+                // the round's tail slot goes back to the producer after its last
+                // read (the constants)
+                float cst[HC];
+#pragma unroll
+                for (int u = 0; u < HC; ++u) cst[u] = bw[u * TF + TDP];
+                fence_proxy_async_smem();  // tails read through the generic proxy
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&t_empty[ts]);
+#pragma unroll
+                for (int u = 0; u < HC; ++u) {
+                    const int kk = CR * r + HC * jw + u;
+                    if (kk < it.k && valid) {
+                        const float v = cst[u] - 0.5f * sv[u];
+                        if (it.lj) it.lj[(int64_t)kk * it.lj_ld + it.p0 + row] = v;
+                        st.add(v);
+                    }
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                break;
+            }
+            // each point's two partial logsumexps, then the tile's sum of lse
+            const int ib = ni & 1;
+            const uint32_t iph = (uint32_t)(ni >> 1) & 1u;
+            float2* mrg = reinterpret_cast<float2*>(sm + S::MRG) + ib * TM;
+            double* red = reinterpret_cast<double*>(sm + S::RED) + ib * 4;
+            if (jw == 1) {
+                mrg[row] = make_float2(st.m, st.l);
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&m_full[ib]);
+            } else {
+                if (!mbar_wait_warp(&m_full[ib], iph, status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const float2 o = mrg[row];
+                st.merge(o.x, o.y);
+                double v = 0.0;
+                if (valid) {
+                    const float lv = st.value();
+                    if (it.lse_out) it.lse_out[it.p0 + row] = lv;
+                    v = (double)lv;
+                }
+                v = warp_sum(v);
+                if (lane == 0) {
+                    red[warp - 2] = v;
+                    tc::mbar_arrive(&r_full[ib]);
+                }
+                if (warp == 2 && lane == 0) {
+                    if (!mbar_wait(&r_full[ib], iph, status)) {
+                        *abort_flag = 1;
+                    } else {
+                        it.part[it.pidx] = red[0] + red[1] + red[2] + red[3];
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
@@ -1221,11 +1516,10 @@ int vjp_run(const GmmArgs& A, const GmmLayout& L, char* ws, size_t ws_bytes, cud
 }
 
 // One concatenated class of the batched form: every stage one launch over all
-// its instances' tiles (prep before and finalize after run in the batched
-// class kernels).
+// its instances' tiles, the forward persistent (prep before and finalize after
+// run in the batched class kernels).
 template <int TDP>
 int cat_run(const TcCatClass& C, cudaStream_t s) {
-    using S = FwdSm<TDP>;
     const int64_t cap = (int64_t)sm_count_tc() * 8;
     auto* xb = (__nv_bfloat16*)C.xb;
     auto* xl = (__nv_bfloat16*)C.xl;
@@ -1242,13 +1536,13 @@ int cat_run(const TcCatClass& C, cudaStream_t s) {
     if (!make_map(&tmx, xb, C.np, TDP) || !make_map(&tmxl, xl, C.np, TDP) || !make_q_maps<TDP>(tq, qb, ql, C.kc) ||
         !make_map_r(&tmr, rb, C.np, (int)C.kr, 16))
         return GPA_ERR_CUDA;
-    auto kf = gmm_tc_fwd_kernel<TDP>;
-    if (!set_smem_tc(kf, S::SMEM)) return GPA_ERR_CUDA;
+    using SP = FwdSm<TDP, true>;
+    auto kf = gmm_tc_fwd_cat_kernel<TDP>;
+    if (!set_smem_tc(kf, SP::SMEM)) return GPA_ERR_CUDA;
     if (C.n_fwd > 0)
         GPA_LAUNCH("gmm_tc_fwd", s,
-                   kf<<<(unsigned)C.n_fwd, 64 + 32 * S::EW, S::SMEM, s>>>(tmx, tmxl, tq[0], tq[1], C.tails, 0, 0, 0,
-                                                                          (int)C.kc, nullptr, 0, nullptr, nullptr,
-                                                                          0, C.inst, C.fwd_tiles, C.status));
+                   kf<<<(unsigned)min64(C.n_fwd, sm_count_tc()), 64 + 32 * SP::EW, SP::SMEM, s>>>(
+                       tmx, tmxl, tq[0], tq[1], C.tails, (int)C.kc, C.n_fwd, C.inst, C.fwd_tiles, C.status));
     const int64_t rwork = C.kr * (C.np / 8);
     GPA_LAUNCH("gmm_tc_r", s,
                tc_cat_r_kernel<<<(unsigned)min64((int64_t)sm_count_tc() * 16, (rwork + 255) / 256), 256, 0, s>>>(
