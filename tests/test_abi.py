@@ -98,3 +98,32 @@ def test_bounded_wait_check_rejects_bad_arguments(lib):
     assert lib.gpa_check_bounded_wait(1_000_000_001, fake, fake, None) == 1
     assert lib.gpa_check_bounded_wait(1000, None, fake, None) == 1
     assert lib.gpa_check_bounded_wait(1000, fake, None, None) == 1
+
+
+def test_host_streaming_entry_checks(lib):
+    """gmm_vjp_host: the workspace query and the host-side rejections, all
+    before its first CUDA call."""
+    from paper_2104_05372_b300 import _lib
+    q = _lib.gpa_gmm_vjp_host_workspace_bytes
+    assert q(1000, 10, 5, 0, 256) > 0
+    assert q(1000, 64, 5, 1, 256) > 0
+    assert q(0, 10, 5, 0, 256) == 0        # no points
+    assert q(1000, 129, 5, 0, 256) == 0    # D out of range
+    assert q(1000, 10, 5, 2, 256) == 0     # unknown precision
+    big = q(1 << 20, 64, 200, 0, 0)
+    assert q(1 << 20, 64, 200, 0, 4096) < big  # smaller chunks, smaller staging
+    fake = C.c_void_p(256)
+    args = [fake] * 5 + [1000, 10, 5, 1.0, 0, 0, 1.0] + [fake] * 5 + [256]
+    # null x
+    assert lib.gmm_vjp_host(None, *args[1:], fake, 1 << 30, None, None) == 1
+    # gamma <= 0
+    bad = list(args)
+    bad[8] = 0.0
+    assert lib.gmm_vjp_host(*bad, fake, 1 << 30, None, None) == 1
+    # tensor cores below their dimension range
+    tc = list(args)
+    tc[10] = 1
+    assert lib.gmm_vjp_host(*tc, fake, 1 << 30, None, None) == 6
+    # misaligned workspace, then a workspace smaller than the query
+    assert lib.gmm_vjp_host(*args, C.c_void_p(260), 1 << 30, None, None) == 7
+    assert lib.gmm_vjp_host(*args, fake, 16, None, None) == 4
