@@ -258,7 +258,7 @@ typedef struct {
     int32_t m;
     double seed;
     int32_t prec; /* GPA_PREC_FP32, or GPA_PREC_BF16_TC for 32 < d <= 128 (the tensor-core
-                     path, run instance by instance in the batch's stream) */
+                     path; see gmm_batched_vjp) */
 } gpa_gmm_instance;
 
 /* Workspace for gmm_batched_prepare / gmm_batched_vjp over these instances

@@ -127,3 +127,30 @@ def test_host_streaming_entry_checks(lib):
     # misaligned workspace, then a workspace smaller than the query
     assert lib.gmm_vjp_host(*args, C.c_void_p(260), 1 << 30, None, None) == 7
     assert lib.gmm_vjp_host(*args, fake, 16, None, None) == 4
+
+
+def test_batched_workspace_query_and_settings_checks(lib):
+    """The batched form's workspace query works from the instance shapes
+    alone (the device pointers are not read) and rejects bad per-class
+    settings and out-of-range tensor-core instances with 0 bytes."""
+    from paper_2104_05372_b300 import _lib
+
+    def inst(n, d, k, prec=0):
+        i = _lib.GmmInstance()
+        for f in ("x", "alpha", "mu", "q", "l", "d_alpha", "d_mu", "d_q", "d_l"):
+            setattr(i, f, 256)
+        i.n, i.d, i.k, i.gamma, i.m, i.seed, i.prec = n, d, k, 1.0, 0, 1.0, prec
+        return i
+
+    arr = (_lib.GmmInstance * 3)(inst(1000, 8, 5), inst(5000, 30, 40), inst(3000, 64, 20, 1))
+    ok = _lib.BatchedOpts.make({})
+    size = lib.gpa_gmm_batched_workspace_bytes_opts(arr, 3, C.byref(ok))
+    assert size > 0
+    assert lib.gpa_gmm_batched_workspace_bytes(arr, 3, 4096) == size  # uniform settings = the default opts
+    assert lib.gpa_gmm_batched_workspace_bytes_opts(arr, 3, None) == 0
+    assert lib.gpa_gmm_batched_workspace_bytes_opts(
+        arr, 3, C.byref(_lib.BatchedOpts.make({1: {"chunk_points": 32}}))) == 0
+    assert lib.gpa_gmm_batched_workspace_bytes_opts(
+        arr, 3, C.byref(_lib.BatchedOpts.make({2: {"ctas_per_sm": -1}}))) == 0
+    tc_small = (_lib.GmmInstance * 1)(inst(1000, 32, 5, 1))  # tensor cores need 32 < D
+    assert lib.gpa_gmm_batched_workspace_bytes_opts(tc_small, 1, C.byref(ok)) == 0
